@@ -1,0 +1,330 @@
+"""Seeded synthetic inputs: Cornell-boxes-in-a-room scenes and G-buffers.
+
+This module only builds input arrays (triangles, radiance, occluder boxes,
+shading points) and the grid parameters that go with them. It holds none of
+the sampling or learning arithmetic; both the CUDA path and the CPU oracle
+consume what it returns.
+
+The paper's scenes ("Cornell Boxes in Salle de Bain", Section 4) are not
+available, so these stand in for them: every emitter patch sits inside its
+own walled cell and lights only that cell, which is the complex-occlusion
+situation the method is built for (Section 4, teaser figure).
+
+Array conventions (all float32, C-contiguous):
+  tris      [N, 3, 3]  triangle vertices; emission is one-sided along the
+                       winding normal (v1 - v0) x (v2 - v0)
+  emission  [N, 3]     RGB radiance
+  boxes     [K, 6]     axis-aligned occluders (xmin, ymin, zmin, xmax, ymax, zmax)
+  pos, nrm  [3, P]     shading point positions / unit normals, SoA
+  albedo    [P]        Lambertian albedo
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class GridConfig:
+    table_size: int          # hash table slots H (power of two)
+    cut_size: int            # M
+    origin: tuple            # grid origin (3 floats)
+    cell_size: float         # h
+    normal_bins: int         # quantisation bins per octahedral axis
+    jitter: bool
+
+
+@dataclasses.dataclass
+class Scene:
+    name: str
+    tris: np.ndarray
+    emission: np.ndarray
+    boxes: np.ndarray
+    pos: np.ndarray
+    nrm: np.ndarray
+    albedo: np.ndarray
+    grid: GridConfig
+    spp: int
+    frames: int
+    seed: int
+    width: int = 0
+    height: int = 0
+    # dynamic lighting (blinking lights): per-light omega [rad/s], phase, mask
+    blink_omega: np.ndarray | None = None
+    blink_phase: np.ndarray | None = None
+    blink_mask: np.ndarray | None = None
+
+    @property
+    def n_lights(self) -> int:
+        return int(self.tris.shape[0])
+
+    @property
+    def n_points(self) -> int:
+        return int(self.pos.shape[1])
+
+    def emission_at(self, frame: int, fps: float = 30.0) -> np.ndarray:
+        """Radiance of every light at a frame: Le0 * (1 + 0.9 sin(w t + phi)) for
+        blinking lights, Le0 for the rest (t = frame / fps seconds)."""
+        if self.blink_mask is None:
+            return self.emission
+        t = frame / fps
+        s = 1.0 + 0.9 * np.sin(self.blink_omega * t + self.blink_phase)
+        scale = np.where(self.blink_mask, s, 1.0).astype(np.float32)
+        return (self.emission * scale[:, None]).astype(np.float32)
+
+    def emission_bound(self) -> np.ndarray:
+        """Radiance bound over all frames (1.9 Le0 for blinking lights)."""
+        if self.blink_mask is None:
+            return self.emission
+        scale = np.where(self.blink_mask, np.float32(1.9), np.float32(1.0)).astype(np.float32)
+        return (self.emission * scale[:, None]).astype(np.float32)
+
+
+def _box(lo, hi):
+    return [lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]]
+
+
+def _quad_patch(center, u_axis, v_axis, nu, nv, rng, jitter=0.0):
+    """Triangulated nu x nv quad grid spanning center +- u_axis/2 +- v_axis/2.
+    Winding makes the normal point along cross(u_axis, v_axis)."""
+    center = np.asarray(center, np.float64)
+    u_axis = np.asarray(u_axis, np.float64)
+    v_axis = np.asarray(v_axis, np.float64)
+    gu = np.linspace(-0.5, 0.5, nu + 1)
+    gv = np.linspace(-0.5, 0.5, nv + 1)
+    P = center + gu[:, None, None] * u_axis + gv[None, :, None] * v_axis
+    if jitter > 0.0:
+        du = np.linalg.norm(u_axis) / nu
+        dv = np.linalg.norm(v_axis) / nv
+        j = rng.uniform(-jitter, jitter, size=(nu + 1, nv + 1, 2))
+        inner = np.zeros((nu + 1, nv + 1, 1))
+        inner[1:-1, 1:-1] = 1.0
+        P = P + inner * (j[..., :1] * du * u_axis / np.linalg.norm(u_axis)
+                         + j[..., 1:] * dv * v_axis / np.linalg.norm(v_axis))
+    tris = []
+    for i in range(nu):
+        for k in range(nv):
+            a, b, c, d = P[i, k], P[i + 1, k], P[i + 1, k + 1], P[i, k + 1]
+            tris.append([a, b, c])
+            tris.append([a, c, d])
+    return np.asarray(tris, np.float64)
+
+
+def _orthonormal(n):
+    n = np.asarray(n, np.float64)
+    n = n / np.linalg.norm(n)
+    t = np.array([1.0, 0.0, 0.0]) if abs(n[0]) < 0.9 else np.array([0.0, 0.0, 1.0])
+    u = np.cross(n, t)
+    u /= np.linalg.norm(u)
+    v = np.cross(n, u)
+    return u, v
+
+
+def _cone_dirs(axis, max_angle, count, rng):
+    """Directions uniformly distributed in solid angle within max_angle of axis."""
+    axis = np.asarray(axis, np.float64)
+    axis = axis / np.linalg.norm(axis)
+    u, v = _orthonormal(axis)
+    cos_max = math.cos(max_angle)
+    z = rng.uniform(cos_max, 1.0, size=count)
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=count)
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    d = (r * np.cos(phi))[:, None] * u + (r * np.sin(phi))[:, None] * v + z[:, None] * axis
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def tiny_scene(seed: int = 0, jitter: bool = False) -> Scene:
+    """Unit-cube room split by full-height walls on x=0.5 and z=0.5 into four
+    Cornell-style cells, one block per cell (8 boxes); a downward-facing
+    0.2 x 0.2 patch of 64 triangles at y = 0.95 per cell (256 lights, RGB
+    radiance U[0.5, 2]); 64 x 64 floor points (normal +y, albedo 0.7);
+    8^3 grid, cut size 16, 4 samples per point, 8 learning iterations."""
+    rng = np.random.default_rng(seed)
+    w0, w1 = 0.495, 0.505
+    boxes = [
+        _box((w0, 0.0, 0.0), (w1, 1.0, 0.5)),
+        _box((w0, 0.0, 0.5), (w1, 1.0, 1.0)),
+        _box((0.0, 0.0, w0), (0.5, 1.0, w1)),
+        _box((0.5, 0.0, w0), (1.0, 1.0, w1)),
+    ]
+    tris = []
+    for cx in (0.25, 0.75):
+        for cz in (0.25, 0.75):
+            bx = cx + rng.uniform(-0.12, 0.12 - 0.15)
+            bz = cz + rng.uniform(-0.12, 0.12 - 0.15)
+            boxes.append(_box((bx, 0.0, bz), (bx + 0.15, 0.4, bz + 0.15)))
+            # winding normal = (+x) cross (+z) = -y: the patch faces the floor
+            tris.append(_quad_patch((cx, 0.95, cz), (0.2, 0, 0), (0, 0, 0.2), 8, 4, rng))
+    tris = np.concatenate(tris).astype(np.float32)
+    emission = rng.uniform(0.5, 2.0, size=(tris.shape[0], 3)).astype(np.float32)
+    n = 64
+    g = (np.arange(n) + 0.5) / n
+    X, Z = np.meshgrid(g, g, indexing="xy")
+    P = n * n
+    pos = np.stack([X.ravel(), np.zeros(P), Z.ravel()]).astype(np.float32)
+    nrm = np.stack([np.zeros(P), np.ones(P), np.zeros(P)]).astype(np.float32)
+    albedo = np.full(P, 0.7, np.float32)
+    grid = GridConfig(table_size=1024, cut_size=16, origin=(0.0, 0.0, 0.0),
+                      cell_size=0.125, normal_bins=1, jitter=jitter)
+    return Scene("tiny", tris, emission, np.asarray(boxes, np.float32), pos, nrm, albedo,
+                 grid, spp=4, frames=8, seed=seed, width=n, height=n)
+
+
+def _room_cells(rng, cells_per_side, n_boxes, wall_t=0.006):
+    """Full-height walls on the interior cell boundaries of a unit room, split
+    into one segment per cell edge, plus random blocks up to n_boxes."""
+    c = cells_per_side
+    pitch = 1.0 / c
+    boxes = []
+    for i in range(1, c):
+        x = i * pitch
+        for j in range(c):
+            boxes.append(_box((x - wall_t, 0.0, j * pitch), (x + wall_t, 1.0, (j + 1) * pitch)))
+            boxes.append(_box((j * pitch, 0.0, x - wall_t), ((j + 1) * pitch, 1.0, x + wall_t)))
+    k = 0
+    while len(boxes) < n_boxes:
+        ci, cj = k % c, (k // c) % c
+        k += 1
+        sx, sy, sz = rng.uniform(0.08, 0.2) * pitch * 2, rng.uniform(0.05, 0.35), rng.uniform(0.08, 0.2) * pitch * 2
+        x0 = ci * pitch + rng.uniform(0.1 * pitch, max(0.1 * pitch, 0.9 * pitch - sx))
+        z0 = cj * pitch + rng.uniform(0.1 * pitch, max(0.1 * pitch, 0.9 * pitch - sz))
+        boxes.append(_box((x0, 0.0, z0), (x0 + sx, sy, z0 + sz)))
+    return np.asarray(boxes[:n_boxes], np.float32)
+
+
+def _emitter_patches(rng, cells_per_side, n_patches, tris_per_patch):
+    """Clustered mesh emitters: each patch a jittered triangulated quad in the
+    upper part of one cell, facing down into the room within 40 degrees."""
+    c = cells_per_side
+    pitch = 1.0 / c
+    nq = tris_per_patch // 2
+    nu = int(2 ** math.floor(math.log2(math.sqrt(nq))))
+    nv = nq // nu
+    patches = []
+    for p in range(n_patches):
+        ci, cj = p % c, (p // c) % c
+        center = (ci * pitch + rng.uniform(0.2, 0.8) * pitch,
+                  rng.uniform(0.6, 0.95),
+                  cj * pitch + rng.uniform(0.2, 0.8) * pitch)
+        normal = _cone_dirs((0.0, -1.0, 0.0), math.radians(40.0), 1, rng)[0]
+        u, v = _orthonormal(normal)
+        size = rng.uniform(0.15, 0.3) * pitch
+        # winding normal = cross(u_axis, v_axis); _orthonormal gives v = n x u,
+        # so cross(u, v) = n and the patch faces along `normal`.
+        patches.append(_quad_patch(center, u * size, v * size, nu, nv, rng, jitter=0.25))
+    return np.concatenate(patches).astype(np.float32)
+
+
+def _gbuffer_planes(rng, width, height, cells_per_side, n_planes=16, normal_jitter_deg=15.0):
+    """width x height shading points on n_planes random plane patches (one
+    rectangular block of pixels per plane), normals jittered within
+    normal_jitter_deg of the plane normal, albedo U[0.2, 0.9]."""
+    c = cells_per_side
+    pitch = 1.0 / c
+    gx = int(round(math.sqrt(n_planes)))
+    gy = n_planes // gx
+    bw, bh = width // gx, height // gy
+    pos = np.zeros((3, height, width), np.float32)
+    nrm = np.zeros((3, height, width), np.float32)
+    ys, xs = np.meshgrid(np.arange(height), np.arange(width), indexing="ij")
+    for k in range(n_planes):
+        px, py = k % gx, k // gx
+        x0, x1 = px * bw, (px + 1) * bw if px < gx - 1 else width
+        y0, y1 = py * bh, (py + 1) * bh if py < gy - 1 else height
+        ci, cj = k % c, (k // c) % c
+        normal = _cone_dirs((0.0, 1.0, 0.0), math.radians(30.0), 1, rng)[0]
+        u, v = _orthonormal(normal)
+        ext = 0.7 * pitch
+        center = np.array([(ci + 0.5) * pitch, rng.uniform(0.0, 0.25), (cj + 0.5) * pitch])
+        su = (xs[y0:y1, x0:x1] - x0 + 0.5) / (x1 - x0) - 0.5
+        sv = (ys[y0:y1, x0:x1] - y0 + 0.5) / (y1 - y0) - 0.5
+        P = center[:, None, None] + ext * (su[None] * u[:, None, None] + sv[None] * v[:, None, None])
+        pos[:, y0:y1, x0:x1] = P
+        npx = (x1 - x0) * (y1 - y0)
+        dirs = _cone_dirs(normal, math.radians(normal_jitter_deg), npx, rng)
+        nrm[:, y0:y1, x0:x1] = dirs.T.reshape(3, y1 - y0, x1 - x0)
+    albedo = rng.uniform(0.2, 0.9, size=width * height).astype(np.float32)
+    return pos.reshape(3, -1).copy(), nrm.reshape(3, -1).copy(), albedo
+
+
+def frame_scene(seed: int = 1, width: int = 1920, height: int = 1080, n_patches: int = 64,
+                tris_per_patch: int = 1024, n_boxes: int = 64, table_size: int = 1 << 20,
+                cut_size: int = 32, frames: int = 32) -> Scene:
+    """Frame-scale static scene: 64K emissive triangles in 64 clustered patches,
+    64 occluder boxes forming 16 walled cells, a 1920 x 1080 G-buffer on 16
+    random planes (normals jittered +-15 deg, albedo U[0.2, 0.9]); 2^20-entry
+    hash grid, cut size 32, 1 sample per point per frame."""
+    rng = np.random.default_rng(seed)
+    c = 4
+    boxes = _room_cells(rng, c, n_boxes)
+    tris = _emitter_patches(rng, c, n_patches, tris_per_patch)
+    emission = rng.uniform(0.5, 2.0, size=(tris.shape[0], 3)).astype(np.float32)
+    pos, nrm, albedo = _gbuffer_planes(rng, width, height, c)
+    grid = GridConfig(table_size=table_size, cut_size=cut_size, origin=(0.0, 0.0, 0.0),
+                      cell_size=1.0 / 128.0, normal_bins=8, jitter=True)
+    return Scene("frame", tris, emission, boxes, pos, nrm, albedo, grid, spp=1,
+                 frames=frames, seed=seed, width=width, height=height)
+
+
+def dynamic_scene(seed: int = 2, width: int = 3840, height: int = 2160, n_patches: int = 1024,
+                  tris_per_patch: int = 1024, n_boxes: int = 64, table_size: int = 1 << 21,
+                  cut_size: int = 64, frames: int = 120, blink_fraction: float = 0.1) -> Scene:
+    """Dynamic lighting: 1M emissive triangles (1024 patches), 10% blinking as
+    1 + 0.9 sin(w t + phi), w ~ U[0.5, 4] rad/s, phi ~ U[0, 2 pi); 3840 x 2160
+    G-buffer; cut size 64; 2^21-entry grid; 120 frames."""
+    rng = np.random.default_rng(seed)
+    c = 4
+    boxes = _room_cells(rng, c, n_boxes)
+    tris = _emitter_patches(rng, c, n_patches, tris_per_patch)
+    n = tris.shape[0]
+    emission = rng.uniform(0.5, 2.0, size=(n, 3)).astype(np.float32)
+    mask = rng.uniform(size=n) < blink_fraction
+    omega = rng.uniform(0.5, 4.0, size=n).astype(np.float32)
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=n).astype(np.float32)
+    pos, nrm, albedo = _gbuffer_planes(rng, width, height, c)
+    grid = GridConfig(table_size=table_size, cut_size=cut_size, origin=(0.0, 0.0, 0.0),
+                      cell_size=1.0 / 256.0, normal_bins=8, jitter=True)
+    return Scene("dynamic", tris, emission, boxes, pos, nrm, albedo, grid, spp=1,
+                 frames=frames, seed=seed, width=width, height=height,
+                 blink_omega=omega, blink_phase=phase, blink_mask=mask)
+
+
+def small_frame_scene(seed: int = 3, width: int = 96, height: int = 64, n_patches: int = 16,
+                      tris_per_patch: int = 64, n_boxes: int = 32, table_size: int = 1 << 12,
+                      cut_size: int = 32, spp: int = 2) -> Scene:
+    """A reduced frame-scale scene (same recipe as frame_scene) small enough
+    for the CPU oracle to finish every sample in about a second."""
+    s = frame_scene(seed=seed, width=width, height=height, n_patches=n_patches,
+                    tris_per_patch=tris_per_patch, n_boxes=n_boxes, table_size=table_size,
+                    cut_size=cut_size, frames=4)
+    s.name = "small_frame"
+    s.grid.cell_size = 1.0 / 32.0
+    s.spp = spp
+    return s
+
+
+def batched_scenes(seed: int = 4, n_scenes: int = 256, light_range=(1 << 10, 1 << 18),
+                   point_range=(1 << 16, 1 << 21), cut_sizes=(16, 32, 64), scale: float = 1.0):
+    """Uneven independent scenes: light counts and shading-point counts
+    log-uniform over the given ranges, cut size uniform over cut_sizes.
+    `scale` shrinks the point and light counts (for tests)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_scenes):
+        nl = int(math.exp(rng.uniform(math.log(light_range[0]), math.log(light_range[1]))) * scale)
+        npnt = int(math.exp(rng.uniform(math.log(point_range[0]), math.log(point_range[1]))) * scale)
+        nl = max(nl, 16)
+        npnt = max(npnt, 64)
+        m = int(rng.choice(cut_sizes))
+        n_patches = max(1, int(round(nl / 256)))
+        tpp = max(2, (nl // n_patches) // 2 * 2)
+        width = int(math.sqrt(npnt * 16 / 9)) // 4 * 4 or 4
+        height = max(4, npnt // width // 4 * 4)
+        table = 1 << max(10, int(math.ceil(math.log2(max(1, width * height) / 4))))
+        s = frame_scene(seed=seed * 100003 + i, width=width, height=height, n_patches=n_patches,
+                        tris_per_patch=tpp, n_boxes=32, table_size=table, cut_size=m, frames=1)
+        s.name = f"batched{i}"
+        out.append(s)
+    return out
