@@ -644,20 +644,23 @@ float orc_importance32(const float* r, const float x[3], const float n[3])
 /* ------------------------------------------------------------------------ */
 /* Shadow test (binary32): segment from o = x + 1e-4 n to the light point y, */
 /* parameter t in (0, 0.9999), slab test against every box (open intervals). */
+/* Each slab plane is t = fma(b, 1/d, -(o * (1/d))): one fused multiply-add, */
+/* correctly rounded (C99 fmaf).                                             */
 /* ------------------------------------------------------------------------ */
 static int orc_occluded32(const float o[3], const float y[3], int nbox, const float* boxes)
 {
-    float d[3], inv[3];
+    float d[3], inv[3], oi[3];
     for (int k = 0; k < 3; ++k) {
         d[k] = y[k] - o[k];
         inv[k] = 1.0f / d[k];
+        oi[k] = o[k] * inv[k];
     }
     for (int b = 0; b < nbox; ++b) {
         const float* bx = boxes + (size_t)b * 6;
         float tn = 0.0f, tf = 0.9999f;
         for (int k = 0; k < 3; ++k) {
-            float t0 = (bx[k] - o[k]) * inv[k];
-            float t1 = (bx[3 + k] - o[k]) * inv[k];
+            float t0 = fmaf(bx[k], inv[k], -oi[k]);
+            float t1 = fmaf(bx[3 + k], inv[k], -oi[k]);
             tn = fmaxf(tn, fminf(t0, t1));
             tf = fminf(tf, fmaxf(t0, t1));
         }
