@@ -1,0 +1,205 @@
+/*
+ * rll.h -- C ABI of the GB300 (sm_103a) implementation of Reinforcement
+ * Lightcuts Learning (Pantaleoni, arXiv 1911.10217).
+ *
+ * Conventions for every entry point:
+ *  - Bulk arrays are plain pointers to DEVICE memory owned by the caller
+ *    (e.g. contiguous torch tensors), unless an argument says "host".
+ *    Layouts are stated per argument; "SoA [3][P]" means all x, then all y,
+ *    then all z.
+ *  - rll_ctx, rll_tree and rll_grid are opaque handles owned by the library
+ *    and released with the matching *_destroy call.
+ *  - Work is enqueued on the context's CUDA stream and returns without
+ *    waiting, except where a call says it synchronises.
+ *  - The return value is a status code (RLL_OK = 0). A failing call leaves a
+ *    message in rll_last_error(ctx). No C++ exception crosses this boundary.
+ *    Problems found on the device (hash table full, a bounds check) set bits
+ *    in a device status word that rll_sync_status() returns and clears.
+ *  - Not thread-safe per context: one host thread drives one context.
+ */
+#ifndef RLL_H
+#define RLL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RLL_OK 0
+#define RLL_E_INVALID 1     /* bad argument (null pointer, size out of range) */
+#define RLL_E_NOMEM 2       /* device allocation failed */
+#define RLL_E_CUDA 3        /* a CUDA runtime call failed */
+#define RLL_E_TABLE_FULL 4  /* device: a hash lookup hit the probe limit (sample used the initial cut) */
+#define RLL_E_TIMEOUT 8     /* device: a bounded wait gave up */
+#define RLL_E_DEVICE 16     /* device: an index failed its bounds check */
+
+/* table precision of Q and C */
+#define RLL_PREC_FP32 0
+#define RLL_PREC_FP16 1
+#define RLL_PREC_BF16 2
+
+/* choice of a light inside the sampled cluster */
+#define RLL_MODE_DESCENT 0  /* stochastic descent by unoccluded bounds (default) */
+#define RLL_MODE_UNIFORM 1  /* uniform over the cluster's lights ("select a light in the cluster randomly", Section 3) */
+
+/* the |c| fed to Eq. 1 */
+#define RLL_REWARD_CLUSTER 0 /* luminance of c / (p_in * p_area): the cluster's contribution estimate (default) */
+#define RLL_REWARD_LITERAL 1 /* luminance of c / p_area: the selected light's contribution */
+
+typedef struct rll_ctx rll_ctx;
+typedef struct rll_tree rll_tree;
+typedef struct rll_grid rll_grid;
+
+/* Parameters of a hash grid (Section 3: 5-d hash table, fixed-size cuts,
+ * Q and C tables, Eq. 1 and Eq. 2, split-collapse threshold). */
+typedef struct rll_grid_params {
+    uint32_t table_size;       /* H slots, a power of two, 2^4 .. 2^26 */
+    uint32_t cut_size;         /* M leaves per cut, 1 .. 256 (min(M, lights) are used) */
+    float origin[3];           /* grid origin */
+    float cell_size;           /* h: position quantisation step, > 0 */
+    uint32_t normal_bins;      /* bins per octahedral normal axis, 1 .. 255 */
+    uint32_t jitter;           /* 1: jitter every lookup by +-1/2 cell / bin (Section 3) */
+    uint32_t precision;        /* RLL_PREC_* for stored Q and C */
+    uint32_t in_cluster_mode;  /* RLL_MODE_* */
+    uint32_t reward_mode;      /* RLL_REWARD_* */
+    float alpha;               /* Eq. 1 learning rate, [0, 1] */
+    float threshold;           /* split-collapse T (> 0) */
+    float eps;                 /* Eq. 2 floor: eps * sum(Q) / m added to each leaf, >= 0 */
+    float q_init;              /* Q of a new cell's leaves, > 0 */
+} rll_grid_params;
+
+/* Per-sample diagnostics (optional outputs of rll_sample_and_shade_ex), each
+ * [P * spp] in sample order (sample id = point * spp + j); any may be NULL. */
+typedef struct rll_sample_debug {
+    int32_t* light;            /* sorted light index chosen */
+    float* p_cut;              /* probability of the chosen cluster */
+    float* p_in;               /* probability of the light inside the cluster */
+} rll_sample_debug;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on `device` that enqueues on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). */
+int rll_ctx_create(rll_ctx** out, int device, void* cuda_stream);
+int rll_ctx_set_stream(rll_ctx* ctx, void* cuda_stream);
+int rll_ctx_destroy(rll_ctx* ctx);
+/* Message of the last failing call on this context ("" if none). */
+const char* rll_last_error(const rll_ctx* ctx);
+/* Synchronises the stream, returns the OR of device status bits raised since
+ * the last call (0 = none) and clears them. Returns a negative value if the
+ * synchronisation itself failed. */
+int rll_sync_status(rll_ctx* ctx);
+
+/* ---- light tree (Section 3, Section 3.1: sort the lights, one binary tree
+ * over all of them, built as an LBVH over light positions) ---------------- */
+
+/* Builds the tree over n triangles. tri: [n][3][3] float (v0, v1, v2);
+ * emission: [n][3] RGB radiance used for the node power bounds (pass the
+ * maximum over time for changing lights). Lights are sorted by the 30-bit
+ * Morton code of their centroid, ties by input index; node numbering:
+ * internal nodes 0..n-2, the leaf of sorted light l is n-1+l, root 0.
+ * Triangles must have non-zero area. n in [1, 2^24]. Synchronises. */
+int rll_build_light_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
+                         rll_tree** out);
+/* Replaces the radiance used for shading (emission: [n][3], input order);
+ * the node power bounds keep the values given at build time. */
+int rll_tree_update_emission(rll_ctx* ctx, rll_tree* tree, const float* emission);
+int64_t rll_tree_num_lights(const rll_tree* tree);
+/* Copies the tree to HOST arrays (any may be NULL): perm [n] sorted->input
+ * index, left/right [n-1], parent [2n-1] (-1 at root), begin/end [2n-1],
+ * rec [2n-1][11] = bmin xyz, bmax xyz, power, cone axis xyz, cone cos.
+ * Synchronises. */
+int rll_tree_export(rll_ctx* ctx, const rll_tree* tree, uint32_t* perm, int32_t* left,
+                    int32_t* right, int32_t* parent, uint32_t* begin, uint32_t* end, float* rec);
+int rll_tree_destroy(rll_tree* tree);
+
+/* ---- hash grid of learned cuts (Section 3) ------------------------------- */
+
+/* Creates a grid whose every slot starts empty and holds the initial cut:
+ * the breadth-first cut of min(M, n) nodes (Section 3), Q = q_init, C from
+ * Eq. 2. Synchronises. */
+int rll_create_grid(rll_ctx* ctx, const rll_tree* tree, const rll_grid_params* params,
+                    rll_grid** out);
+/* Number of leaves m = min(M, lights) in every cut. */
+uint32_t rll_grid_cut_len(const rll_grid* grid);
+/* Copies the grid to HOST arrays (any may be NULL): keys [H] (empty slots
+ * 0xFFFFFFFFFFFFFFFF), cut [H][M] node ids, q and c [H][M] as float (16-bit
+ * tables widened exactly). Only the first m entries of a row are meaningful.
+ * Also the checkpoint format. Synchronises. */
+int rll_grid_export(rll_ctx* ctx, const rll_grid* grid, uint64_t* keys, int32_t* cut, float* q,
+                    float* c);
+/* Loads a state written by rll_grid_export (HOST arrays, same shapes; q and c
+ * are rounded to the table precision). Every occupied slot becomes a touched
+ * cell, so a following rll_split_collapse adapts all of them. Synchronises. */
+int rll_grid_import(rll_ctx* ctx, rll_grid* grid, const uint64_t* keys, const int32_t* cut,
+                    const float* q, const float* c);
+int rll_grid_destroy(rll_grid* grid);
+
+/* ---- one rendering pass: sampling (Section 3 / Section 3.1) ------------- */
+
+/* For every shading point and sample: hash the (jittered) point to its cell
+ * (creating it on first access), pick a cluster by binary search in C, a
+ * light inside it (descent or uniform), a point on that triangle, and
+ * evaluate the shadowed contribution against the boxes. Writes the
+ * per-point mean estimate and one learning record per sample.
+ *   pos, nrm: SoA [3][P] float; albedo [P]; boxes [K][6] (min xyz, max xyz),
+ *   K <= 1024; rgb: SoA [3][P] output; rec_key [P*spp]: slot * M + cluster
+ *   (0xFFFFFFFF when no cell could be created); rec_val [P*spp]: |c| (Eq. 1
+ *   reward). rec_key / rec_val may both be NULL (no learning).
+ * Random numbers: Philox4x32-10, key = seed, counter = (point * spp + j,
+ * frame, draw block, 0). P * spp < 2^32. Q and C are only read. */
+int rll_sample_and_shade(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos,
+                         const float* nrm, const float* albedo, int64_t n_points,
+                         const float* boxes, int32_t n_boxes, uint64_t seed, uint32_t frame,
+                         int32_t spp, float* rgb, uint32_t* rec_key, float* rec_val);
+/* Same, with optional per-sample diagnostics (dbg may be NULL). */
+int rll_sample_and_shade_ex(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos,
+                            const float* nrm, const float* albedo, int64_t n_points,
+                            const float* boxes, int32_t n_boxes, uint64_t seed, uint32_t frame,
+                            int32_t spp, float* rgb, uint32_t* rec_key, float* rec_val,
+                            const rll_sample_debug* dbg);
+
+/* Energy-based baseline (Section 4): lights chosen in proportion to their
+ * emitted power by inversion of one global cdf; same shading, same Philox
+ * stream (cluster draw reused as the cdf draw). rgb: SoA [3][P]. */
+int rll_sample_power(rll_ctx* ctx, const rll_tree* tree, const float* pos, const float* nrm,
+                     const float* albedo, int64_t n_points, const float* boxes, int32_t n_boxes,
+                     uint64_t seed, uint32_t frame, int32_t spp, float* rgb, int32_t* light_out);
+
+/* ---- end of pass: learning (Section 3, Eq. 1 and Eq. 2) ------------------ */
+
+/* Applies Eq. 1, Q(s) := (1 - alpha) Q(s) + alpha |c|, for every record, in
+ * sample order per (cell, cluster) -- a deterministic segmented reduction
+ * (stable radix sort by key, then one warp per touched cell composing the
+ * affine updates) -- then rebuilds C of every touched cell by Eq. 2 with the
+ * eps floor. Records with key 0xFFFFFFFF are skipped. Remembers the touched
+ * cells for rll_split_collapse. Uses library-owned scratch memory. */
+int rll_learn_update(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key, const float* rec_val,
+                     int64_t n_records);
+
+/* Split-collapse (Section 3, Fig. "TreeCuts"; Section 3.1: one thread group
+ * per cell) on every cell touched by the last rll_learn_update: split the
+ * non-single-light leaf of largest Q into its children and collapse the
+ * parent of two cut leaves of smallest Q if Q(l_max) > T * Q(p_min); then
+ * rebuild C (Eq. 2). */
+int rll_split_collapse(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree);
+
+/* ---- one whole pass from host memory ------------------------------------- */
+
+/* Copies the G-buffer (HOST pos/nrm SoA [3][P], albedo [P]) and boxes (HOST
+ * [K][6]) to the device, runs rll_sample_and_shade, rll_learn_update and (if
+ * do_split) rll_split_collapse, and copies rgb (HOST SoA [3][P]) back.
+ * Pinned host memory makes the copies asynchronous. Synchronises. */
+int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos,
+                         const float* nrm, const float* albedo, int64_t n_points,
+                         const float* boxes, int32_t n_boxes, uint64_t seed, uint32_t frame,
+                         int32_t spp, int32_t do_split, float* rgb);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLL_H */

@@ -1,0 +1,519 @@
+// C ABI of the library (include/rll.h): argument checks, handle lifetimes,
+// library-owned scratch, host staging. Every entry point returns a status
+// and never throws.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <deque>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rll_device.cuh"
+#include "rll_internal.h"
+
+namespace rll {
+
+int fail(rll_ctx* ctx, int code, const std::string& msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int check_cuda(rll_ctx* ctx, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return RLL_OK;
+    if (ctx) ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? RLL_E_NOMEM : RLL_E_CUDA;
+}
+
+void* ws_get(rll_ctx* ctx, size_t bytes)
+{
+    if (bytes <= ctx->ws_bytes) return ctx->ws;
+    // the old buffer may still be read by enqueued work
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    const size_t want = bytes + bytes / 4 + 4096;
+    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "cannot allocate " + std::to_string(want) + " bytes of scratch";
+        return nullptr;
+    }
+    ctx->ws_bytes = want;
+    return ctx->ws;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t elem_bytes(uint32_t precision) { return precision == RLL_PREC_FP32 ? 4 : 2; }
+
+void free_tree(rll_tree* t)
+{
+    if (!t) return;
+    cudaFree(t->nodes);
+    cudaFree(t->pairs);
+    cudaFree(t->lights);
+    cudaFree(t->perm);
+    cudaFree(t->left);
+    cudaFree(t->right);
+    cudaFree(t->parent);
+    cudaFree(t->light_cdf);
+    delete t;
+}
+
+void free_grid(rll_grid* g)
+{
+    if (!g) return;
+    cudaFree(g->keys);
+    cudaFree(g->cut);
+    cudaFree(g->Q);
+    cudaFree(g->C);
+    cudaFree(g->def_cut);
+    cudaFree(g->def_Q);
+    cudaFree(g->def_C);
+    cudaFree(g->touched);
+    cudaFree(g->touched_start);
+    cudaFree(g->n_touched);
+    delete g;
+}
+
+int check_params(rll_ctx* ctx, const rll_grid_params* p)
+{
+    if (!p) return fail(ctx, RLL_E_INVALID, "params is NULL");
+    const uint32_t H = p->table_size;
+    if (H < 16 || H > (1u << 26) || (H & (H - 1)) != 0)
+        return fail(ctx, RLL_E_INVALID, "table_size must be a power of two in [16, 2^26]");
+    if (p->cut_size < 1 || p->cut_size > (uint32_t)kMaxCut) return fail(ctx, RLL_E_INVALID, "cut_size must be in [1, 256]");
+    if ((uint64_t)H * p->cut_size > (1ull << 31)) return fail(ctx, RLL_E_INVALID, "table_size * cut_size must be <= 2^31");
+    if (!(p->cell_size > 0.0f) || !std::isfinite(p->cell_size)) return fail(ctx, RLL_E_INVALID, "cell_size must be > 0");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(p->origin[k])) return fail(ctx, RLL_E_INVALID, "origin must be finite");
+    if (p->normal_bins < 1 || p->normal_bins > 255) return fail(ctx, RLL_E_INVALID, "normal_bins must be in [1, 255]");
+    if (p->jitter > 1) return fail(ctx, RLL_E_INVALID, "jitter must be 0 or 1");
+    if (p->precision > RLL_PREC_BF16) return fail(ctx, RLL_E_INVALID, "unknown precision");
+    if (p->in_cluster_mode > RLL_MODE_UNIFORM) return fail(ctx, RLL_E_INVALID, "unknown in_cluster_mode");
+    if (p->reward_mode > RLL_REWARD_LITERAL) return fail(ctx, RLL_E_INVALID, "unknown reward_mode");
+    if (!(p->alpha >= 0.0f && p->alpha <= 1.0f)) return fail(ctx, RLL_E_INVALID, "alpha must be in [0, 1]");
+    if (!(p->threshold > 0.0f) || !std::isfinite(p->threshold)) return fail(ctx, RLL_E_INVALID, "threshold must be > 0");
+    if (!(p->eps >= 0.0f) || !std::isfinite(p->eps)) return fail(ctx, RLL_E_INVALID, "eps must be >= 0");
+    if (!(p->q_init > 0.0f) || !std::isfinite(p->q_init)) return fail(ctx, RLL_E_INVALID, "q_init must be > 0");
+    return RLL_OK;
+}
+
+// Breadth-first initial cut of min(M, n) nodes (Section 3), sorted by range
+// begin. Topology and node begins are copied to the host once per grid.
+int initial_cut(rll_ctx* ctx, const rll_tree* t, uint32_t M, std::vector<uint32_t>* cut)
+{
+    const int64_t n = t->n;
+    const uint32_t m = (uint32_t)std::min<int64_t>(M, n);
+    std::vector<int32_t> left(std::max<int64_t>(n - 1, 1)), right(std::max<int64_t>(n - 1, 1));
+    std::vector<uint32_t> begin(2 * n - 1);
+    cudaError_t e = cudaSuccess;
+    if (n > 1) {
+        e = cudaMemcpyAsync(left.data(), t->left, sizeof(int32_t) * (n - 1), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(right.data(), t->right, sizeof(int32_t) * (n - 1), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(begin.data(), sizeof(uint32_t), &t->nodes[0].begin, sizeof(NodeRec), sizeof(uint32_t),
+                              (size_t)(2 * n - 1), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "initial cut: copy tree");
+    std::deque<int64_t> q;
+    q.push_back(0);
+    while (q.size() < m) {
+        const int64_t id = q.front();
+        q.pop_front();
+        if (id >= n - 1) {
+            q.push_back(id);
+        } else {
+            q.push_back(left[id]);
+            q.push_back(right[id]);
+        }
+    }
+    cut->assign(q.begin(), q.end());
+    std::sort(cut->begin(), cut->end(), [&](uint32_t a, uint32_t b) { return begin[a] < begin[b]; });
+    return RLL_OK;
+}
+
+}  // namespace
+}  // namespace rll
+
+using namespace rll;
+
+extern "C" {
+
+int rll_ctx_create(rll_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return RLL_E_INVALID;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return RLL_E_CUDA;
+    }
+    rll_ctx* ctx = new (std::nothrow) rll_ctx();
+    if (!ctx) return RLL_E_NOMEM;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    DeviceGuard g(device);
+    if (cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return RLL_E_NOMEM;
+    }
+    *out = ctx;
+    return RLL_OK;
+}
+
+int rll_ctx_set_stream(rll_ctx* ctx, void* cuda_stream)
+{
+    if (!ctx) return RLL_E_INVALID;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return RLL_OK;
+}
+
+int rll_ctx_destroy(rll_ctx* ctx)
+{
+    if (!ctx) return RLL_OK;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->ws);
+    cudaFree(ctx->stage);
+    delete ctx;
+    return RLL_OK;
+}
+
+const char* rll_last_error(const rll_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int rll_sync_status(rll_ctx* ctx)
+{
+    if (!ctx) return -RLL_E_INVALID;
+    DeviceGuard g(ctx->device);
+    uint32_t bits = 0;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&bits, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        check_cuda(ctx, e, "sync_status");
+        return -RLL_E_CUDA;
+    }
+    return (int)bits;
+}
+
+int rll_build_light_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, rll_tree** out)
+{
+    if (!ctx || !out) return RLL_E_INVALID;
+    *out = nullptr;
+    if (!tri || !emission) return fail(ctx, RLL_E_INVALID, "tri / emission is NULL");
+    if (n < 1 || n > (1ll << 24)) return fail(ctx, RLL_E_INVALID, "light count must be in [1, 2^24]");
+    DeviceGuard g(ctx->device);
+    rll_tree* t = new (std::nothrow) rll_tree();
+    if (!t) return fail(ctx, RLL_E_NOMEM, "host allocation");
+    t->device = ctx->device;
+    const int rc = build_tree(ctx, tri, emission, n, t);
+    if (rc != RLL_OK) {
+        free_tree(t);
+        return rc;
+    }
+    *out = t;
+    return RLL_OK;
+}
+
+int rll_tree_update_emission(rll_ctx* ctx, rll_tree* tree, const float* emission)
+{
+    if (!ctx || !tree || !emission) return ctx ? fail(ctx, RLL_E_INVALID, "NULL argument") : RLL_E_INVALID;
+    DeviceGuard g(ctx->device);
+    return tree_update_emission(ctx, tree, emission);
+}
+
+int64_t rll_tree_num_lights(const rll_tree* tree) { return tree ? tree->n : 0; }
+
+int rll_tree_export(rll_ctx* ctx, const rll_tree* t, uint32_t* perm, int32_t* left, int32_t* right, int32_t* parent,
+                    uint32_t* begin, uint32_t* end, float* rec)
+{
+    if (!ctx || !t) return RLL_E_INVALID;
+    DeviceGuard g(ctx->device);
+    const int64_t n = t->n, nn = 2 * n - 1;
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (perm) e = cudaMemcpyAsync(perm, t->perm, 4 * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && left && n > 1) e = cudaMemcpyAsync(left, t->left, 4 * (n - 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && right && n > 1) e = cudaMemcpyAsync(right, t->right, 4 * (n - 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && parent) e = cudaMemcpyAsync(parent, t->parent, 4 * nn, cudaMemcpyDeviceToHost, s);
+    std::vector<NodeRec> nodes;
+    if (e == cudaSuccess && (begin || end || rec)) {
+        nodes.resize(nn);
+        e = cudaMemcpyAsync(nodes.data(), t->nodes, sizeof(NodeRec) * nn, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "tree export");
+    for (int64_t i = 0; i < (int64_t)nodes.size(); ++i) {
+        const NodeRec& r = nodes[i];
+        if (begin) begin[i] = r.begin;
+        if (end) end[i] = r.end;
+        if (rec) {
+            float* o = rec + i * 11;
+            for (int k = 0; k < 3; ++k) {
+                o[k] = r.bmin[k];
+                o[3 + k] = r.bmax[k];
+                o[7 + k] = r.axis[k];
+            }
+            o[6] = r.phi;
+            o[10] = r.cos_t;
+        }
+    }
+    return RLL_OK;
+}
+
+int rll_tree_destroy(rll_tree* tree)
+{
+    if (!tree) return RLL_OK;
+    DeviceGuard g(tree->device);
+    cudaDeviceSynchronize();
+    free_tree(tree);
+    return RLL_OK;
+}
+
+int rll_create_grid(rll_ctx* ctx, const rll_tree* tree, const rll_grid_params* params, rll_grid** out)
+{
+    if (!ctx || !out) return RLL_E_INVALID;
+    *out = nullptr;
+    if (!tree) return fail(ctx, RLL_E_INVALID, "tree is NULL");
+    int rc = check_params(ctx, params);
+    if (rc != RLL_OK) return rc;
+    DeviceGuard dg(ctx->device);
+    rll_grid* g = new (std::nothrow) rll_grid();
+    if (!g) return fail(ctx, RLL_E_NOMEM, "host allocation");
+    g->device = ctx->device;
+    g->p = *params;
+    g->H = params->table_size;
+    g->M = params->cut_size;
+    g->n_lights = tree->n;
+    std::vector<uint32_t> cut;
+    rc = initial_cut(ctx, tree, g->M, &cut);
+    if (rc != RLL_OK) {
+        free_grid(g);
+        return rc;
+    }
+    g->m = (uint32_t)cut.size();
+    const size_t eb = elem_bytes(params->precision);
+    const size_t rows = (size_t)g->H * g->M;
+    cudaError_t e = cudaMalloc((void**)&g->keys, 8 * (size_t)g->H);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->cut, 4 * rows);
+    if (e == cudaSuccess) e = cudaMalloc(&g->Q, eb * rows);
+    if (e == cudaSuccess) e = cudaMalloc(&g->C, eb * rows);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->def_cut, 4 * g->m);
+    if (e == cudaSuccess) e = cudaMalloc(&g->def_Q, eb * g->m);
+    if (e == cudaSuccess) e = cudaMalloc(&g->def_C, eb * g->m);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->touched, 4 * (size_t)g->H);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->touched_start, 4 * (size_t)g->H);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->n_touched, 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->keys, 0xFF, 8 * (size_t)g->H, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->n_touched, 0, 4, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->def_cut, cut.data(), 4 * g->m, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+        rc = check_cuda(ctx, e, "create_grid");
+        free_grid(g);
+        return rc;
+    }
+    rc = grid_init(ctx, g);
+    if (rc == RLL_OK) rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "create_grid");
+    if (rc != RLL_OK) {
+        free_grid(g);
+        return rc;
+    }
+    *out = g;
+    return RLL_OK;
+}
+
+uint32_t rll_grid_cut_len(const rll_grid* grid) { return grid ? grid->m : 0; }
+
+int rll_grid_export(rll_ctx* ctx, const rll_grid* g, uint64_t* keys, int32_t* cut, float* q, float* c)
+{
+    if (!ctx || !g) return RLL_E_INVALID;
+    DeviceGuard dg(ctx->device);
+    const size_t rows = (size_t)g->H * g->M;
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (keys) e = cudaMemcpyAsync(keys, g->keys, 8 * (size_t)g->H, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && cut) e = cudaMemcpyAsync(cut, g->cut, 4 * rows, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "grid export");
+    if (q || c) {
+        float* w = (float*)ws_get(ctx, 8 * rows);
+        if (!w) return RLL_E_NOMEM;
+        int rc = grid_to_float(ctx, g, w, w + rows);
+        if (rc != RLL_OK) return rc;
+        if (q) e = cudaMemcpyAsync(q, w, 4 * rows, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && c) e = cudaMemcpyAsync(c, w + rows, 4 * rows, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return check_cuda(ctx, e, "grid export");
+}
+
+int rll_grid_import(rll_ctx* ctx, rll_grid* g, const uint64_t* keys, const int32_t* cut, const float* q, const float* c)
+{
+    if (!ctx || !g) return RLL_E_INVALID;
+    if (!keys || !cut || !q || !c) return fail(ctx, RLL_E_INVALID, "grid import needs keys, cut, q and c");
+    DeviceGuard dg(ctx->device);
+    const size_t rows = (size_t)g->H * g->M;
+    cudaStream_t s = ctx->stream;
+    float* w = (float*)ws_get(ctx, 8 * rows);
+    if (!w) return RLL_E_NOMEM;
+    cudaError_t e = cudaMemcpyAsync(g->keys, keys, 8 * (size_t)g->H, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->cut, cut, 4 * rows, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w, q, 4 * rows, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w + rows, c, 4 * rows, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "grid import");
+    int rc = grid_from_float(ctx, g, w, w + rows);
+    if (rc == RLL_OK) rc = grid_mark_occupied(ctx, g);
+    if (rc != RLL_OK) return rc;
+    return check_cuda(ctx, cudaStreamSynchronize(s), "grid import");
+}
+
+int rll_grid_destroy(rll_grid* grid)
+{
+    if (!grid) return RLL_OK;
+    DeviceGuard g(grid->device);
+    cudaDeviceSynchronize();
+    free_grid(grid);
+    return RLL_OK;
+}
+
+static int check_pass_args(rll_ctx* ctx, const rll_grid* grid, const rll_tree* tree, const float* pos,
+                           const float* nrm, const float* albedo, int64_t n_points, const float* boxes,
+                           int32_t n_boxes, int32_t spp, const float* rgb)
+{
+    if (!grid || !tree) return fail(ctx, RLL_E_INVALID, "grid / tree is NULL");
+    if (grid->n_lights != tree->n) return fail(ctx, RLL_E_INVALID, "grid was created for another tree");
+    if (n_points < 0) return fail(ctx, RLL_E_INVALID, "n_points < 0");
+    if (spp < 1 || spp > 65536) return fail(ctx, RLL_E_INVALID, "spp must be in [1, 65536]");
+    if ((uint64_t)n_points * (uint64_t)spp >= 0xFFFFFFFFull) return fail(ctx, RLL_E_INVALID, "n_points * spp must be < 2^32");
+    if (n_boxes < 0 || n_boxes > kMaxBoxes) return fail(ctx, RLL_E_INVALID, "n_boxes must be in [0, 1024]");
+    if (n_boxes > 0 && !boxes) return fail(ctx, RLL_E_INVALID, "boxes is NULL");
+    if (n_points > 0 && (!pos || !nrm || !albedo || !rgb)) return fail(ctx, RLL_E_INVALID, "NULL G-buffer or rgb");
+    return RLL_OK;
+}
+
+int rll_sample_and_shade_ex(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos, const float* nrm,
+                            const float* albedo, int64_t n_points, const float* boxes, int32_t n_boxes,
+                            uint64_t seed, uint32_t frame, int32_t spp, float* rgb, uint32_t* rec_key,
+                            float* rec_val, const rll_sample_debug* dbg)
+{
+    if (!ctx) return RLL_E_INVALID;
+    int rc = check_pass_args(ctx, grid, tree, pos, nrm, albedo, n_points, boxes, n_boxes, spp, rgb);
+    if (rc != RLL_OK) return rc;
+    if ((rec_key == nullptr) != (rec_val == nullptr)) return fail(ctx, RLL_E_INVALID, "rec_key and rec_val go together");
+    DeviceGuard g(ctx->device);
+    return sample_and_shade(ctx, grid, tree, pos, nrm, albedo, n_points, boxes, n_boxes, seed, frame, spp, rgb,
+                            rec_key, rec_val, dbg);
+}
+
+int rll_sample_and_shade(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos, const float* nrm,
+                         const float* albedo, int64_t n_points, const float* boxes, int32_t n_boxes, uint64_t seed,
+                         uint32_t frame, int32_t spp, float* rgb, uint32_t* rec_key, float* rec_val)
+{
+    return rll_sample_and_shade_ex(ctx, grid, tree, pos, nrm, albedo, n_points, boxes, n_boxes, seed, frame, spp,
+                                   rgb, rec_key, rec_val, nullptr);
+}
+
+int rll_sample_power(rll_ctx* ctx, const rll_tree* tree, const float* pos, const float* nrm, const float* albedo,
+                     int64_t n_points, const float* boxes, int32_t n_boxes, uint64_t seed, uint32_t frame,
+                     int32_t spp, float* rgb, int32_t* light_out)
+{
+    if (!ctx) return RLL_E_INVALID;
+    if (!tree) return fail(ctx, RLL_E_INVALID, "tree is NULL");
+    if (n_points < 0 || spp < 1 || (uint64_t)n_points * (uint64_t)spp >= 0xFFFFFFFFull)
+        return fail(ctx, RLL_E_INVALID, "bad n_points / spp");
+    if (n_boxes < 0 || n_boxes > kMaxBoxes || (n_boxes > 0 && !boxes)) return fail(ctx, RLL_E_INVALID, "bad boxes");
+    if (n_points > 0 && (!pos || !nrm || !albedo || !rgb)) return fail(ctx, RLL_E_INVALID, "NULL G-buffer or rgb");
+    DeviceGuard g(ctx->device);
+    return sample_power(ctx, tree, pos, nrm, albedo, n_points, boxes, n_boxes, seed, frame, spp, rgb, light_out);
+}
+
+int rll_learn_update(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key, const float* rec_val, int64_t n_records)
+{
+    if (!ctx) return RLL_E_INVALID;
+    if (!grid) return fail(ctx, RLL_E_INVALID, "grid is NULL");
+    if (n_records < 0 || n_records >= 0xFFFFFFFFll) return fail(ctx, RLL_E_INVALID, "n_records out of range");
+    if (n_records > 0 && (!rec_key || !rec_val)) return fail(ctx, RLL_E_INVALID, "NULL records");
+    DeviceGuard g(ctx->device);
+    return learn_update(ctx, grid, rec_key, rec_val, n_records);
+}
+
+int rll_split_collapse(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree)
+{
+    if (!ctx) return RLL_E_INVALID;
+    if (!grid || !tree) return fail(ctx, RLL_E_INVALID, "grid / tree is NULL");
+    if (grid->n_lights != tree->n) return fail(ctx, RLL_E_INVALID, "grid was created for another tree");
+    DeviceGuard g(ctx->device);
+    return split_collapse(ctx, grid, tree);
+}
+
+int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos, const float* nrm,
+                         const float* albedo, int64_t n_points, const float* boxes, int32_t n_boxes, uint64_t seed,
+                         uint32_t frame, int32_t spp, int32_t do_split, float* rgb)
+{
+    if (!ctx) return RLL_E_INVALID;
+    int rc = check_pass_args(ctx, grid, tree, pos, nrm, albedo, n_points, boxes, n_boxes, spp, rgb);
+    if (rc != RLL_OK) return rc;
+    DeviceGuard g(ctx->device);
+    const int64_t P = n_points, S = n_points * spp;
+    auto a = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t need = a(12 * P) * 3 + a(4 * P) + a(24 * (size_t)std::max(n_boxes, 1)) + a(4 * S) * 2;
+    if (need > ctx->stage_bytes) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        if (cudaMalloc(&ctx->stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, RLL_E_NOMEM, "cannot allocate staging buffers");
+        }
+        ctx->stage_bytes = need;
+    }
+    char* w = (char*)ctx->stage;
+    float* d_pos = (float*)w; w += a(12 * P);
+    float* d_nrm = (float*)w; w += a(12 * P);
+    float* d_rgb = (float*)w; w += a(12 * P);
+    float* d_alb = (float*)w; w += a(4 * P);
+    float* d_box = (float*)w; w += a(24 * (size_t)std::max(n_boxes, 1));
+    uint32_t* d_key = (uint32_t*)w; w += a(4 * S);
+    float* d_val = (float*)w;
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync(d_pos, pos, 12 * P, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_nrm, nrm, 12 * P, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_alb, albedo, 4 * P, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_boxes > 0) e = cudaMemcpyAsync(d_box, boxes, 24 * (size_t)n_boxes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "render_pass_host: upload");
+    rc = sample_and_shade(ctx, grid, tree, d_pos, d_nrm, d_alb, P, d_box, n_boxes, seed, frame, spp, d_rgb, d_key,
+                          d_val, nullptr);
+    if (rc == RLL_OK) rc = learn_update(ctx, grid, d_key, d_val, S);
+    if (rc == RLL_OK && do_split) rc = split_collapse(ctx, grid, tree);
+    if (rc != RLL_OK) return rc;
+    e = cudaMemcpyAsync(rgb, d_rgb, 12 * P, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return check_cuda(ctx, e, "render_pass_host");
+}
+
+}  // extern "C"

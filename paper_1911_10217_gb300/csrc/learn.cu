@@ -1,0 +1,511 @@
+// End-of-pass learning (Section 3, Eq. 1 and Eq. 2) and split-collapse
+// (Section 3, Fig. "TreeCuts"; Section 3.1).
+//
+// learn_update:
+//   1. stable radix sort of the records by key = slot * M + cluster (records
+//      arrive in sample order, so each key's records stay in sample order);
+//   2. one thread per sorted record marks the first record of every cell and
+//      appends (cell, first record) to the touched-cell list;
+//   3. one warp per touched cell walks its records 32 at a time: a segmented
+//      inclusive scan (by cluster) composes the affine maps
+//      q -> (1 - alpha) q + alpha |c| of Eq. 1 in sample order, and the last
+//      lane of each segment applies the composite to the cluster's Q held in
+//      shared memory; the row is then stored in the table precision and its
+//      cdf rebuilt (Eq. 2 with the floor, prefix sum across the warp).
+// The result is independent of thread scheduling: deterministic.
+//
+// split_collapse: one warp per touched cell (the paper uses one thread group
+// per cell): warp arg-max over the leaves that are not single lights, warp
+// arg-min over parents whose two children are both cut leaves, the
+// threshold test, then one lane emits the new cut and the cdf is rebuilt.
+#include <cuda_runtime.h>
+
+#include "rll_device.cuh"
+#include "rll_internal.h"
+
+namespace rll {
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Eq. 2 with the floor: q holds the stored Q of one row (m values, shared
+// memory); c and bits are shared scratch of the same length. Writes the
+// stored cdf row. Called by all 32 lanes of a warp.
+template <int P>
+__device__ void warp_rebuild_cdf(const float* q, int m, float eps, typename Store<P>::T* out, float* c,
+                                 uint16_t* bits)
+{
+    const int lane = threadIdx.x & 31;
+    float part = 0.0f;
+    for (int s = lane; s < m; s += 32) part += q[s];
+    const float S = warp_sum(part);
+    const bool uniform = !(S > 0.0f) || !isfinite(S);
+    const float add = eps * S / (float)m;
+    const int ipl = (m + 31) >> 5;
+    const int b = lane * ipl, e = min(m, b + ipl);
+    float run = 0.0f;
+    for (int s = b; s < e; ++s) {
+        run += uniform ? 1.0f : q[s] + add;
+        c[s] = run;
+    }
+    float x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const float before = x - run;
+    for (int s = b; s < e; ++s) c[s] += before;
+    __syncwarp();
+    if constexpr (P == RLL_PREC_FP32) {
+        for (int s = lane; s < m; s += 32) out[s] = Store<P>::store(c[s]);
+        __syncwarp();
+        return;
+    } else {
+        const float total = c[m - 1];
+        for (int s = lane; s < m; s += 32) bits[s] = Store<P>::bits(Store<P>::store(c[s] / total));
+        __syncwarp();
+        if (lane == 0) {
+            const uint16_t one = Store<P>::bits(Store<P>::store(1.0f));
+            bits[m - 1] = one;
+            uint16_t prev = 0;
+            for (int s = 0; s < m - 1; ++s) {
+                if (bits[s] <= prev) bits[s] = (uint16_t)(prev + 1);
+                prev = bits[s];
+            }
+            for (int s = m - 2; s >= 0; --s)
+                if (bits[s] >= bits[s + 1]) bits[s] = (uint16_t)(bits[s + 1] - 1);
+        }
+        __syncwarp();
+        for (int s = lane; s < m; s += 32) out[s] = Store<P>::from_bits(bits[s]);
+        __syncwarp();
+    }
+}
+
+// one warp: the default row (Q = q_init, C by Eq. 2)
+template <int P>
+__global__ void k_default_row(uint32_t m, float q_init, float eps, typename Store<P>::T* def_Q,
+                              typename Store<P>::T* def_C)
+{
+    __shared__ float s_q[kMaxCut], s_c[kMaxCut];
+    __shared__ uint16_t s_b[kMaxCut];
+    for (uint32_t s = threadIdx.x; s < m; s += 32) {
+        const typename Store<P>::T v = Store<P>::store(q_init);
+        def_Q[s] = v;
+        s_q[s] = Store<P>::load(v);
+    }
+    __syncwarp();
+    warp_rebuild_cdf<P>(s_q, (int)m, eps, def_C, s_c, s_b);
+}
+
+template <int P>
+__global__ void k_fill_rows(int64_t total, uint32_t M, uint32_t m, const uint32_t* __restrict__ def_cut,
+                            const typename Store<P>::T* __restrict__ def_Q,
+                            const typename Store<P>::T* __restrict__ def_C, uint32_t* __restrict__ cut,
+                            typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = (uint32_t)(i % M);
+        if (s < m) {
+            cut[i] = def_cut[s];
+            Q[i] = def_Q[s];
+            C[i] = def_C[s];
+        } else {
+            cut[i] = 0u;
+            Q[i] = Store<P>::store(0.0f);
+            C[i] = Store<P>::store(0.0f);
+        }
+    }
+}
+
+template <int P>
+__global__ void k_to_float(int64_t total, const typename Store<P>::T* __restrict__ Q,
+                           const typename Store<P>::T* __restrict__ C, float* __restrict__ q, float* __restrict__ c)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        if (q) q[i] = Store<P>::load(Q[i]);
+        if (c) c[i] = Store<P>::load(C[i]);
+    }
+}
+
+template <int P>
+__global__ void k_from_float(int64_t total, const float* __restrict__ q, const float* __restrict__ c,
+                             typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        Q[i] = Store<P>::store(q[i]);
+        C[i] = Store<P>::store(c[i]);
+    }
+}
+
+__global__ void k_cell_heads(const uint32_t* __restrict__ sk, int64_t n, uint32_t HM, uint32_t M,
+                             uint32_t* __restrict__ touched, uint32_t* __restrict__ touched_start,
+                             uint32_t* __restrict__ n_touched)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool head = false;
+    uint32_t cell = 0;
+    if (i < n) {
+        const uint32_t key = sk[i];
+        if (key < HM) {
+            cell = key / M;
+            head = (i == 0) || (sk[i - 1] / M != cell);
+        }
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, head);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(mask) - 1) base = atomicAdd(n_touched, (uint32_t)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+    if (head) {
+        const uint32_t slot = base + __popc(mask & lanemask_lt());
+        touched[slot] = cell;
+        touched_start[slot] = (uint32_t)i;
+    }
+}
+
+// every occupied slot becomes a touched cell (after an import)
+__global__ void k_mark_occupied(const unsigned long long* __restrict__ keys, uint32_t H, uint32_t* __restrict__ touched,
+                                uint32_t* __restrict__ n_touched)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool occ = i < H && keys[i] != kEmptyKey;
+    const uint32_t mask = __ballot_sync(0xffffffffu, occ);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(mask) - 1) base = atomicAdd(n_touched, (uint32_t)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+    if (occ) touched[base + __popc(mask & lanemask_lt())] = i;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_learn_cells(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, int64_t n, uint32_t HM,
+              uint32_t M, uint32_t m, const uint32_t* __restrict__ touched,
+              const uint32_t* __restrict__ touched_start, const uint32_t* __restrict__ n_touched,
+              typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C, float alpha, float eps)
+{
+    __shared__ float s_q[kWarpsPerBlock][kMaxCut];
+    __shared__ float s_c[kWarpsPerBlock][kMaxCut];
+    __shared__ uint16_t s_b[kWarpsPerBlock][kMaxCut];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t total = *n_touched;
+    const float a1 = 1.0f - alpha;
+    float* q = s_q[warp];
+    for (uint32_t w = blockIdx.x * kWarpsPerBlock + warp; w < total; w += gridDim.x * kWarpsPerBlock) {
+        const uint32_t cell = touched[w];
+        const int64_t start = touched_start[w];
+        typename Store<P>::T* qrow = Q + (int64_t)cell * M;
+        typename Store<P>::T* crow = C + (int64_t)cell * M;
+        for (uint32_t s = lane; s < m; s += 32) q[s] = Store<P>::load(qrow[s]);
+        __syncwarp();
+        for (int64_t pos = start;; pos += 32) {
+            const int64_t i = pos + lane;
+            const uint32_t key = i < n ? sk[i] : 0xFFFFFFFFu;
+            const bool valid = key < HM && key / M == cell;
+            const uint32_t mask = __ballot_sync(0xffffffffu, valid);
+            if (!mask) break;
+            const uint32_t s = valid ? key % M : 0xFFFFFFFFu;
+            float A = valid ? a1 : 1.0f;
+            float B = valid ? alpha * __uint_as_float(sv[i]) : 0.0f;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float Ao = __shfl_up_sync(0xffffffffu, A, o);
+                const float Bo = __shfl_up_sync(0xffffffffu, B, o);
+                const uint32_t so = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o && so == s) {
+                    B = A * Bo + B;
+                    A = A * Ao;
+                }
+            }
+            const uint32_t s_next = __shfl_down_sync(0xffffffffu, s, 1);
+            const bool last = valid && (lane == 31 || s_next != s);
+            if (last && s < m) q[s] = A * q[s] + B;
+            __syncwarp();
+            if (mask != 0xffffffffu) break;
+        }
+        for (uint32_t s = lane; s < m; s += 32) {
+            const typename Store<P>::T st = Store<P>::store(q[s]);
+            qrow[s] = st;
+            q[s] = Store<P>::load(st);
+        }
+        __syncwarp();
+        warp_rebuild_cdf<P>(q, (int)m, eps, crow, s_c[warp], s_b[warp]);
+    }
+}
+
+struct ArgBest {
+    float v;
+    uint32_t i;
+};
+
+__device__ __forceinline__ ArgBest warp_argmax(ArgBest a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, a.v, o);
+        const uint32_t i = __shfl_xor_sync(0xffffffffu, a.i, o);
+        if (i != 0xFFFFFFFFu && (a.i == 0xFFFFFFFFu || v > a.v || (v == a.v && i < a.i))) {
+            a.v = v;
+            a.i = i;
+        }
+    }
+    return a;
+}
+
+__device__ __forceinline__ ArgBest warp_argmin(ArgBest a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, a.v, o);
+        const uint32_t i = __shfl_xor_sync(0xffffffffu, a.i, o);
+        if (i != 0xFFFFFFFFu && (a.i == 0xFFFFFFFFu || v < a.v || (v == a.v && i < a.i))) {
+            a.v = v;
+            a.i = i;
+        }
+    }
+    return a;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_split(uint32_t M, uint32_t m, const uint32_t* __restrict__ touched, const uint32_t* __restrict__ n_touched,
+        uint32_t* __restrict__ cut, typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C,
+        const NodeRec* __restrict__ nodes, const int32_t* __restrict__ parent,
+        const int32_t* __restrict__ left, const int32_t* __restrict__ right, float T, float eps,
+        int64_t n_nodes, uint32_t* __restrict__ status)
+{
+    __shared__ float s_q[kWarpsPerBlock][kMaxCut];
+    __shared__ float s_c[kWarpsPerBlock][kMaxCut];
+    __shared__ uint32_t s_cut[kWarpsPerBlock][kMaxCut];
+    __shared__ uint32_t s_nc[kWarpsPerBlock][kMaxCut];
+    __shared__ uint16_t s_b[kWarpsPerBlock][kMaxCut];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t total = *n_touched;
+    float* q = s_q[warp];
+    uint32_t* cs = s_cut[warp];
+    for (uint32_t w = blockIdx.x * kWarpsPerBlock + warp; w < total; w += gridDim.x * kWarpsPerBlock) {
+        const uint32_t cell = touched[w];
+        uint32_t* crow = cut + (int64_t)cell * M;
+        typename Store<P>::T* qrow = Q + (int64_t)cell * M;
+        bool bad = false;
+        for (uint32_t s = lane; s < m; s += 32) {
+            cs[s] = crow[s];
+            q[s] = Store<P>::load(qrow[s]);
+            bad |= (int64_t)cs[s] >= n_nodes;
+        }
+        if (__any_sync(0xffffffffu, bad)) {  // corrupt cut row: flag and leave the cell alone
+            if (lane == 0) atomicOr(status, (uint32_t)RLL_E_DEVICE);
+            continue;
+        }
+        __syncwarp();
+        ArgBest hi{0.0f, 0xFFFFFFFFu}, lo{0.0f, 0xFFFFFFFFu};
+        for (uint32_t s = lane; s < m; s += 32) {
+            const NodeRec& r = nodes[cs[s]];
+            if (r.end - r.begin > 1u && (hi.i == 0xFFFFFFFFu || q[s] > hi.v)) {
+                hi.v = q[s];
+                hi.i = s;
+            }
+            if (s + 1 < m) {
+                const int32_t pa = parent[cs[s]];
+                if (pa >= 0 && pa == parent[cs[s + 1]]) {
+                    const float v = fadd(q[s], q[s + 1]);
+                    if (lo.i == 0xFFFFFFFFu || v < lo.v) {
+                        lo.v = v;
+                        lo.i = s;
+                    }
+                }
+            }
+        }
+        hi = warp_argmax(hi);
+        lo = warp_argmin(lo);
+        const bool apply = hi.i != 0xFFFFFFFFu && lo.i != 0xFFFFFFFFu && hi.i != lo.i && hi.i != lo.i + 1 &&
+                           hi.v > fmul(T, lo.v);
+        if (!apply) continue;
+        // one lane emits the new row into shared scratch rows
+        if (lane == 0) {
+            float* nq = s_c[warp];
+            uint32_t* nc = s_nc[warp];
+            uint32_t k = 0;
+            for (uint32_t i = 0; i < m; ++i) {
+                if (i == hi.i) {
+                    const uint32_t node = cs[i];
+                    const uint32_t a = (uint32_t)left[node], c = (uint32_t)right[node];
+                    const float pa = nodes[a].phi, pc = nodes[c].phi;
+                    const float sum = pa + pc;
+                    const float fa = sum > 0.0f ? pa / sum : 0.5f;
+                    const float fc = sum > 0.0f ? pc / sum : 0.5f;
+                    nc[k] = a; nq[k] = q[i] * fa; ++k;
+                    nc[k] = c; nq[k] = q[i] * fc; ++k;
+                } else if (i == lo.i) {
+                    nc[k] = (uint32_t)parent[cs[i]];
+                    nq[k] = q[i] + q[i + 1];
+                    ++k;
+                    ++i;
+                } else {
+                    nc[k] = cs[i];
+                    nq[k] = q[i];
+                    ++k;
+                }
+            }
+            for (uint32_t i = 0; i < m; ++i) {
+                cs[i] = nc[i];
+                q[i] = nq[i];
+            }
+        }
+        __syncwarp();
+        for (uint32_t s = lane; s < m; s += 32) {
+            crow[s] = cs[s];
+            const typename Store<P>::T st = Store<P>::store(q[s]);
+            qrow[s] = st;
+            q[s] = Store<P>::load(st);
+        }
+        __syncwarp();
+        warp_rebuild_cdf<P>(q, (int)m, eps, C + (int64_t)cell * M, s_c[warp], s_b[warp]);
+    }
+}
+
+int key_bits(uint64_t hm_plus_one)
+{
+    int b = 0;
+    while ((1ull << b) < hm_plus_one) ++b;
+    return b;
+}
+
+int device_sm_count(int device)
+{
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    return v > 0 ? v : 1;
+}
+
+template <int P>
+int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n)
+{
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "memset touched");
+    if (n <= 0) return RLL_OK;
+    const uint32_t HM = g->H * g->M;
+    void* ws = ws_get(ctx, radix_sort_scratch_bytes(n));
+    if (!ws) return RLL_E_NOMEM;
+    uint32_t *sk, *sv;
+    e = radix_sort_pairs(s, rec_key, reinterpret_cast<const uint32_t*>(rec_val), n, key_bits((uint64_t)HM + 1), HM,
+                         ws, &sk, &sv);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "radix sort (records)");
+    k_cell_heads<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sk, n, HM, g->M, g->touched, g->touched_start,
+                                                            g->n_touched);
+    const int blocks = device_sm_count(g->device) * 8;
+    using T = typename Store<P>::T;
+    k_learn_cells<P><<<blocks, kWarpsPerBlock * 32, 0, s>>>(sk, sv, n, HM, g->M, g->m, g->touched, g->touched_start,
+                                                             g->n_touched, (T*)g->Q, (T*)g->C, g->p.alpha, g->p.eps);
+    return check_cuda(ctx, cudaGetLastError(), "learn kernels");
+}
+
+template <int P>
+int split_t(rll_ctx* ctx, rll_grid* g, const rll_tree* t)
+{
+    using T = typename Store<P>::T;
+    const int blocks = device_sm_count(g->device) * 8;
+    k_split<P><<<blocks, kWarpsPerBlock * 32, 0, ctx->stream>>>(g->M, g->m, g->touched, g->n_touched, g->cut,
+                                                                  (T*)g->Q, (T*)g->C, t->nodes, t->parent, t->left,
+                                                                  t->right, g->p.threshold, g->p.eps, 2 * t->n - 1,
+                                                                  ctx->d_status);
+    return check_cuda(ctx, cudaGetLastError(), "split kernel");
+}
+
+template <int P>
+int init_t(rll_ctx* ctx, rll_grid* g)
+{
+    using T = typename Store<P>::T;
+    cudaStream_t s = ctx->stream;
+    k_default_row<P><<<1, 32, 0, s>>>(g->m, g->p.q_init, g->p.eps, (T*)g->def_Q, (T*)g->def_C);
+    const int64_t total = (int64_t)g->H * g->M;
+    k_fill_rows<P><<<device_sm_count(g->device) * 4, 256, 0, s>>>(total, g->M, g->m, g->def_cut, (const T*)g->def_Q,
+                                                                  (const T*)g->def_C, g->cut, (T*)g->Q, (T*)g->C);
+    return check_cuda(ctx, cudaGetLastError(), "grid init");
+}
+
+}  // namespace
+
+int grid_init(rll_ctx* ctx, rll_grid* g)
+{
+    switch (g->p.precision) {
+    case RLL_PREC_FP16: return init_t<RLL_PREC_FP16>(ctx, g);
+    case RLL_PREC_BF16: return init_t<RLL_PREC_BF16>(ctx, g);
+    default: return init_t<RLL_PREC_FP32>(ctx, g);
+    }
+}
+
+int grid_to_float(rll_ctx* ctx, const rll_grid* g, float* q, float* c)
+{
+    const int64_t total = (int64_t)g->H * g->M;
+    const unsigned blocks = device_sm_count(g->device) * 4;
+    switch (g->p.precision) {
+    case RLL_PREC_FP16:
+        k_to_float<RLL_PREC_FP16><<<blocks, 256, 0, ctx->stream>>>(total, (const __half*)g->Q, (const __half*)g->C, q, c);
+        break;
+    case RLL_PREC_BF16:
+        k_to_float<RLL_PREC_BF16><<<blocks, 256, 0, ctx->stream>>>(total, (const __nv_bfloat16*)g->Q,
+                                                                   (const __nv_bfloat16*)g->C, q, c);
+        break;
+    default:
+        k_to_float<RLL_PREC_FP32><<<blocks, 256, 0, ctx->stream>>>(total, (const float*)g->Q, (const float*)g->C, q, c);
+    }
+    return check_cuda(ctx, cudaGetLastError(), "grid export");
+}
+
+int grid_from_float(rll_ctx* ctx, rll_grid* g, const float* q, const float* c)
+{
+    const int64_t total = (int64_t)g->H * g->M;
+    const unsigned blocks = device_sm_count(g->device) * 4;
+    switch (g->p.precision) {
+    case RLL_PREC_FP16:
+        k_from_float<RLL_PREC_FP16><<<blocks, 256, 0, ctx->stream>>>(total, q, c, (__half*)g->Q, (__half*)g->C);
+        break;
+    case RLL_PREC_BF16:
+        k_from_float<RLL_PREC_BF16><<<blocks, 256, 0, ctx->stream>>>(total, q, c, (__nv_bfloat16*)g->Q,
+                                                                     (__nv_bfloat16*)g->C);
+        break;
+    default:
+        k_from_float<RLL_PREC_FP32><<<blocks, 256, 0, ctx->stream>>>(total, q, c, (float*)g->Q, (float*)g->C);
+    }
+    return check_cuda(ctx, cudaGetLastError(), "grid import");
+}
+
+int grid_mark_occupied(rll_ctx* ctx, rll_grid* g)
+{
+    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, sizeof(uint32_t), ctx->stream);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "memset touched");
+    k_mark_occupied<<<(g->H + 255) / 256, 256, 0, ctx->stream>>>(g->keys, g->H, g->touched, g->n_touched);
+    return check_cuda(ctx, cudaGetLastError(), "mark occupied");
+}
+
+int learn_update(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n)
+{
+    switch (g->p.precision) {
+    case RLL_PREC_FP16: return learn_t<RLL_PREC_FP16>(ctx, g, rec_key, rec_val, n);
+    case RLL_PREC_BF16: return learn_t<RLL_PREC_BF16>(ctx, g, rec_key, rec_val, n);
+    default: return learn_t<RLL_PREC_FP32>(ctx, g, rec_key, rec_val, n);
+    }
+}
+
+int split_collapse(rll_ctx* ctx, rll_grid* g, const rll_tree* t)
+{
+    switch (g->p.precision) {
+    case RLL_PREC_FP16: return split_t<RLL_PREC_FP16>(ctx, g, t);
+    case RLL_PREC_BF16: return split_t<RLL_PREC_BF16>(ctx, g, t);
+    default: return split_t<RLL_PREC_FP32>(ctx, g, t);
+    }
+}
+
+}  // namespace rll

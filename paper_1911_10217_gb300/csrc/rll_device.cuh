@@ -1,0 +1,266 @@
+// Device-side building blocks of the GB300 Reinforcement Lightcuts Learning
+// library: record layouts, Philox4x32-10, the binary32 decision arithmetic,
+// table storage formats.
+//
+// Decision arithmetic. Every floating-point value that decides an integer
+// (hash cell, Morton code, descent branch, shadow test, split choice) is
+// evaluated with explicitly rounded binary32 intrinsics (__fadd_rn, __fmul_rn,
+// ...), so that no multiply-add is contracted and the result is the IEEE
+// value of the stated formula. Continuous quantities (contribution, pdf,
+// reward) use ordinary fp32 arithmetic.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/rll.h"
+
+namespace rll {
+
+constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
+constexpr uint32_t kInvalidRecord = 0xFFFFFFFFu;
+constexpr int kMaxProbes = 64;
+constexpr int kMaxCut = 256;
+constexpr int kMaxBoxes = 1024;
+constexpr float kShadowOffset = 1e-4f;
+constexpr float kShadowTmax = 0.9999f;
+
+// Node bounds record, 64 bytes. The descent reads the records of both
+// children of an internal node i from pairs[2i], pairs[2i+1]: one aligned
+// 128-byte line per level.
+struct __align__(16) NodeRec {
+    float bmin[3];
+    float bmax[3];
+    float phi;       // power bound: sum over lights of lum(Le) * area
+    float axis[3];   // orientation cone axis
+    float cos_t;     // orientation cone: cos of the half angle
+    uint32_t id;     // node id (leaf of sorted light l: n - 1 + l)
+    uint32_t begin;  // first sorted light
+    uint32_t end;    // one past the last sorted light
+};
+static_assert(sizeof(NodeRec) == 64, "NodeRec must be 64 bytes");
+
+// Sorted light, 64 bytes.
+struct __align__(16) LightRec {
+    float v0[3];
+    float v1[3];
+    float v2[3];
+    float le[3];     // current RGB radiance
+    float n[3];      // unit winding normal
+    float area;
+};
+static_assert(sizeof(LightRec) == 64, "LightRec must be 64 bytes");
+
+// ---------------------------------------------------------------- exact ops
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds, multipliers 0xD2511F53 and
+// 0xCD9E8D57, key bumped by 0x9E3779B9 / 0xBB67AE85 between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform in [0, 1): top 24 bits times 2^-24 (exact in binary32)
+__device__ __forceinline__ float u24(uint32_t x) { return __uint2float_rn(x >> 8) * 0x1p-24f; }
+
+// Draw layout of one light sample: draw i is word (i mod 4) of
+// Philox(counter = (sample id, frame, i / 4, 0), key = (seed lo, seed hi)).
+//   0 cut search, 1-2 triangle point, 3 uniform in-cluster choice,
+//   4-7 jitter x, y, z, normal u, 8 jitter normal v, 9 + k descent level k.
+enum : uint32_t {
+    kDrawCut = 0, kDrawTriA = 1, kDrawTriB = 2, kDrawUniform = 3, kDrawJit = 4, kDrawDescent = 9
+};
+
+struct SampleStream {
+    uint2 key;
+    uint32_t sample_id, frame;
+    uint32_t block;
+    uint4 words;
+
+    __device__ __forceinline__ void init(unsigned long long seed, uint32_t sid, uint32_t fr)
+    {
+        key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+        sample_id = sid;
+        frame = fr;
+        block = 0xFFFFFFFFu;
+    }
+    __device__ __forceinline__ float draw(uint32_t i)
+    {
+        const uint32_t b = i >> 2;
+        if (b != block) {
+            words = philox4x32_10(make_uint4(sample_id, frame, b, 0u), key);
+            block = b;
+        }
+        const uint32_t k = i & 3u;
+        const uint32_t w = k == 0 ? words.x : (k == 1 ? words.y : (k == 2 ? words.z : words.w));
+        return u24(w);
+    }
+};
+
+// ---------------------------------------------------------------- hashing
+// MurmurHash3 64-bit finaliser (Appleby).
+__device__ __forceinline__ unsigned long long fmix64(unsigned long long k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+__device__ __forceinline__ uint32_t quant_pos(float p, float o, float h, bool jit, float u)
+{
+    float t = fdiv(fsub(p, o), h);
+    if (jit) t = fadd(t, fsub(u, 0.5f));
+    float f = floorf(t);
+    f = fminf(fmaxf(f, -32767.0f), 32766.0f);
+    return (uint32_t)((int)f + 32768);
+}
+
+__device__ __forceinline__ uint32_t quant_nrm(float a, uint32_t nb, bool jit, float u)
+{
+    float q = fmul(fmul(fadd(a, 1.0f), 0.5f), (float)nb);
+    if (jit) q = fadd(q, fsub(u, 0.5f));
+    float f = floorf(q);
+    f = fminf(fmaxf(f, 0.0f), (float)(nb - 1));
+    return (uint32_t)f;
+}
+
+// 5-d cell key: 16-bit biased x, y, z cells, 8-bit octahedral normal bins
+// (y up). Never equals kEmptyKey (the top byte is at most 254).
+__device__ __forceinline__ unsigned long long cell_key(float px, float py, float pz, float nx, float ny,
+                                                       float nz, const float origin[3], float h,
+                                                       uint32_t nb, bool jit, const float j[5])
+{
+    const uint32_t fx = quant_pos(px, origin[0], h, jit, j[0]);
+    const uint32_t fy = quant_pos(py, origin[1], h, jit, j[1]);
+    const uint32_t fz = quant_pos(pz, origin[2], h, jit, j[2]);
+    const float s = fadd(fadd(fabsf(nx), fabsf(ny)), fabsf(nz));
+    float a = 0.0f, b = 0.0f;
+    if (s > 0.0f) {
+        a = fdiv(nx, s);
+        b = fdiv(nz, s);
+        if (ny < 0.0f) {
+            const float sa = a >= 0.0f ? 1.0f : -1.0f, sb = b >= 0.0f ? 1.0f : -1.0f;
+            const float na = fmul(fsub(1.0f, fabsf(b)), sa);
+            const float nbv = fmul(fsub(1.0f, fabsf(a)), sb);
+            a = na;
+            b = nbv;
+        }
+    }
+    const uint32_t iu = quant_nrm(a, nb, jit, j[3]);
+    const uint32_t iv = quant_nrm(b, nb, jit, j[4]);
+    return (unsigned long long)fx | ((unsigned long long)fy << 16) | ((unsigned long long)fz << 32) |
+           ((unsigned long long)iu << 48) | ((unsigned long long)iv << 56);
+}
+
+// ---------------------------------------------------------------- bounds
+// Unoccluded importance of a node seen from (x, n): power times the receiver
+// and emitter cosine bounds over the node's bounding sphere, over distance^2.
+__device__ __forceinline__ float importance(const NodeRec& r, float x0, float x1, float x2, float n0,
+                                            float n1, float n2)
+{
+    const float cx = fmul(fadd(r.bmin[0], r.bmax[0]), 0.5f);
+    const float cy = fmul(fadd(r.bmin[1], r.bmax[1]), 0.5f);
+    const float cz = fmul(fadd(r.bmin[2], r.bmax[2]), 0.5f);
+    const float dx = fsub(cx, x0), dy = fsub(cy, x1), dz = fsub(cz, x2);
+    const float d2 = fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz));
+    const float ex = fsub(r.bmax[0], r.bmin[0]), ey = fsub(r.bmax[1], r.bmin[1]),
+                ez = fsub(r.bmax[2], r.bmin[2]);
+    const float r2 = fmul(0.25f, fadd(fadd(fmul(ex, ex), fmul(ey, ey)), fmul(ez, ez)));
+    const float phi = r.phi;
+    if (d2 <= r2) return fdiv(phi, fmaxf(r2, 1e-30f));
+    const float inv = fdiv(1.0f, fsqrt(d2));
+    const float sb2 = fdiv(r2, d2);
+    const float cb = fsqrt(fsub(1.0f, sb2));
+    const float sb = fsqrt(sb2);
+    float cg = fmul(fadd(fadd(fmul(n0, dx), fmul(n1, dy)), fmul(n2, dz)), inv);
+    cg = fminf(1.0f, fmaxf(-1.0f, cg));
+    const float sg = fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(cg, cg))));
+    const float brecv = (cg >= cb) ? 1.0f : fmaxf(0.0f, fadd(fmul(cg, cb), fmul(sg, sb)));
+    const float ct = r.cos_t;
+    float bemit;
+    if (ct <= -cb) {
+        bemit = 1.0f;
+    } else {
+        const float st = fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(ct, ct))));
+        const float cphi = fsub(fmul(ct, cb), fmul(st, sb));
+        const float t = fadd(fadd(fmul(r.axis[0], dx), fmul(r.axis[1], dy)), fmul(r.axis[2], dz));
+        float cpsi = fmul(-t, inv);
+        cpsi = fminf(1.0f, fmaxf(-1.0f, cpsi));
+        if (cphi <= cpsi) {
+            bemit = 1.0f;
+        } else {
+            const float spsi = fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(cpsi, cpsi))));
+            const float sphi = fadd(fmul(st, cb), fmul(ct, sb));
+            bemit = fmaxf(0.0f, fadd(fmul(cpsi, cphi), fmul(spsi, sphi)));
+        }
+    }
+    return fdiv(fmul(fmul(phi, brecv), bemit), d2);
+}
+
+// ---------------------------------------------------------------- storage
+template <int P> struct Store;
+template <> struct Store<RLL_PREC_FP32> {
+    using T = float;
+    __device__ __forceinline__ static float load(T v) { return v; }
+    __device__ __forceinline__ static T store(float v) { return v; }
+    __device__ __forceinline__ static uint16_t bits(T) { return 0; }
+};
+template <> struct Store<RLL_PREC_FP16> {
+    using T = __half;
+    __device__ __forceinline__ static float load(T v) { return __half2float(v); }
+    // saturating: values beyond the largest finite half are stored as 65504
+    __device__ __forceinline__ static T store(float v)
+    {
+        return __float2half_rn(fminf(fmaxf(v, -65504.0f), 65504.0f));
+    }
+    __device__ __forceinline__ static uint16_t bits(T v) { return __half_as_ushort(v); }
+    __device__ __forceinline__ static T from_bits(uint16_t b) { return __ushort_as_half(b); }
+};
+template <> struct Store<RLL_PREC_BF16> {
+    using T = __nv_bfloat16;
+    __device__ __forceinline__ static float load(T v) { return __bfloat162float(v); }
+    __device__ __forceinline__ static T store(float v)
+    {
+        const float mx = 3.3895313892515355e38f;  // largest finite bfloat16
+        return __float2bfloat16_rn(fminf(fmaxf(v, -mx), mx));
+    }
+    __device__ __forceinline__ static uint16_t bits(T v) { return __bfloat16_as_ushort(v); }
+    __device__ __forceinline__ static T from_bits(uint16_t b) { return __ushort_as_bfloat16(b); }
+};
+
+// ordered-integer image of a float for atomicMin / atomicMax
+__device__ __forceinline__ int float_to_ordered(float f)
+{
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float ordered_to_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace rll

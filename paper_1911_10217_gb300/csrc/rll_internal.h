@@ -1,0 +1,100 @@
+// Host-side state behind the opaque handles of rll.h, and the launchers each
+// translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rll.h"
+
+namespace rll {
+struct NodeRec;
+struct LightRec;
+}  // namespace rll
+
+struct rll_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t* d_status = nullptr;   // device status bits (RLL_E_* >= RLL_E_TABLE_FULL)
+    std::string err;
+    // growable library-owned scratch (sort buffers, staging)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // staging for rll_render_pass_host
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+struct rll_tree {
+    int device = 0;
+    int64_t n = 0;
+    rll::NodeRec* nodes = nullptr;   // [2n-1] every node
+    rll::NodeRec* pairs = nullptr;   // [2(n-1)] children of internal i at 2i, 2i+1
+    rll::LightRec* lights = nullptr; // [n] sorted lights
+    uint32_t* perm = nullptr;        // [n] sorted -> input index
+    int32_t* left = nullptr;         // [n-1]
+    int32_t* right = nullptr;        // [n-1]
+    int32_t* parent = nullptr;       // [2n-1]
+    float* light_cdf = nullptr;      // [n] inclusive prefix of leaf power (energy sampler)
+};
+
+struct rll_grid {
+    int device = 0;
+    rll_grid_params p{};
+    uint32_t H = 0, M = 0, m = 0;
+    int64_t n_lights = 0;
+    unsigned long long* keys = nullptr;  // [H]
+    uint32_t* cut = nullptr;             // [H*M]
+    void* Q = nullptr;                   // [H*M] table precision
+    void* C = nullptr;                   // [H*M] table precision
+    uint32_t* def_cut = nullptr;         // [m]
+    void* def_Q = nullptr;               // [m]
+    void* def_C = nullptr;               // [m]
+    uint32_t* touched = nullptr;         // [H] cells touched by the last learn_update
+    uint32_t* touched_start = nullptr;   // [H] first sorted record of each touched cell
+    uint32_t* n_touched = nullptr;       // [1]
+};
+
+namespace rll {
+
+// status helpers (api.cu)
+int fail(rll_ctx* ctx, int code, const std::string& msg);
+int check_cuda(rll_ctx* ctx, cudaError_t e, const char* what);
+void* ws_get(rll_ctx* ctx, size_t bytes);  // nullptr on failure (error recorded)
+
+// ---- sort.cu
+// Scratch bytes needed by radix_sort_pairs for n items.
+size_t radix_sort_scratch_bytes(int64_t n);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of
+// min(key, clamp). Input arrays are not modified; the sorted arrays are
+// written to scratch and returned through kout / vout.
+cudaError_t radix_sort_pairs(cudaStream_t s, const uint32_t* kin, const uint32_t* vin, int64_t n,
+                             int bits, uint32_t clamp, void* scratch, uint32_t** kout,
+                             uint32_t** vout);
+// Inclusive prefix sum of n floats (n <= 2^24) into out; scratch >= 4 * 4096 bytes.
+cudaError_t inclusive_scan_f32(cudaStream_t s, const float* in, float* out, int64_t n, void* scratch);
+
+// ---- tree.cu
+int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, rll_tree* t);
+int tree_update_emission(rll_ctx* ctx, rll_tree* t, const float* emission);
+
+// ---- learn.cu
+int grid_init(rll_ctx* ctx, rll_grid* g);
+int grid_to_float(rll_ctx* ctx, const rll_grid* g, float* q_out, float* c_out);   // device out
+int grid_from_float(rll_ctx* ctx, rll_grid* g, const float* q_in, const float* c_in); // device in
+int grid_mark_occupied(rll_ctx* ctx, rll_grid* g);  // touched list := every occupied slot
+int learn_update(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n);
+int split_collapse(rll_ctx* ctx, rll_grid* g, const rll_tree* t);
+
+// ---- sample.cu
+int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* pos, const float* nrm,
+                     const float* albedo, int64_t n_points, const float* boxes, int n_boxes,
+                     uint64_t seed, uint32_t frame, int spp, float* rgb, uint32_t* rec_key,
+                     float* rec_val, const rll_sample_debug* dbg);
+int sample_power(rll_ctx* ctx, const rll_tree* t, const float* pos, const float* nrm,
+                 const float* albedo, int64_t n_points, const float* boxes, int n_boxes, uint64_t seed,
+                 uint32_t frame, int spp, float* rgb, int32_t* light_out);
+
+}  // namespace rll

@@ -1,0 +1,400 @@
+// Render-time sampling (Section 3, "Main contribution"; Section 3.1: "sampling
+// the cdf is performed by a standard binary search").
+//
+// One thread per shading point (spp samples in a loop); occluder boxes staged
+// in shared memory once per block. Per sample:
+//   hash lookup / lazy insert of the (jittered) 5-d cell   (64-bit CAS)
+//   binary search of the cell's C for the cluster s        (log2 m loads of one row)
+//   in-cluster choice: bound-driven descent (two child records = one 128-byte
+//   line per level) or a uniform pick over the cluster's lights
+//   uniform point on the light triangle, contribution, shadow segment vs boxes
+//   estimate accumulation and one learning record (key, |c|).
+// The decisions (cell, branch, visibility) are exact binary32 formulas; the
+// cdf and descent comparisons u * total < c are made exactly with one fma.
+#include <cuda_runtime.h>
+
+#include "rll_device.cuh"
+#include "rll_internal.h"
+
+namespace rll {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct SampleArgs {
+    const float* pos;
+    const float* nrm;
+    const float* albedo;
+    int64_t n_points;
+    const float* boxes;
+    int n_boxes;
+    unsigned long long* keys;
+    const uint32_t* cut;
+    const void* C;
+    uint32_t H, M, m;
+    const uint32_t* def_cut;
+    const void* def_C;
+    float origin[3];
+    float h;
+    uint32_t nb;
+    uint32_t jitter;
+    uint32_t reward_mode;
+    const NodeRec* pairs;
+    const NodeRec* nodes;
+    const LightRec* lights;
+    const float* light_cdf;
+    int64_t n_lights;
+    unsigned long long seed;
+    uint32_t frame;
+    int spp;
+    float* rgb;
+    uint32_t* rec_key;
+    float* rec_val;
+    int32_t* dbg_light;
+    float* dbg_pcut;
+    float* dbg_pin;
+    uint32_t* status;
+};
+
+__device__ __forceinline__ int64_t lookup_insert(unsigned long long* keys, uint32_t H, unsigned long long key)
+{
+    const unsigned long long h = fmix64(key);
+    for (int i = 0; i < kMaxProbes; ++i) {
+        const uint32_t slot = (uint32_t)((h + (unsigned long long)i) & (unsigned long long)(H - 1));
+        const unsigned long long k = __ldcg(keys + slot);
+        if (k == key) return slot;
+        if (k == kEmptyKey) {
+            const unsigned long long old = atomicCAS(keys + slot, kEmptyKey, key);
+            if (old == kEmptyKey || old == key) return slot;
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ NodeRec load_node(const NodeRec* p)
+{
+    NodeRec r;
+    const float4* s = reinterpret_cast<const float4*>(p);
+    float4* d = reinterpret_cast<float4*>(&r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = __ldg(s + k);
+    return r;
+}
+
+__device__ __forceinline__ LightRec load_light(const LightRec* p)
+{
+    LightRec r;
+    const float4* s = reinterpret_cast<const float4*>(p);
+    float4* d = reinterpret_cast<float4*>(&r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = __ldg(s + k);
+    return r;
+}
+
+struct ShadeOut {
+    float est[3];
+    float reward;
+};
+
+// light point, shadow test, contribution (x, n: shading point and normal)
+__device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1, float x2, float n0, float n1,
+                                          float n2, float albedo, float pdf_sel, float p_in, SampleStream& rs,
+                                          const float* s_box, int n_boxes, uint32_t reward_mode)
+{
+    const float ua = rs.draw(kDrawTriA), ub = rs.draw(kDrawTriB);
+    const float su = fsqrt(ua);
+    const float b0 = fsub(1.0f, su), b1 = fmul(ub, su), b2 = fsub(su, b1);
+    const float y0 = fadd(fadd(fmul(b0, L.v0[0]), fmul(b1, L.v1[0])), fmul(b2, L.v2[0]));
+    const float y1 = fadd(fadd(fmul(b0, L.v0[1]), fmul(b1, L.v1[1])), fmul(b2, L.v2[1]));
+    const float y2 = fadd(fadd(fmul(b0, L.v0[2]), fmul(b1, L.v1[2])), fmul(b2, L.v2[2]));
+    const float o0 = fadd(x0, fmul(kShadowOffset, n0));
+    const float o1 = fadd(x1, fmul(kShadowOffset, n1));
+    const float o2 = fadd(x2, fmul(kShadowOffset, n2));
+    const float i0 = fdiv(1.0f, fsub(y0, o0)), i1 = fdiv(1.0f, fsub(y1, o1)), i2 = fdiv(1.0f, fsub(y2, o2));
+    const float q0 = -fmul(o0, i0), q1 = -fmul(o1, i1), q2 = -fmul(o2, i2);
+    bool occluded = false;
+    for (int b = 0; b < n_boxes && !occluded; ++b) {
+        const float* bx = s_box + 6 * b;
+        const float ta0 = __fmaf_rn(bx[0], i0, q0), tb0 = __fmaf_rn(bx[3], i0, q0);
+        const float ta1 = __fmaf_rn(bx[1], i1, q1), tb1 = __fmaf_rn(bx[4], i1, q1);
+        const float ta2 = __fmaf_rn(bx[2], i2, q2), tb2 = __fmaf_rn(bx[5], i2, q2);
+        float tn = fmaxf(0.0f, fminf(ta0, tb0));
+        float tf = fminf(kShadowTmax, fmaxf(ta0, tb0));
+        tn = fmaxf(tn, fminf(ta1, tb1));
+        tf = fminf(tf, fmaxf(ta1, tb1));
+        tn = fmaxf(tn, fminf(ta2, tb2));
+        tf = fminf(tf, fmaxf(ta2, tb2));
+        occluded = tn < tf;
+    }
+    ShadeOut o;
+    const float wx = y0 - x0, wy = y1 - x1, wz = y2 - x2;
+    const float d2 = wx * wx + wy * wy + wz * wz;
+    const float inv_d = rsqrtf(d2);
+    const float cx = fmaxf(0.0f, (n0 * wx + n1 * wy + n2 * wz) * inv_d);
+    const float cl = fmaxf(0.0f, -(L.n[0] * wx + L.n[1] * wy + L.n[2] * wz) * inv_d);
+    const float geo = occluded ? 0.0f : cx * cl / d2;
+    const float f = albedo * 0.31830988618379067f;
+    const float c0 = f * L.le[0] * geo, c1 = f * L.le[1] * geo, c2 = f * L.le[2] * geo;
+    const float w = L.area / pdf_sel;
+    o.est[0] = c0 * w;
+    o.est[1] = c1 * w;
+    o.est[2] = c2 * w;
+    const float lum = 0.2126f * c0 + 0.7152f * c1 + 0.0722f * c2;
+    o.reward = reward_mode == RLL_REWARD_CLUSTER ? lum * L.area / p_in : lum * L.area;
+    return o;
+}
+
+template <int P, int MODE, bool DBG>
+__global__ void __launch_bounds__(kThreads) k_sample(SampleArgs a)
+{
+    using T = typename Store<P>::T;
+    extern __shared__ float s_box[];
+    for (int i = threadIdx.x; i < a.n_boxes * 6; i += blockDim.x) s_box[i] = a.boxes[i];
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n_points) return;
+    const int64_t np = a.n_points;
+    const float x0 = a.pos[p], x1 = a.pos[np + p], x2 = a.pos[2 * np + p];
+    const float n0 = a.nrm[p], n1 = a.nrm[np + p], n2 = a.nrm[2 * np + p];
+    const float alb = a.albedo[p];
+    const T* Ctab = static_cast<const T*>(a.C);
+    const T* Cdef = static_cast<const T*>(a.def_C);
+    const uint32_t m = a.m;
+    const int64_t nl1 = a.n_lights - 1;
+    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
+    for (int j = 0; j < a.spp; ++j) {
+        const uint32_t sid = (uint32_t)(p * a.spp + j);
+        SampleStream rs;
+        rs.init(a.seed, sid, a.frame);
+        float jit[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (a.jitter) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) jit[k] = rs.draw(kDrawJit + k);
+        }
+        const unsigned long long key =
+            cell_key(x0, x1, x2, n0, n1, n2, a.origin, a.h, a.nb, a.jitter != 0, jit);
+        const int64_t slot = lookup_insert(a.keys, a.H, key);
+        const T* crow;
+        const uint32_t* cutrow;
+        if (slot >= 0) {
+            crow = Ctab + slot * a.M;
+            cutrow = a.cut + slot * a.M;
+        } else {
+            crow = Cdef;
+            cutrow = a.def_cut;
+            atomicOr(a.status, (uint32_t)RLL_E_TABLE_FULL);
+        }
+        // cluster: first s with C(s) > u * C(m-1)
+        const float u = rs.draw(kDrawCut);
+        const float total = Store<P>::load(crow[m - 1]);
+        uint32_t lo = 0, hi = m - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__fmaf_rn(-u, total, Store<P>::load(crow[mid])) > 0.0f) hi = mid;
+            else lo = mid + 1;
+        }
+        const uint32_t s = lo;
+        const float cprev = s > 0 ? Store<P>::load(crow[s - 1]) : 0.0f;
+        const float p_cut = (Store<P>::load(crow[s]) - cprev) / total;
+        uint32_t node = cutrow[s];
+        if ((int64_t)node >= 2 * a.n_lights - 1) {  // corrupt cut row: flag, sample from the root
+            atomicOr(a.status, (uint32_t)RLL_E_DEVICE);
+            node = 0;
+        }
+        float p_in = 1.0f;
+        int64_t light;
+        if (MODE == RLL_MODE_UNIFORM) {
+            const NodeRec& r = a.nodes[node];
+            const uint32_t w = r.end - r.begin;
+            const uint32_t u24v = (uint32_t)(rs.draw(kDrawUniform) * 16777216.0f);
+            light = (int64_t)r.begin + (int64_t)(((unsigned long long)u24v * w) >> 24);
+            p_in = 1.0f / (float)w;
+        } else {
+            uint32_t level = 0;
+            while ((int64_t)node < nl1) {
+                const NodeRec L = load_node(a.pairs + 2 * (int64_t)node);
+                const NodeRec R = load_node(a.pairs + 2 * (int64_t)node + 1);
+                const float il = importance(L, x0, x1, x2, n0, n1, n2);
+                const float ir = importance(R, x0, x1, x2, n0, n1, n2);
+                float wl = il, wr = ir;
+                float ssum = fadd(il, ir);
+                if (!(ssum > 0.0f)) {
+                    wl = L.phi;
+                    wr = R.phi;
+                    ssum = fadd(wl, wr);
+                }
+                const float ud = rs.draw(kDrawDescent + level);
+                ++level;
+                bool left;
+                float ratio;
+                if (ssum > 0.0f) {
+                    left = __fmaf_rn(ud, ssum, -wl) < 0.0f;
+                    ratio = (left ? wl : wr) / (wl + wr);
+                } else {
+                    left = ud < 0.5f;
+                    ratio = 0.5f;
+                }
+                p_in *= ratio;
+                node = left ? L.id : R.id;
+            }
+            light = (int64_t)node - nl1;
+        }
+        const LightRec Lr = load_light(a.lights + light);
+        const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, p_cut * p_in, p_in, rs, s_box, a.n_boxes,
+                                 a.reward_mode);
+        acc0 += o.est[0];
+        acc1 += o.est[1];
+        acc2 += o.est[2];
+        if (a.rec_key) {
+            a.rec_key[sid] = slot >= 0 ? (uint32_t)slot * a.M + s : kInvalidRecord;
+            a.rec_val[sid] = o.reward;
+        }
+        if (DBG) {
+            if (a.dbg_light) a.dbg_light[sid] = (int32_t)light;
+            if (a.dbg_pcut) a.dbg_pcut[sid] = p_cut;
+            if (a.dbg_pin) a.dbg_pin[sid] = p_in;
+        }
+    }
+    const float inv_spp = 1.0f / (float)a.spp;
+    a.rgb[p] = acc0 * inv_spp;
+    a.rgb[np + p] = acc1 * inv_spp;
+    a.rgb[2 * np + p] = acc2 * inv_spp;
+}
+
+// Energy-based baseline (Section 4): inversion of the cdf of leaf power.
+__global__ void __launch_bounds__(kThreads) k_sample_power(SampleArgs a, int32_t* light_out)
+{
+    extern __shared__ float s_box[];
+    for (int i = threadIdx.x; i < a.n_boxes * 6; i += blockDim.x) s_box[i] = a.boxes[i];
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n_points) return;
+    const int64_t np = a.n_points;
+    const float x0 = a.pos[p], x1 = a.pos[np + p], x2 = a.pos[2 * np + p];
+    const float n0 = a.nrm[p], n1 = a.nrm[np + p], n2 = a.nrm[2 * np + p];
+    const float alb = a.albedo[p];
+    const int64_t nl = a.n_lights;
+    const float total = a.light_cdf[nl - 1];
+    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
+    for (int j = 0; j < a.spp; ++j) {
+        const uint32_t sid = (uint32_t)(p * a.spp + j);
+        SampleStream rs;
+        rs.init(a.seed, sid, a.frame);
+        const float u = rs.draw(kDrawCut);
+        int64_t lo = 0, hi = nl - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__fmaf_rn(-u, total, a.light_cdf[mid]) > 0.0f) hi = mid;
+            else lo = mid + 1;
+        }
+        const float pl = a.nodes[nl - 1 + lo].phi / total;
+        const LightRec Lr = load_light(a.lights + lo);
+        const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, pl, 1.0f, rs, s_box, a.n_boxes, 0);
+        acc0 += o.est[0];
+        acc1 += o.est[1];
+        acc2 += o.est[2];
+        if (light_out) light_out[sid] = (int32_t)lo;
+    }
+    const float inv_spp = 1.0f / (float)a.spp;
+    a.rgb[p] = acc0 * inv_spp;
+    a.rgb[np + p] = acc1 * inv_spp;
+    a.rgb[2 * np + p] = acc2 * inv_spp;
+}
+
+template <int P, int MODE, bool DBG>
+cudaError_t launch(const SampleArgs& a, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((a.n_points + kThreads - 1) / kThreads);
+    k_sample<P, MODE, DBG><<<blocks, kThreads, sizeof(float) * 6 * a.n_boxes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_p(const SampleArgs& a, int mode, bool dbg, cudaStream_t s)
+{
+    if (mode == RLL_MODE_UNIFORM)
+        return dbg ? launch<P, RLL_MODE_UNIFORM, true>(a, s) : launch<P, RLL_MODE_UNIFORM, false>(a, s);
+    return dbg ? launch<P, RLL_MODE_DESCENT, true>(a, s) : launch<P, RLL_MODE_DESCENT, false>(a, s);
+}
+
+}  // namespace
+
+int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* pos, const float* nrm,
+                     const float* albedo, int64_t n_points, const float* boxes, int n_boxes, uint64_t seed,
+                     uint32_t frame, int spp, float* rgb, uint32_t* rec_key, float* rec_val,
+                     const rll_sample_debug* dbg)
+{
+    if (n_points == 0) return RLL_OK;
+    SampleArgs a{};
+    a.pos = pos;
+    a.nrm = nrm;
+    a.albedo = albedo;
+    a.n_points = n_points;
+    a.boxes = boxes;
+    a.n_boxes = n_boxes;
+    a.keys = g->keys;
+    a.cut = g->cut;
+    a.C = g->C;
+    a.H = g->H;
+    a.M = g->M;
+    a.m = g->m;
+    a.def_cut = g->def_cut;
+    a.def_C = g->def_C;
+    for (int k = 0; k < 3; ++k) a.origin[k] = g->p.origin[k];
+    a.h = g->p.cell_size;
+    a.nb = g->p.normal_bins;
+    a.jitter = g->p.jitter;
+    a.reward_mode = g->p.reward_mode;
+    a.pairs = t->pairs;
+    a.nodes = t->nodes;
+    a.lights = t->lights;
+    a.light_cdf = t->light_cdf;
+    a.n_lights = t->n;
+    a.seed = seed;
+    a.frame = frame;
+    a.spp = spp;
+    a.rgb = rgb;
+    a.rec_key = rec_key;
+    a.rec_val = rec_val;
+    a.status = ctx->d_status;
+    const bool use_dbg = dbg && (dbg->light || dbg->p_cut || dbg->p_in);
+    if (use_dbg) {
+        a.dbg_light = dbg->light;
+        a.dbg_pcut = dbg->p_cut;
+        a.dbg_pin = dbg->p_in;
+    }
+    cudaError_t e;
+    switch (g->p.precision) {
+    case RLL_PREC_FP16: e = launch_p<RLL_PREC_FP16>(a, g->p.in_cluster_mode, use_dbg, ctx->stream); break;
+    case RLL_PREC_BF16: e = launch_p<RLL_PREC_BF16>(a, g->p.in_cluster_mode, use_dbg, ctx->stream); break;
+    default: e = launch_p<RLL_PREC_FP32>(a, g->p.in_cluster_mode, use_dbg, ctx->stream);
+    }
+    return check_cuda(ctx, e, "sample_and_shade");
+}
+
+int sample_power(rll_ctx* ctx, const rll_tree* t, const float* pos, const float* nrm, const float* albedo,
+                 int64_t n_points, const float* boxes, int n_boxes, uint64_t seed, uint32_t frame, int spp,
+                 float* rgb, int32_t* light_out)
+{
+    if (n_points == 0) return RLL_OK;
+    SampleArgs a{};
+    a.pos = pos;
+    a.nrm = nrm;
+    a.albedo = albedo;
+    a.n_points = n_points;
+    a.boxes = boxes;
+    a.n_boxes = n_boxes;
+    a.nodes = t->nodes;
+    a.lights = t->lights;
+    a.light_cdf = t->light_cdf;
+    a.n_lights = t->n;
+    a.seed = seed;
+    a.frame = frame;
+    a.spp = spp;
+    a.rgb = rgb;
+    const unsigned blocks = (unsigned)((n_points + kThreads - 1) / kThreads);
+    k_sample_power<<<blocks, kThreads, sizeof(float) * 6 * n_boxes, ctx->stream>>>(a, light_out);
+    return check_cuda(ctx, cudaGetLastError(), "sample_power");
+}
+
+}  // namespace rll

@@ -1,0 +1,329 @@
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs and an fp32
+// inclusive scan, both hand-written for sm_103a.
+//
+// Radix pass (8-bit digit, tiles of 2048 items = 256 threads x 8):
+//   1. hist:    per-tile digit histogram (shared-memory atomics) -> counts[d][tile],
+//               per-digit totals (global atomics).
+//   2. scan:    one block per digit, exclusive scan of counts[d][*] over tiles.
+//   3. scatter: each tile ranks its items stably (warp match_any + per-warp
+//               digit counts, in index order), reorders them in shared memory by
+//               digit and writes each digit's run contiguously.
+// Keys are ranked by min(key, clamp), so out-of-range keys sort last.
+#include <cuda_runtime.h>
+
+#include "rll_device.cuh"
+#include "rll_internal.h"
+
+namespace rll {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;
+constexpr int kDigits = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t clamp, int shift)
+{
+    return (min(key, clamp) >> shift) & 0xFFu;
+}
+
+__global__ void __launch_bounds__(kThreads) k_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                   uint32_t clamp, uint32_t* __restrict__ counts,
+                                                   uint32_t* __restrict__ totals, int64_t tiles)
+{
+    __shared__ uint32_t h[kDigits];
+    const int t = threadIdx.x;
+    h[t] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t i = base + j * kThreads + t;
+        if (i < n) atomicAdd(&h[digit_of(keys[i], clamp, shift)], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)t * tiles + blockIdx.x] = h[t];
+    if (h[t]) atomicAdd(&totals[t], h[t]);
+}
+
+// exclusive scan of v over a 1024-thread block; returns the block total in *total
+__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t* s_warp, uint32_t* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t before = warp > 0 ? s_warp[warp - 1] : 0u;
+    *total = s_warp[31];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* __restrict__ counts, int64_t tiles)
+{
+    __shared__ uint32_t s_warp[32];
+    uint32_t* row = counts + (int64_t)blockIdx.x * tiles;
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < tiles; b += 1024) {
+        const int64_t i = b + threadIdx.x;
+        const uint32_t v = i < tiles ? row[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan_1024(v, s_warp, &tot);
+        if (i < tiles) row[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t* __restrict__ kin,
+                                                      const uint32_t* __restrict__ vin,
+                                                      uint32_t* __restrict__ kout,
+                                                      uint32_t* __restrict__ vout, int64_t n, int shift,
+                                                      uint32_t clamp, const uint32_t* __restrict__ counts,
+                                                      const uint32_t* __restrict__ totals, int64_t tiles)
+{
+    __shared__ uint32_t s_base[kDigits];
+    __shared__ uint32_t s_start[kDigits];
+    __shared__ uint32_t s_cnt[kDigits];
+    __shared__ uint32_t s_run[kDigits];
+    __shared__ uint32_t s_wc[kWarps][kDigits];
+    __shared__ uint32_t s_k[kTile];
+    __shared__ uint32_t s_v[kTile];
+    __shared__ uint32_t s_scan[kWarps];
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    uint32_t k[kItems], v[kItems], d[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t i = base + j * kThreads + t;
+        if (i < n) {
+            k[j] = kin[i];
+            v[j] = vin[i];
+            d[j] = digit_of(k[j], clamp, shift);
+        } else {
+            k[j] = 0xFFFFFFFFu;
+            v[j] = 0u;
+            d[j] = kDigits - 1;  // padding ranks after every real item of the tile
+        }
+    }
+    s_cnt[t] = 0;
+    s_run[t] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kItems; ++j)
+        if (base + j * kThreads + t < n) atomicAdd(&s_cnt[d[j]], 1u);
+    __syncthreads();
+    // tile-local digit starts: exclusive scan of s_cnt over 256 threads
+    {
+        const uint32_t c = s_cnt[t];
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_scan[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += s_scan[w];
+        s_start[t] = before + x - c;
+    }
+    // global digit base: exclusive scan of totals + this tile's offset
+    {
+        const uint32_t c = totals[t];
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        __syncthreads();
+        if (lane == 31) s_scan[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += s_scan[w];
+        s_base[t] = before + x - c + counts[(int64_t)t * tiles + blockIdx.x];
+    }
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        for (int w = 0; w < kWarps; ++w) s_wc[w][t] = 0;
+        __syncthreads();
+        const uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
+        const uint32_t rank_w = __popc(peers & lt);
+        if (rank_w == 0) s_wc[warp][d[j]] = __popc(peers);
+        __syncthreads();
+        uint32_t off = s_run[d[j]] + rank_w;
+        for (int w = 0; w < warp; ++w) off += s_wc[w][d[j]];
+        const uint32_t pos = s_start[d[j]] + off;
+        s_k[pos] = k[j];
+        s_v[pos] = v[j];
+        __syncthreads();
+        uint32_t add = 0;
+        for (int w = 0; w < kWarps; ++w) add += s_wc[w][t];
+        s_run[t] += add;
+    }
+    __syncthreads();
+    const int64_t valid = min((int64_t)kTile, n - base);
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int idx = j * kThreads + t;
+        if (idx < valid) {
+            const uint32_t key = s_k[idx];
+            const uint32_t dg = digit_of(key, clamp, shift);
+            const uint32_t dst = s_base[dg] + (uint32_t)idx - s_start[dg];
+            kout[dst] = key;
+            vout[dst] = s_v[idx];
+        }
+    }
+}
+
+__host__ __device__ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------- float scan
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+__device__ __forceinline__ float block_incl_scan_f32(float v, float* s_warp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        float w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const float before = warp > 0 ? s_warp[warp - 1] : 0.0f;
+    __syncthreads();
+    return before + x;
+}
+
+// each block scans kScanBlock consecutive items (kScanItems per thread,
+// thread-contiguous); block totals to sums[blockIdx]
+__global__ void __launch_bounds__(kScanThreads) k_scan_f32(const float* __restrict__ in, float* __restrict__ out,
+                                                           int64_t n, float* __restrict__ sums)
+{
+    __shared__ float s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+    float v[kScanItems];
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = base + j < n ? in[base + j] : 0.0f;
+        acc += v[j];
+        v[j] = acc;
+    }
+    const float incl = block_incl_scan_f32(acc, s_warp);
+    const float before = incl - acc;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (base + j < n) out[base + j] = before + v[j];
+    if (sums && threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = incl;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(float* __restrict__ out, int64_t n,
+                                                           const float* __restrict__ sums)
+{
+    if (blockIdx.x == 0) return;
+    const float add = sums[blockIdx.x - 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (base + j < n) out[base + j] += add;
+}
+
+}  // namespace
+
+size_t radix_sort_scratch_bytes(int64_t n)
+{
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    return 4 * align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)) +
+           align256(sizeof(uint32_t) * kDigits * (size_t)(tiles > 0 ? tiles : 1)) +
+           align256(sizeof(uint32_t) * kDigits);
+}
+
+cudaError_t radix_sort_pairs(cudaStream_t s, const uint32_t* kin, const uint32_t* vin, int64_t n, int bits,
+                             uint32_t clamp, void* scratch, uint32_t** kout, uint32_t** vout)
+{
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    char* p = (char*)scratch;
+    const size_t nb = align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    uint32_t* ka = (uint32_t*)p; p += nb;
+    uint32_t* va = (uint32_t*)p; p += nb;
+    uint32_t* kb = (uint32_t*)p; p += nb;
+    uint32_t* vb = (uint32_t*)p; p += nb;
+    uint32_t* counts = (uint32_t*)p; p += align256(sizeof(uint32_t) * kDigits * (size_t)(tiles > 0 ? tiles : 1));
+    uint32_t* totals = (uint32_t*)p;
+    const uint32_t* ck = kin;
+    const uint32_t* cv = vin;
+    uint32_t* dk = ka;
+    uint32_t* dv = va;
+    if (n <= 0) {
+        *kout = ka;
+        *vout = va;
+        return cudaSuccess;
+    }
+    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        cudaError_t e = cudaMemsetAsync(totals, 0, sizeof(uint32_t) * kDigits, s);
+        if (e != cudaSuccess) return e;
+        k_hist<<<(unsigned)tiles, kThreads, 0, s>>>(ck, n, shift, clamp, counts, totals, tiles);
+        k_scan_tiles<<<kDigits, 1024, 0, s>>>(counts, tiles);
+        k_scatter<<<(unsigned)tiles, kThreads, 0, s>>>(ck, cv, dk, dv, n, shift, clamp, counts, totals, tiles);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        ck = dk;
+        cv = dv;
+        dk = (dk == ka) ? kb : ka;
+        dv = (dv == va) ? vb : va;
+    }
+    *kout = const_cast<uint32_t*>(ck);
+    *vout = const_cast<uint32_t*>(cv);
+    return cudaSuccess;
+}
+
+cudaError_t inclusive_scan_f32(cudaStream_t s, const float* in, float* out, int64_t n, void* scratch)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = (n + kScanBlock - 1) / kScanBlock;
+    if (blocks > kScanBlock) return cudaErrorInvalidValue;
+    float* sums = (float*)scratch;
+    k_scan_f32<<<(unsigned)blocks, kScanThreads, 0, s>>>(in, out, n, blocks > 1 ? sums : nullptr);
+    if (blocks > 1) {
+        k_scan_f32<<<1, kScanThreads, 0, s>>>(sums, sums, blocks, nullptr);
+        k_scan_add<<<(unsigned)blocks, kScanThreads, 0, s>>>(out, n, sums);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rll

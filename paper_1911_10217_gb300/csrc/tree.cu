@@ -1,0 +1,363 @@
+// Light tree build (Section 3: sort all lights and build one binary tree over
+// them; Section 3.1: an LBVH over the 3-d light positions).
+//
+//   centroids + scene box -> 30-bit Morton codes -> stable radix sort
+//   (ties by input index) -> binary radix tree over (code << 32 | index)
+//   (Karras, HPG 2012: one thread per internal node, no recursion) ->
+//   leaf records -> bottom-up bounds (atomic arrival counter per node, the
+//   second child to arrive finishes its parent) -> cone axis -> cone cosine
+//   minimum over each node's lights (one thread per light walks to the root)
+//   -> child-pair records for the descent -> prefix sum of leaf power.
+#include <cuda_runtime.h>
+
+#include "rll_device.cuh"
+#include "rll_internal.h"
+
+namespace rll {
+namespace {
+
+constexpr int kBlock = 256;
+
+inline unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+__global__ void k_bbox_init(int* bbox)
+{
+    if (threadIdx.x < 3) bbox[threadIdx.x] = float_to_ordered(INFINITY);
+    else if (threadIdx.x < 6) bbox[threadIdx.x] = float_to_ordered(-INFINITY);
+}
+
+__device__ __forceinline__ float centroid(const float* v, int k)
+{
+    return fdiv(fadd(fadd(v[k], v[3 + k]), v[6 + k]), 3.0f);
+}
+
+__global__ void k_centroid_bbox(const float* __restrict__ tri, int64_t n, int* __restrict__ bbox)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (i < n) {
+        const float* v = tri + i * 9;
+        for (int k = 0; k < 3; ++k) {
+            const float c = centroid(v, k);
+            lo[k] = c;
+            hi[k] = c;
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&bbox[k], float_to_ordered(lo[k]));
+            atomicMax(&bbox[3 + k], float_to_ordered(hi[k]));
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v)
+{
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_morton(const float* __restrict__ tri, int64_t n, const int* __restrict__ bbox,
+                         uint32_t* __restrict__ codes, uint32_t* __restrict__ idx)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* v = tri + i * 9;
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+        const float lo = ordered_to_float(bbox[k]), hi = ordered_to_float(bbox[3 + k]);
+        const float ext = fsub(hi, lo);
+        const float u = ext > 0.0f ? fdiv(fsub(centroid(v, k), lo), ext) : 0.0f;
+        float f = floorf(fmul(u, 1024.0f));
+        f = fminf(fmaxf(f, 0.0f), 1023.0f);
+        q[k] = (uint32_t)f;
+    }
+    codes[i] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    idx[i] = (uint32_t)i;
+}
+
+__device__ __forceinline__ int delta(const uint32_t* codes, const uint32_t* idx, int64_t n, int64_t i, int64_t j)
+{
+    if (j < 0 || j >= n) return -1;
+    const unsigned long long a = ((unsigned long long)codes[i] << 32) | idx[i];
+    const unsigned long long b = ((unsigned long long)codes[j] << 32) | idx[j];
+    return __clzll((long long)(a ^ b));
+}
+
+__global__ void k_karras(const uint32_t* __restrict__ codes, const uint32_t* __restrict__ idx, int64_t n,
+                         int32_t* __restrict__ left, int32_t* __restrict__ right, int32_t* __restrict__ parent,
+                         uint32_t* __restrict__ begin, uint32_t* __restrict__ end)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (delta(codes, idx, n, i, i + 1) - delta(codes, idx, n, i, i - 1)) > 0 ? 1 : -1;
+    const int dmin = delta(codes, idx, n, i, i - d);
+    int64_t lmax = 2;
+    while (delta(codes, idx, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(codes, idx, n, i, i + (l + t) * d) > dmin) l += t;
+    const int64_t j = i + l * d;
+    const int dnode = delta(codes, idx, n, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(codes, idx, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int64_t g = i + s * d + (d < 0 ? -1 : 0);
+    const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    const int32_t a = (lo == g) ? (int32_t)(n - 1 + g) : (int32_t)g;
+    const int32_t c = (hi == g + 1) ? (int32_t)(n - 1 + g + 1) : (int32_t)(g + 1);
+    left[i] = a;
+    right[i] = c;
+    parent[a] = (int32_t)i;
+    parent[c] = (int32_t)i;
+    begin[i] = (uint32_t)lo;
+    end[i] = (uint32_t)(hi + 1);
+}
+
+__device__ __forceinline__ void cross32(const float* v, float cr[3], float* len)
+{
+    const float e1x = fsub(v[3], v[0]), e1y = fsub(v[4], v[1]), e1z = fsub(v[5], v[2]);
+    const float e2x = fsub(v[6], v[0]), e2y = fsub(v[7], v[1]), e2z = fsub(v[8], v[2]);
+    cr[0] = fsub(fmul(e1y, e2z), fmul(e1z, e2y));
+    cr[1] = fsub(fmul(e1z, e2x), fmul(e1x, e2z));
+    cr[2] = fsub(fmul(e1x, e2y), fmul(e1y, e2x));
+    *len = fsqrt(fadd(fadd(fmul(cr[0], cr[0]), fmul(cr[1], cr[1])), fmul(cr[2], cr[2])));
+}
+
+__global__ void k_leaves(const float* __restrict__ tri, const float* __restrict__ emis, int64_t n,
+                         const uint32_t* __restrict__ sorted_idx, uint32_t* __restrict__ perm,
+                         LightRec* __restrict__ lights, NodeRec* __restrict__ nodes,
+                         float* __restrict__ axis_sum)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const uint32_t i = sorted_idx[l];
+    perm[l] = i;
+    const float* v = tri + (int64_t)i * 9;
+    const float* le = emis + (int64_t)i * 3;
+    float cr[3], len;
+    cross32(v, cr, &len);
+    const float area = fmul(0.5f, len);
+    LightRec L;
+    NodeRec R;
+    for (int k = 0; k < 3; ++k) {
+        L.v0[k] = v[k];
+        L.v1[k] = v[3 + k];
+        L.v2[k] = v[6 + k];
+        L.le[k] = le[k];
+        L.n[k] = fdiv(cr[k], len);
+        R.bmin[k] = fminf(fminf(v[k], v[3 + k]), v[6 + k]);
+        R.bmax[k] = fmaxf(fmaxf(v[k], v[3 + k]), v[6 + k]);
+        R.axis[k] = 0.0f;
+    }
+    L.area = area;
+    const float lum = fadd(fadd(fmul(0.2126f, le[0]), fmul(0.7152f, le[1])), fmul(0.0722f, le[2]));
+    R.phi = fmul(lum, area);
+    R.cos_t = 1.0f;
+    const int64_t id = n - 1 + l;
+    R.id = (uint32_t)id;
+    R.begin = (uint32_t)l;
+    R.end = (uint32_t)(l + 1);
+    lights[l] = L;
+    nodes[id] = R;
+    axis_sum[id * 3 + 0] = cr[0];
+    axis_sum[id * 3 + 1] = cr[1];
+    axis_sum[id * 3 + 2] = cr[2];
+}
+
+__device__ __forceinline__ NodeRec load_node_cg(const NodeRec* p)
+{
+    NodeRec r;
+    const float4* s = reinterpret_cast<const float4*>(p);
+    float4* d = reinterpret_cast<float4*>(&r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = __ldcg(s + k);
+    return r;
+}
+
+__global__ void k_bottom_up(int64_t n, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                            const int32_t* __restrict__ parent, NodeRec* nodes, float* axis_sum,
+                            uint32_t* counters)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    int64_t node = n - 1 + l;
+    int32_t p = parent[node];
+    while (p >= 0) {
+        __threadfence();
+        if (atomicAdd(&counters[p], 1u) == 0u) return;  // the sibling finishes p
+        __threadfence();
+        const int32_t a = left[p], c = right[p];
+        const NodeRec A = load_node_cg(nodes + a), Cn = load_node_cg(nodes + c);
+        NodeRec R;
+        for (int k = 0; k < 3; ++k) {
+            R.bmin[k] = fminf(A.bmin[k], Cn.bmin[k]);
+            R.bmax[k] = fmaxf(A.bmax[k], Cn.bmax[k]);
+            R.axis[k] = 0.0f;
+            axis_sum[(int64_t)p * 3 + k] =
+                fadd(__ldcg(axis_sum + (int64_t)a * 3 + k), __ldcg(axis_sum + (int64_t)c * 3 + k));
+        }
+        R.phi = fadd(A.phi, Cn.phi);
+        R.cos_t = 1.0f;
+        R.id = (uint32_t)p;
+        R.begin = A.begin;
+        R.end = Cn.end;
+        nodes[p] = R;
+        node = p;
+        p = parent[p];
+    }
+}
+
+__global__ void k_axis(int64_t nn, NodeRec* __restrict__ nodes, const float* __restrict__ axis_sum,
+                       int* __restrict__ cosmin)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const float sx = axis_sum[i * 3], sy = axis_sum[i * 3 + 1], sz = axis_sum[i * 3 + 2];
+    const float len = fsqrt(fadd(fadd(fmul(sx, sx), fmul(sy, sy)), fmul(sz, sz)));
+    NodeRec& r = nodes[i];
+    if (len > 0.0f) {
+        r.axis[0] = fdiv(sx, len);
+        r.axis[1] = fdiv(sy, len);
+        r.axis[2] = fdiv(sz, len);
+        cosmin[i] = float_to_ordered(1.0f);
+    } else {
+        r.axis[0] = 0.0f;
+        r.axis[1] = 0.0f;
+        r.axis[2] = 1.0f;
+        cosmin[i] = float_to_ordered(-1.0f);
+    }
+}
+
+__global__ void k_cone(int64_t n, const LightRec* __restrict__ lights, const NodeRec* __restrict__ nodes,
+                       const int32_t* __restrict__ parent, int* __restrict__ cosmin)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const float nx = lights[l].n[0], ny = lights[l].n[1], nz = lights[l].n[2];
+    int64_t node = n - 1 + l;
+    int guard = 0;
+    while (node >= 0 && guard++ < 128) {
+        const NodeRec& r = nodes[node];
+        const float d = fadd(fadd(fmul(r.axis[0], nx), fmul(r.axis[1], ny)), fmul(r.axis[2], nz));
+        atomicMin(&cosmin[node], float_to_ordered(d));
+        node = parent[node];
+    }
+}
+
+__global__ void k_finalize(int64_t nn, NodeRec* __restrict__ nodes, const int* __restrict__ cosmin)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    nodes[i].cos_t = fmaxf(-1.0f, ordered_to_float(cosmin[i]));
+}
+
+__global__ void k_pairs(int64_t n, const NodeRec* __restrict__ nodes, const int32_t* __restrict__ left,
+                        const int32_t* __restrict__ right, NodeRec* __restrict__ pairs, float* __restrict__ leaf_phi)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n - 1) {
+        pairs[2 * i] = nodes[left[i]];
+        pairs[2 * i + 1] = nodes[right[i]];
+    }
+    if (i < n) leaf_phi[i] = nodes[n - 1 + i].phi;
+}
+
+__global__ void k_update_emission(int64_t n, const uint32_t* __restrict__ perm, const float* __restrict__ emis,
+                                  LightRec* __restrict__ lights)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const uint32_t i = perm[l];
+    lights[l].le[0] = emis[(int64_t)i * 3];
+    lights[l].le[1] = emis[(int64_t)i * 3 + 1];
+    lights[l].le[2] = emis[(int64_t)i * 3 + 2];
+}
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, rll_tree* t)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t nn = 2 * n - 1;
+    t->n = n;
+    cudaError_t e;
+#define RLL_ALLOC(ptr, bytes)                                                 \
+    e = cudaMalloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 64);               \
+    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaMalloc(tree)");
+    RLL_ALLOC(t->nodes, sizeof(NodeRec) * nn);
+    RLL_ALLOC(t->pairs, sizeof(NodeRec) * 2 * (n - 1));
+    RLL_ALLOC(t->lights, sizeof(LightRec) * n);
+    RLL_ALLOC(t->perm, sizeof(uint32_t) * n);
+    RLL_ALLOC(t->left, sizeof(int32_t) * (n - 1));
+    RLL_ALLOC(t->right, sizeof(int32_t) * (n - 1));
+    RLL_ALLOC(t->parent, sizeof(int32_t) * nn);
+    RLL_ALLOC(t->light_cdf, sizeof(float) * n);
+#undef RLL_ALLOC
+    // scratch: codes, idx, sort, begin/end (unused after build), axis sums,
+    // counters, cone minima, bbox, scan sums
+    const size_t sort_b = radix_sort_scratch_bytes(n);
+    const size_t need = a256(4 * n) * 2 + sort_b + a256(4 * nn) * 2 + a256(12 * nn) + a256(4 * n) +
+                        a256(4 * nn) + a256(64) + a256(4 * 4096) + a256(4 * n);
+    char* w = (char*)ws_get(ctx, need);
+    if (!w) return RLL_E_NOMEM;
+    uint32_t* codes = (uint32_t*)w; w += a256(4 * n);
+    uint32_t* idx = (uint32_t*)w; w += a256(4 * n);
+    void* sort_ws = w; w += sort_b;
+    uint32_t* begin = (uint32_t*)w; w += a256(4 * nn);
+    uint32_t* end = (uint32_t*)w; w += a256(4 * nn);
+    float* axis_sum = (float*)w; w += a256(12 * nn);
+    uint32_t* counters = (uint32_t*)w; w += a256(4 * n);
+    int* cosmin = (int*)w; w += a256(4 * nn);
+    int* bbox = (int*)w; w += a256(64);
+    void* scan_ws = w; w += a256(4 * 4096);
+    float* leaf_phi = (float*)w;
+
+    k_bbox_init<<<1, 32, 0, s>>>(bbox);
+    k_centroid_bbox<<<grid_for(n), kBlock, 0, s>>>(tri, n, bbox);
+    k_morton<<<grid_for(n), kBlock, 0, s>>>(tri, n, bbox, codes, idx);
+    uint32_t *scodes, *sidx;
+    e = radix_sort_pairs(s, codes, idx, n, 30, 0xFFFFFFFFu, sort_ws, &scodes, &sidx);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "radix sort (tree)");
+    e = cudaMemsetAsync(t->parent, 0xFF, sizeof(int32_t) * nn, s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "memset parent");
+    if (n > 1) k_karras<<<grid_for(n - 1), kBlock, 0, s>>>(scodes, sidx, n, t->left, t->right, t->parent, begin, end);
+    k_leaves<<<grid_for(n), kBlock, 0, s>>>(tri, emission, n, sidx, t->perm, t->lights, t->nodes, axis_sum);
+    e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * n, s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "memset counters");
+    if (n > 1) k_bottom_up<<<grid_for(n), kBlock, 0, s>>>(n, t->left, t->right, t->parent, t->nodes, axis_sum, counters);
+    k_axis<<<grid_for(nn), kBlock, 0, s>>>(nn, t->nodes, axis_sum, cosmin);
+    k_cone<<<grid_for(n), kBlock, 0, s>>>(n, t->lights, t->nodes, t->parent, cosmin);
+    k_finalize<<<grid_for(nn), kBlock, 0, s>>>(nn, t->nodes, cosmin);
+    k_pairs<<<grid_for(n), kBlock, 0, s>>>(n, t->nodes, t->left, t->right, t->pairs, leaf_phi);
+    e = inclusive_scan_f32(s, leaf_phi, t->light_cdf, n, scan_ws);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "scan (light cdf)");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(ctx, e, "tree kernels");
+    // the scratch is reused by later calls: finish before returning
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "tree build");
+    return RLL_OK;
+}
+
+int tree_update_emission(rll_ctx* ctx, rll_tree* t, const float* emission)
+{
+    k_update_emission<<<grid_for(t->n), kBlock, 0, ctx->stream>>>(t->n, t->perm, emission, t->lights);
+    return check_cuda(ctx, cudaGetLastError(), "update emission");
+}
+
+}  // namespace rll

@@ -1,0 +1,307 @@
+"""Python binding of the C ABI in include/rll.h (ctypes; argument marshalling
+only -- every step of the method runs in the CUDA library).
+
+Arrays are passed as device pointers taken from contiguous torch CUDA tensors
+(or as raw integer addresses / host numpy arrays where the C call says
+"host"). The library is loaded from paper_1911_10217_gb300/_build/librll.so;
+there is no fallback: if it is missing, import of this module's functions
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RLL_OK = 0
+ERRORS = {1: "RLL_E_INVALID", 2: "RLL_E_NOMEM", 3: "RLL_E_CUDA", 4: "RLL_E_TABLE_FULL",
+          8: "RLL_E_TIMEOUT", 16: "RLL_E_DEVICE"}
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
+MODE = {"descent": 0, "uniform": 1}
+REWARD = {"cluster": 0, "literal": 1}
+
+# every symbol declared in include/rll.h
+EXPORTS = [
+    "rll_ctx_create", "rll_ctx_set_stream", "rll_ctx_destroy", "rll_last_error", "rll_sync_status",
+    "rll_build_light_tree", "rll_tree_update_emission", "rll_tree_num_lights", "rll_tree_export",
+    "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_export", "rll_grid_import",
+    "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_power",
+    "rll_learn_update", "rll_split_collapse", "rll_render_pass_host",
+]
+
+
+class RllError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GridParams(ctypes.Structure):
+    _fields_ = [("table_size", ctypes.c_uint32), ("cut_size", ctypes.c_uint32),
+                ("origin", ctypes.c_float * 3), ("cell_size", ctypes.c_float),
+                ("normal_bins", ctypes.c_uint32), ("jitter", ctypes.c_uint32),
+                ("precision", ctypes.c_uint32), ("in_cluster_mode", ctypes.c_uint32),
+                ("reward_mode", ctypes.c_uint32), ("alpha", ctypes.c_float),
+                ("threshold", ctypes.c_float), ("eps", ctypes.c_float), ("q_init", ctypes.c_float)]
+
+
+class SampleDebug(ctypes.Structure):
+    _fields_ = [("light", ctypes.c_void_p), ("p_cut", ctypes.c_void_p), ("p_in", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librll.so (building it first if asked and absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path}")
+        _build.build()
+    L = ctypes.CDLL(path)
+    P, I32, I64, U32, U64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                             ctypes.c_uint64)
+    L.rll_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P]
+    L.rll_ctx_set_stream.argtypes = [P, P]
+    L.rll_ctx_destroy.argtypes = [P]
+    L.rll_last_error.argtypes = [P]
+    L.rll_last_error.restype = ctypes.c_char_p
+    L.rll_sync_status.argtypes = [P]
+    L.rll_build_light_tree.argtypes = [P, P, P, I64, ctypes.POINTER(P)]
+    L.rll_tree_update_emission.argtypes = [P, P, P]
+    L.rll_tree_num_lights.argtypes = [P]
+    L.rll_tree_num_lights.restype = I64
+    L.rll_tree_export.argtypes = [P, P, P, P, P, P, P, P, P]
+    L.rll_tree_destroy.argtypes = [P]
+    L.rll_create_grid.argtypes = [P, P, ctypes.POINTER(GridParams), ctypes.POINTER(P)]
+    L.rll_grid_cut_len.argtypes = [P]
+    L.rll_grid_cut_len.restype = U32
+    L.rll_grid_export.argtypes = [P, P, P, P, P, P]
+    L.rll_grid_import.argtypes = [P, P, P, P, P, P]
+    L.rll_grid_destroy.argtypes = [P]
+    L.rll_sample_and_shade.argtypes = [P, P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P, P]
+    L.rll_sample_and_shade_ex.argtypes = [P, P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P, P,
+                                          ctypes.POINTER(SampleDebug)]
+    L.rll_sample_power.argtypes = [P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P]
+    L.rll_learn_update.argtypes = [P, P, P, P, I64]
+    L.rll_split_collapse.argtypes = [P, P, P]
+    L.rll_render_pass_host.argtypes = [P, P, P, P, P, P, I64, P, I32, U64, U32, I32, I32, P]
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Device (or host) address of a tensor / array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check_tensor(t, dtype_name, device=True):
+    if t is None:
+        return
+    if hasattr(t, "dtype"):
+        if str(t.dtype).split(".")[-1] != dtype_name:
+            raise TypeError(f"expected {dtype_name}, got {t.dtype}")
+        if device and hasattr(t, "is_cuda") and not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+
+
+class Context:
+    """rll_ctx: a device and the CUDA stream work is enqueued on."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.rll_ctx_create(ctypes.byref(h), int(device), self._stream_ptr(stream))
+        if rc != RLL_OK:
+            raise RllError(rc, "rll_ctx_create failed")
+        self.h = h
+        self.device = device
+
+    @staticmethod
+    def _stream_ptr(stream):
+        if stream is None:
+            return None
+        if isinstance(stream, int):
+            return stream
+        return stream.cuda_stream
+
+    def set_stream(self, stream):
+        self._check(self.lib.rll_ctx_set_stream(self.h, self._stream_ptr(stream)))
+
+    def _check(self, rc):
+        if rc != RLL_OK:
+            raise RllError(rc, self.lib.rll_last_error(self.h).decode())
+
+    def sync_status(self) -> int:
+        r = self.lib.rll_sync_status(self.h)
+        if r < 0:
+            raise RllError(-r, self.lib.rll_last_error(self.h).decode())
+        return r
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rll_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tree:
+    """rll_tree built by rll_build_light_tree."""
+
+    def __init__(self, ctx: Context, tri, emission):
+        _check_tensor(tri, "float32")
+        _check_tensor(emission, "float32")
+        n = int(tri.shape[0])
+        h = ctypes.c_void_p()
+        ctx._check(ctx.lib.rll_build_light_tree(ctx.h, _ptr(tri), _ptr(emission), n, ctypes.byref(h)))
+        self.ctx, self.h, self.n = ctx, h, n
+
+    def update_emission(self, emission):
+        _check_tensor(emission, "float32")
+        self.ctx._check(self.ctx.lib.rll_tree_update_emission(self.ctx.h, self.h, _ptr(emission)))
+
+    def export(self):
+        n = self.n
+        nn = 2 * n - 1
+        out = dict(perm=np.zeros(n, np.uint32), left=np.zeros(max(n - 1, 1), np.int32),
+                   right=np.zeros(max(n - 1, 1), np.int32), parent=np.zeros(nn, np.int32),
+                   begin=np.zeros(nn, np.uint32), end=np.zeros(nn, np.uint32),
+                   rec=np.zeros((nn, 11), np.float32))
+        self.ctx._check(self.ctx.lib.rll_tree_export(
+            self.ctx.h, self.h, *[_ptr(out[k]) for k in ("perm", "left", "right", "parent", "begin",
+                                                         "end", "rec")]))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.rll_tree_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grid_params(table_size, cut_size, origin=(0.0, 0.0, 0.0), cell_size=1.0, normal_bins=1,
+                jitter=False, precision="fp32", mode="descent", reward="cluster", alpha=0.1,
+                threshold=2.0, eps=0.01, q_init=1.0) -> GridParams:
+    return GridParams(int(table_size), int(cut_size), (ctypes.c_float * 3)(*origin), float(cell_size),
+                      int(normal_bins), int(bool(jitter)), PREC[precision], MODE[mode], REWARD[reward],
+                      float(alpha), float(threshold), float(eps), float(q_init))
+
+
+class Grid:
+    """rll_grid created by rll_create_grid."""
+
+    def __init__(self, ctx: Context, tree: Tree, params: GridParams):
+        h = ctypes.c_void_p()
+        ctx._check(ctx.lib.rll_create_grid(ctx.h, tree.h, ctypes.byref(params), ctypes.byref(h)))
+        self.ctx, self.h, self.tree, self.params = ctx, h, tree, params
+        self.H, self.M = int(params.table_size), int(params.cut_size)
+        self.m = int(ctx.lib.rll_grid_cut_len(h))
+
+    def export(self):
+        H, M = self.H, self.M
+        out = dict(keys=np.zeros(H, np.uint64), cut=np.zeros((H, M), np.int32),
+                   q=np.zeros((H, M), np.float32), c=np.zeros((H, M), np.float32))
+        self.ctx._check(self.ctx.lib.rll_grid_export(self.ctx.h, self.h, _ptr(out["keys"]),
+                                                     _ptr(out["cut"]), _ptr(out["q"]),
+                                                     _ptr(out["c"])))
+        return out
+
+    def import_state(self, keys, cut, q, c):
+        keys = np.ascontiguousarray(keys, np.uint64)
+        cut = np.ascontiguousarray(cut, np.int32)
+        q = np.ascontiguousarray(q, np.float32)
+        c = np.ascontiguousarray(c, np.float32)
+        self.ctx._check(self.ctx.lib.rll_grid_import(self.ctx.h, self.h, _ptr(keys), _ptr(cut),
+                                                     _ptr(q), _ptr(c)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.rll_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sample_and_shade(ctx: Context, grid: Grid, tree: Tree, pos, nrm, albedo, boxes, seed, frame, spp,
+                     rgb, rec_key=None, rec_val=None, dbg_light=None, dbg_pcut=None, dbg_pin=None):
+    for t, d in ((pos, "float32"), (nrm, "float32"), (albedo, "float32"), (boxes, "float32"),
+                 (rgb, "float32"), (rec_key, "int32"), (rec_val, "float32")):
+        _check_tensor(t, d)
+    n = int(albedo.shape[0])
+    k = int(boxes.shape[0]) if boxes is not None else 0
+    if dbg_light is None and dbg_pcut is None and dbg_pin is None:
+        ctx._check(ctx.lib.rll_sample_and_shade(ctx.h, grid.h, tree.h, _ptr(pos), _ptr(nrm),
+                                                _ptr(albedo), n, _ptr(boxes), k, int(seed),
+                                                int(frame), int(spp), _ptr(rgb), _ptr(rec_key),
+                                                _ptr(rec_val)))
+    else:
+        dbg = SampleDebug(_ptr(dbg_light), _ptr(dbg_pcut), _ptr(dbg_pin))
+        ctx._check(ctx.lib.rll_sample_and_shade_ex(ctx.h, grid.h, tree.h, _ptr(pos), _ptr(nrm),
+                                                   _ptr(albedo), n, _ptr(boxes), k, int(seed),
+                                                   int(frame), int(spp), _ptr(rgb), _ptr(rec_key),
+                                                   _ptr(rec_val), ctypes.byref(dbg)))
+
+
+def sample_power(ctx: Context, tree: Tree, pos, nrm, albedo, boxes, seed, frame, spp, rgb,
+                 light_out=None):
+    n = int(albedo.shape[0])
+    k = int(boxes.shape[0]) if boxes is not None else 0
+    ctx._check(ctx.lib.rll_sample_power(ctx.h, tree.h, _ptr(pos), _ptr(nrm), _ptr(albedo), n,
+                                        _ptr(boxes), k, int(seed), int(frame), int(spp), _ptr(rgb),
+                                        _ptr(light_out)))
+
+
+def learn_update(ctx: Context, grid: Grid, rec_key, rec_val, n_records=None):
+    n = int(rec_key.shape[0]) if n_records is None else int(n_records)
+    ctx._check(ctx.lib.rll_learn_update(ctx.h, grid.h, _ptr(rec_key), _ptr(rec_val), n))
+
+
+def split_collapse(ctx: Context, grid: Grid, tree: Tree):
+    ctx._check(ctx.lib.rll_split_collapse(ctx.h, grid.h, tree.h))
+
+
+def render_pass_host(ctx: Context, grid: Grid, tree: Tree, pos, nrm, albedo, boxes, seed, frame,
+                     spp, rgb, do_split=True):
+    """Whole pass from HOST buffers (numpy or pinned CPU tensors)."""
+    n = int(albedo.shape[0])
+    k = int(boxes.shape[0])
+    ctx._check(ctx.lib.rll_render_pass_host(ctx.h, grid.h, tree.h, _ptr(pos), _ptr(nrm),
+                                            _ptr(albedo), n, _ptr(boxes), k, int(seed), int(frame),
+                                            int(spp), int(bool(do_split)), _ptr(rgb)))

@@ -1,0 +1,105 @@
+"""Shared helpers of the GPU tests: device copies of a scene, one pass through
+the C ABI, comparisons against the oracle keyed by cell key."""
+import numpy as np
+
+# tolerance on learned values and cdfs per table precision: binary32 is the
+# stated 1e-4 relative; a 16-bit table adds one rounding of its format
+# (2^-11 for binary16, 2^-8 for bfloat16) on each side
+RTOL = {"fp32": 1e-4, "fp16": 2.5e-3, "bf16": 2e-2}
+
+
+def device_scene(scene, dev, emission=None):
+    import torch
+    t = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    return dict(tri=t(scene.tris.reshape(-1, 9)), em=t(scene.emission if emission is None else emission),
+                boxes=t(scene.boxes), pos=t(scene.pos), nrm=t(scene.nrm), alb=t(scene.albedo))
+
+
+def params_for(rll, scene, **kw):
+    g = scene.grid
+    args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin, cell_size=g.cell_size,
+                normal_bins=g.normal_bins, jitter=g.jitter)
+    args.update(kw)
+    return rll.grid_params(**args)
+
+
+def run_sample(rll, ctx, grid, tree, d, seed, frame, spp):
+    import torch
+    dev = d["pos"].device
+    P = d["alb"].shape[0]
+    out = dict(rgb=torch.empty(3, P, device=dev),
+               key=torch.empty(P * spp, dtype=torch.int32, device=dev),
+               val=torch.empty(P * spp, device=dev),
+               light=torch.empty(P * spp, dtype=torch.int32, device=dev),
+               pcut=torch.empty(P * spp, device=dev), pin=torch.empty(P * spp, device=dev))
+    rll.sample_and_shade(ctx, grid, tree, d["pos"], d["nrm"], d["alb"], d["boxes"], seed, frame, spp,
+                         out["rgb"], out["key"], out["val"], dbg_light=out["light"],
+                         dbg_pcut=out["pcut"], dbg_pin=out["pin"])
+    return out
+
+
+def to_host(out):
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def compare_samples(gpu, orc, gpu_keys, orc_keys, M, rtol=1e-4):
+    """Light index bit-exact except draws within 1e-6 of a threshold (at most
+    1e-5 of the samples); the same cell key and cluster; estimates and
+    rewards within rtol."""
+    light_g = gpu["light"].astype(np.int64)
+    n = light_g.size
+    mism = light_g != orc["light"]
+    near = orc["margin"] < 1e-6
+    assert not np.any(mism & ~near), f"{int(np.sum(mism & ~near))} light choices differ away from a boundary"
+    assert mism.sum() <= max(1, int(1e-5 * n)), f"{int(mism.sum())} boundary mismatches of {n}"
+    ok = ~mism
+    kg = gpu["key"].view(np.uint32).astype(np.int64)
+    slot_g = np.where(kg == 0xFFFFFFFF, -1, kg // M)
+    s_g = np.where(kg == 0xFFFFFFFF, -1, kg % M)
+    cell_g = np.where(slot_g >= 0, gpu_keys[np.maximum(slot_g, 0)], np.uint64(0))
+    cell_o = np.where(orc["slot"] >= 0, orc_keys[np.maximum(orc["slot"], 0)], np.uint64(0))
+    assert np.array_equal(cell_g[ok], cell_o[ok]), "cell keys differ"
+    assert np.array_equal(s_g[ok], orc["s"][ok]), "clusters differ"
+    rv = gpu["val"].astype(np.float64)
+    assert np.allclose(rv[ok], orc["reward"][ok], rtol=rtol, atol=1e-7 * max(1.0, np.abs(orc["reward"]).max())), \
+        "rewards differ"
+    pdf_g = gpu["pcut"].astype(np.float64) * gpu["pin"]
+    pdf_o = orc["p_cut"] * orc["p_in"]
+    assert np.allclose(pdf_g[ok], pdf_o[ok], rtol=rtol), "pdfs differ"
+    if mism.sum() == 0:
+        assert np.allclose(gpu["rgb"], orc["rgb"], rtol=rtol, atol=1e-7 * max(1.0, np.abs(orc["rgb"]).max())), \
+            "estimates differ"
+    return int(mism.sum())
+
+
+def rows_by_key(keys, *tables):
+    occ = np.nonzero(keys != np.uint64(0xFFFFFFFFFFFFFFFF))[0]
+    return {int(keys[i]): tuple(t[i] for t in tables) for i in occ}
+
+
+def compare_tables(gstate, ostate, m, rtol, check_cut=True, only=None):
+    """Compare two grid states cell by cell (matched by key)."""
+    g = rows_by_key(gstate["keys"], gstate["cut"], gstate["q"], gstate["c"])
+    o = rows_by_key(ostate["keys"], ostate["cut"], ostate["q"], ostate["c"])
+    assert set(g) == set(o), f"cell sets differ: {len(set(g) ^ set(o))}"
+    keys = o.keys() if only is None else only
+    for k in keys:
+        gc, gq, gcc = g[k]
+        oc, oq, occ = o[k]
+        if check_cut:
+            assert np.array_equal(gc[:m], oc[:m]), f"cut differs in cell {k:#x}"
+        assert np.allclose(gq[:m], oq[:m], rtol=rtol, atol=1e-12), f"Q differs in cell {k:#x}"
+        assert np.allclose(gcc[:m], occ[:m], rtol=rtol, atol=1e-12), f"C differs in cell {k:#x}"
+
+
+def oracle_state(og):
+    return dict(keys=og.keys.copy(), cut=og.cut.copy(), q=og.Q.copy(), c=og.C.copy())
+
+
+def clone_oracle_grid(O, og):
+    p = og.params
+    g2 = O.Grid(og.tree, og.H, og.M, origin=p["origin"], cell_size=p["cell_size"],
+                normal_bins=p["normal_bins"], jitter=p["jitter"], mode=p["mode"], reward=p["reward"],
+                precision=p["precision"], alpha=p["alpha"], T=p["T"], eps=p["eps"])
+    g2.copy_state_from(og.keys, og.cut, og.Q, og.C)
+    return g2

@@ -1,0 +1,279 @@
+"""GPU-vs-oracle parity through the C ABI (marked gpu).
+
+Every step starts from a state the oracle produced (imported into the device
+grid): the device never feeds the oracle. Decisions are compared exactly
+(light index, cell, cluster, cut), continuous values within the stated
+tolerance (1e-4 relative for binary32 tables).
+"""
+import numpy as np
+import pytest
+
+from paper_1911_10217_gb300 import scenes
+
+from .gpu_common import (RTOL, clone_oracle_grid, compare_samples, compare_tables, device_scene,
+                         oracle_state, params_for, run_sample, to_host)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import oracle as O
+    from paper_1911_10217_gb300 import rll
+    dev = torch.device("cuda:0")
+    ctx = rll.Context(0, torch.cuda.current_stream(dev))
+    return dict(torch=torch, O=O, rll=rll, dev=dev, ctx=ctx)
+
+
+def _trees(env, scene):
+    O, rll = env["O"], env["rll"]
+    d = device_scene(scene, env["dev"])
+    return O.Tree(scene.tris, scene.emission), rll.Tree(env["ctx"], d["tri"], d["em"]), d
+
+
+@pytest.mark.parametrize("maker", ["tiny", "small_frame", "frame"])
+def test_tree_matches_oracle_bit_exact(env, maker):
+    s = getattr(scenes, maker + "_scene")()
+    ot, dt, _ = _trees(env, s)
+    ex = dt.export()
+    assert np.array_equal(ex["perm"], ot.perm)
+    assert np.array_equal(ex["left"], ot.left) and np.array_equal(ex["right"], ot.right)
+    assert np.array_equal(ex["parent"], ot.parent)
+    assert np.array_equal(ex["begin"], ot.begin) and np.array_equal(ex["end"], ot.end)
+    assert np.array_equal(ex["rec"].view(np.uint32), ot.rec.view(np.uint32)), "node records differ"
+
+
+@pytest.mark.parametrize("variant", [
+    dict(),
+    dict(mode="uniform"),
+    dict(precision="fp16"),
+    dict(precision="bf16"),
+    dict(jitter=True),
+    dict(reward="literal", cut_size=8),
+])
+def test_lockstep_learning_tiny(env, variant):
+    """Eight passes of the tiny scene. At each pass the oracle's state is
+    imported; sampling, Eq. 1 + Eq. 2 and split-collapse are compared."""
+    O, rll, ctx = env["O"], env["rll"], env["ctx"]
+    s = scenes.tiny_scene(jitter=variant.get("jitter", False))
+    ot, dt, d = _trees(env, s)
+    okw = {k: v for k, v in variant.items() if k in ("mode", "precision", "reward", "cut_size")}
+    og = O.Grid.for_scene(ot, s, **okw)
+    dkw = dict(okw)
+    dg = rll.Grid(ctx, dt, params_for(rll, s, **dkw))
+    assert dg.m == og.m
+    prec = variant.get("precision", "fp32")
+    rtol = RTOL[prec]
+    A = O.scene_arrays(s)
+    for f in range(s.frames):
+        dg.import_state(og.keys, og.cut, og.Q, og.C)
+        g = to_host(run_sample(rll, ctx, dg, dt, d, s.seed, f, s.spp))
+        o = og.sample_frame(A, s.seed, f, s.spp)
+        after = dg.export()
+        mism = compare_samples(g, o, after["keys"], og.keys, dg.M, rtol=1e-4)
+        # Eq. 1 + Eq. 2 on the device's own records
+        import torch
+        rll.learn_update(ctx, dg, torch.from_numpy(g["key"]).to(env["dev"]),
+                         torch.from_numpy(g["val"]).to(env["dev"]))
+        touched = og.learn(o["slot"], o["s"], o["reward"])
+        if mism == 0:
+            compare_tables(dg.export(), oracle_state(og), og.m, rtol, check_cut=True)
+        # split-collapse from the oracle's post-learn state, all cells
+        dg.import_state(og.keys, og.cut, og.Q, og.C)
+        rll.split_collapse(ctx, dg, dt)
+        o2 = clone_oracle_grid(O, og)
+        occupied = og.keys != np.uint64(0xFFFFFFFFFFFFFFFF)
+        changed = o2.split_collapse(occupied)
+        compare_tables(dg.export(), oracle_state(o2), og.m, max(rtol, 1e-5), check_cut=True)
+        og.split_collapse(touched)
+        assert ctx.sync_status() == 0
+    assert changed >= 0
+
+
+def test_learning_is_deterministic(env):
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    s = scenes.small_frame_scene()
+    _, dt, d = _trees(env, s)
+    results = []
+    for rep in range(2):
+        dg = rll.Grid(ctx, dt, params_for(rll, s))
+        for f in range(3):
+            g = run_sample(rll, ctx, dg, dt, d, s.seed, f, s.spp)
+            rll.learn_update(ctx, dg, g["key"], g["val"])
+            rll.split_collapse(ctx, dg, dt)
+        st = dg.export()
+        order = np.argsort(st["keys"])
+        results.append((g["rgb"].cpu().numpy(), st["keys"][order], st["cut"][order], st["q"][order],
+                        st["c"][order]))
+    for a, b in zip(*results):
+        assert np.array_equal(a, b)
+
+
+def test_unbiased_against_bruteforce(env):
+    """Mean of 2^20 device samples at one point equals exact direct lighting
+    (oracle quadrature) within 5 standard errors, after learning."""
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    s = scenes.tiny_scene()
+    _, dt, d = _trees(env, s)
+    dg = rll.Grid(ctx, dt, params_for(rll, s))
+    for f in range(4):
+        g = run_sample(rll, ctx, dg, dt, d, s.seed, f, s.spp)
+        rll.learn_update(ctx, dg, g["key"], g["val"])
+        rll.split_collapse(ctx, dg, dt)
+    R = 1 << 20
+    for idx in (64 * 16 + 16, 64 * 40 + 50):
+        dr = dict(d)
+        dr["pos"] = d["pos"][:, idx:idx + 1].repeat(1, R).contiguous()
+        dr["nrm"] = d["nrm"][:, idx:idx + 1].repeat(1, R).contiguous()
+        dr["alb"] = d["alb"][idx:idx + 1].repeat(R).contiguous()
+        rgb = torch.empty(3, R, device=env["dev"])
+        rll.sample_and_shade(ctx, dg, dt, dr["pos"], dr["nrm"], dr["alb"], d["boxes"], 99, 1000, 1, rgb)
+        v = rgb.double().cpu().numpy()
+        ref = O.direct_bruteforce(s.pos[:, idx], s.nrm[:, idx], s.albedo[idx], s.tris, s.emission,
+                                  s.boxes, level=5)
+        for k in range(3):
+            m, se = v[k].mean(), v[k].std() / np.sqrt(R)
+            assert abs(m - ref[k]) < 5 * se + 2e-3 * ref[k], (idx, k, m, ref[k], se)
+
+
+def test_frame_scale_parity(env):
+    """1920 x 1080 frame: tree, then one pass from the empty grid. Sampled
+    pixel ranges are compared one by one; learning on the oracle's full set
+    of records is compared cell by cell."""
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    s = scenes.frame_scene()
+    ot, dt, d = _trees(env, s)
+    og = O.Grid.for_scene(ot, s)
+    dg = rll.Grid(ctx, dt, params_for(rll, s))
+    g = to_host(run_sample(rll, ctx, dg, dt, d, s.seed, 0, s.spp))
+    st = dg.export()
+    A = O.scene_arrays(s)
+    rng = np.random.default_rng(0)
+    P = s.n_points
+    for start in rng.integers(0, P - 4096, size=6):
+        sub = O.Grid.for_scene(ot, s)
+        o = sub.sample_frame(A, s.seed, 0, s.spp, first=int(start), count=4096)
+        sl = slice(int(start), int(start) + 4096)
+        gsub = {k: (v[:, sl] if k == "rgb" else v[sl]) for k, v in g.items()}
+        compare_samples(gsub, o, st["keys"], sub.keys, dg.M)
+    # full pass on the oracle, then Eq. 1 + Eq. 2 compared on every cell
+    o = og.sample_frame(A, s.seed, 0, s.spp)
+    mism = compare_samples(g, o, st["keys"], og.keys, dg.M)
+    rll.learn_update(ctx, dg, torch.from_numpy(g["key"]).to(env["dev"]),
+                     torch.from_numpy(g["val"]).to(env["dev"]))
+    og.learn(o["slot"], o["s"], o["reward"])
+    if mism == 0:
+        compare_tables(dg.export(), oracle_state(og), og.m, RTOL["fp32"])
+    assert ctx.sync_status() == 0
+
+
+def test_edge_cases(env):
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    dev = env["dev"]
+    s = scenes.tiny_scene()
+    ot, dt, d = _trees(env, s)
+    # ragged point count, no boxes, 3 samples per point
+    P = 1000
+    dr = dict(pos=d["pos"][:, :P].contiguous(), nrm=d["nrm"][:, :P].contiguous(),
+              alb=d["alb"][:P].contiguous(), boxes=d["boxes"][:0].contiguous())
+    og = O.Grid.for_scene(ot, s)
+    dg = rll.Grid(ctx, dt, params_for(rll, s))
+    g = to_host(run_sample(rll, ctx, dg, dt, dr, 5, 2, 3))
+    sub = scenes.Scene("r", s.tris, s.emission, s.boxes[:0].copy(), s.pos[:, :P].copy(),
+                       s.nrm[:, :P].copy(), s.albedo[:P].copy(), s.grid, 3, 1, 5)
+    o = og.sample_frame(O.scene_arrays(sub), 5, 2, 3)
+    compare_samples(g, o, dg.export()["keys"], og.keys, dg.M)
+    # no points: nothing happens
+    e = torch.empty(3, 0, device=dev)
+    rll.sample_and_shade(ctx, dg, dt, e, e, torch.empty(0, device=dev), d["boxes"], 0, 0, 1,
+                         torch.empty(3, 0, device=dev))
+    rll.learn_update(ctx, dg, torch.empty(0, dtype=torch.int32, device=dev), torch.empty(0, device=dev))
+    # cut size above the light count: every light is its own cluster
+    dg2 = rll.Grid(ctx, dt, params_for(rll, s, cut_size=256))
+    assert dg2.m == 256
+    og2 = O.Grid.for_scene(ot, s, cut_size=256)
+    g2 = to_host(run_sample(rll, ctx, dg2, dt, d, 1, 0, 1))
+    o2 = og2.sample_frame(O.scene_arrays(s), 1, 0, 1)
+    compare_samples(g2, o2, dg2.export()["keys"], og2.keys, dg2.M)
+    # a single light
+    one = s.tris[:1].copy()
+    t1 = rll.Tree(ctx, torch.from_numpy(one.reshape(-1, 9)).to(dev), d["em"][:1].contiguous())
+    g1 = rll.Grid(ctx, t1, params_for(rll, s))
+    assert g1.m == 1
+    run_sample(rll, ctx, g1, t1, d, 0, 0, 1)
+    # a table too small for the cells: flagged, estimates still finite
+    gs = rll.Grid(ctx, dt, params_for(rll, s, table_size=16, cell_size=1.0 / 64))
+    out = run_sample(rll, ctx, gs, dt, d, 0, 0, 1)
+    assert ctx.sync_status() & 4
+    assert torch.isfinite(out["rgb"]).all()
+    rll.learn_update(ctx, gs, out["key"], out["val"])
+    assert ctx.sync_status() == 0
+    # invalid arguments are refused without launching
+    with pytest.raises(rll.RllError):
+        rll.sample_and_shade(ctx, dg, dt, d["pos"], d["nrm"], d["alb"], d["boxes"], 0, 0, 0, g["rgb"])
+    with pytest.raises(rll.RllError):
+        rll.Grid(ctx, dt, params_for(rll, s, table_size=1000))
+
+
+def test_power_sampler(env):
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    s = scenes.small_frame_scene()
+    ot, dt, d = _trees(env, s)
+    P = s.n_points
+    rgb = torch.empty(3, P, device=env["dev"])
+    light = torch.empty(P * s.spp, dtype=torch.int32, device=env["dev"])
+    rll.sample_power(ctx, dt, d["pos"], d["nrm"], d["alb"], d["boxes"], 3, 0, s.spp, rgb, light)
+    orgb, olight = O.sample_power(ot, O.scene_arrays(s), 3, 0, s.spp)
+    lg = light.cpu().numpy()
+    # the device cdf is a binary32 prefix sum: only boundary draws may differ
+    assert np.mean(lg != olight) < 1e-3
+    same = np.all((lg == olight).reshape(P, s.spp), axis=1)
+    assert np.allclose(rgb.cpu().numpy()[:, same], orgb[:, same], rtol=1e-3, atol=1e-7)
+
+
+def test_checkpoint_resume_is_exact(env):
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    s = scenes.small_frame_scene()
+    _, dt, d = _trees(env, s)
+
+    def run(grid, frames):
+        for f in frames:
+            g = run_sample(rll, ctx, grid, dt, d, s.seed, f, s.spp)
+            rll.learn_update(ctx, grid, g["key"], g["val"])
+            rll.split_collapse(ctx, grid, dt)
+        return g["rgb"].cpu().numpy()
+
+    a = rll.Grid(ctx, dt, params_for(rll, s))
+    run(a, range(4))
+    full = a.export()
+    b = rll.Grid(ctx, dt, params_for(rll, s))
+    run(b, range(2))
+    ck = b.export()
+    c = rll.Grid(ctx, dt, params_for(rll, s))
+    c.import_state(ck["keys"], ck["cut"], ck["q"], ck["c"])
+    run(c, range(2, 4))
+    resumed = c.export()
+    # slots of keys inserted in the same pass may differ: compare by key
+    fo, ro = np.argsort(full["keys"]), np.argsort(resumed["keys"])
+    for k in ("keys", "cut", "q", "c"):
+        assert np.array_equal(full[k][fo], resumed[k][ro]), k
+
+
+def test_host_pass_matches_device_pass(env):
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    s = scenes.small_frame_scene()
+    _, dt, d = _trees(env, s)
+    a = rll.Grid(ctx, dt, params_for(rll, s))
+    b = rll.Grid(ctx, dt, params_for(rll, s))
+    for f in range(2):
+        g = run_sample(rll, ctx, a, dt, d, s.seed, f, s.spp)
+        rll.learn_update(ctx, a, g["key"], g["val"])
+        rll.split_collapse(ctx, a, dt)
+        rgb = np.zeros((3, s.n_points), np.float32)
+        rll.render_pass_host(ctx, b, dt, np.ascontiguousarray(s.pos), np.ascontiguousarray(s.nrm),
+                             np.ascontiguousarray(s.albedo), np.ascontiguousarray(s.boxes), s.seed, f,
+                             s.spp, rgb)
+        assert np.array_equal(rgb, g["rgb"].cpu().numpy())
