@@ -1,0 +1,374 @@
+"""Benchmark: light samples per second of one learning pass (sample + shade +
+shadow + learn + split-collapse) on the frame-scale static scene
+(1920 x 1080 G-buffer, 64K emissive triangles in 64 patches, 64 occluder
+boxes, 2^20-entry hash grid, cut size 32, 1 sample per point).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line. A step is one full pass over the frame. Inputs are
+resident in device memory; L2 is flushed (512 MB write) between timed steps,
+outside the timed region; every step is timed with CUDA events on the
+library's stream. `e2e` repeats the measurement through the host-buffer C
+entry point (G-buffer uploaded and rgb read back inside the timed region).
+With --impl reference the CPU oracle is timed on a bounded slice of the same
+workload (there is no other implementation of the method to run).
+Under torchrun each rank renders its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("light samples/sec (sample+shade+shadow+learn) at 1 GB300; MSE at equal spp; "
+          "p99 frame ms")
+UNIT = "light samples/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return dict(PEAKS_FALLBACK, sm_max_mhz=2070.0), "fallback"
+
+
+def workload_config(scene):
+    g = scene.grid
+    return {"workload": "frame-scale static walled-cells scene, 1920x1080 G-buffer on 16 planes, "
+                        "64K emissive triangles in 64 patches, 64 occluder boxes, one learning pass "
+                        "(sample+shade+shadow, Eq.1, Eq.2, split-collapse) per step",
+            "points": scene.n_points, "lights": scene.n_lights, "boxes": int(scene.boxes.shape[0]),
+            "spp": scene.spp, "cut_size": g.cut_size, "table_size": g.table_size,
+            "cell_size": g.cell_size, "normal_bins": g.normal_bins, "jitter": g.jitter,
+            "table_precision": "fp32", "in_cluster": "descent",
+            "l2": "flushed between timed steps (512 MB write, untimed)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ops_per_sample(n_boxes, n_lights, m):
+    """Algorithmic binary32 operations of one light sample (the count used
+    for the ALU roofline of the sampling kernel): 18 per slab-tested box
+    (6 fma, 12 min/max/compare), 90 per descent level (two node importances
+    of ~45 operations), descent depth log2(N / m), and 250 for hashing, the
+    cdf search, Philox, the triangle point and shading."""
+    levels = max(0.0, math.log2(max(1.0, n_lights / max(1, m))))
+    return 18 * n_boxes + 90 * levels + 250
+
+
+def bytes_per_sample():
+    """Algorithmic HBM bytes of one sample in the sampling kernel: G-buffer
+    28 B read (position, normal, albedo), rgb 12 B and record 8 B written."""
+    return 28 + 12 + 8
+
+
+def cpu_baseline(scene, seconds=12.0, chunk=65536):
+    """Oracle (single thread) on consecutive point slices of the frame until
+    `seconds` of CPU work: samples per second of sample + Eq. 1 + Eq. 2."""
+    from oracle import oracle as O
+    tree = O.Tree(scene.tris, scene.emission)
+    grid = O.Grid.for_scene(tree, scene)
+    A = O.scene_arrays(scene)
+    done = 0
+    t0 = time.perf_counter()
+    start, frame = 0, 0
+    while time.perf_counter() - t0 < seconds:
+        cnt = min(chunk, scene.n_points - start)
+        out = grid.sample_frame(A, scene.seed, frame, scene.spp, first=start, count=cnt)
+        grid.learn(out["slot"], out["s"], out["reward"])
+        done += cnt * scene.spp
+        start += cnt
+        if start >= scene.n_points:
+            start, frame = 0, frame + 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} samples: consecutive {chunk}-point slices of the same frame-scale "
+                      f"workload (frames 0..{frame}), oracle sample+Eq.1+Eq.2, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, scene):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    tree = O.Tree(scene.tris, scene.emission)
+    grid = O.Grid.for_scene(tree, scene)
+    A = O.scene_arrays(scene)
+    chunk = 131072
+    times = []
+    for i in range(args.warmup + args.steps):
+        start = (i * chunk) % (scene.n_points - chunk)
+        t0 = time.perf_counter()
+        out = grid.sample_frame(A, scene.seed, i, scene.spp, first=start, count=chunk)
+        touched = grid.learn(out["slot"], out["s"], out["reward"])
+        grid.split_collapse(touched)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = chunk * scene.spp * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(scene),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{chunk} consecutive points of the frame per step, "
+                                       "oracle sample+Eq.1+Eq.2+split-collapse, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-quality", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from paper_1911_10217_gb300 import scenes
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    scene = scenes.frame_scene(seed=1 + rank)
+    if args.impl == "reference":
+        return run_reference(args, scene)
+
+    import torch
+    from paper_1911_10217_gb300 import rll
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = rll.Context(local, stream)
+
+    def T(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    tri, em, boxes = T(scene.tris.reshape(-1, 9)), T(scene.emission), T(scene.boxes)
+    pos, nrm, alb = T(scene.pos), T(scene.nrm), T(scene.albedo)
+    P, S = scene.n_points, scene.spp
+    tree = rll.Tree(ctx, tri, em)
+    g = scene.grid
+    params = rll.grid_params(g.table_size, g.cut_size, g.origin, g.cell_size, g.normal_bins, g.jitter)
+    grid = rll.Grid(ctx, tree, params)
+    rgb = torch.empty(3, P, device=dev)
+    key = torch.empty(P * S, dtype=torch.int32, device=dev)
+    val = torch.empty(P * S, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(frame, ev=None):
+        if ev:
+            ev[0].record(stream)
+        rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, scene.seed, frame, S, rgb, key, val)
+        if ev:
+            ev[1].record(stream)
+        rll.learn_update(ctx, grid, key, val)
+        if ev:
+            ev[2].record(stream)
+        rll.split_collapse(ctx, grid, tree)
+        if ev:
+            ev[3].record(stream)
+
+    frame = 0
+    for _ in range(args.warmup):
+        step(frame)
+        frame += 1
+    torch.cuda.synchronize()
+    if ctx.sync_status() != 0:
+        raise RuntimeError("device status raised during warm-up")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        step(frame, evs[i])
+        frame += 1
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    status = ctx.sync_status()
+    t_sample = [e[0].elapsed_time(e[1]) for e in evs]
+    t_learn = [e[1].elapsed_time(e[2]) for e in evs]
+    t_split = [e[2].elapsed_time(e[3]) for e in evs]
+    t_step = [e[0].elapsed_time(e[3]) for e in evs]
+    total_ms = sum(t_step)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * P * S / (ms_step * 1e-3)
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    hpos = torch.from_numpy(np.ascontiguousarray(scene.pos)).pin_memory()
+    hnrm = torch.from_numpy(np.ascontiguousarray(scene.nrm)).pin_memory()
+    halb = torch.from_numpy(np.ascontiguousarray(scene.albedo)).pin_memory()
+    hbox = torch.from_numpy(np.ascontiguousarray(scene.boxes)).pin_memory()
+    hrgb = torch.empty(3, P, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        rll.render_pass_host(ctx, grid, tree, hpos, hnrm, halb, hbox, scene.seed, frame, S, hrgb)
+        frame += 1
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rll.render_pass_host(ctx, grid, tree, hpos, hnrm, halb, hbox, scene.seed, frame, S, hrgb)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        frame += 1
+    e2e_step = statistics.mean(e2e_ms)
+
+    out = None
+    if rank == 0:
+        peaks, peak_kind = load_peaks()
+        sm_clock = peaks.get("sm_max_mhz", 2070.0)
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_clock * 1e6 / 1e12  # Tops/s
+        n_sample = P * S
+        ops = ops_per_sample(int(scene.boxes.shape[0]), scene.n_lights, grid.m) * n_sample
+        t_s = statistics.mean(t_sample) * 1e-3
+        achieved = ops / t_s / 1e12
+        hbm_ach = bytes_per_sample() * n_sample / t_s / 1e9
+        learn_bytes = 8 * n_sample  # records read once (keys + rewards)
+        t_l = statistics.mean(t_learn) * 1e-3
+        launches_per_step = 1 + 3 * math.ceil(math.ceil(math.log2(g.table_size * g.cut_size + 1)) / 8) + 2 + 1
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": workload_config(scene),
+               "roofline": {"kernel": "k_sample (sample_and_shade)", "bound": "alu",
+                            "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                            "frac": achieved / alu_peak, "traffic": None,
+                            "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                           f"{sm_clock:.0f} MHz ({peak_kind} sm_max_mhz)",
+                            "ops_per_sample": ops / n_sample,
+                            "hbm_achieved_gbs": hbm_ach,
+                            "hbm_frac_of_measured": hbm_ach / peaks.get("hbm_gbs", 6800.0)},
+               "e2e": {"value": world * P * S / (e2e_step * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": int(28 * P + 24 * scene.boxes.shape[0]),
+                       "d2h_bytes_per_step": int(12 * P)},
+               "gpu_launches": args.steps * launches_per_step,
+               "clocks": clk,
+               "extras": {"per_kernel_ms": {"sample_and_shade": statistics.mean(t_sample),
+                                            "learn_update": statistics.mean(t_learn),
+                                            "split_collapse": statistics.mean(t_split)},
+                          "p50_frame_ms": statistics.median(t_step),
+                          "p99_frame_ms": float(np.percentile(t_step, 99)),
+                          "learn_update_algorithmic_gbs": learn_bytes / t_l / 1e9,
+                          "wall_s_timed_region_incl_flush": wall,
+                          "device_status": status}}
+        if not args.no_quality:
+            out["extras"]["mse_equal_spp"] = quality(rll, ctx, grid, tree, scene, pos, nrm, alb, boxes, dev)
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(scene)
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def quality(rll, ctx, grid, tree, scene, pos, nrm, alb, boxes, dev):
+    """MSE at 1 spp of the learned sampler and of the energy-based sampler
+    against a 256-spp energy-sampler reference (not timed)."""
+    import torch
+    P = scene.n_points
+    ref = torch.zeros(3, P, device=dev, dtype=torch.float64)
+    tmp = torch.empty(3, P, device=dev)
+    n_ref = 32
+    for i in range(n_ref):
+        rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 7777, 100000 + i, 8, tmp)
+        ref += tmp.double()
+    ref /= n_ref
+    rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, 4242, 90000, 1, tmp)
+    mse_rll = float(((tmp.double() - ref) ** 2).mean())
+    rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 4242, 90000, 1, tmp)
+    mse_pow = float(((tmp.double() - ref) ** 2).mean())
+    return {"rll_1spp": mse_rll, "energy_sampler_1spp": mse_pow, "ratio": mse_pow / mse_rll,
+            "reference": "energy sampler, 256 spp"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -132,8 +132,9 @@ uint32_t rll_grid_cut_len(const rll_grid* grid);
 int rll_grid_export(rll_ctx* ctx, const rll_grid* grid, uint64_t* keys, int32_t* cut, float* q,
                     float* c);
 /* Loads a state written by rll_grid_export (HOST arrays, same shapes; q and c
- * are rounded to the table precision). Every occupied slot becomes a touched
- * cell, so a following rll_split_collapse adapts all of them. Synchronises. */
+ * are rounded to the table precision). Rows of empty slots are ignored and
+ * reset to the initial cut. Every occupied slot becomes a touched cell, so a
+ * following rll_split_collapse adapts all of them. Synchronises. */
 int rll_grid_import(rll_ctx* ctx, rll_grid* grid, const uint64_t* keys, const int32_t* cut,
                     const float* q, const float* c);
 int rll_grid_destroy(rll_grid* grid);

@@ -125,6 +125,28 @@ __global__ void k_fill_rows(int64_t total, uint32_t M, uint32_t m, const uint32_
     }
 }
 
+// rows of empty slots hold the initial cut (a cell created later starts from it)
+template <int P>
+__global__ void k_reset_empty_rows(int64_t total, uint32_t M, uint32_t m, const unsigned long long* __restrict__ keys,
+                                   const uint32_t* __restrict__ def_cut, const typename Store<P>::T* __restrict__ def_Q,
+                                   const typename Store<P>::T* __restrict__ def_C, uint32_t* __restrict__ cut,
+                                   typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = (uint32_t)(i % M);
+        if (keys[i / M] != kEmptyKey) continue;
+        if (s < m) {
+            cut[i] = def_cut[s];
+            Q[i] = def_Q[s];
+            C[i] = def_C[s];
+        } else {
+            cut[i] = 0u;
+            Q[i] = Store<P>::store(0.0f);
+            C[i] = Store<P>::store(0.0f);
+        }
+    }
+}
+
 template <int P>
 __global__ void k_to_float(int64_t total, const typename Store<P>::T* __restrict__ Q,
                            const typename Store<P>::T* __restrict__ C, float* __restrict__ q, float* __restrict__ c)
@@ -464,20 +486,23 @@ int grid_to_float(rll_ctx* ctx, const rll_grid* g, float* q, float* c)
     return check_cuda(ctx, cudaGetLastError(), "grid export");
 }
 
-int grid_from_float(rll_ctx* ctx, rll_grid* g, const float* q, const float* c)
+template <int P>
+void from_float_t(rll_ctx* ctx, rll_grid* g, const float* q, const float* c)
 {
+    using T = typename Store<P>::T;
     const int64_t total = (int64_t)g->H * g->M;
     const unsigned blocks = device_sm_count(g->device) * 4;
+    k_from_float<P><<<blocks, 256, 0, ctx->stream>>>(total, q, c, (T*)g->Q, (T*)g->C);
+    k_reset_empty_rows<P><<<blocks, 256, 0, ctx->stream>>>(total, g->M, g->m, g->keys, g->def_cut, (const T*)g->def_Q,
+                                                           (const T*)g->def_C, g->cut, (T*)g->Q, (T*)g->C);
+}
+
+int grid_from_float(rll_ctx* ctx, rll_grid* g, const float* q, const float* c)
+{
     switch (g->p.precision) {
-    case RLL_PREC_FP16:
-        k_from_float<RLL_PREC_FP16><<<blocks, 256, 0, ctx->stream>>>(total, q, c, (__half*)g->Q, (__half*)g->C);
-        break;
-    case RLL_PREC_BF16:
-        k_from_float<RLL_PREC_BF16><<<blocks, 256, 0, ctx->stream>>>(total, q, c, (__nv_bfloat16*)g->Q,
-                                                                     (__nv_bfloat16*)g->C);
-        break;
-    default:
-        k_from_float<RLL_PREC_FP32><<<blocks, 256, 0, ctx->stream>>>(total, q, c, (float*)g->Q, (float*)g->C);
+    case RLL_PREC_FP16: from_float_t<RLL_PREC_FP16>(ctx, g, q, c); break;
+    case RLL_PREC_BF16: from_float_t<RLL_PREC_BF16>(ctx, g, q, c); break;
+    default: from_float_t<RLL_PREC_FP32>(ctx, g, q, c);
     }
     return check_cuda(ctx, cudaGetLastError(), "grid import");
 }

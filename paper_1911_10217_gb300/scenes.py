@@ -292,7 +292,7 @@ def dynamic_scene(seed: int = 2, width: int = 3840, height: int = 2160, n_patche
 
 
 def small_frame_scene(seed: int = 3, width: int = 96, height: int = 64, n_patches: int = 16,
-                      tris_per_patch: int = 64, n_boxes: int = 32, table_size: int = 1 << 12,
+                      tris_per_patch: int = 64, n_boxes: int = 32, table_size: int = 1 << 14,
                       cut_size: int = 32, spp: int = 2) -> Scene:
     """A reduced frame-scale scene (same recipe as frame_scene) small enough
     for the CPU oracle to finish every sample in about a second."""

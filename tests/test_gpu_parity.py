@@ -30,6 +30,7 @@ def env():
 
 def _trees(env, scene):
     O, rll = env["O"], env["rll"]
+    env["ctx"].sync_status()  # clear device status bits left by an earlier test
     d = device_scene(scene, env["dev"])
     return O.Tree(scene.tris, scene.emission), rll.Tree(env["ctx"], d["tri"], d["em"]), d
 
@@ -124,7 +125,7 @@ def test_unbiased_against_bruteforce(env):
         rll.learn_update(ctx, dg, g["key"], g["val"])
         rll.split_collapse(ctx, dg, dt)
     R = 1 << 20
-    for idx in (64 * 16 + 16, 64 * 40 + 50):
+    for idx in (64 * 16 + 20, 64 * 40 + 50, 64 * 10 + 40):
         dr = dict(d)
         dr["pos"] = d["pos"][:, idx:idx + 1].repeat(1, R).contiguous()
         dr["nrm"] = d["nrm"][:, idx:idx + 1].repeat(1, R).contiguous()
@@ -136,7 +137,7 @@ def test_unbiased_against_bruteforce(env):
                                   s.boxes, level=5)
         for k in range(3):
             m, se = v[k].mean(), v[k].std() / np.sqrt(R)
-            assert abs(m - ref[k]) < 5 * se + 2e-3 * ref[k], (idx, k, m, ref[k], se)
+            assert abs(m - ref[k]) <= 5 * se + 2e-3 * ref[k], (idx, k, m, ref[k], se)
 
 
 def test_frame_scale_parity(env):
@@ -268,11 +269,17 @@ def test_host_pass_matches_device_pass(env):
     _, dt, d = _trees(env, s)
     a = rll.Grid(ctx, dt, params_for(rll, s))
     b = rll.Grid(ctx, dt, params_for(rll, s))
+    P = s.n_points
     for f in range(2):
-        g = run_sample(rll, ctx, a, dt, d, s.seed, f, s.spp)
+        # the plain kernel (no per-sample diagnostics), as the host pass uses
+        g = dict(rgb=torch.empty(3, P, device=env["dev"]),
+                 key=torch.empty(P * s.spp, dtype=torch.int32, device=env["dev"]),
+                 val=torch.empty(P * s.spp, device=env["dev"]))
+        rll.sample_and_shade(ctx, a, dt, d["pos"], d["nrm"], d["alb"], d["boxes"], s.seed, f, s.spp,
+                             g["rgb"], g["key"], g["val"])
         rll.learn_update(ctx, a, g["key"], g["val"])
         rll.split_collapse(ctx, a, dt)
-        rgb = np.zeros((3, s.n_points), np.float32)
+        rgb = np.zeros((3, P), np.float32)
         rll.render_pass_host(ctx, b, dt, np.ascontiguousarray(s.pos), np.ascontiguousarray(s.nrm),
                              np.ascontiguousarray(s.albedo), np.ascontiguousarray(s.boxes), s.seed, f,
                              s.spp, rgb)
