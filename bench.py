@@ -193,6 +193,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -288,17 +289,18 @@ def main():
     halb = torch.from_numpy(np.ascontiguousarray(scene.albedo)).pin_memory()
     hbox = torch.from_numpy(np.ascontiguousarray(scene.boxes)).pin_memory()
     hrgb = torch.empty(3, P, dtype=torch.float32).pin_memory()
-    for _ in range(2):
+    for _ in range(0 if args.no_e2e else 2):
         rll.render_pass_host(ctx, grid, tree, hpos, hnrm, halb, hbox, scene.seed, frame, S, hrgb)
         frame += 1
-    e2e_ms = []
-    for _ in range(max(3, args.steps // 2)):
+    e2e_ms = [float("nan")]
+    for _ in range(0 if args.no_e2e else max(3, args.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rll.render_pass_host(ctx, grid, tree, hpos, hnrm, halb, hbox, scene.seed, frame, S, hrgb)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         frame += 1
+    e2e_ms = [t for t in e2e_ms if t == t] or [float("nan")]
     e2e_step = statistics.mean(e2e_ms)
 
     out = None
