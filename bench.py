@@ -194,6 +194,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sample-min-blocks", type=int, default=4)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -217,6 +218,7 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     ctx = rll.Context(local, stream)
+    ctx.set_option("sample_min_blocks", args.sample_min_blocks)
 
     def T(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -226,7 +228,8 @@ def main():
     P, S = scene.n_points, scene.spp
     tree = rll.Tree(ctx, tri, em)
     g = scene.grid
-    params = rll.grid_params(g.table_size, g.cut_size, g.origin, g.cell_size, g.normal_bins, g.jitter)
+    params = rll.grid_params(g.table_size, g.cut_size, g.origin, g.cell_size, g.normal_bins, g.jitter,
+                             q_init=g.q_init)
     grid = rll.Grid(ctx, tree, params)
     rgb = torch.empty(3, P, device=dev)
     key = torch.empty(P * S, dtype=torch.int32, device=dev)

@@ -187,7 +187,7 @@ class Grid:
         self.params = dict(origin=tuple(float(o) for o in origin), cell_size=float(cell_size),
                            normal_bins=int(normal_bins), jitter=bool(jitter), mode=mode,
                            reward=reward, precision=precision, alpha=float(alpha), T=float(T),
-                           eps=float(eps))
+                           eps=float(eps), q_init=float(q_init))
         self._s = _Grid(H, M, m, (ctypes.c_float * 3)(*origin), float(cell_size), int(normal_bins),
                         int(bool(jitter)), MODE[mode], REWARD[reward], PREC[precision],
                         float(alpha), float(T), float(eps), _p(self.keys), _p(self.cut),
@@ -197,7 +197,8 @@ class Grid:
     def for_scene(cls, tree, scene, **kw):
         g = scene.grid
         args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin,
-                    cell_size=g.cell_size, normal_bins=g.normal_bins, jitter=g.jitter)
+                    cell_size=g.cell_size, normal_bins=g.normal_bins, jitter=g.jitter,
+                    q_init=g.q_init)
         args.update(kw)
         return cls(tree, **args)
 

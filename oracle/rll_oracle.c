@@ -600,45 +600,38 @@ int64_t orc_lookup_insert(orc_grid* g, uint64_t key)
 /*   I = phi * Brecv * Bemit / d^2,  d = AABB centre - x, r = half diagonal,  */
 /*   sin(beta) = r / |d|; Brecv bounds max(0, n . w) and Bemit bounds         */
 /*   max(0, -n_l . w) over directions w within beta of d/|d| and normals n_l */
-/*   within the node's cone; a point inside the bounding sphere gets          */
-/*   I = phi / r^2. Angle sums by the addition formulas (no trigonometry).   */
+/*   within the node's cone (axis, half angle theta); a point inside the      */
+/*   bounding sphere gets I = phi / r^2. Angle sums by the addition formulas; */
+/*   every cosine and sine is carried multiplied by |d| so that only         */
+/*   sqrt(d^2 - r^2) and two more square roots and one division are needed.   */
+/*   Node constants (centre, r^2, r, sin theta) are binary32 values of the    */
+/*   node record, computed with the same operations on both sides.           */
 /* ------------------------------------------------------------------------ */
 float orc_importance32(const float* r, const float x[3], const float n[3])
 {
     float cx = (r[0] + r[3]) * 0.5f, cy = (r[1] + r[4]) * 0.5f, cz = (r[2] + r[5]) * 0.5f;
-    float dx = cx - x[0], dy = cy - x[1], dz = cz - x[2];
-    float d2 = (dx * dx + dy * dy) + dz * dz;
     float ex = r[3] - r[0], ey = r[4] - r[1], ez = r[5] - r[2];
     float r2 = 0.25f * ((ex * ex + ey * ey) + ez * ez);
-    float phi = r[6];
-    if (d2 <= r2) return phi / fmaxf(r2, 1e-30f);
-    float inv = 1.0f / sqrtf(d2);
-    float sb2 = r2 / d2;
-    float cb = sqrtf(1.0f - sb2);
-    float sb = sqrtf(sb2);
-    float cg = ((n[0] * dx + n[1] * dy) + n[2] * dz) * inv;
-    cg = fminf(1.0f, fmaxf(-1.0f, cg));
-    float sg = sqrtf(fmaxf(0.0f, 1.0f - cg * cg));
-    float brecv = (cg >= cb) ? 1.0f : fmaxf(0.0f, cg * cb + sg * sb);
+    float rr = sqrtf(r2);
     float ct = r[10];
-    float bemit;
-    if (ct <= -cb) {
-        bemit = 1.0f;
-    } else {
-        float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
-        float cphi = ct * cb - st * sb;
-        float t = (r[7] * dx + r[8] * dy) + r[9] * dz;
-        float cpsi = (-t) * inv;
-        cpsi = fminf(1.0f, fmaxf(-1.0f, cpsi));
-        if (cphi <= cpsi) {
-            bemit = 1.0f;
-        } else {
-            float spsi = sqrtf(fmaxf(0.0f, 1.0f - cpsi * cpsi));
-            float sphi = st * cb + ct * sb;
-            bemit = fmaxf(0.0f, cpsi * cphi + spsi * sphi);
-        }
-    }
-    return ((phi * brecv) * bemit) / d2;
+    float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    float phi = r[6];
+    float dx = cx - x[0], dy = cy - x[1], dz = cz - x[2];
+    float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    if (d2 <= r2) return phi / fmaxf(r2, 1e-30f);
+    float cb = sqrtf(d2 - r2);                              /* |d| cos(beta)        */
+    float nd = fmaf(n[2], dz, fmaf(n[1], dy, n[0] * dx));   /* |d| cos(gamma)       */
+    float A;                                                /* |d|^2 Brecv          */
+    if (nd >= cb) A = d2;
+    else A = fmaxf(0.0f, fmaf(nd, cb, sqrtf(fmaxf(0.0f, fmaf(-nd, nd, d2))) * rr));
+    float ad = -fmaf(r[9], dz, fmaf(r[8], dy, r[7] * dx));  /* |d| cos(psi)         */
+    float sphi = fmaf(st, cb, ct * rr);                     /* |d| sin(theta+beta)  */
+    float cphi = fmaf(ct, cb, -(st * rr));                  /* |d| cos(theta+beta)  */
+    float B;                                                /* |d|^2 Bemit          */
+    if (sphi <= 0.0f || cphi <= ad) B = d2;
+    else B = fmaxf(0.0f, fmaf(ad, cphi, sqrtf(fmaxf(0.0f, fmaf(-ad, ad, d2))) * sphi));
+    float inv = 1.0f / d2;
+    return ((phi * (A * inv)) * (B * inv)) * inv;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -191,6 +191,18 @@ int rll_ctx_set_stream(rll_ctx* ctx, void* cuda_stream)
     return RLL_OK;
 }
 
+int rll_ctx_set_option(rll_ctx* ctx, const char* name, int64_t value)
+{
+    if (!ctx || !name) return RLL_E_INVALID;
+    const std::string n(name);
+    if (n == "sample_min_blocks") {
+        if (value != 3 && value != 4) return fail(ctx, RLL_E_INVALID, "sample_min_blocks must be 3 or 4");
+        ctx->sample_min_blocks = (int)value;
+        return RLL_OK;
+    }
+    return fail(ctx, RLL_E_INVALID, "unknown option " + n);
+}
+
 int rll_ctx_destroy(rll_ctx* ctx)
 {
     if (!ctx) return RLL_OK;

@@ -167,30 +167,56 @@ __global__ void k_from_float(int64_t total, const float* __restrict__ q, const f
     }
 }
 
-__global__ void k_cell_heads(const uint32_t* __restrict__ sk, int64_t n, uint32_t HM, uint32_t M,
-                             uint32_t* __restrict__ touched, uint32_t* __restrict__ touched_start,
-                             uint32_t* __restrict__ n_touched)
+// one block of 256 threads covers 256 * kHeadItems sorted records; one
+// global atomic per block reserves the block's share of the touched list
+constexpr int kHeadItems = 8;
+__global__ void __launch_bounds__(256) k_cell_heads(const uint32_t* __restrict__ sk, int64_t n, uint32_t HM, uint32_t M,
+                                                    uint32_t* __restrict__ touched, uint32_t* __restrict__ touched_start,
+                                                    uint32_t* __restrict__ n_touched)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool head = false;
-    uint32_t cell = 0;
-    if (i < n) {
-        const uint32_t key = sk[i];
-        if (key < HM) {
-            cell = key / M;
-            head = (i == 0) || (sk[i - 1] / M != cell);
+    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base_i = (int64_t)blockIdx.x * 256 * kHeadItems;
+    bool head[kHeadItems];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kHeadItems; ++j) {
+        const int64_t i = base_i + (int64_t)j * 256 + threadIdx.x;
+        head[j] = false;
+        if (i < n) {
+            const uint32_t key = sk[i];
+            if (key < HM) head[j] = (i == 0) || (sk[i - 1] / M != key / M);
         }
+        cnt += head[j];
     }
-    const uint32_t mask = __ballot_sync(0xffffffffu, head);
-    if (!mask) return;
-    const int lane = threadIdx.x & 31;
-    uint32_t base = 0;
-    if (lane == __ffs(mask) - 1) base = atomicAdd(n_touched, (uint32_t)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
-    if (head) {
-        const uint32_t slot = base + __popc(mask & lanemask_lt());
-        touched[slot] = cell;
+    // block exclusive scan of the per-thread counts
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t v = s_warp[w];
+            s_warp[w] = tot;
+            tot += v;
+        }
+        s_base = tot ? atomicAdd(n_touched, tot) : 0u;
+    }
+    __syncthreads();
+    uint32_t slot = s_base + s_warp[warp] + x - cnt;
+#pragma unroll
+    for (int j = 0; j < kHeadItems; ++j) {
+        if (!head[j]) continue;
+        const int64_t i = base_i + (int64_t)j * 256 + threadIdx.x;
+        touched[slot] = sk[i] / M;
         touched_start[slot] = (uint32_t)i;
+        ++slot;
     }
 }
 
@@ -331,9 +357,9 @@ k_split(uint32_t M, uint32_t m, const uint32_t* __restrict__ touched, const uint
         }
         __syncwarp();
         ArgBest hi{0.0f, 0xFFFFFFFFu}, lo{0.0f, 0xFFFFFFFFu};
+        const uint32_t n_internal = (uint32_t)((n_nodes - 1) / 2);  // ids below are internal nodes
         for (uint32_t s = lane; s < m; s += 32) {
-            const NodeRec& r = nodes[cs[s]];
-            if (r.end - r.begin > 1u && (hi.i == 0xFFFFFFFFu || q[s] > hi.v)) {
+            if (cs[s] < n_internal && (hi.i == 0xFFFFFFFFu || q[s] > hi.v)) {
                 hi.v = q[s];
                 hi.i = s;
             }
@@ -424,8 +450,8 @@ int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec
     e = radix_sort_pairs(s, rec_key, reinterpret_cast<const uint32_t*>(rec_val), n, key_bits((uint64_t)HM + 1), HM,
                          ws, &sk, &sv);
     if (e != cudaSuccess) return check_cuda(ctx, e, "radix sort (records)");
-    k_cell_heads<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sk, n, HM, g->M, g->touched, g->touched_start,
-                                                            g->n_touched);
+    k_cell_heads<<<(unsigned)((n + 256 * kHeadItems - 1) / (256 * kHeadItems)), 256, 0, s>>>(
+        sk, n, HM, g->M, g->touched, g->touched_start, g->n_touched);
     const int blocks = device_sm_count(g->device) * 8;
     using T = typename Store<P>::T;
     k_learn_cells<P><<<blocks, kWarpsPerBlock * 32, 0, s>>>(sk, sv, n, HM, g->M, g->m, g->touched, g->touched_start,

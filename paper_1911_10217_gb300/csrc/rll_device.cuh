@@ -41,6 +41,23 @@ struct __align__(16) NodeRec {
 };
 static_assert(sizeof(NodeRec) == 64, "NodeRec must be 64 bytes");
 
+// Descent record of one child, 64 bytes: the constants of the importance
+// bound precomputed (binary32, same operations as on the fly). The records
+// of both children of internal node i are pairs[2i], pairs[2i+1]: one
+// aligned 128-byte line per descent level.
+struct __align__(16) DescRec {
+    float c[3];      // AABB centre
+    float r2;        // squared half diagonal
+    float r;         // half diagonal
+    float phi;       // power bound
+    float axis[3];   // cone axis
+    float cos_t;     // cone cos(theta)
+    float sin_t;     // cone sin(theta)
+    uint32_t id;     // node id
+    uint32_t pad[4];
+};
+static_assert(sizeof(DescRec) == 64, "DescRec must be 64 bytes");
+
 // Sorted light, 64 bytes.
 struct __align__(16) LightRec {
     float v0[3];
@@ -173,48 +190,47 @@ __device__ __forceinline__ unsigned long long cell_key(float px, float py, float
 }
 
 // ---------------------------------------------------------------- bounds
+// Descent constants of a node (centre, r^2, r, sin theta).
+__device__ __forceinline__ DescRec make_desc(const NodeRec& n)
+{
+    DescRec d;
+    const float ex = fsub(n.bmax[0], n.bmin[0]), ey = fsub(n.bmax[1], n.bmin[1]), ez = fsub(n.bmax[2], n.bmin[2]);
+    for (int k = 0; k < 3; ++k) {
+        d.c[k] = fmul(fadd(n.bmin[k], n.bmax[k]), 0.5f);
+        d.axis[k] = n.axis[k];
+    }
+    d.r2 = fmul(0.25f, fadd(fadd(fmul(ex, ex), fmul(ey, ey)), fmul(ez, ez)));
+    d.r = fsqrt(d.r2);
+    d.phi = n.phi;
+    d.cos_t = n.cos_t;
+    d.sin_t = fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(n.cos_t, n.cos_t))));
+    d.id = n.id;
+    d.pad[0] = d.pad[1] = d.pad[2] = d.pad[3] = 0u;
+    return d;
+}
+
 // Unoccluded importance of a node seen from (x, n): power times the receiver
 // and emitter cosine bounds over the node's bounding sphere, over distance^2.
-__device__ __forceinline__ float importance(const NodeRec& r, float x0, float x1, float x2, float n0,
+// Cosines and sines are carried multiplied by |d| (2-3 square roots, one
+// division).
+__device__ __forceinline__ float importance(const DescRec& r, float x0, float x1, float x2, float n0,
                                             float n1, float n2)
 {
-    const float cx = fmul(fadd(r.bmin[0], r.bmax[0]), 0.5f);
-    const float cy = fmul(fadd(r.bmin[1], r.bmax[1]), 0.5f);
-    const float cz = fmul(fadd(r.bmin[2], r.bmax[2]), 0.5f);
-    const float dx = fsub(cx, x0), dy = fsub(cy, x1), dz = fsub(cz, x2);
-    const float d2 = fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz));
-    const float ex = fsub(r.bmax[0], r.bmin[0]), ey = fsub(r.bmax[1], r.bmin[1]),
-                ez = fsub(r.bmax[2], r.bmin[2]);
-    const float r2 = fmul(0.25f, fadd(fadd(fmul(ex, ex), fmul(ey, ey)), fmul(ez, ez)));
-    const float phi = r.phi;
-    if (d2 <= r2) return fdiv(phi, fmaxf(r2, 1e-30f));
-    const float inv = fdiv(1.0f, fsqrt(d2));
-    const float sb2 = fdiv(r2, d2);
-    const float cb = fsqrt(fsub(1.0f, sb2));
-    const float sb = fsqrt(sb2);
-    float cg = fmul(fadd(fadd(fmul(n0, dx), fmul(n1, dy)), fmul(n2, dz)), inv);
-    cg = fminf(1.0f, fmaxf(-1.0f, cg));
-    const float sg = fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(cg, cg))));
-    const float brecv = (cg >= cb) ? 1.0f : fmaxf(0.0f, fadd(fmul(cg, cb), fmul(sg, sb)));
-    const float ct = r.cos_t;
-    float bemit;
-    if (ct <= -cb) {
-        bemit = 1.0f;
-    } else {
-        const float st = fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(ct, ct))));
-        const float cphi = fsub(fmul(ct, cb), fmul(st, sb));
-        const float t = fadd(fadd(fmul(r.axis[0], dx), fmul(r.axis[1], dy)), fmul(r.axis[2], dz));
-        float cpsi = fmul(-t, inv);
-        cpsi = fminf(1.0f, fmaxf(-1.0f, cpsi));
-        if (cphi <= cpsi) {
-            bemit = 1.0f;
-        } else {
-            const float spsi = fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(cpsi, cpsi))));
-            const float sphi = fadd(fmul(st, cb), fmul(ct, sb));
-            bemit = fmaxf(0.0f, fadd(fmul(cpsi, cphi), fmul(spsi, sphi)));
-        }
-    }
-    return fdiv(fmul(fmul(phi, brecv), bemit), d2);
+    const float dx = fsub(r.c[0], x0), dy = fsub(r.c[1], x1), dz = fsub(r.c[2], x2);
+    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, fmul(dx, dx)));
+    if (d2 <= r.r2) return fdiv(r.phi, fmaxf(r.r2, 1e-30f));
+    const float cb = fsqrt(fsub(d2, r.r2));
+    const float nd = __fmaf_rn(n2, dz, __fmaf_rn(n1, dy, fmul(n0, dx)));
+    float A = d2;
+    if (nd < cb) A = fmaxf(0.0f, __fmaf_rn(nd, cb, fmul(fsqrt(fmaxf(0.0f, __fmaf_rn(-nd, nd, d2))), r.r)));
+    const float ad = -__fmaf_rn(r.axis[2], dz, __fmaf_rn(r.axis[1], dy, fmul(r.axis[0], dx)));
+    const float sphi = __fmaf_rn(r.sin_t, cb, fmul(r.cos_t, r.r));
+    const float cphi = __fmaf_rn(r.cos_t, cb, -fmul(r.sin_t, r.r));
+    float B = d2;
+    if (!(sphi <= 0.0f || cphi <= ad))
+        B = fmaxf(0.0f, __fmaf_rn(ad, cphi, fmul(fsqrt(fmaxf(0.0f, __fmaf_rn(-ad, ad, d2))), sphi)));
+    const float inv = fdiv(1.0f, d2);
+    return fmul(fmul(fmul(r.phi, fmul(A, inv)), fmul(B, inv)), inv);
 }
 
 // ---------------------------------------------------------------- storage

@@ -11,6 +11,7 @@
 
 namespace rll {
 struct NodeRec;
+struct DescRec;
 struct LightRec;
 }  // namespace rll
 
@@ -25,13 +26,15 @@ struct rll_ctx {
     // staging for rll_render_pass_host
     void* stage = nullptr;
     size_t stage_bytes = 0;
+    // launch tuning (rll_ctx_set_option)
+    int sample_min_blocks = 4;
 };
 
 struct rll_tree {
     int device = 0;
     int64_t n = 0;
     rll::NodeRec* nodes = nullptr;   // [2n-1] every node
-    rll::NodeRec* pairs = nullptr;   // [2(n-1)] children of internal i at 2i, 2i+1
+    rll::DescRec* pairs = nullptr;   // [2(n-1)] descent records of the children of internal i at 2i, 2i+1
     rll::LightRec* lights = nullptr; // [n] sorted lights
     uint32_t* perm = nullptr;        // [n] sorted -> input index
     int32_t* left = nullptr;         // [n-1]

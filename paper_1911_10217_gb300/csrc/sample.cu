@@ -39,7 +39,7 @@ struct SampleArgs {
     uint32_t nb;
     uint32_t jitter;
     uint32_t reward_mode;
-    const NodeRec* pairs;
+    const DescRec* pairs;
     const NodeRec* nodes;
     const LightRec* lights;
     const float* light_cdf;
@@ -71,9 +71,9 @@ __device__ __forceinline__ int64_t lookup_insert(unsigned long long* keys, uint3
     return -1;
 }
 
-__device__ __forceinline__ NodeRec load_node(const NodeRec* p)
+__device__ __forceinline__ DescRec load_desc(const DescRec* p)
 {
-    NodeRec r;
+    DescRec r;
     const float4* s = reinterpret_cast<const float4*>(p);
     float4* d = reinterpret_cast<float4*>(&r);
 #pragma unroll
@@ -144,8 +144,10 @@ __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1,
     return o;
 }
 
-template <int P, int MODE, bool DBG>
-__global__ void __launch_bounds__(kThreads) k_sample(SampleArgs a)
+// MINB: resident blocks per SM the register allocation is held to (3: no
+// cap at 256 threads, 4: at most 64 registers per thread).
+template <int P, int MODE, bool DBG, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_sample(SampleArgs a)
 {
     using T = typename Store<P>::T;
     extern __shared__ float s_box[];
@@ -212,8 +214,8 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleArgs a)
         } else {
             uint32_t level = 0;
             while ((int64_t)node < nl1) {
-                const NodeRec L = load_node(a.pairs + 2 * (int64_t)node);
-                const NodeRec R = load_node(a.pairs + 2 * (int64_t)node + 1);
+                const DescRec L = load_desc(a.pairs + 2 * (int64_t)node);
+                const DescRec R = load_desc(a.pairs + 2 * (int64_t)node + 1);
                 const float il = importance(L, x0, x1, x2, n0, n1, n2);
                 const float ir = importance(R, x0, x1, x2, n0, n1, n2);
                 float wl = il, wr = ir;
@@ -301,20 +303,26 @@ __global__ void __launch_bounds__(kThreads) k_sample_power(SampleArgs a, int32_t
     a.rgb[2 * np + p] = acc2 * inv_spp;
 }
 
-template <int P, int MODE, bool DBG>
+template <int P, int MODE, bool DBG, int MINB>
 cudaError_t launch(const SampleArgs& a, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)((a.n_points + kThreads - 1) / kThreads);
-    k_sample<P, MODE, DBG><<<blocks, kThreads, sizeof(float) * 6 * a.n_boxes, s>>>(a);
+    k_sample<P, MODE, DBG, MINB><<<blocks, kThreads, sizeof(float) * 6 * a.n_boxes, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int P>
-cudaError_t launch_p(const SampleArgs& a, int mode, bool dbg, cudaStream_t s)
+template <int P, int MODE>
+cudaError_t launch_m(const SampleArgs& a, bool dbg, int minb, cudaStream_t s)
 {
-    if (mode == RLL_MODE_UNIFORM)
-        return dbg ? launch<P, RLL_MODE_UNIFORM, true>(a, s) : launch<P, RLL_MODE_UNIFORM, false>(a, s);
-    return dbg ? launch<P, RLL_MODE_DESCENT, true>(a, s) : launch<P, RLL_MODE_DESCENT, false>(a, s);
+    if (dbg) return launch<P, MODE, true, 3>(a, s);
+    return minb >= 4 ? launch<P, MODE, false, 4>(a, s) : launch<P, MODE, false, 3>(a, s);
+}
+
+template <int P>
+cudaError_t launch_p(const SampleArgs& a, int mode, bool dbg, int minb, cudaStream_t s)
+{
+    if (mode == RLL_MODE_UNIFORM) return launch_m<P, RLL_MODE_UNIFORM>(a, dbg, minb, s);
+    return launch_m<P, RLL_MODE_DESCENT>(a, dbg, minb, s);
 }
 
 }  // namespace
@@ -364,10 +372,11 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
         a.dbg_pin = dbg->p_in;
     }
     cudaError_t e;
+    const int minb = ctx->sample_min_blocks;
     switch (g->p.precision) {
-    case RLL_PREC_FP16: e = launch_p<RLL_PREC_FP16>(a, g->p.in_cluster_mode, use_dbg, ctx->stream); break;
-    case RLL_PREC_BF16: e = launch_p<RLL_PREC_BF16>(a, g->p.in_cluster_mode, use_dbg, ctx->stream); break;
-    default: e = launch_p<RLL_PREC_FP32>(a, g->p.in_cluster_mode, use_dbg, ctx->stream);
+    case RLL_PREC_FP16: e = launch_p<RLL_PREC_FP16>(a, g->p.in_cluster_mode, use_dbg, minb, ctx->stream); break;
+    case RLL_PREC_BF16: e = launch_p<RLL_PREC_BF16>(a, g->p.in_cluster_mode, use_dbg, minb, ctx->stream); break;
+    default: e = launch_p<RLL_PREC_FP32>(a, g->p.in_cluster_mode, use_dbg, minb, ctx->stream);
     }
     return check_cuda(ctx, e, "sample_and_shade");
 }

@@ -265,12 +265,12 @@ __global__ void k_finalize(int64_t nn, NodeRec* __restrict__ nodes, const int* _
 }
 
 __global__ void k_pairs(int64_t n, const NodeRec* __restrict__ nodes, const int32_t* __restrict__ left,
-                        const int32_t* __restrict__ right, NodeRec* __restrict__ pairs, float* __restrict__ leaf_phi)
+                        const int32_t* __restrict__ right, DescRec* __restrict__ pairs, float* __restrict__ leaf_phi)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n - 1) {
-        pairs[2 * i] = nodes[left[i]];
-        pairs[2 * i + 1] = nodes[right[i]];
+        pairs[2 * i] = make_desc(nodes[left[i]]);
+        pairs[2 * i + 1] = make_desc(nodes[right[i]]);
     }
     if (i < n) leaf_phi[i] = nodes[n - 1 + i].phi;
 }
@@ -300,7 +300,7 @@ int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
     e = cudaMalloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 64);               \
     if (e != cudaSuccess) return check_cuda(ctx, e, "cudaMalloc(tree)");
     RLL_ALLOC(t->nodes, sizeof(NodeRec) * nn);
-    RLL_ALLOC(t->pairs, sizeof(NodeRec) * 2 * (n - 1));
+    RLL_ALLOC(t->pairs, sizeof(DescRec) * 2 * (n - 1));
     RLL_ALLOC(t->lights, sizeof(LightRec) * n);
     RLL_ALLOC(t->perm, sizeof(uint32_t) * n);
     RLL_ALLOC(t->left, sizeof(int32_t) * (n - 1));

@@ -25,7 +25,7 @@ REWARD = {"cluster": 0, "literal": 1}
 
 # every symbol declared in include/rll.h
 EXPORTS = [
-    "rll_ctx_create", "rll_ctx_set_stream", "rll_ctx_destroy", "rll_last_error", "rll_sync_status",
+    "rll_ctx_create", "rll_ctx_set_stream", "rll_ctx_set_option", "rll_ctx_destroy", "rll_last_error", "rll_sync_status",
     "rll_build_light_tree", "rll_tree_update_emission", "rll_tree_num_lights", "rll_tree_export",
     "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_export", "rll_grid_import",
     "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_power",
@@ -74,6 +74,7 @@ def load(build_if_missing: bool = True):
                              ctypes.c_uint64)
     L.rll_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P]
     L.rll_ctx_set_stream.argtypes = [P, P]
+    L.rll_ctx_set_option.argtypes = [P, ctypes.c_char_p, I64]
     L.rll_ctx_destroy.argtypes = [P]
     L.rll_last_error.argtypes = [P]
     L.rll_last_error.restype = ctypes.c_char_p
@@ -150,6 +151,9 @@ class Context:
 
     def set_stream(self, stream):
         self._check(self.lib.rll_ctx_set_stream(self.h, self._stream_ptr(stream)))
+
+    def set_option(self, name: str, value: int):
+        self._check(self.lib.rll_ctx_set_option(self.h, name.encode(), int(value)))
 
     def _check(self, rc):
         if rc != RLL_OK:

@@ -34,6 +34,7 @@ class GridConfig:
     cell_size: float         # h
     normal_bins: int         # quantisation bins per octahedral axis
     jitter: bool
+    q_init: float = 1e-3     # Q of a new cell's leaves (below the reward scale of these scenes)
 
 
 @dataclasses.dataclass
@@ -255,15 +256,17 @@ def frame_scene(seed: int = 1, width: int = 1920, height: int = 1080, n_patches:
     """Frame-scale static scene: 64K emissive triangles in 64 clustered patches,
     64 occluder boxes forming 16 walled cells, a 1920 x 1080 G-buffer on 16
     random planes (normals jittered +-15 deg, albedo U[0.2, 0.9]); 2^20-entry
-    hash grid, cut size 32, 1 sample per point per frame."""
+    hash grid, cut size 32, 1 sample per point per frame. The cell size
+    scales with the resolution so that a cell keeps the same pixel count."""
     rng = np.random.default_rng(seed)
     c = 4
     boxes = _room_cells(rng, c, n_boxes)
     tris = _emitter_patches(rng, c, n_patches, tris_per_patch)
     emission = rng.uniform(0.5, 2.0, size=(tris.shape[0], 3)).astype(np.float32)
     pos, nrm, albedo = _gbuffer_planes(rng, width, height, c)
+    # cells of ~43 x 43 pixels on the planes: ~100 samples per cell per frame
     grid = GridConfig(table_size=table_size, cut_size=cut_size, origin=(0.0, 0.0, 0.0),
-                      cell_size=1.0 / 128.0, normal_bins=8, jitter=True)
+                      cell_size=1.0 / 64.0 * (1920.0 / width), normal_bins=2, jitter=True)
     return Scene("frame", tris, emission, boxes, pos, nrm, albedo, grid, spp=1,
                  frames=frames, seed=seed, width=width, height=height)
 
@@ -285,7 +288,7 @@ def dynamic_scene(seed: int = 2, width: int = 3840, height: int = 2160, n_patche
     phase = rng.uniform(0.0, 2.0 * math.pi, size=n).astype(np.float32)
     pos, nrm, albedo = _gbuffer_planes(rng, width, height, c)
     grid = GridConfig(table_size=table_size, cut_size=cut_size, origin=(0.0, 0.0, 0.0),
-                      cell_size=1.0 / 256.0, normal_bins=8, jitter=True)
+                      cell_size=1.0 / 64.0 * (1920.0 / width), normal_bins=2, jitter=True)
     return Scene("dynamic", tris, emission, boxes, pos, nrm, albedo, grid, spp=1,
                  frames=frames, seed=seed, width=width, height=height,
                  blink_omega=omega, blink_phase=phase, blink_mask=mask)
@@ -300,7 +303,6 @@ def small_frame_scene(seed: int = 3, width: int = 96, height: int = 64, n_patche
                     tris_per_patch=tris_per_patch, n_boxes=n_boxes, table_size=table_size,
                     cut_size=cut_size, frames=4)
     s.name = "small_frame"
-    s.grid.cell_size = 1.0 / 32.0
     s.spp = spp
     return s
 

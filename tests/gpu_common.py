@@ -18,7 +18,7 @@ def device_scene(scene, dev, emission=None):
 def params_for(rll, scene, **kw):
     g = scene.grid
     args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin, cell_size=g.cell_size,
-                normal_bins=g.normal_bins, jitter=g.jitter)
+                normal_bins=g.normal_bins, jitter=g.jitter, q_init=g.q_init)
     args.update(kw)
     return rll.grid_params(**args)
 
@@ -100,6 +100,6 @@ def clone_oracle_grid(O, og):
     p = og.params
     g2 = O.Grid(og.tree, og.H, og.M, origin=p["origin"], cell_size=p["cell_size"],
                 normal_bins=p["normal_bins"], jitter=p["jitter"], mode=p["mode"], reward=p["reward"],
-                precision=p["precision"], alpha=p["alpha"], T=p["T"], eps=p["eps"])
+                precision=p["precision"], alpha=p["alpha"], T=p["T"], eps=p["eps"], q_init=p["q_init"])
     g2.copy_state_from(og.keys, og.cut, og.Q, og.C)
     return g2
