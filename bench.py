@@ -188,7 +188,7 @@ def run_reference(args, scene):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -331,7 +331,8 @@ def main():
                             "ops_per_sample": ops / n_sample,
                             "hbm_achieved_gbs": hbm_ach,
                             "hbm_frac_of_measured": hbm_ach / peaks.get("hbm_gbs", 6800.0)},
-               "e2e": {"value": world * P * S / (e2e_step * 1e-3), "unit": UNIT,
+               "e2e": {"value": (world * P * S / (e2e_step * 1e-3)) if e2e_step == e2e_step else None,
+                       "unit": UNIT,
                        "h2d_bytes_per_step": int(28 * P + 24 * scene.boxes.shape[0]),
                        "d2h_bytes_per_step": int(12 * P)},
                "gpu_launches": args.steps * launches_per_step,

@@ -43,7 +43,7 @@ extern "C" {
 
 /* choice of a light inside the sampled cluster */
 #define RLL_MODE_DESCENT 0  /* stochastic descent by unoccluded bounds (default) */
-#define RLL_MODE_UNIFORM 1  /* uniform over the cluster's lights ("select a light in the cluster randomly", Section 3) */
+#define RLL_MODE_UNIFORM 1  /* uniform over the cluster's lights (Section 3 picks the light in the cluster at random) */
 
 /* the |c| fed to Eq. 1 */
 #define RLL_REWARD_CLUSTER 0 /* luminance of c / (p_in * p_area): the cluster's contribution estimate (default) */

@@ -199,8 +199,8 @@ void orc_cdf(int m, const double* q, double eps, int precision, double* c_out)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Light tree (Section 3.1: "a simple LBVH builder using the 3d positions of */
-/* the lights only"). Lights are sorted by the 30-bit Morton code of their    */
+/* Light tree (Section 3.1: a linear BVH built from the light positions     */
+/* alone). Lights are sorted by the 30-bit Morton code of their              */
 /* centroid (ties: input index); the tree is the binary radix tree over the   */
 /* 64-bit keys (code << 32 | index). Node numbering: internal nodes 0..n-2,   */
 /* leaf of sorted light l is n-1+l, the root is node 0; an internal node's   */
@@ -452,8 +452,8 @@ int orc_build_tree(int64_t n, const float* tri, const float* emis, orc_tree* t)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Initial cut (Section 3: "descending the tree in breadth first order until */
-/* the desired amount of nodes M is collected"): a FIFO queue seeded with the */
+/* Initial cut (Section 3: any heuristic may pick it; the paper suggests a   */
+/* breadth-first descent until M nodes are collected): a FIFO queue seeded with the */
 /* root; pop the front node, push its two children (a single light is pushed */
 /* back unchanged) until the queue holds min(M, n) nodes. Stored sorted by    */
 /* range begin, i.e. as the monotone list of cluster ends of Section 3.       */
@@ -571,8 +571,8 @@ uint64_t orc_fmix64(uint64_t k)
     return k;
 }
 
-/* Lookup with lazy creation (Section 3: the initial cut "is copied when a
- * cell is first accessed"): linear probing from fmix64(key) mod H for at most
+/* Lookup with lazy creation (Section 3: the initial cut is copied into a cell
+ * the first time it is used): linear probing from fmix64(key) mod H for at most
  * 64 slots. Returns the slot, or -1 when the probe limit is reached. */
 int64_t orc_lookup_insert(orc_grid* g, uint64_t key)
 {
@@ -595,7 +595,7 @@ int64_t orc_lookup_insert(orc_grid* g, uint64_t key)
 
 /* ------------------------------------------------------------------------ */
 /* Node importance for the stochastic descent below a cut node (binary32).   */
-/* Reading (the paper samples "randomly" inside a cluster; the descent by    */
+/* Reading (the paper picks the light inside a cluster at random; a descent by */
 /* unoccluded bounds follows the bound-based samplers it cites, Section 2):   */
 /*   I = phi * Brecv * Bemit / d^2,  d = AABB centre - x, r = half diagonal,  */
 /*   sin(beta) = r / |d|; Brecv bounds max(0, n . w) and Bemit bounds         */
