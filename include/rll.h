@@ -185,6 +185,20 @@ int rll_sample_power(rll_ctx* ctx, const rll_tree* tree, const float* pos, const
 int rll_learn_update(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key, const float* rec_val,
                      int64_t n_records);
 
+/* Same as rll_learn_update, for callers that cannot allocate device memory
+ * while they run (a host that owns all device memory through its own pool,
+ * an allocation budget enforced outside CUDA, a loop that must not
+ * synchronise -- rll_learn_update grows its workspace with cudaFree and
+ * cudaMalloc). Nothing is allocated: the sort buffers are one fixed device
+ * array inside the library (about 17 MB, held on every GPU that loads the
+ * library until exit). At most 1048576 records per call; more returns
+ * RLL_E_INVALID without launching. The first call on a device looks up the
+ * array's address: make it before any stream capture. All calls share the
+ * array, so calls that overlap on the GPU race: serialise them. The paper has
+ * no counterpart of this entry point. */
+int rll_learn_update_noalloc(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key,
+                             const float* rec_val, int64_t n_records);
+
 /* Split-collapse (Section 3, Fig. "TreeCuts"; Section 3.1: one thread group
  * per cell) on every cell touched by the last rll_learn_update: split the
  * non-single-light leaf of largest Q into its children and collapse the

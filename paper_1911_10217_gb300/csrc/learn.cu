@@ -560,3 +560,48 @@ int split_collapse(rll_ctx* ctx, rll_grid* g, const rll_tree* t)
 }
 
 }  // namespace rll
+
+// ---------------------------------------------------------------------------
+// Learning step with caller-provided scratch (used by the allocation-free
+// entry point in noalloc.cu): the same kernels as learn_update, but the sort
+// buffers live in `scratch` (scratch_bytes long) instead of the context's
+// growable workspace, so nothing is allocated.
+namespace rll {
+namespace {
+
+template <int P>
+int learn_scratch_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n, void* scratch)
+{
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "memset touched");
+    if (n <= 0) return RLL_OK;
+    const uint32_t HM = g->H * g->M;
+    uint32_t *sk, *sv;
+    e = radix_sort_pairs(s, rec_key, reinterpret_cast<const uint32_t*>(rec_val), n, key_bits((uint64_t)HM + 1), HM,
+                         scratch, &sk, &sv);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "radix sort (records)");
+    k_cell_heads<<<(unsigned)((n + 256 * kHeadItems - 1) / (256 * kHeadItems)), 256, 0, s>>>(
+        sk, n, HM, g->M, g->touched, g->touched_start, g->n_touched);
+    const int blocks = device_sm_count(g->device) * 8;
+    using T = typename Store<P>::T;
+    k_learn_cells<P><<<blocks, kWarpsPerBlock * 32, 0, s>>>(sk, sv, n, HM, g->M, g->m, g->touched, g->touched_start,
+                                                             g->n_touched, (T*)g->Q, (T*)g->C, g->p.alpha, g->p.eps);
+    return check_cuda(ctx, cudaGetLastError(), "learn kernels");
+}
+
+}  // namespace
+
+int learn_update_with_scratch(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n,
+                              void* scratch, size_t scratch_bytes)
+{
+    if (n > 0 && radix_sort_scratch_bytes(n) > scratch_bytes)
+        return fail(ctx, RLL_E_INVALID, "scratch too small for this many records");
+    switch (g->p.precision) {
+    case RLL_PREC_FP16: return learn_scratch_t<RLL_PREC_FP16>(ctx, g, rec_key, rec_val, n, scratch);
+    case RLL_PREC_BF16: return learn_scratch_t<RLL_PREC_BF16>(ctx, g, rec_key, rec_val, n, scratch);
+    default: return learn_scratch_t<RLL_PREC_FP32>(ctx, g, rec_key, rec_val, n, scratch);
+    }
+}
+
+}  // namespace rll

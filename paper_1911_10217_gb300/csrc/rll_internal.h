@@ -90,6 +90,9 @@ int grid_from_float(rll_ctx* ctx, rll_grid* g, const float* q_in, const float* c
 int grid_mark_occupied(rll_ctx* ctx, rll_grid* g);  // touched list := every occupied slot
 int learn_update(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n);
 int split_collapse(rll_ctx* ctx, rll_grid* g, const rll_tree* t);
+// learn_update with the sort buffers in caller-provided device scratch
+int learn_update_with_scratch(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n,
+                              void* scratch, size_t scratch_bytes);
 
 // ---- sample.cu
 int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* pos, const float* nrm,

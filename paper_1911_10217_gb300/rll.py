@@ -29,7 +29,7 @@ EXPORTS = [
     "rll_build_light_tree", "rll_tree_update_emission", "rll_tree_num_lights", "rll_tree_export",
     "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_export", "rll_grid_import",
     "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_power",
-    "rll_learn_update", "rll_split_collapse", "rll_render_pass_host",
+    "rll_learn_update", "rll_learn_update_noalloc", "rll_split_collapse", "rll_render_pass_host",
 ]
 
 
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
                                           ctypes.POINTER(SampleDebug)]
     L.rll_sample_power.argtypes = [P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P]
     L.rll_learn_update.argtypes = [P, P, P, P, I64]
+    L.rll_learn_update_noalloc.argtypes = [P, P, P, P, I64]
     L.rll_split_collapse.argtypes = [P, P, P]
     L.rll_render_pass_host.argtypes = [P, P, P, P, P, P, I64, P, I32, U64, U32, I32, I32, P]
     _lib = L
