@@ -167,16 +167,20 @@ static double orc_next_down(double v, int precision)
 /* Eq. 2 (Section 3): C(0) = Q(0), C(s) = C(s-1) + Q(s), computed after the  */
 /* pass. Reading (the paper is silent on zero probabilities): every leaf     */
 /* gets a floor eps * sum(Q) / m added before the prefix sum, so no cluster  */
-/* with a possible contribution has probability zero; a cell whose Q sums to */
-/* zero samples its clusters uniformly. With a 16-bit table the cdf is       */
-/* stored normalised (C(m-1) = 1) and forced strictly increasing.            */
+/* with a possible contribution has probability zero; a cell whose largest Q */
+/* is below the smallest normal binary32 value (2^-126; in particular a cell */
+/* whose Q are all zero) samples its clusters uniformly. With a 16-bit table */
+/* the cdf is stored normalised (C(m-1) = 1) and forced strictly increasing. */
 /* ------------------------------------------------------------------------ */
 void orc_cdf(int m, const double* q, double eps, int precision, double* c_out)
 {
-    double sum = 0.0;
-    for (int s = 0; s < m; ++s) sum += q[s];
+    double sum = 0.0, qmax = 0.0;
+    for (int s = 0; s < m; ++s) {
+        sum += q[s];
+        if (q[s] > qmax) qmax = q[s];
+    }
     double acc = 0.0;
-    int uniform = !(sum > 0.0) || !isfinite(sum);
+    int uniform = !(qmax >= 0x1p-126) || !isfinite(sum);
     for (int s = 0; s < m; ++s) {
         double qt = uniform ? 1.0 : q[s] + eps * sum / (double)m;
         acc += qt;

@@ -43,10 +43,16 @@ __device__ void warp_rebuild_cdf(const float* q, int m, float eps, typename Stor
                                  uint16_t* bits)
 {
     const int lane = threadIdx.x & 31;
-    float part = 0.0f;
-    for (int s = lane; s < m; s += 32) part += q[s];
+    float part = 0.0f, qmax = 0.0f;
+    for (int s = lane; s < m; s += 32) {
+        part += q[s];
+        qmax = fmaxf(qmax, q[s]);
+    }
     const float S = warp_sum(part);
-    const bool uniform = !(S > 0.0f) || !isfinite(S);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+    // uniform when every Q is below the smallest normal binary32 value
+    const bool uniform = !(qmax >= 0x1p-126f) || !isfinite(S);
     const float add = eps * S / (float)m;
     const int ipl = (m + 31) >> 5;
     const int b = lane * ipl, e = min(m, b + ipl);

@@ -54,7 +54,13 @@ struct SampleArgs {
     float* dbg_pcut;
     float* dbg_pin;
     uint32_t* status;
+    int prefetch;  // 1: prefetch the next descent lines and the cell's rows into L1
 };
+
+__device__ __forceinline__ void prefetch_l1(const void* p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 
 __device__ __forceinline__ int64_t lookup_insert(unsigned long long* keys, uint32_t H, unsigned long long key)
 {
@@ -98,7 +104,7 @@ struct ShadeOut {
 
 // light point, shadow test, contribution (x, n: shading point and normal)
 __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1, float x2, float n0, float n1,
-                                          float n2, float albedo, float pdf_sel, float p_in, SampleStream& rs,
+                                          float n2, float albedo, float p_cut, float p_in, SampleStream& rs,
                                           const float* s_box, int n_boxes, uint32_t reward_mode)
 {
     const float ua = rs.draw(kDrawTriA), ub = rs.draw(kDrawTriB);
@@ -132,15 +138,17 @@ __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1,
     const float inv_d = rsqrtf(d2);
     const float cx = fmaxf(0.0f, (n0 * wx + n1 * wy + n2 * wz) * inv_d);
     const float cl = fmaxf(0.0f, -(L.n[0] * wx + L.n[1] * wy + L.n[2] * wz) * inv_d);
-    const float geo = occluded ? 0.0f : cx * cl / d2;
+    const float geo = (occluded || !(d2 > 0.0f)) ? 0.0f : cx * cl / d2;
     const float f = albedo * 0.31830988618379067f;
     const float c0 = f * L.le[0] * geo, c1 = f * L.le[1] * geo, c2 = f * L.le[2] * geo;
-    const float w = L.area / pdf_sel;
+    // a zero contribution is zero whatever its pdf (a long-unrewarded
+    // cluster's probability may underflow binary32)
+    const float w = geo > 0.0f ? (L.area / p_cut) / p_in : 0.0f;
     o.est[0] = c0 * w;
     o.est[1] = c1 * w;
     o.est[2] = c2 * w;
     const float lum = 0.2126f * c0 + 0.7152f * c1 + 0.0722f * c2;
-    o.reward = reward_mode == RLL_REWARD_CLUSTER ? lum * L.area / p_in : lum * L.area;
+    o.reward = !(lum > 0.0f) ? 0.0f : (reward_mode == RLL_REWARD_CLUSTER ? lum * L.area / p_in : lum * L.area);
     return o;
 }
 
@@ -186,6 +194,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sample(SampleArgs a)
             cutrow = a.def_cut;
             atomicOr(a.status, (uint32_t)RLL_E_TABLE_FULL);
         }
+        if (a.prefetch) {
+            prefetch_l1(crow + (m - 1));
+            prefetch_l1(crow);
+        }
         // cluster: first s with C(s) > u * C(m-1)
         const float u = rs.draw(kDrawCut);
         const float total = Store<P>::load(crow[m - 1]);
@@ -216,6 +228,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sample(SampleArgs a)
             while ((int64_t)node < nl1) {
                 const DescRec L = load_desc(a.pairs + 2 * (int64_t)node);
                 const DescRec R = load_desc(a.pairs + 2 * (int64_t)node + 1);
+                if (a.prefetch) {  // both possible next lines, while this level's bounds are computed
+                    if ((int64_t)L.id < nl1) prefetch_l1(a.pairs + 2 * (int64_t)L.id);
+                    if ((int64_t)R.id < nl1) prefetch_l1(a.pairs + 2 * (int64_t)R.id);
+                }
                 const float il = importance(L, x0, x1, x2, n0, n1, n2);
                 const float ir = importance(R, x0, x1, x2, n0, n1, n2);
                 float wl = il, wr = ir;
@@ -242,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sample(SampleArgs a)
             light = (int64_t)node - nl1;
         }
         const LightRec Lr = load_light(a.lights + light);
-        const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, p_cut * p_in, p_in, rs, s_box, a.n_boxes,
+        const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, p_cut, p_in, rs, s_box, a.n_boxes,
                                  a.reward_mode);
         acc0 += o.est[0];
         acc1 += o.est[1];
@@ -365,6 +381,7 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
     a.rec_key = rec_key;
     a.rec_val = rec_val;
     a.status = ctx->d_status;
+    a.prefetch = ctx->sample_prefetch;
     const bool use_dbg = dbg && (dbg->light || dbg->p_cut || dbg->p_in);
     if (use_dbg) {
         a.dbg_light = dbg->light;

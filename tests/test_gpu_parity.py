@@ -284,3 +284,27 @@ def test_host_pass_matches_device_pass(env):
                              np.ascontiguousarray(s.albedo), np.ascontiguousarray(s.boxes), s.seed, f,
                              s.spp, rgb)
         assert np.array_equal(rgb, g["rgb"].cpu().numpy())
+
+
+def test_long_run_stays_finite(env):
+    """Hundreds of passes drive the Q of always-occluded clusters into
+    binary32 subnormals; estimates, Q and C stay finite and every stored
+    cdf row stays strictly increasing."""
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    s = scenes.tiny_scene()
+    _, dt, d = _trees(env, s)
+    for prec in ("fp32", "fp16"):
+        dg = rll.Grid(ctx, dt, params_for(rll, s, precision=prec))
+        for f in range(400):
+            g = run_sample(rll, ctx, dg, dt, d, s.seed, f, s.spp)
+            rll.learn_update(ctx, dg, g["key"], g["val"])
+            rll.split_collapse(ctx, dg, dt)
+            if f % 100 == 99:
+                assert torch.isfinite(g["rgb"]).all(), (prec, f)
+                assert torch.isfinite(g["val"]).all(), (prec, f)
+        st = dg.export()
+        occ = st["keys"] != np.uint64(0xFFFFFFFFFFFFFFFF)
+        q, c = st["q"][occ, :dg.m], st["c"][occ, :dg.m]
+        assert np.isfinite(q).all() and np.isfinite(c).all()
+        assert np.all(np.diff(c, axis=1) > 0) and np.all(c[:, 0] > 0)
+        assert ctx.sync_status() == 0
