@@ -195,7 +195,7 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
-    ap.add_argument("--sample-prefetch", type=int, default=1)
+    ap.add_argument("--sample-prefetch", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
