@@ -208,6 +208,54 @@ int rll_learn_update_noalloc(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_k
  * rebuild C (Eq. 2). */
 int rll_split_collapse(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree);
 
+/* ---- many uneven scenes in one persistent launch per stage --------------- */
+
+/* One scene of a batch: its grid and tree and one pass's inputs/outputs
+ * (device pointers, layouts as in rll_sample_and_shade). */
+typedef struct rll_batch_item {
+    rll_grid* grid;
+    const rll_tree* tree;
+    const float* pos;          /* SoA [3][P] */
+    const float* nrm;          /* SoA [3][P] */
+    const float* albedo;       /* [P] */
+    int64_t n_points;          /* P */
+    const float* boxes;        /* [K][6] */
+    int32_t n_boxes;           /* K <= 1024 */
+    uint64_t seed;             /* Philox key of this scene */
+    uint32_t frame;            /* frame of the first pass (advanced by one per pass) */
+    int32_t spp;
+    float* rgb;                /* SoA [3][P] output */
+} rll_batch_item;
+
+typedef struct rll_batch rll_batch;
+
+/* Creates a batch over n_items scenes (all grids with the same table
+ * precision and in-cluster mode, cut sizes <= 64, sum of table sizes
+ * < 2^26). Allocates the batch's record, sort and work buffers once.
+ * One pass = sampling of every item by one persistent kernel that takes
+ * tiles of points from a global counter, one sort of all records, Eq. 1 +
+ * Eq. 2 for every touched cell, optional split-collapse, then each item's
+ * frame += 1. Per scene the result equals a pass run for that scene alone
+ * through the batch (records are keyed by scene). Synchronises. */
+int rll_batch_create(rll_ctx* ctx, const rll_batch_item* items, int32_t n_items, rll_batch** out);
+/* Sets the sampling tile (points per work item, 32..2^20) and the occupancy
+ * target (3 | 4 resident 256-thread blocks per SM). Drops a recorded graph. */
+int rll_batch_set_config(rll_ctx* ctx, rll_batch* b, int32_t tile_points, int32_t min_blocks);
+/* Autotuner: times the sampling stage for every tile size in
+ * {128 .. 8192} x occupancy {3, 4} (best of two timed runs after a warm-up)
+ * and keeps the fastest; reports the choice through the optional outputs.
+ * Runs sampling passes (hash cells may be created; Q and C are untouched).
+ * Synchronises. */
+int rll_batch_tune(rll_ctx* ctx, rll_batch* b, int32_t* tile_points_out, int32_t* min_blocks_out);
+/* Enqueues one pass on the context stream. */
+int rll_batch_run(rll_ctx* ctx, rll_batch* b, int32_t do_split);
+/* Records one pass as a CUDA graph (on a stream of the batch's own) after
+ * synchronising the context stream; rll_batch_launch replays it on the
+ * context stream, each replay one pass with the next frame. */
+int rll_batch_capture(rll_ctx* ctx, rll_batch* b, int32_t do_split);
+int rll_batch_launch(rll_ctx* ctx, rll_batch* b);
+int rll_batch_destroy(rll_batch* b);
+
 /* ---- one whole pass from host memory ------------------------------------- */
 
 /* Copies the G-buffer (HOST pos/nrm SoA [3][P], albedo [P]) and boxes (HOST

@@ -20,6 +20,7 @@
 // threshold test, then one lane emits the new cut and the cdf is rebuilt.
 #include <cuda_runtime.h>
 
+#include "learn_core.cuh"
 #include "rll_device.cuh"
 #include "rll_internal.h"
 
@@ -27,73 +28,6 @@ namespace rll {
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Eq. 2 with the floor: q holds the stored Q of one row (m values, shared
-// memory); c and bits are shared scratch of the same length. Writes the
-// stored cdf row. Called by all 32 lanes of a warp.
-template <int P>
-__device__ void warp_rebuild_cdf(const float* q, int m, float eps, typename Store<P>::T* out, float* c,
-                                 uint16_t* bits)
-{
-    const int lane = threadIdx.x & 31;
-    float part = 0.0f, qmax = 0.0f;
-    for (int s = lane; s < m; s += 32) {
-        part += q[s];
-        qmax = fmaxf(qmax, q[s]);
-    }
-    const float S = warp_sum(part);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
-    // uniform when every Q is below the smallest normal binary32 value
-    const bool uniform = !(qmax >= 0x1p-126f) || !isfinite(S);
-    const float add = eps * S / (float)m;
-    const int ipl = (m + 31) >> 5;
-    const int b = lane * ipl, e = min(m, b + ipl);
-    float run = 0.0f;
-    for (int s = b; s < e; ++s) {
-        run += uniform ? 1.0f : q[s] + add;
-        c[s] = run;
-    }
-    float x = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const float y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    const float before = x - run;
-    for (int s = b; s < e; ++s) c[s] += before;
-    __syncwarp();
-    if constexpr (P == RLL_PREC_FP32) {
-        for (int s = lane; s < m; s += 32) out[s] = Store<P>::store(c[s]);
-        __syncwarp();
-        return;
-    } else {
-        const float total = c[m - 1];
-        for (int s = lane; s < m; s += 32) bits[s] = Store<P>::bits(Store<P>::store(c[s] / total));
-        __syncwarp();
-        if (lane == 0) {
-            const uint16_t one = Store<P>::bits(Store<P>::store(1.0f));
-            bits[m - 1] = one;
-            uint16_t prev = 0;
-            for (int s = 0; s < m - 1; ++s) {
-                if (bits[s] <= prev) bits[s] = (uint16_t)(prev + 1);
-                prev = bits[s];
-            }
-            for (int s = m - 2; s >= 0; --s)
-                if (bits[s] >= bits[s + 1]) bits[s] = (uint16_t)(bits[s + 1] - 1);
-        }
-        __syncwarp();
-        for (int s = lane; s < m; s += 32) out[s] = Store<P>::from_bits(bits[s]);
-        __syncwarp();
-    }
-}
 
 // one warp: the default row (Q = q_init, C by Eq. 2)
 template <int P>
@@ -241,6 +175,13 @@ __global__ void k_mark_occupied(const unsigned long long* __restrict__ keys, uin
     if (occ) touched[base + __popc(mask & lanemask_lt())] = i;
 }
 
+// record key slot * M + cluster of one grid
+struct GridKey {
+    uint32_t HM, M, cell;
+    __device__ __forceinline__ bool same(uint32_t k) const { return k < HM && k / M == cell; }
+    __device__ __forceinline__ uint32_t cluster(uint32_t k) const { return k % M; }
+};
+
 template <int P>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_learn_cells(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, int64_t n, uint32_t HM,
@@ -251,83 +192,14 @@ k_learn_cells(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, 
     __shared__ float s_q[kWarpsPerBlock][kMaxCut];
     __shared__ float s_c[kWarpsPerBlock][kMaxCut];
     __shared__ uint16_t s_b[kWarpsPerBlock][kMaxCut];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const uint32_t total = *n_touched;
-    const float a1 = 1.0f - alpha;
-    float* q = s_q[warp];
     for (uint32_t w = blockIdx.x * kWarpsPerBlock + warp; w < total; w += gridDim.x * kWarpsPerBlock) {
         const uint32_t cell = touched[w];
-        const int64_t start = touched_start[w];
-        typename Store<P>::T* qrow = Q + (int64_t)cell * M;
-        typename Store<P>::T* crow = C + (int64_t)cell * M;
-        for (uint32_t s = lane; s < m; s += 32) q[s] = Store<P>::load(qrow[s]);
-        __syncwarp();
-        for (int64_t pos = start;; pos += 32) {
-            const int64_t i = pos + lane;
-            const uint32_t key = i < n ? sk[i] : 0xFFFFFFFFu;
-            const bool valid = key < HM && key / M == cell;
-            const uint32_t mask = __ballot_sync(0xffffffffu, valid);
-            if (!mask) break;
-            const uint32_t s = valid ? key % M : 0xFFFFFFFFu;
-            float A = valid ? a1 : 1.0f;
-            float B = valid ? alpha * __uint_as_float(sv[i]) : 0.0f;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float Ao = __shfl_up_sync(0xffffffffu, A, o);
-                const float Bo = __shfl_up_sync(0xffffffffu, B, o);
-                const uint32_t so = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o && so == s) {
-                    B = A * Bo + B;
-                    A = A * Ao;
-                }
-            }
-            const uint32_t s_next = __shfl_down_sync(0xffffffffu, s, 1);
-            const bool last = valid && (lane == 31 || s_next != s);
-            if (last && s < m) q[s] = A * q[s] + B;
-            __syncwarp();
-            if (mask != 0xffffffffu) break;
-        }
-        for (uint32_t s = lane; s < m; s += 32) {
-            const typename Store<P>::T st = Store<P>::store(q[s]);
-            qrow[s] = st;
-            q[s] = Store<P>::load(st);
-        }
-        __syncwarp();
-        warp_rebuild_cdf<P>(q, (int)m, eps, crow, s_c[warp], s_b[warp]);
+        const GridKey key{HM, M, cell};
+        learn_one_cell<P>(sk, sv, n, touched_start[w], key, Q + (int64_t)cell * M, C + (int64_t)cell * M, m, alpha,
+                          eps, s_q[warp], s_c[warp], s_b[warp]);
     }
-}
-
-struct ArgBest {
-    float v;
-    uint32_t i;
-};
-
-__device__ __forceinline__ ArgBest warp_argmax(ArgBest a)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float v = __shfl_xor_sync(0xffffffffu, a.v, o);
-        const uint32_t i = __shfl_xor_sync(0xffffffffu, a.i, o);
-        if (i != 0xFFFFFFFFu && (a.i == 0xFFFFFFFFu || v > a.v || (v == a.v && i < a.i))) {
-            a.v = v;
-            a.i = i;
-        }
-    }
-    return a;
-}
-
-__device__ __forceinline__ ArgBest warp_argmin(ArgBest a)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float v = __shfl_xor_sync(0xffffffffu, a.v, o);
-        const uint32_t i = __shfl_xor_sync(0xffffffffu, a.i, o);
-        if (i != 0xFFFFFFFFu && (a.i == 0xFFFFFFFFu || v < a.v || (v == a.v && i < a.i))) {
-            a.v = v;
-            a.i = i;
-        }
-    }
-    return a;
 }
 
 template <int P>
@@ -343,104 +215,15 @@ k_split(uint32_t M, uint32_t m, const uint32_t* __restrict__ touched, const uint
     __shared__ uint32_t s_cut[kWarpsPerBlock][kMaxCut];
     __shared__ uint32_t s_nc[kWarpsPerBlock][kMaxCut];
     __shared__ uint16_t s_b[kWarpsPerBlock][kMaxCut];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const uint32_t total = *n_touched;
-    float* q = s_q[warp];
-    uint32_t* cs = s_cut[warp];
     for (uint32_t w = blockIdx.x * kWarpsPerBlock + warp; w < total; w += gridDim.x * kWarpsPerBlock) {
-        const uint32_t cell = touched[w];
-        uint32_t* crow = cut + (int64_t)cell * M;
-        typename Store<P>::T* qrow = Q + (int64_t)cell * M;
-        bool bad = false;
-        for (uint32_t s = lane; s < m; s += 32) {
-            cs[s] = crow[s];
-            q[s] = Store<P>::load(qrow[s]);
-            bad |= (int64_t)cs[s] >= n_nodes;
-        }
-        if (__any_sync(0xffffffffu, bad)) {  // corrupt cut row: flag and leave the cell alone
-            if (lane == 0) atomicOr(status, (uint32_t)RLL_E_DEVICE);
-            continue;
-        }
-        __syncwarp();
-        ArgBest hi{0.0f, 0xFFFFFFFFu}, lo{0.0f, 0xFFFFFFFFu};
-        const uint32_t n_internal = (uint32_t)((n_nodes - 1) / 2);  // ids below are internal nodes
-        for (uint32_t s = lane; s < m; s += 32) {
-            if (cs[s] < n_internal && (hi.i == 0xFFFFFFFFu || q[s] > hi.v)) {
-                hi.v = q[s];
-                hi.i = s;
-            }
-            if (s + 1 < m) {
-                const int32_t pa = parent[cs[s]];
-                if (pa >= 0 && pa == parent[cs[s + 1]]) {
-                    const float v = fadd(q[s], q[s + 1]);
-                    if (lo.i == 0xFFFFFFFFu || v < lo.v) {
-                        lo.v = v;
-                        lo.i = s;
-                    }
-                }
-            }
-        }
-        hi = warp_argmax(hi);
-        lo = warp_argmin(lo);
-        const bool apply = hi.i != 0xFFFFFFFFu && lo.i != 0xFFFFFFFFu && hi.i != lo.i && hi.i != lo.i + 1 &&
-                           hi.v > fmul(T, lo.v);
-        if (!apply) continue;
-        // one lane emits the new row into shared scratch rows
-        if (lane == 0) {
-            float* nq = s_c[warp];
-            uint32_t* nc = s_nc[warp];
-            uint32_t k = 0;
-            for (uint32_t i = 0; i < m; ++i) {
-                if (i == hi.i) {
-                    const uint32_t node = cs[i];
-                    const uint32_t a = (uint32_t)left[node], c = (uint32_t)right[node];
-                    const float pa = nodes[a].phi, pc = nodes[c].phi;
-                    const float sum = pa + pc;
-                    const float fa = sum > 0.0f ? pa / sum : 0.5f;
-                    const float fc = sum > 0.0f ? pc / sum : 0.5f;
-                    nc[k] = a; nq[k] = q[i] * fa; ++k;
-                    nc[k] = c; nq[k] = q[i] * fc; ++k;
-                } else if (i == lo.i) {
-                    nc[k] = (uint32_t)parent[cs[i]];
-                    nq[k] = q[i] + q[i + 1];
-                    ++k;
-                    ++i;
-                } else {
-                    nc[k] = cs[i];
-                    nq[k] = q[i];
-                    ++k;
-                }
-            }
-            for (uint32_t i = 0; i < m; ++i) {
-                cs[i] = nc[i];
-                q[i] = nq[i];
-            }
-        }
-        __syncwarp();
-        for (uint32_t s = lane; s < m; s += 32) {
-            crow[s] = cs[s];
-            const typename Store<P>::T st = Store<P>::store(q[s]);
-            qrow[s] = st;
-            q[s] = Store<P>::load(st);
-        }
-        __syncwarp();
-        warp_rebuild_cdf<P>(q, (int)m, eps, C + (int64_t)cell * M, s_c[warp], s_b[warp]);
+        const int64_t row = (int64_t)touched[w] * M;
+        split_one_cell<P>(cut + row, Q + row, C + row, m, nodes, parent, left, right, T, eps, n_nodes, status,
+                          s_q[warp], s_c[warp], s_cut[warp], s_nc[warp], s_b[warp]);
     }
 }
 
-int key_bits(uint64_t hm_plus_one)
-{
-    int b = 0;
-    while ((1ull << b) < hm_plus_one) ++b;
-    return b;
-}
-
-int device_sm_count(int device)
-{
-    int v = 0;
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
-    return v > 0 ? v : 1;
-}
 
 template <int P>
 int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n)
@@ -491,6 +274,20 @@ int init_t(rll_ctx* ctx, rll_grid* g)
 
 }  // namespace
 
+int key_bits(uint64_t hm_plus_one)
+{
+    int b = 0;
+    while ((1ull << b) < hm_plus_one) ++b;
+    return b;
+}
+
+int device_sm_count(int device)
+{
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    return v > 0 ? v : 1;
+}
+
 int grid_init(rll_ctx* ctx, rll_grid* g)
 {
     switch (g->p.precision) {
@@ -537,6 +334,14 @@ int grid_from_float(rll_ctx* ctx, rll_grid* g, const float* q, const float* c)
     default: from_float_t<RLL_PREC_FP32>(ctx, g, q, c);
     }
     return check_cuda(ctx, cudaGetLastError(), "grid import");
+}
+
+void launch_cell_heads(cudaStream_t s, const uint32_t* sk, int64_t n, uint32_t HM, uint32_t M, uint32_t* touched,
+                       uint32_t* touched_start, uint32_t* n_touched)
+{
+    if (n <= 0) return;
+    k_cell_heads<<<(unsigned)((n + 256 * kHeadItems - 1) / (256 * kHeadItems)), 256, 0, s>>>(sk, n, HM, M, touched,
+                                                                                           touched_start, n_touched);
 }
 
 int grid_mark_occupied(rll_ctx* ctx, rll_grid* g)

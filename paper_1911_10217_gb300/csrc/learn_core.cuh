@@ -1,0 +1,246 @@
+// Per-cell learning and split-collapse shared by the single-grid kernels
+// (learn.cu) and the batched kernels (batched.cu). One warp works on one
+// cell; q, c, cs, nc, bits are that warp's shared-memory rows (kMaxCut each).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rll_device.cuh"
+
+namespace rll {
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Eq. 2 with the floor: q holds the stored Q of one row (m values, shared
+// memory); c and bits are shared scratch of the same length. Writes the
+// stored cdf row. Called by all 32 lanes of a warp.
+template <int P>
+__device__ void warp_rebuild_cdf(const float* q, int m, float eps, typename Store<P>::T* out, float* c,
+                                 uint16_t* bits)
+{
+    const int lane = threadIdx.x & 31;
+    float part = 0.0f, qmax = 0.0f;
+    for (int s = lane; s < m; s += 32) {
+        part += q[s];
+        qmax = fmaxf(qmax, q[s]);
+    }
+    const float S = warp_sum(part);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+    // uniform when every Q is below the smallest normal binary32 value
+    const bool uniform = !(qmax >= 0x1p-126f) || !isfinite(S);
+    const float add = eps * S / (float)m;
+    const int ipl = (m + 31) >> 5;
+    const int b = lane * ipl, e = min(m, b + ipl);
+    float run = 0.0f;
+    for (int s = b; s < e; ++s) {
+        run += uniform ? 1.0f : q[s] + add;
+        c[s] = run;
+    }
+    float x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const float before = x - run;
+    for (int s = b; s < e; ++s) c[s] += before;
+    __syncwarp();
+    if constexpr (P == RLL_PREC_FP32) {
+        for (int s = lane; s < m; s += 32) out[s] = Store<P>::store(c[s]);
+        __syncwarp();
+        return;
+    } else {
+        const float total = c[m - 1];
+        for (int s = lane; s < m; s += 32) bits[s] = Store<P>::bits(Store<P>::store(c[s] / total));
+        __syncwarp();
+        if (lane == 0) {
+            const uint16_t one = Store<P>::bits(Store<P>::store(1.0f));
+            bits[m - 1] = one;
+            uint16_t prev = 0;
+            for (int s = 0; s < m - 1; ++s) {
+                if (bits[s] <= prev) bits[s] = (uint16_t)(prev + 1);
+                prev = bits[s];
+            }
+            for (int s = m - 2; s >= 0; --s)
+                if (bits[s] >= bits[s + 1]) bits[s] = (uint16_t)(bits[s + 1] - 1);
+        }
+        __syncwarp();
+        for (int s = lane; s < m; s += 32) out[s] = Store<P>::from_bits(bits[s]);
+        __syncwarp();
+    }
+}
+
+struct ArgBest {
+    float v;
+    uint32_t i;
+};
+
+__device__ __forceinline__ ArgBest warp_argmax(ArgBest a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, a.v, o);
+        const uint32_t i = __shfl_xor_sync(0xffffffffu, a.i, o);
+        if (i != 0xFFFFFFFFu && (a.i == 0xFFFFFFFFu || v > a.v || (v == a.v && i < a.i))) {
+            a.v = v;
+            a.i = i;
+        }
+    }
+    return a;
+}
+
+__device__ __forceinline__ ArgBest warp_argmin(ArgBest a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, a.v, o);
+        const uint32_t i = __shfl_xor_sync(0xffffffffu, a.i, o);
+        if (i != 0xFFFFFFFFu && (a.i == 0xFFFFFFFFu || v < a.v || (v == a.v && i < a.i))) {
+            a.v = v;
+            a.i = i;
+        }
+    }
+    return a;
+}
+
+// Eq. 1 for one cell: walk the cell's sorted records from `start` 32 at a
+// time; a segmented inclusive scan (by cluster) composes the affine maps
+// q -> (1 - alpha) q + alpha |c| in sample order and the last lane of each
+// segment applies the composite to the cluster's Q. Then the row is stored
+// in the table precision and its cdf rebuilt (Eq. 2). `key` tells whether a
+// record belongs to the cell (same()) and its cluster (cluster()).
+template <int P, class Key>
+__device__ void learn_one_cell(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, int64_t n,
+                               int64_t start, const Key& key, typename Store<P>::T* qrow,
+                               typename Store<P>::T* crow, uint32_t m, float alpha, float eps, float* q, float* c,
+                               uint16_t* bits)
+{
+    const int lane = threadIdx.x & 31;
+    const float a1 = 1.0f - alpha;
+    for (uint32_t s = lane; s < m; s += 32) q[s] = Store<P>::load(qrow[s]);
+    __syncwarp();
+    for (int64_t pos = start;; pos += 32) {
+        const int64_t i = pos + lane;
+        const uint32_t k = i < n ? sk[i] : 0xFFFFFFFFu;
+        const bool valid = i < n && key.same(k);
+        const uint32_t mask = __ballot_sync(0xffffffffu, valid);
+        if (!mask) break;
+        const uint32_t s = valid ? key.cluster(k) : 0xFFFFFFFFu;
+        float A = valid ? a1 : 1.0f;
+        float B = valid ? alpha * __uint_as_float(sv[i]) : 0.0f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float Ao = __shfl_up_sync(0xffffffffu, A, o);
+            const float Bo = __shfl_up_sync(0xffffffffu, B, o);
+            const uint32_t so = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o && so == s) {
+                B = A * Bo + B;
+                A = A * Ao;
+            }
+        }
+        const uint32_t s_next = __shfl_down_sync(0xffffffffu, s, 1);
+        const bool last = valid && (lane == 31 || s_next != s);
+        if (last && s < m) q[s] = A * q[s] + B;
+        __syncwarp();
+        if (mask != 0xffffffffu) break;
+    }
+    for (uint32_t s = lane; s < m; s += 32) {
+        const typename Store<P>::T st = Store<P>::store(q[s]);
+        qrow[s] = st;
+        q[s] = Store<P>::load(st);
+    }
+    __syncwarp();
+    warp_rebuild_cdf<P>(q, (int)m, eps, crow, c, bits);
+}
+
+// Split-collapse of one cell (cut row crow, Q row qrow, cdf row ccrow).
+template <int P>
+__device__ void split_one_cell(uint32_t* crow, typename Store<P>::T* qrow, typename Store<P>::T* ccrow, uint32_t m,
+                               const NodeRec* __restrict__ nodes, const int32_t* __restrict__ parent,
+                               const int32_t* __restrict__ left, const int32_t* __restrict__ right, float T,
+                               float eps, int64_t n_nodes, uint32_t* status, float* q, float* c, uint32_t* cs,
+                               uint32_t* nc, uint16_t* bits)
+{
+    const int lane = threadIdx.x & 31;
+    bool bad = false;
+    for (uint32_t s = lane; s < m; s += 32) {
+        cs[s] = crow[s];
+        q[s] = Store<P>::load(qrow[s]);
+        bad |= (int64_t)cs[s] >= n_nodes;
+    }
+    if (__any_sync(0xffffffffu, bad)) {  // corrupt cut row: flag and leave the cell alone
+        if (lane == 0) atomicOr(status, (uint32_t)RLL_E_DEVICE);
+        return;
+    }
+    __syncwarp();
+    ArgBest hi{0.0f, 0xFFFFFFFFu}, lo{0.0f, 0xFFFFFFFFu};
+    const uint32_t n_internal = (uint32_t)((n_nodes - 1) / 2);  // ids below are internal nodes
+    for (uint32_t s = lane; s < m; s += 32) {
+        if (cs[s] < n_internal && (hi.i == 0xFFFFFFFFu || q[s] > hi.v)) {
+            hi.v = q[s];
+            hi.i = s;
+        }
+        if (s + 1 < m) {
+            const int32_t pa = parent[cs[s]];
+            if (pa >= 0 && pa == parent[cs[s + 1]]) {
+                const float v = fadd(q[s], q[s + 1]);
+                if (lo.i == 0xFFFFFFFFu || v < lo.v) {
+                    lo.v = v;
+                    lo.i = s;
+                }
+            }
+        }
+    }
+    hi = warp_argmax(hi);
+    lo = warp_argmin(lo);
+    const bool apply = hi.i != 0xFFFFFFFFu && lo.i != 0xFFFFFFFFu && hi.i != lo.i && hi.i != lo.i + 1 &&
+                       hi.v > fmul(T, lo.v);
+    if (!apply) return;
+    // one lane emits the new row into the shared scratch rows
+    if (lane == 0) {
+        float* nq = c;
+        uint32_t k = 0;
+        for (uint32_t i = 0; i < m; ++i) {
+            if (i == hi.i) {
+                const uint32_t node = cs[i];
+                const uint32_t a = (uint32_t)left[node], cc = (uint32_t)right[node];
+                const float pa = nodes[a].phi, pc = nodes[cc].phi;
+                const float sum = pa + pc;
+                const float fa = sum > 0.0f ? pa / sum : 0.5f;
+                const float fc = sum > 0.0f ? pc / sum : 0.5f;
+                nc[k] = a; nq[k] = q[i] * fa; ++k;
+                nc[k] = cc; nq[k] = q[i] * fc; ++k;
+            } else if (i == lo.i) {
+                nc[k] = (uint32_t)parent[cs[i]];
+                nq[k] = q[i] + q[i + 1];
+                ++k;
+                ++i;
+            } else {
+                nc[k] = cs[i];
+                nq[k] = q[i];
+                ++k;
+            }
+        }
+        for (uint32_t i = 0; i < m; ++i) {
+            cs[i] = nc[i];
+            q[i] = nq[i];
+        }
+    }
+    __syncwarp();
+    for (uint32_t s = lane; s < m; s += 32) {
+        crow[s] = cs[s];
+        const typename Store<P>::T st = Store<P>::store(q[s]);
+        qrow[s] = st;
+        q[s] = Store<P>::load(st);
+    }
+    __syncwarp();
+    warp_rebuild_cdf<P>(q, (int)m, eps, ccrow, c, bits);
+}
+
+}  // namespace rll

@@ -15,268 +15,22 @@
 
 #include "rll_device.cuh"
 #include "rll_internal.h"
+#include "sample_core.cuh"
 
 namespace rll {
 namespace {
 
 constexpr int kThreads = 256;
 
-struct SampleArgs {
-    const float* pos;
-    const float* nrm;
-    const float* albedo;
-    int64_t n_points;
-    const float* boxes;
-    int n_boxes;
-    unsigned long long* keys;
-    const uint32_t* cut;
-    const void* C;
-    uint32_t H, M, m;
-    const uint32_t* def_cut;
-    const void* def_C;
-    float origin[3];
-    float h;
-    uint32_t nb;
-    uint32_t jitter;
-    uint32_t reward_mode;
-    const DescRec* pairs;
-    const NodeRec* nodes;
-    const LightRec* lights;
-    const float* light_cdf;
-    int64_t n_lights;
-    unsigned long long seed;
-    uint32_t frame;
-    int spp;
-    float* rgb;
-    uint32_t* rec_key;
-    float* rec_val;
-    int32_t* dbg_light;
-    float* dbg_pcut;
-    float* dbg_pin;
-    uint32_t* status;
-    int prefetch;  // 1: prefetch the next descent lines and the cell's rows into L1
-};
-
-__device__ __forceinline__ void prefetch_l1(const void* p)
-{
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
-__device__ __forceinline__ int64_t lookup_insert(unsigned long long* keys, uint32_t H, unsigned long long key)
-{
-    const unsigned long long h = fmix64(key);
-    for (int i = 0; i < kMaxProbes; ++i) {
-        const uint32_t slot = (uint32_t)((h + (unsigned long long)i) & (unsigned long long)(H - 1));
-        const unsigned long long k = __ldcg(keys + slot);
-        if (k == key) return slot;
-        if (k == kEmptyKey) {
-            const unsigned long long old = atomicCAS(keys + slot, kEmptyKey, key);
-            if (old == kEmptyKey || old == key) return slot;
-        }
-    }
-    return -1;
-}
-
-__device__ __forceinline__ DescRec load_desc(const DescRec* p)
-{
-    DescRec r;
-    const float4* s = reinterpret_cast<const float4*>(p);
-    float4* d = reinterpret_cast<float4*>(&r);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) d[k] = __ldg(s + k);
-    return r;
-}
-
-__device__ __forceinline__ LightRec load_light(const LightRec* p)
-{
-    LightRec r;
-    const float4* s = reinterpret_cast<const float4*>(p);
-    float4* d = reinterpret_cast<float4*>(&r);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) d[k] = __ldg(s + k);
-    return r;
-}
-
-struct ShadeOut {
-    float est[3];
-    float reward;
-};
-
-// light point, shadow test, contribution (x, n: shading point and normal)
-__device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1, float x2, float n0, float n1,
-                                          float n2, float albedo, float p_cut, float p_in, SampleStream& rs,
-                                          const float* s_box, int n_boxes, uint32_t reward_mode)
-{
-    const float ua = rs.draw(kDrawTriA), ub = rs.draw(kDrawTriB);
-    const float su = fsqrt(ua);
-    const float b0 = fsub(1.0f, su), b1 = fmul(ub, su), b2 = fsub(su, b1);
-    const float y0 = fadd(fadd(fmul(b0, L.v0[0]), fmul(b1, L.v1[0])), fmul(b2, L.v2[0]));
-    const float y1 = fadd(fadd(fmul(b0, L.v0[1]), fmul(b1, L.v1[1])), fmul(b2, L.v2[1]));
-    const float y2 = fadd(fadd(fmul(b0, L.v0[2]), fmul(b1, L.v1[2])), fmul(b2, L.v2[2]));
-    const float o0 = fadd(x0, fmul(kShadowOffset, n0));
-    const float o1 = fadd(x1, fmul(kShadowOffset, n1));
-    const float o2 = fadd(x2, fmul(kShadowOffset, n2));
-    const float i0 = fdiv(1.0f, fsub(y0, o0)), i1 = fdiv(1.0f, fsub(y1, o1)), i2 = fdiv(1.0f, fsub(y2, o2));
-    const float q0 = -fmul(o0, i0), q1 = -fmul(o1, i1), q2 = -fmul(o2, i2);
-    bool occluded = false;
-    for (int b = 0; b < n_boxes && !occluded; ++b) {
-        const float* bx = s_box + 6 * b;
-        const float ta0 = __fmaf_rn(bx[0], i0, q0), tb0 = __fmaf_rn(bx[3], i0, q0);
-        const float ta1 = __fmaf_rn(bx[1], i1, q1), tb1 = __fmaf_rn(bx[4], i1, q1);
-        const float ta2 = __fmaf_rn(bx[2], i2, q2), tb2 = __fmaf_rn(bx[5], i2, q2);
-        float tn = fmaxf(0.0f, fminf(ta0, tb0));
-        float tf = fminf(kShadowTmax, fmaxf(ta0, tb0));
-        tn = fmaxf(tn, fminf(ta1, tb1));
-        tf = fminf(tf, fmaxf(ta1, tb1));
-        tn = fmaxf(tn, fminf(ta2, tb2));
-        tf = fminf(tf, fmaxf(ta2, tb2));
-        occluded = tn < tf;
-    }
-    ShadeOut o;
-    const float wx = y0 - x0, wy = y1 - x1, wz = y2 - x2;
-    const float d2 = wx * wx + wy * wy + wz * wz;
-    const float inv_d = rsqrtf(d2);
-    const float cx = fmaxf(0.0f, (n0 * wx + n1 * wy + n2 * wz) * inv_d);
-    const float cl = fmaxf(0.0f, -(L.n[0] * wx + L.n[1] * wy + L.n[2] * wz) * inv_d);
-    const float geo = (occluded || !(d2 > 0.0f)) ? 0.0f : cx * cl / d2;
-    const float f = albedo * 0.31830988618379067f;
-    const float c0 = f * L.le[0] * geo, c1 = f * L.le[1] * geo, c2 = f * L.le[2] * geo;
-    // a zero contribution is zero whatever its pdf (a long-unrewarded
-    // cluster's probability may underflow binary32)
-    const float w = geo > 0.0f ? (L.area / p_cut) / p_in : 0.0f;
-    o.est[0] = c0 * w;
-    o.est[1] = c1 * w;
-    o.est[2] = c2 * w;
-    const float lum = 0.2126f * c0 + 0.7152f * c1 + 0.0722f * c2;
-    o.reward = !(lum > 0.0f) ? 0.0f : (reward_mode == RLL_REWARD_CLUSTER ? lum * L.area / p_in : lum * L.area);
-    return o;
-}
-
-// MINB: resident blocks per SM the register allocation is held to (3: no
-// cap at 256 threads, 4: at most 64 registers per thread).
 template <int P, int MODE, bool DBG, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_sample(SampleArgs a)
 {
-    using T = typename Store<P>::T;
     extern __shared__ float s_box[];
     for (int i = threadIdx.x; i < a.n_boxes * 6; i += blockDim.x) s_box[i] = a.boxes[i];
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n_points) return;
-    const int64_t np = a.n_points;
-    const float x0 = a.pos[p], x1 = a.pos[np + p], x2 = a.pos[2 * np + p];
-    const float n0 = a.nrm[p], n1 = a.nrm[np + p], n2 = a.nrm[2 * np + p];
-    const float alb = a.albedo[p];
-    const T* Ctab = static_cast<const T*>(a.C);
-    const T* Cdef = static_cast<const T*>(a.def_C);
-    const uint32_t m = a.m;
-    const int64_t nl1 = a.n_lights - 1;
-    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
-    for (int j = 0; j < a.spp; ++j) {
-        const uint32_t sid = (uint32_t)(p * a.spp + j);
-        SampleStream rs;
-        rs.init(a.seed, sid, a.frame);
-        float jit[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (a.jitter) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) jit[k] = rs.draw(kDrawJit + k);
-        }
-        const unsigned long long key =
-            cell_key(x0, x1, x2, n0, n1, n2, a.origin, a.h, a.nb, a.jitter != 0, jit);
-        const int64_t slot = lookup_insert(a.keys, a.H, key);
-        const T* crow;
-        const uint32_t* cutrow;
-        if (slot >= 0) {
-            crow = Ctab + slot * a.M;
-            cutrow = a.cut + slot * a.M;
-        } else {
-            crow = Cdef;
-            cutrow = a.def_cut;
-            atomicOr(a.status, (uint32_t)RLL_E_TABLE_FULL);
-        }
-        if (a.prefetch) {
-            prefetch_l1(crow + (m - 1));
-            prefetch_l1(crow);
-        }
-        // cluster: first s with C(s) > u * C(m-1)
-        const float u = rs.draw(kDrawCut);
-        const float total = Store<P>::load(crow[m - 1]);
-        uint32_t lo = 0, hi = m - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (__fmaf_rn(-u, total, Store<P>::load(crow[mid])) > 0.0f) hi = mid;
-            else lo = mid + 1;
-        }
-        const uint32_t s = lo;
-        const float cprev = s > 0 ? Store<P>::load(crow[s - 1]) : 0.0f;
-        const float p_cut = (Store<P>::load(crow[s]) - cprev) / total;
-        uint32_t node = cutrow[s];
-        if ((int64_t)node >= 2 * a.n_lights - 1) {  // corrupt cut row: flag, sample from the root
-            atomicOr(a.status, (uint32_t)RLL_E_DEVICE);
-            node = 0;
-        }
-        float p_in = 1.0f;
-        int64_t light;
-        if (MODE == RLL_MODE_UNIFORM) {
-            const NodeRec& r = a.nodes[node];
-            const uint32_t w = r.end - r.begin;
-            const uint32_t u24v = (uint32_t)(rs.draw(kDrawUniform) * 16777216.0f);
-            light = (int64_t)r.begin + (int64_t)(((unsigned long long)u24v * w) >> 24);
-            p_in = 1.0f / (float)w;
-        } else {
-            uint32_t level = 0;
-            while ((int64_t)node < nl1) {
-                const DescRec L = load_desc(a.pairs + 2 * (int64_t)node);
-                const DescRec R = load_desc(a.pairs + 2 * (int64_t)node + 1);
-                if (a.prefetch) {  // both possible next lines, while this level's bounds are computed
-                    if ((int64_t)L.id < nl1) prefetch_l1(a.pairs + 2 * (int64_t)L.id);
-                    if ((int64_t)R.id < nl1) prefetch_l1(a.pairs + 2 * (int64_t)R.id);
-                }
-                const float il = importance(L, x0, x1, x2, n0, n1, n2);
-                const float ir = importance(R, x0, x1, x2, n0, n1, n2);
-                float wl = il, wr = ir;
-                float ssum = fadd(il, ir);
-                if (!(ssum > 0.0f)) {
-                    wl = L.phi;
-                    wr = R.phi;
-                    ssum = fadd(wl, wr);
-                }
-                const float ud = rs.draw(kDrawDescent + level);
-                ++level;
-                bool left;
-                float ratio;
-                if (ssum > 0.0f) {
-                    left = __fmaf_rn(ud, ssum, -wl) < 0.0f;
-                    ratio = (left ? wl : wr) / (wl + wr);
-                } else {
-                    left = ud < 0.5f;
-                    ratio = 0.5f;
-                }
-                p_in *= ratio;
-                node = left ? L.id : R.id;
-            }
-            light = (int64_t)node - nl1;
-        }
-        const LightRec Lr = load_light(a.lights + light);
-        const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, p_cut, p_in, rs, s_box, a.n_boxes,
-                                 a.reward_mode);
-        acc0 += o.est[0];
-        acc1 += o.est[1];
-        acc2 += o.est[2];
-        if (a.rec_key) {
-            a.rec_key[sid] = slot >= 0 ? (uint32_t)slot * a.M + s : kInvalidRecord;
-            a.rec_val[sid] = o.reward;
-        }
-        if (DBG) {
-            if (a.dbg_light) a.dbg_light[sid] = (int32_t)light;
-            if (a.dbg_pcut) a.dbg_pcut[sid] = p_cut;
-            if (a.dbg_pin) a.dbg_pin[sid] = p_in;
-        }
-    }
-    const float inv_spp = 1.0f / (float)a.spp;
-    a.rgb[p] = acc0 * inv_spp;
-    a.rgb[np + p] = acc1 * inv_spp;
-    a.rgb[2 * np + p] = acc2 * inv_spp;
+    sample_point<P, MODE, DBG>(a, p, s_box);
 }
 
 // Energy-based baseline (Section 4): inversion of the cdf of leaf power.

@@ -30,6 +30,8 @@ EXPORTS = [
     "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_export", "rll_grid_import",
     "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_power",
     "rll_learn_update", "rll_learn_update_noalloc", "rll_split_collapse", "rll_render_pass_host",
+    "rll_batch_create", "rll_batch_set_config", "rll_batch_tune", "rll_batch_run", "rll_batch_capture",
+    "rll_batch_launch", "rll_batch_destroy",
 ]
 
 
@@ -46,6 +48,13 @@ class GridParams(ctypes.Structure):
                 ("precision", ctypes.c_uint32), ("in_cluster_mode", ctypes.c_uint32),
                 ("reward_mode", ctypes.c_uint32), ("alpha", ctypes.c_float),
                 ("threshold", ctypes.c_float), ("eps", ctypes.c_float), ("q_init", ctypes.c_float)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_void_p), ("tree", ctypes.c_void_p), ("pos", ctypes.c_void_p),
+                ("nrm", ctypes.c_void_p), ("albedo", ctypes.c_void_p), ("n_points", ctypes.c_int64),
+                ("boxes", ctypes.c_void_p), ("n_boxes", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("frame", ctypes.c_uint32), ("spp", ctypes.c_int32), ("rgb", ctypes.c_void_p)]
 
 
 class SampleDebug(ctypes.Structure):
@@ -99,6 +108,13 @@ def load(build_if_missing: bool = True):
     L.rll_learn_update_noalloc.argtypes = [P, P, P, P, I64]
     L.rll_split_collapse.argtypes = [P, P, P]
     L.rll_render_pass_host.argtypes = [P, P, P, P, P, P, I64, P, I32, U64, U32, I32, I32, P]
+    L.rll_batch_create.argtypes = [P, ctypes.POINTER(BatchItem), I32, ctypes.POINTER(P)]
+    L.rll_batch_set_config.argtypes = [P, P, I32, I32]
+    L.rll_batch_tune.argtypes = [P, P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
+    L.rll_batch_run.argtypes = [P, P, I32]
+    L.rll_batch_capture.argtypes = [P, P, I32]
+    L.rll_batch_launch.argtypes = [P, P]
+    L.rll_batch_destroy.argtypes = [P]
     _lib = L
     return L
 
@@ -310,3 +326,48 @@ def render_pass_host(ctx: Context, grid: Grid, tree: Tree, pos, nrm, albedo, box
     ctx._check(ctx.lib.rll_render_pass_host(ctx.h, grid.h, tree.h, _ptr(pos), _ptr(nrm),
                                             _ptr(albedo), n, _ptr(boxes), k, int(seed), int(frame),
                                             int(spp), int(bool(do_split)), _ptr(rgb)))
+
+
+class Batch:
+    """rll_batch: many scenes sampled by one persistent launch per stage.
+    `items` is a list of dicts with keys grid, tree, pos, nrm, albedo, boxes,
+    seed, frame, spp, rgb (device tensors for the arrays)."""
+
+    def __init__(self, ctx: Context, items):
+        arr = (BatchItem * len(items))()
+        for i, it in enumerate(items):
+            arr[i] = BatchItem(it["grid"].h.value, it["tree"].h.value, _ptr(it["pos"]), _ptr(it["nrm"]),
+                               _ptr(it["albedo"]), int(it["albedo"].shape[0]), _ptr(it["boxes"]),
+                               int(it["boxes"].shape[0]), int(it["seed"]), int(it.get("frame", 0)),
+                               int(it.get("spp", 1)), _ptr(it["rgb"]))
+        h = ctypes.c_void_p()
+        ctx._check(ctx.lib.rll_batch_create(ctx.h, arr, len(items), ctypes.byref(h)))
+        self.ctx, self.h, self.items = ctx, h, items
+
+    def set_config(self, tile_points, min_blocks):
+        self.ctx._check(self.ctx.lib.rll_batch_set_config(self.ctx.h, self.h, int(tile_points), int(min_blocks)))
+
+    def tune(self):
+        tp, mb = ctypes.c_int32(), ctypes.c_int32()
+        self.ctx._check(self.ctx.lib.rll_batch_tune(self.ctx.h, self.h, ctypes.byref(tp), ctypes.byref(mb)))
+        return tp.value, mb.value
+
+    def run(self, do_split=True):
+        self.ctx._check(self.ctx.lib.rll_batch_run(self.ctx.h, self.h, int(bool(do_split))))
+
+    def capture(self, do_split=True):
+        self.ctx._check(self.ctx.lib.rll_batch_capture(self.ctx.h, self.h, int(bool(do_split))))
+
+    def launch(self):
+        self.ctx._check(self.ctx.lib.rll_batch_launch(self.ctx.h, self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.rll_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

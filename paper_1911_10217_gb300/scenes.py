@@ -104,13 +104,11 @@ def _quad_patch(center, u_axis, v_axis, nu, nv, rng, jitter=0.0):
         inner[1:-1, 1:-1] = 1.0
         P = P + inner * (j[..., :1] * du * u_axis / np.linalg.norm(u_axis)
                          + j[..., 1:] * dv * v_axis / np.linalg.norm(v_axis))
-    tris = []
-    for i in range(nu):
-        for k in range(nv):
-            a, b, c, d = P[i, k], P[i + 1, k], P[i + 1, k + 1], P[i, k + 1]
-            tris.append([a, b, c])
-            tris.append([a, c, d])
-    return np.asarray(tris, np.float64)
+    a, b = P[:-1, :-1], P[1:, :-1]
+    c, d = P[1:, 1:], P[:-1, 1:]
+    t1 = np.stack([a, b, c], axis=2)            # [nu, nv, 3, 3]
+    t2 = np.stack([a, c, d], axis=2)
+    return np.stack([t1, t2], axis=2).reshape(-1, 3, 3)  # (i, k) quad -> two triangles
 
 
 def _orthonormal(n):
@@ -324,7 +322,7 @@ def batched_scenes(seed: int = 4, n_scenes: int = 256, light_range=(1 << 10, 1 <
         tpp = max(2, (nl // n_patches) // 2 * 2)
         width = int(math.sqrt(npnt * 16 / 9)) // 4 * 4 or 4
         height = max(4, npnt // width // 4 * 4)
-        table = 1 << max(10, int(math.ceil(math.log2(max(1, width * height) / 4))))
+        table = 1 << max(10, int(math.ceil(math.log2(max(1, width * height) / 16))))
         s = frame_scene(seed=seed * 100003 + i, width=width, height=height, n_patches=n_patches,
                         tris_per_patch=tpp, n_boxes=32, table_size=table, cut_size=m, frames=1)
         s.name = f"batched{i}"

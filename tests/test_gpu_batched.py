@@ -1,0 +1,150 @@
+"""GPU tests of the batched form: many uneven scenes sampled by one
+persistent launch, learned by one sort and one per-cell kernel, replayed
+as a CUDA graph, with an autotuned tile size."""
+import numpy as np
+import pytest
+
+from paper_1911_10217_gb300 import scenes
+
+from .gpu_common import RTOL, compare_tables, device_scene, oracle_state, params_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _mini_scenes():
+    """Uneven scenes: light counts, point counts and cut sizes all differ."""
+    specs = [(64, 48, 8, 64, 16, 1), (96, 64, 16, 128, 32, 2), (40, 24, 4, 32, 64, 1), (128, 72, 24, 64, 32, 1)]
+    out = []
+    for i, (w, h, npatch, tpp, M, spp) in enumerate(specs):
+        s = scenes.frame_scene(seed=50 + i, width=w, height=h, n_patches=npatch, tris_per_patch=tpp,
+                               n_boxes=32, table_size=1 << 13, cut_size=M, frames=1)
+        s.spp = spp
+        out.append(s)
+    return out
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import oracle as O
+    from paper_1911_10217_gb300 import rll
+    dev = torch.device("cuda:0")
+    ctx = rll.Context(0, torch.cuda.current_stream(dev))
+    ctx.sync_status()
+    return dict(torch=torch, O=O, rll=rll, dev=dev, ctx=ctx)
+
+
+def _build(env, sc, which=None):
+    rll, ctx, torch = env["rll"], env["ctx"], env["torch"]
+    objs = []
+    for i, s in enumerate(sc):
+        if which is not None and i not in which:
+            continue
+        d = device_scene(s, env["dev"])
+        tree = rll.Tree(ctx, d["tri"], d["em"])
+        grid = rll.Grid(ctx, tree, params_for(rll, s))
+        rgb = torch.zeros(3, s.n_points, device=env["dev"])
+        objs.append(dict(scene=s, d=d, tree=tree, grid=grid, rgb=rgb, idx=i))
+    items = [dict(grid=o["grid"], tree=o["tree"], pos=o["d"]["pos"], nrm=o["d"]["nrm"], albedo=o["d"]["alb"],
+                  boxes=o["d"]["boxes"], seed=o["scene"].seed, frame=0, spp=o["scene"].spp, rgb=o["rgb"])
+             for o in objs]
+    return objs, rll.Batch(ctx, items)
+
+
+def _sorted_state(grid):
+    st = grid.export()
+    o = np.argsort(st["keys"])
+    occ = st["keys"][o] != np.uint64(0xFFFFFFFFFFFFFFFF)
+    return {k: v[o][occ] for k, v in st.items()}
+
+
+def test_batch_alone_equals_in_the_mix(env):
+    sc = _mini_scenes()
+    mix_objs, mix = _build(env, sc)
+    for _ in range(3):
+        mix.run(do_split=True)
+    for k in range(len(sc)):
+        alone_objs, alone = _build(env, sc, which=[k])
+        for _ in range(3):
+            alone.run(do_split=True)
+        a, b = alone_objs[0], mix_objs[k]
+        assert np.array_equal(a["rgb"].cpu().numpy(), b["rgb"].cpu().numpy())
+        sa, sb = _sorted_state(a["grid"]), _sorted_state(b["grid"])
+        for key in ("keys", "cut", "q", "c"):
+            assert np.array_equal(sa[key], sb[key]), (k, key)
+    assert env["ctx"].sync_status() == 0
+
+
+def test_batch_matches_single_grid_path(env):
+    rll, ctx, torch = env["rll"], env["ctx"], env["torch"]
+    sc = _mini_scenes()
+    objs, batch = _build(env, sc)
+    singles = []
+    for o in objs:
+        g = rll.Grid(ctx, o["tree"], params_for(rll, o["scene"]))
+        singles.append(g)
+    for frame in range(2):
+        batch.run(do_split=True)
+        for o, g in zip(objs, singles):
+            s, d = o["scene"], o["d"]
+            P = s.n_points
+            rgb = torch.empty(3, P, device=env["dev"])
+            key = torch.empty(P * s.spp, dtype=torch.int32, device=env["dev"])
+            val = torch.empty(P * s.spp, device=env["dev"])
+            rll.sample_and_shade(ctx, g, o["tree"], d["pos"], d["nrm"], d["alb"], d["boxes"], s.seed, frame,
+                                 s.spp, rgb, key, val)
+            rll.learn_update(ctx, g, key, val)
+            rll.split_collapse(ctx, g, o["tree"])
+            assert np.allclose(o["rgb"].cpu().numpy(), rgb.cpu().numpy(), rtol=1e-5, atol=1e-9)
+            compare_tables(o["grid"].export(), g.export(), g.m, RTOL["fp32"])
+    assert ctx.sync_status() == 0
+
+
+def test_batch_frame0_matches_oracle(env):
+    O = env["O"]
+    sc = _mini_scenes()
+    objs, batch = _build(env, sc)
+    batch.run(do_split=False)
+    for o in objs:
+        s = o["scene"]
+        ot = O.Tree(s.tris, s.emission)
+        og = O.Grid.for_scene(ot, s)
+        out = og.sample_frame(O.scene_arrays(s), s.seed, 0, s.spp)
+        assert np.allclose(o["rgb"].cpu().numpy(), out["rgb"], rtol=1e-4, atol=1e-7)
+        og.learn(out["slot"], out["s"], out["reward"])
+        compare_tables(o["grid"].export(), oracle_state(og), og.m, RTOL["fp32"])
+
+
+def test_graph_replay_equals_direct_passes(env):
+    sc = _mini_scenes()
+    a_objs, a = _build(env, sc)
+    b_objs, b = _build(env, sc)
+    for _ in range(3):
+        a.run(do_split=True)
+    b.capture(do_split=True)
+    for _ in range(3):
+        b.launch()
+    env["torch"].cuda.synchronize()
+    for x, y in zip(a_objs, b_objs):
+        assert np.array_equal(x["rgb"].cpu().numpy(), y["rgb"].cpu().numpy())
+        sx, sy = _sorted_state(x["grid"]), _sorted_state(y["grid"])
+        for key in ("keys", "cut", "q", "c"):
+            assert np.array_equal(sx[key], sy[key]), key
+
+
+def test_autotuner_picks_a_valid_config_and_keeps_results(env):
+    rll = env["rll"]
+    sc = _mini_scenes()
+    a_objs, a = _build(env, sc)
+    b_objs, b = _build(env, sc)
+    tp, mb = b.tune()
+    assert tp in (128, 256, 512, 1024, 2048, 4096, 8192) and mb in (3, 4)
+    for _ in range(2):
+        a.run()
+        b.run()
+    for x, y in zip(a_objs, b_objs):
+        assert np.array_equal(x["rgb"].cpu().numpy(), y["rgb"].cpu().numpy())
+    with pytest.raises(rll.RllError):
+        b.set_config(7, 4)
