@@ -254,6 +254,92 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Continuous batching of frame requests from many sessions (half of the
+    frame-scale shape, half of the 4K / 1M-light shape, BF16 tables), Poisson
+    arrivals at a fixed fraction of the measured capacity, admission by an HBM
+    budget; p50 / p99 frame latency and served samples per second."""
+    import torch
+    from paper_1911_10217_gb300 import rll, scenes, serving
+    dev = torch.device("cuda:0")
+    n_sessions, frames = args.serving_sessions, args.serving_frames
+    sc = args.serving_scale
+    t0 = time.perf_counter()
+    shape_a = scenes.frame_scene(seed=1, width=int(1920 * sc), height=int(1080 * sc))
+    shape_b = scenes.dynamic_scene(seed=2, width=int(3840 * sc), height=int(2160 * sc))
+    gen_s = time.perf_counter() - t0
+    prec = "bf16"
+    shapes = {sid: (shape_a if sid % 2 == 0 else shape_b) for sid in range(n_sessions)}
+    max_items, max_records, max_cells = 64, 1 << 26, (1 << 26) - 1
+    ex = serving.GpuExecutor(torch, rll, dev, max_items, max_records, max_cells)
+    budget = int(args.serving_budget_gb * 1e9)
+    sched = serving.Scheduler(budget, max_items, max_records, max_cells,
+                              reserved_bytes=ex.reserved_bytes(max_records, max_cells))
+
+    def size(s):
+        return serving.session_bytes(s.n_lights, s.n_points, s.grid.table_size, s.grid.cut_size, prec)
+
+    # capacity: full launches of one session of each shape, repeated
+    cal = {10**6: shape_a, 10**6 + 1: shape_b}
+    for sid, s in cal.items():
+        ex.create(sid, s, prec, seed=sid)
+    items_sched = serving.Scheduler(10**15, max_items, max_records, max_cells)
+    for sid, s in cal.items():
+        items_sched.add_session(sid, 0, s.n_points * s.spp, s.grid.table_size, 10)
+    items_sched.admit()
+    cal_samples, t_cal = 0, 0.0
+    for f in range(8):
+        for sid in cal:
+            items_sched.arrive(serving.Request(sid, f, 0.0))
+        batch = items_sched.form_batch()
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        ex.launch(0, batch, {r.session: f for r in batch})
+        while not ex.poll():
+            pass
+        dt = time.perf_counter() - c0
+        items_sched.complete(batch, 0.0)
+        if f >= 2:
+            t_cal += dt
+            cal_samples += sum(cal[r.session].n_points * cal[r.session].spp for r in batch)
+    for sid in cal:
+        ex.release(sid)
+    capacity = cal_samples / t_cal
+    mean_samples = np.mean([shapes[s].n_points * shapes[s].spp for s in shapes])
+    rate_total = args.serving_load * capacity / mean_samples   # frames per second
+    rng = np.random.default_rng(11)
+    arrivals = {sid: serving.poisson_arrivals(rng, frames, rate_total / n_sessions) for sid in shapes}
+    for sid, s in shapes.items():
+        sched.add_session(sid, size(s), s.n_points * s.spp, s.grid.table_size, frames)
+    seeded = {sid: s for sid, s in shapes.items()}
+    # each session its own Philox seed
+    orig_create = ex.create
+    ex.create = lambda sid, s, p: orig_create(sid, s, p, seed=1000 + sid)
+    w0 = time.perf_counter()
+    log = serving.serve(ex, sched, seeded, arrivals, precision=prec, timeout_s=3600.0)
+    wall = time.perf_counter() - w0
+    lat = np.array([1e3 * (r.done - r.arrival) for r in log])
+    starts = {}
+    for r in log:
+        starts.setdefault(r.start, []).append(r)
+    served = sum(shapes[r.session].n_points * shapes[r.session].spp for r in log)
+    status = ex.status()
+    line = {"metric": METRIC, "workload": "serving", "value": served / wall, "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32 arithmetic, bf16 tables", "data": "synthetic",
+            "p50_frame_ms": float(np.percentile(lat, 50)), "p99_frame_ms": float(np.percentile(lat, 99)),
+            "frames": len(log), "launches": len(starts), "mean_sessions_per_launch": len(log) / len(starts),
+            "offered_load_fraction": args.serving_load, "capacity_samples_per_s": capacity,
+            "config": {"workload": f"{n_sessions} sessions, continuous batching, HBM-budget admission",
+                       "sessions": n_sessions, "frames_per_session": frames,
+                       "shape_a": f"{shape_a.width}x{shape_a.height}, {shape_a.n_lights} lights, M={shape_a.grid.cut_size}",
+                       "shape_b": f"{shape_b.width}x{shape_b.height}, {shape_b.n_lights} lights, M={shape_b.grid.cut_size}",
+                       "budget_gb": args.serving_budget_gb, "table_precision": prec,
+                       "resident_gb": sum(size(s) for s in shapes.values()) / 1e9},
+            "wall_s": wall, "generation_s": gen_s, "device_status": status}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -265,7 +351,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
     ap.add_argument("--sample-prefetch", type=int, default=0)
-    ap.add_argument("--workload", default="frame", choices=["frame", "batched"])
+    ap.add_argument("--workload", default="frame", choices=["frame", "batched", "serving"])
+    ap.add_argument("--serving-sessions", type=int, default=64)
+    ap.add_argument("--serving-frames", type=int, default=160)
+    ap.add_argument("--serving-scale", type=float, default=1.0)
+    ap.add_argument("--serving-load", type=float, default=0.7)
+    ap.add_argument("--serving-budget-gb", type=float, default=80.0)
     ap.add_argument("--batched-scenes", type=int, default=256)
     ap.add_argument("--batched-scale", type=float, default=1.0)
     args = ap.parse_args()
@@ -273,6 +364,8 @@ def main():
 
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     from paper_1911_10217_gb300 import scenes
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -229,9 +229,18 @@ typedef struct rll_batch_item {
 
 typedef struct rll_batch rll_batch;
 
-/* Creates a batch over n_items scenes (all grids with the same table
- * precision and in-cluster mode, cut sizes <= 64, sum of table sizes
- * < 2^26). Allocates the batch's record, sort and work buffers once.
+/* Reserves a batch able to hold up to max_items scenes with at most
+ * max_records samples and max_cells table slots in total (< 2^26); all
+ * device buffers are allocated here, once. */
+int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int64_t max_cells,
+                      rll_batch** out);
+/* Sets the scenes of the next passes (all grids with the same table
+ * precision and in-cluster mode, cut sizes <= 64, each grid at most once,
+ * within the reserved capacity). Uploads descriptors only, allocates
+ * nothing; drops a recorded graph. Synchronises the context stream. */
+int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items, int32_t n_items);
+/* rll_batch_reserve for exactly these items, then rll_batch_set_items.
+ *
  * One pass = sampling of every item by one persistent kernel that takes
  * tiles of points from a global counter, one sort of all records, Eq. 1 +
  * Eq. 2 for every touched cell, optional split-collapse, then each item's

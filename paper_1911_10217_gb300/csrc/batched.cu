@@ -192,6 +192,9 @@ struct rll_batch {
     uint32_t* n_touched = nullptr;
     int max_boxes = 0;
     uint32_t* status = nullptr;
+    int32_t cap_items = 0;
+    int64_t cap_records = 0;
+    int64_t cap_cells = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
 };
@@ -321,60 +324,88 @@ struct DevGuard {
 
 extern "C" {
 
-int rll_batch_create(rll_ctx* ctx, const rll_batch_item* items, int32_t n_items, rll_batch** out)
+int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int64_t max_cells, rll_batch** out)
 {
     if (!ctx || !out) return RLL_E_INVALID;
     *out = nullptr;
-    if (!items || n_items < 1 || n_items > 65536) return fail(ctx, RLL_E_INVALID, "need 1..65536 items");
+    if (max_items < 1 || max_items > 65536) return fail(ctx, RLL_E_INVALID, "max_items must be in [1, 65536]");
+    if (max_records < 0 || max_records >= 0xFFFFFFFFll) return fail(ctx, RLL_E_INVALID, "max_records must be < 2^32");
+    if (max_cells < 1 || (max_cells << kBatchClusterBits) >= 0xFFFFFFFFll)
+        return fail(ctx, RLL_E_INVALID, "max_cells must be in [1, 2^26)");
     DevGuard dg(ctx->device);
     rll_batch* b = new (std::nothrow) rll_batch();
     if (!b) return fail(ctx, RLL_E_NOMEM, "host allocation");
     b->device = ctx->device;
-    b->n = n_items;
     b->status = ctx->d_status;
-    uint64_t cells = 0, recs = 0;
-    for (int i = 0; i < n_items; ++i) {
-        const rll_batch_item& it = items[i];
-        if (!it.grid || !it.tree) return free_batch(b), fail(ctx, RLL_E_INVALID, "item without grid or tree");
-        const rll_grid* g = it.grid;
-        if (g->n_lights != it.tree->n) return free_batch(b), fail(ctx, RLL_E_INVALID, "item grid built for another tree");
-        if (i == 0) {
-            b->precision = g->p.precision;
-            b->mode = g->p.in_cluster_mode;
-        } else if (g->p.precision != b->precision || g->p.in_cluster_mode != b->mode) {
-            return free_batch(b), fail(ctx, RLL_E_INVALID, "all items need the same table precision and in-cluster mode");
-        }
-        if (g->M > (1u << kBatchClusterBits)) return free_batch(b), fail(ctx, RLL_E_INVALID, "batched cut size must be <= 64");
-        if (it.n_points < 0 || it.spp < 1 || it.spp > 65536 || (uint64_t)it.n_points * it.spp >= 0xFFFFFFFFull)
-            return free_batch(b), fail(ctx, RLL_E_INVALID, "bad n_points / spp");
-        if (it.n_boxes < 0 || it.n_boxes > kMaxBoxes || (it.n_boxes > 0 && !it.boxes))
-            return free_batch(b), fail(ctx, RLL_E_INVALID, "bad boxes");
-        if (it.n_points > 0 && (!it.pos || !it.nrm || !it.albedo || !it.rgb))
-            return free_batch(b), fail(ctx, RLL_E_INVALID, "NULL G-buffer or rgb");
-        if (it.n_points > 0xFFFFFFFFll) return free_batch(b), fail(ctx, RLL_E_INVALID, "too many points in one item");
-        cells += g->H;
-        recs += (uint64_t)it.n_points * it.spp;
-        b->max_boxes = std::max(b->max_boxes, (int)it.n_boxes);
-    }
-    if ((cells << kBatchClusterBits) >= 0xFFFFFFFFull) return free_batch(b), fail(ctx, RLL_E_INVALID, "too many cells in the batch (sum of table sizes must be < 2^26)");
-    if (recs >= 0xFFFFFFFFull) return free_batch(b), fail(ctx, RLL_E_INVALID, "too many samples in the batch");
-    b->total_cells = (uint32_t)cells;
-    b->n_records = (int64_t)recs;
-    cudaError_t e = cudaMalloc((void**)&b->rec_key, 4 * std::max<size_t>(recs, 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->rec_val, 4 * std::max<size_t>(recs, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->sort_ws, radix_sort_scratch_bytes((int64_t)recs));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched, 4 * std::max<size_t>(cells, 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched_start, 4 * std::max<size_t>(cells, 1));
+    b->cap_items = max_items;
+    b->cap_records = max_records;
+    b->cap_cells = max_cells;
+    cudaError_t e = cudaMalloc((void**)&b->rec_key, 4 * std::max<size_t>(max_records, 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->rec_val, 4 * std::max<size_t>(max_records, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->sort_ws, radix_sort_scratch_bytes(max_records));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched, 4 * (size_t)max_cells);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched_start, 4 * (size_t)max_cells);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->n_touched, 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_work, 4);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, sizeof(BatchItemDev) * n_items);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tile_prefix, 4 * (n_items + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cell_prefix, 4 * (n_items + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, sizeof(BatchItemDev) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tile_prefix, 4 * (max_items + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cell_prefix, 4 * (max_items + 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->n_touched, 0, 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         const int rc = check_cuda(ctx, e, "batch allocation");
         free_batch(b);
         return rc;
     }
+    *out = b;
+    return RLL_OK;
+}
+
+int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items, int32_t n_items)
+{
+    if (!ctx || !b) return RLL_E_INVALID;
+    if (!items || n_items < 1 || n_items > b->cap_items) return fail(ctx, RLL_E_INVALID, "need 1..max_items items");
+    DevGuard dg(ctx->device);
+    uint32_t precision = 0, mode = 0;
+    uint64_t cells = 0, recs = 0;
+    int max_boxes = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const rll_batch_item& it = items[i];
+        if (!it.grid || !it.tree) return fail(ctx, RLL_E_INVALID, "item without grid or tree");
+        const rll_grid* g = it.grid;
+        if (g->n_lights != it.tree->n) return fail(ctx, RLL_E_INVALID, "item grid built for another tree");
+        if (i == 0) {
+            precision = g->p.precision;
+            mode = g->p.in_cluster_mode;
+        } else if (g->p.precision != precision || g->p.in_cluster_mode != mode) {
+            return fail(ctx, RLL_E_INVALID, "all items need the same table precision and in-cluster mode");
+        }
+        if (g->M > (1u << kBatchClusterBits)) return fail(ctx, RLL_E_INVALID, "batched cut size must be <= 64");
+        for (int j = 0; j < i; ++j)
+            if (items[j].grid == g) return fail(ctx, RLL_E_INVALID, "a grid appears twice in one batch");
+        if (it.n_points < 0 || it.n_points > 0xFFFFFFFFll || it.spp < 1 || it.spp > 65536 ||
+            (uint64_t)it.n_points * it.spp >= 0xFFFFFFFFull)
+            return fail(ctx, RLL_E_INVALID, "bad n_points / spp");
+        if (it.n_boxes < 0 || it.n_boxes > kMaxBoxes || (it.n_boxes > 0 && !it.boxes))
+            return fail(ctx, RLL_E_INVALID, "bad boxes");
+        if (it.n_points > 0 && (!it.pos || !it.nrm || !it.albedo || !it.rgb))
+            return fail(ctx, RLL_E_INVALID, "NULL G-buffer or rgb");
+        cells += g->H;
+        recs += (uint64_t)it.n_points * it.spp;
+        max_boxes = std::max(max_boxes, (int)it.n_boxes);
+    }
+    if ((int64_t)cells > b->cap_cells) return fail(ctx, RLL_E_INVALID, "items exceed the batch's cell capacity");
+    if ((int64_t)recs > b->cap_records) return fail(ctx, RLL_E_INVALID, "items exceed the batch's record capacity");
+    if (b->graph) {  // a recorded pass holds the old sizes
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->n = n_items;
+    b->precision = precision;
+    b->mode = mode;
+    b->max_boxes = max_boxes;
+    b->total_cells = (uint32_t)cells;
+    b->n_records = (int64_t)recs;
     b->host.resize(n_items);
     b->points_per_item.resize(n_items);
     std::vector<uint32_t> cell_pre(n_items + 1, 0);
@@ -416,7 +447,7 @@ int rll_batch_create(rll_ctx* ctx, const rll_batch_item* items, int32_t n_items,
         a.rgb = it.rgb;
         a.rec_key = b->rec_key + rec_off;
         a.rec_val = b->rec_val + rec_off;
-        a.status = ctx->d_status;
+        a.status = b->status;
         a.prefetch = 0;
         a.key_cells = 1;
         a.cell_base = cell_pre[i];
@@ -436,14 +467,34 @@ int rll_batch_create(rll_ctx* ctx, const rll_batch_item* items, int32_t n_items,
         rec_off += (uint64_t)it.n_points * it.spp;
         b->points_per_item[i] = (uint32_t)it.n_points;
     }
-    e = cudaMemcpyAsync(b->d_items, b->host.data(), sizeof(BatchItemDev) * n_items, cudaMemcpyHostToDevice, ctx->stream);
+    cudaError_t e = cudaMemcpyAsync(b->d_items, b->host.data(), sizeof(BatchItemDev) * n_items,
+                                    cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_cell_prefix, cell_pre.data(), 4 * (n_items + 1), cudaMemcpyHostToDevice, ctx->stream);
     int rc = check_cuda(ctx, e, "batch upload");
-    if (rc == RLL_OK) rc = set_tiles(ctx, b, 1024);
-    if (rc == RLL_OK) rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "batch create");
+    if (rc == RLL_OK) rc = set_tiles(ctx, b, b->tile_points);
+    // the host-side descriptor and prefix arrays are pageable: finish the copies
+    if (rc == RLL_OK) rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "batch items");
+    return rc;
+}
+
+int rll_batch_create(rll_ctx* ctx, const rll_batch_item* items, int32_t n_items, rll_batch** out)
+{
+    if (!ctx || !out) return RLL_E_INVALID;
+    *out = nullptr;
+    if (!items || n_items < 1) return fail(ctx, RLL_E_INVALID, "need at least one item");
+    int64_t recs = 0, cells = 0;
+    for (int i = 0; i < n_items; ++i) {
+        if (!items[i].grid) return fail(ctx, RLL_E_INVALID, "item without grid");
+        recs += std::max<int64_t>(items[i].n_points, 0) * std::max(items[i].spp, 1);
+        cells += items[i].grid->H;
+    }
+    rll_batch* b = nullptr;
+    int rc = rll_batch_reserve(ctx, n_items, recs, cells, &b);
+    if (rc != RLL_OK) return rc;
+    rc = rll_batch_set_items(ctx, b, items, n_items);
     if (rc != RLL_OK) {
-        free_batch(b);
+        rll_batch_destroy(b);
         return rc;
     }
     *out = b;

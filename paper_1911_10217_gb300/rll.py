@@ -30,7 +30,7 @@ EXPORTS = [
     "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_export", "rll_grid_import",
     "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_power",
     "rll_learn_update", "rll_learn_update_noalloc", "rll_split_collapse", "rll_render_pass_host",
-    "rll_batch_create", "rll_batch_set_config", "rll_batch_tune", "rll_batch_run", "rll_batch_capture",
+    "rll_batch_reserve", "rll_batch_set_items", "rll_batch_create", "rll_batch_set_config", "rll_batch_tune", "rll_batch_run", "rll_batch_capture",
     "rll_batch_launch", "rll_batch_destroy",
 ]
 
@@ -109,6 +109,8 @@ def load(build_if_missing: bool = True):
     L.rll_split_collapse.argtypes = [P, P, P]
     L.rll_render_pass_host.argtypes = [P, P, P, P, P, P, I64, P, I32, U64, U32, I32, I32, P]
     L.rll_batch_create.argtypes = [P, ctypes.POINTER(BatchItem), I32, ctypes.POINTER(P)]
+    L.rll_batch_reserve.argtypes = [P, I32, I64, I64, ctypes.POINTER(P)]
+    L.rll_batch_set_items.argtypes = [P, P, ctypes.POINTER(BatchItem), I32]
     L.rll_batch_set_config.argtypes = [P, P, I32, I32]
     L.rll_batch_tune.argtypes = [P, P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
     L.rll_batch_run.argtypes = [P, P, I32]
@@ -333,16 +335,28 @@ class Batch:
     `items` is a list of dicts with keys grid, tree, pos, nrm, albedo, boxes,
     seed, frame, spp, rgb (device tensors for the arrays)."""
 
-    def __init__(self, ctx: Context, items):
+    def __init__(self, ctx: Context, items=None, max_items=None, max_records=None, max_cells=None):
+        h = ctypes.c_void_p()
+        if items is not None:
+            ctx._check(ctx.lib.rll_batch_create(ctx.h, self._array(items), len(items), ctypes.byref(h)))
+        else:
+            ctx._check(ctx.lib.rll_batch_reserve(ctx.h, int(max_items), int(max_records), int(max_cells),
+                                                 ctypes.byref(h)))
+        self.ctx, self.h, self.items = ctx, h, items
+
+    @staticmethod
+    def _array(items):
         arr = (BatchItem * len(items))()
         for i, it in enumerate(items):
             arr[i] = BatchItem(it["grid"].h.value, it["tree"].h.value, _ptr(it["pos"]), _ptr(it["nrm"]),
                                _ptr(it["albedo"]), int(it["albedo"].shape[0]), _ptr(it["boxes"]),
                                int(it["boxes"].shape[0]), int(it["seed"]), int(it.get("frame", 0)),
                                int(it.get("spp", 1)), _ptr(it["rgb"]))
-        h = ctypes.c_void_p()
-        ctx._check(ctx.lib.rll_batch_create(ctx.h, arr, len(items), ctypes.byref(h)))
-        self.ctx, self.h, self.items = ctx, h, items
+        return arr
+
+    def set_items(self, items):
+        self.ctx._check(self.ctx.lib.rll_batch_set_items(self.ctx.h, self.h, self._array(items), len(items)))
+        self.items = items
 
     def set_config(self, tile_points, min_blocks):
         self.ctx._check(self.ctx.lib.rll_batch_set_config(self.ctx.h, self.h, int(tile_points), int(min_blocks)))
