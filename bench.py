@@ -340,6 +340,81 @@ def run_serving(args):
     return 0
 
 
+def run_dynamic(args):
+    """Dynamic lighting (1M triangles, 10% blinking, 3840x2160, M = 64,
+    split-collapse every frame) with FP32, FP16 and BF16 tables: time per
+    frame and 1-spp MSE against a high-spp energy-sampler reference of the
+    last frame."""
+    import torch
+    from paper_1911_10217_gb300 import rll, scenes
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    ctx = rll.Context(0, stream)
+    sc = args.dynamic_scale
+    s = scenes.dynamic_scene(width=int(3840 * sc), height=int(2160 * sc))
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    tri, bound, em0 = T(s.tris.reshape(-1, 9)), T(s.emission_bound()), T(s.emission)
+    omega, phase = T(s.blink_omega), T(s.blink_phase)
+    mask = T(s.blink_mask.astype(np.float32))
+    boxes, pos, nrm, alb = T(s.boxes), T(s.pos), T(s.nrm), T(s.albedo)
+    tree = rll.Tree(ctx, tri, bound)
+    P = s.n_points
+    em = torch.empty_like(em0)
+
+    def set_emission(frame):
+        t = frame / 30.0
+        scale = 1.0 + mask * 0.9 * torch.sin(omega * t + phase)
+        torch.mul(em0, scale[:, None], out=em)
+        tree.update_emission(em)
+
+    rgb = torch.empty(3, P, device=dev)
+    key = torch.empty(P * s.spp, dtype=torch.int32, device=dev)
+    val = torch.empty(P * s.spp, device=dev)
+    g = s.grid
+    results = {}
+    frames = args.dynamic_frames
+    for prec in ("fp32", "fp16", "bf16"):
+        grid = rll.Grid(ctx, tree, rll.grid_params(g.table_size, g.cut_size, g.origin, g.cell_size, g.normal_bins,
+                                                   g.jitter, precision=prec, q_init=g.q_init))
+        ms = []
+        for f in range(frames):
+            set_emission(f)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, s.seed, f, s.spp, rgb, key, val)
+            rll.learn_update(ctx, grid, key, val)
+            rll.split_collapse(ctx, grid, tree)
+            e1.record(stream)
+            ms.append((e0, e1))
+        torch.cuda.synchronize()
+        t = [a.elapsed_time(b) for a, b in ms][3:]
+        # reference of the last frame: energy sampler, 256 spp
+        set_emission(frames - 1)
+        ref = torch.zeros(3, P, device=dev, dtype=torch.float64)
+        tmp = torch.empty(3, P, device=dev)
+        for i in range(32):
+            rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 9999, 200000 + i, 8, tmp)
+            ref += tmp.double()
+        ref /= 32
+        rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, 4242, 300000, 1, tmp)
+        mse = float(((tmp.double() - ref) ** 2).mean())
+        rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 4242, 300000, 1, tmp)
+        mse_pow = float(((tmp.double() - ref) ** 2).mean())
+        e = 4 if prec == "fp32" else 2
+        results[prec] = {"ms_per_frame": statistics.mean(t), "p99_frame_ms": float(np.percentile(t, 99)),
+                         "samples_per_s": P * s.spp / (statistics.mean(t) * 1e-3),
+                         "mse_1spp": mse, "energy_sampler_mse_1spp": mse_pow, "mse_ratio_vs_energy": mse_pow / mse,
+                         "table_bytes": g.table_size * g.cut_size * (4 + 2 * e)}
+        grid.close()
+    line = {"metric": METRIC, "workload": "dynamic", "unit": UNIT, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "dynamic lighting, 10% blinking lights, split-collapse every frame",
+                       "points": P, "lights": s.n_lights, "cut_size": g.cut_size, "table_size": g.table_size,
+                       "frames": frames, "boxes": int(s.boxes.shape[0])},
+            "precisions": results, "device_status": ctx.sync_status()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -351,7 +426,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
     ap.add_argument("--sample-prefetch", type=int, default=0)
-    ap.add_argument("--workload", default="frame", choices=["frame", "batched", "serving"])
+    ap.add_argument("--workload", default="frame", choices=["frame", "batched", "serving", "dynamic"])
+    ap.add_argument("--dynamic-scale", type=float, default=1.0)
+    ap.add_argument("--dynamic-frames", type=int, default=120)
     ap.add_argument("--serving-sessions", type=int, default=64)
     ap.add_argument("--serving-frames", type=int, default=160)
     ap.add_argument("--serving-scale", type=float, default=1.0)
@@ -366,6 +443,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "dynamic":
+        return run_dynamic(args)
     from paper_1911_10217_gb300 import scenes
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
