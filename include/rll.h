@@ -192,7 +192,7 @@ int rll_learn_update(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key, cons
  * an allocation budget enforced outside CUDA, a loop that must not
  * synchronise -- rll_learn_update grows its workspace with cudaFree and
  * cudaMalloc). Nothing is allocated: the sort buffers are one fixed device
- * array inside the library (about 17 MB, held on every GPU that loads the
+ * array inside the library (about 18 MB, held on every GPU that loads the
  * library until exit). At most 1048576 records per call; more returns
  * RLL_E_INVALID without launching. The first call on a device looks up the
  * array's address: make it before any stream capture. All calls share the

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
 k_sample_batched(const BatchItemDev* __restrict__ items, int n_items, const uint32_t* __restrict__ tile_prefix,
                  uint32_t total_tiles, uint32_t tile_points, uint32_t* __restrict__ work)
 {
-    extern __shared__ float s_box[];
+    extern __shared__ float4 s_box[];
     __shared__ uint32_t s_tile;
     __shared__ int s_item;
     __shared__ SampleArgs s_args;  // the current item's arguments
@@ -80,9 +80,7 @@ k_sample_batched(const BatchItemDev* __restrict__ items, int n_items, const uint
             const uint32_t* src = reinterpret_cast<const uint32_t*>(&items[it].s);
             uint32_t* dst = reinterpret_cast<uint32_t*>(&s_args);
             for (int i = threadIdx.x; i < (int)(sizeof(SampleArgs) / 4); i += blockDim.x) dst[i] = src[i];
-            const float* bx = items[it].s.boxes;
-            const int nb6 = items[it].s.n_boxes * 6;
-            for (int i = threadIdx.x; i < nb6; i += blockDim.x) s_box[i] = bx[i];
+            stage_boxes(s_box, items[it].s.boxes, items[it].s.n_boxes);
             cur = it;
         }
         __syncthreads();
@@ -243,7 +241,7 @@ template <int P, int MODE, int MINB>
 cudaError_t launch_sample_t(rll_batch* b, cudaStream_t s)
 {
     int per_sm = 0;
-    const size_t smem = sizeof(float) * 6 * (size_t)std::max(b->max_boxes, 1);
+    const size_t smem = sizeof(float4) * 2 * (size_t)std::max(b->max_boxes, 1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_batched<P, MODE, MINB>, kBatchThreads, smem);
     const int blocks = std::max(1, per_sm) * device_sm_count(b->device);
     cudaError_t e = cudaMemsetAsync(b->d_work, 0, sizeof(uint32_t), s);

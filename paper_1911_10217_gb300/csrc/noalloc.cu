@@ -28,11 +28,8 @@ namespace {
 // Largest record count one call accepts.
 constexpr int64_t kNoAllocMaxRecords = int64_t(1) << 20;
 
-// Sort scratch for kNoAllocMaxRecords records: four key/value arrays of 4 B
-// per record, the per-tile digit counts (256 digits x 512 tiles of 2048) and
-// the 256 digit totals, each rounded up to 256 bytes.
-constexpr size_t kNoAllocScratchBytes =
-    4 * (size_t)(4 * kNoAllocMaxRecords) + (size_t)(4 * 256 * (kNoAllocMaxRecords / 2048)) + (size_t)(4 * 256);
+// Sort scratch for kNoAllocMaxRecords records (the sort's own formula).
+constexpr size_t kNoAllocScratchBytes = rll::sort_scratch_bytes_for(kNoAllocMaxRecords);
 
 static __device__ __align__(256) unsigned char g_learn_scratch[kNoAllocScratchBytes];
 

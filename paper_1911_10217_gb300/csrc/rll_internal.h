@@ -69,7 +69,18 @@ int check_cuda(rll_ctx* ctx, cudaError_t e, const char* what);
 void* ws_get(rll_ctx* ctx, size_t bytes);  // nullptr on failure (error recorded)
 
 // ---- sort.cu
-// Scratch bytes needed by radix_sort_pairs for n items.
+// Scratch of radix_sort_pairs for n items: four key/value arrays, the
+// per-tile digit counts (up to 512 digits, tiles of 2048) and the digit
+// totals, each rounded up to 256 bytes.
+constexpr int kSortTile = 2048;
+constexpr int kSortMaxDigits = 512;
+constexpr size_t sort_align256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t sort_scratch_bytes_for(int64_t n)
+{
+    return 4 * sort_align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)) +
+           sort_align256(sizeof(uint32_t) * kSortMaxDigits * (size_t)(n > 0 ? (n + kSortTile - 1) / kSortTile : 1)) +
+           sort_align256(sizeof(uint32_t) * kSortMaxDigits);
+}
 size_t radix_sort_scratch_bytes(int64_t n);
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of
 // min(key, clamp). Input arrays are not modified; the sorted arrays are

@@ -25,8 +25,8 @@ constexpr int kThreads = 256;
 template <int P, int MODE, bool DBG, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_sample(SampleArgs a)
 {
-    extern __shared__ float s_box[];
-    for (int i = threadIdx.x; i < a.n_boxes * 6; i += blockDim.x) s_box[i] = a.boxes[i];
+    extern __shared__ float4 s_box[];
+    stage_boxes(s_box, a.boxes, a.n_boxes);
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n_points) return;
@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sample(SampleArgs a)
 // Energy-based baseline (Section 4): inversion of the cdf of leaf power.
 __global__ void __launch_bounds__(kThreads) k_sample_power(SampleArgs a, int32_t* light_out)
 {
-    extern __shared__ float s_box[];
-    for (int i = threadIdx.x; i < a.n_boxes * 6; i += blockDim.x) s_box[i] = a.boxes[i];
+    extern __shared__ float4 s_box[];
+    stage_boxes(s_box, a.boxes, a.n_boxes);
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n_points) return;
@@ -77,7 +77,7 @@ template <int P, int MODE, bool DBG, int MINB>
 cudaError_t launch(const SampleArgs& a, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)((a.n_points + kThreads - 1) / kThreads);
-    k_sample<P, MODE, DBG, MINB><<<blocks, kThreads, sizeof(float) * 6 * a.n_boxes, s>>>(a);
+    k_sample<P, MODE, DBG, MINB><<<blocks, kThreads, sizeof(float4) * 2 * a.n_boxes, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -173,7 +173,7 @@ int sample_power(rll_ctx* ctx, const rll_tree* t, const float* pos, const float*
     a.spp = spp;
     a.rgb = rgb;
     const unsigned blocks = (unsigned)((n_points + kThreads - 1) / kThreads);
-    k_sample_power<<<blocks, kThreads, sizeof(float) * 6 * n_boxes, ctx->stream>>>(a, light_out);
+    k_sample_power<<<blocks, kThreads, sizeof(float4) * 2 * n_boxes, ctx->stream>>>(a, light_out);
     return check_cuda(ctx, cudaGetLastError(), "sample_power");
 }
 

@@ -101,7 +101,7 @@ struct ShadeOut {
 // light point, shadow test, contribution (x, n: shading point and normal)
 __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1, float x2, float n0, float n1,
                                           float n2, float albedo, float p_cut, float p_in, SampleStream& rs,
-                                          const float* s_box, int n_boxes, uint32_t reward_mode)
+                                          const float4* s_box, int n_boxes, uint32_t reward_mode)
 {
     const float ua = rs.draw(kDrawTriA), ub = rs.draw(kDrawTriB);
     const float su = fsqrt(ua);
@@ -114,12 +114,23 @@ __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1,
     const float o2 = fadd(x2, fmul(kShadowOffset, n2));
     const float i0 = fdiv(1.0f, fsub(y0, o0)), i1 = fdiv(1.0f, fsub(y1, o1)), i2 = fdiv(1.0f, fsub(y2, o2));
     const float q0 = -fmul(o0, i0), q1 = -fmul(o1, i1), q2 = -fmul(o2, i2);
+    // Conservative prefilter: a box can only block the segment if it meets the
+    // segment's bounding box widened by del; del exceeds the rounding error of
+    // the slab planes below (a few ulps of |o| + |y|), so no box the exact
+    // slab test would report is skipped and the decision is unchanged.
+    const float e0 = 1e-5f * (1.0f + fabsf(o0) + fabsf(y0));
+    const float e1 = 1e-5f * (1.0f + fabsf(o1) + fabsf(y1));
+    const float e2 = 1e-5f * (1.0f + fabsf(o2) + fabsf(y2));
+    const float lo0 = fminf(o0, y0) - e0, hi0 = fmaxf(o0, y0) + e0;
+    const float lo1 = fminf(o1, y1) - e1, hi1 = fmaxf(o1, y1) + e1;
+    const float lo2 = fminf(o2, y2) - e2, hi2 = fmaxf(o2, y2) + e2;
     bool occluded = false;
     for (int b = 0; b < n_boxes && !occluded; ++b) {
-        const float* bx = s_box + 6 * b;
-        const float ta0 = __fmaf_rn(bx[0], i0, q0), tb0 = __fmaf_rn(bx[3], i0, q0);
-        const float ta1 = __fmaf_rn(bx[1], i1, q1), tb1 = __fmaf_rn(bx[4], i1, q1);
-        const float ta2 = __fmaf_rn(bx[2], i2, q2), tb2 = __fmaf_rn(bx[5], i2, q2);
+        const float4 bmin = s_box[2 * b], bmax = s_box[2 * b + 1];
+        if (bmin.x > hi0 || bmax.x < lo0 || bmin.y > hi1 || bmax.y < lo1 || bmin.z > hi2 || bmax.z < lo2) continue;
+        const float ta0 = __fmaf_rn(bmin.x, i0, q0), tb0 = __fmaf_rn(bmax.x, i0, q0);
+        const float ta1 = __fmaf_rn(bmin.y, i1, q1), tb1 = __fmaf_rn(bmax.y, i1, q1);
+        const float ta2 = __fmaf_rn(bmin.z, i2, q2), tb2 = __fmaf_rn(bmax.z, i2, q2);
         float tn = fmaxf(0.0f, fminf(ta0, tb0));
         float tf = fminf(kShadowTmax, fmaxf(ta0, tb0));
         tn = fmaxf(tn, fminf(ta1, tb1));
@@ -150,9 +161,20 @@ __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1,
 
 // MINB: resident blocks per SM the register allocation is held to (3: no
 // cap at 256 threads, 4: at most 64 registers per thread).
-// All samples of shading point p (s_box: the point's boxes in shared memory).
+// Boxes in shared memory as float4 pairs: s_box[2b] = (min xyz, 0),
+// s_box[2b + 1] = (max xyz, 0). Filled by all threads of the block.
+__device__ __forceinline__ void stage_boxes(float4* s_box, const float* boxes, int n_boxes)
+{
+    for (int b = threadIdx.x; b < n_boxes; b += blockDim.x) {
+        const float* bx = boxes + 6 * b;
+        s_box[2 * b] = make_float4(bx[0], bx[1], bx[2], 0.0f);
+        s_box[2 * b + 1] = make_float4(bx[3], bx[4], bx[5], 0.0f);
+    }
+}
+
+// All samples of shading point p (s_box: the point's boxes, see stage_boxes).
 template <int P, int MODE, bool DBG>
-__device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, const float* s_box)
+__device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, const float4* s_box)
 {
     using T = typename Store<P>::T;
     const int64_t np = a.n_points;

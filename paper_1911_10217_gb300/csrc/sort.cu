@@ -20,31 +20,35 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;
-constexpr int kDigits = 256;
 constexpr int kWarps = kThreads / 32;
+static_assert(kTile == kSortTile, "tile size");
 
+template <int DB>
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t clamp, int shift)
 {
-    return (min(key, clamp) >> shift) & 0xFFu;
+    return (min(key, clamp) >> shift) & ((1u << DB) - 1u);
 }
 
+template <int DB>
 __global__ void __launch_bounds__(kThreads) k_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
                                                    uint32_t clamp, uint32_t* __restrict__ counts,
                                                    uint32_t* __restrict__ totals, int64_t tiles)
 {
+    constexpr int kDigits = 1 << DB;
     __shared__ uint32_t h[kDigits];
-    const int t = threadIdx.x;
-    h[t] = 0;
+    for (int d = threadIdx.x; d < kDigits; d += kThreads) h[d] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kTile;
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const int64_t i = base + j * kThreads + t;
-        if (i < n) atomicAdd(&h[digit_of(keys[i], clamp, shift)], 1u);
+        const int64_t i = base + j * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[digit_of<DB>(keys[i], clamp, shift)], 1u);
     }
     __syncthreads();
-    counts[(int64_t)t * tiles + blockIdx.x] = h[t];
-    if (h[t]) atomicAdd(&totals[t], h[t]);
+    for (int d = threadIdx.x; d < kDigits; d += kThreads) {
+        counts[(int64_t)d * tiles + blockIdx.x] = h[d];
+        if (h[d]) atomicAdd(&totals[d], h[d]);
+    }
 }
 
 // exclusive scan of v over a 1024-thread block; returns the block total in *total
@@ -90,6 +94,38 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* __restrict__ coun
     }
 }
 
+// exclusive scan over kThreads * DPT values held DPT per thread (thread t
+// owns entries t*DPT .. t*DPT+DPT-1); s_scan: kWarps words of scratch
+template <int DPT>
+__device__ __forceinline__ void block_excl_scan_owned(const uint32_t* in, uint32_t* out, uint32_t* s_scan)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t v[DPT], sum = 0;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+        v[k] = in[t * DPT + k];
+        sum += v[k];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();  // s_scan may still be read by an earlier scan
+    if (lane == 31) s_scan[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += s_scan[w];
+    uint32_t run = before + x - sum;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+        out[t * DPT + k] = run;
+        run += v[k];
+    }
+}
+
+template <int DB>
 __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t* __restrict__ kin,
                                                       const uint32_t* __restrict__ vin,
                                                       uint32_t* __restrict__ kout,
@@ -97,6 +133,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t* __restrict
                                                       uint32_t clamp, const uint32_t* __restrict__ counts,
                                                       const uint32_t* __restrict__ totals, int64_t tiles)
 {
+    constexpr int kDigits = 1 << DB;
+    constexpr int DPT = kDigits / kThreads;
     __shared__ uint32_t s_base[kDigits];
     __shared__ uint32_t s_start[kDigits];
     __shared__ uint32_t s_cnt[kDigits];
@@ -115,55 +153,32 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t* __restrict
         if (i < n) {
             k[j] = kin[i];
             v[j] = vin[i];
-            d[j] = digit_of(k[j], clamp, shift);
+            d[j] = digit_of<DB>(k[j], clamp, shift);
         } else {
             k[j] = 0xFFFFFFFFu;
             v[j] = 0u;
             d[j] = kDigits - 1;  // padding ranks after every real item of the tile
         }
     }
-    s_cnt[t] = 0;
-    s_run[t] = 0;
+    for (int q = t; q < kDigits; q += kThreads) {
+        s_cnt[q] = 0;
+        s_run[q] = 0;
+        s_base[q] = totals[q];
+    }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kItems; ++j)
         if (base + j * kThreads + t < n) atomicAdd(&s_cnt[d[j]], 1u);
     __syncthreads();
-    // tile-local digit starts: exclusive scan of s_cnt over 256 threads
-    {
-        const uint32_t c = s_cnt[t];
-        uint32_t x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_scan[warp] = x;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += s_scan[w];
-        s_start[t] = before + x - c;
-    }
-    // global digit base: exclusive scan of totals + this tile's offset
-    {
-        const uint32_t c = totals[t];
-        uint32_t x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        __syncthreads();
-        if (lane == 31) s_scan[warp] = x;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += s_scan[w];
-        s_base[t] = before + x - c + counts[(int64_t)t * tiles + blockIdx.x];
-    }
+    block_excl_scan_owned<DPT>(s_cnt, s_start, s_scan);  // tile-local digit starts
+    block_excl_scan_owned<DPT>(s_base, s_base, s_scan);  // global digit starts (in place: own entries only)
+    __syncthreads();
+    for (int q = t; q < kDigits; q += kThreads) s_base[q] += counts[(int64_t)q * tiles + blockIdx.x];
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        for (int w = 0; w < kWarps; ++w) s_wc[w][t] = 0;
+        for (int w = 0; w < kWarps; ++w)
+            for (int q = t; q < kDigits; q += kThreads) s_wc[w][q] = 0;
         __syncthreads();
         const uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
         const uint32_t rank_w = __popc(peers & lt);
@@ -175,9 +190,11 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t* __restrict
         s_k[pos] = k[j];
         s_v[pos] = v[j];
         __syncthreads();
-        uint32_t add = 0;
-        for (int w = 0; w < kWarps; ++w) add += s_wc[w][t];
-        s_run[t] += add;
+        for (int q = t; q < kDigits; q += kThreads) {
+            uint32_t add = 0;
+            for (int w = 0; w < kWarps; ++w) add += s_wc[w][q];
+            s_run[q] += add;
+        }
     }
     __syncthreads();
     const int64_t valid = min((int64_t)kTile, n - base);
@@ -186,15 +203,13 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t* __restrict
         const int idx = j * kThreads + t;
         if (idx < valid) {
             const uint32_t key = s_k[idx];
-            const uint32_t dg = digit_of(key, clamp, shift);
+            const uint32_t dg = digit_of<DB>(key, clamp, shift);
             const uint32_t dst = s_base[dg] + (uint32_t)idx - s_start[dg];
             kout[dst] = key;
             vout[dst] = s_v[idx];
         }
     }
 }
-
-__host__ __device__ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // ---------------------------------------------------------------- float scan
 constexpr int kScanThreads = 1024;
@@ -263,43 +278,29 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(float* __restrict__ o
 
 }  // namespace
 
-size_t radix_sort_scratch_bytes(int64_t n)
-{
-    const int64_t tiles = (n + kTile - 1) / kTile;
-    return 4 * align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)) +
-           align256(sizeof(uint32_t) * kDigits * (size_t)(tiles > 0 ? tiles : 1)) +
-           align256(sizeof(uint32_t) * kDigits);
-}
+size_t radix_sort_scratch_bytes(int64_t n) { return sort_scratch_bytes_for(n); }
 
-cudaError_t radix_sort_pairs(cudaStream_t s, const uint32_t* kin, const uint32_t* vin, int64_t n, int bits,
-                             uint32_t clamp, void* scratch, uint32_t** kout, uint32_t** vout)
+namespace {
+
+template <int DB>
+cudaError_t sort_passes(cudaStream_t s, const uint32_t* kin, const uint32_t* vin, int64_t n, int bits, uint32_t clamp,
+                        uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t* counts, uint32_t* totals,
+                        uint32_t** kout, uint32_t** vout)
 {
+    constexpr int kDigits = 1 << DB;
     const int64_t tiles = (n + kTile - 1) / kTile;
-    char* p = (char*)scratch;
-    const size_t nb = align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
-    uint32_t* ka = (uint32_t*)p; p += nb;
-    uint32_t* va = (uint32_t*)p; p += nb;
-    uint32_t* kb = (uint32_t*)p; p += nb;
-    uint32_t* vb = (uint32_t*)p; p += nb;
-    uint32_t* counts = (uint32_t*)p; p += align256(sizeof(uint32_t) * kDigits * (size_t)(tiles > 0 ? tiles : 1));
-    uint32_t* totals = (uint32_t*)p;
     const uint32_t* ck = kin;
     const uint32_t* cv = vin;
     uint32_t* dk = ka;
     uint32_t* dv = va;
-    if (n <= 0) {
-        *kout = ka;
-        *vout = va;
-        return cudaSuccess;
-    }
-    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    const int passes = bits <= 0 ? 1 : (bits + DB - 1) / DB;
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
+        const int shift = DB * pass;
         cudaError_t e = cudaMemsetAsync(totals, 0, sizeof(uint32_t) * kDigits, s);
         if (e != cudaSuccess) return e;
-        k_hist<<<(unsigned)tiles, kThreads, 0, s>>>(ck, n, shift, clamp, counts, totals, tiles);
+        k_hist<DB><<<(unsigned)tiles, kThreads, 0, s>>>(ck, n, shift, clamp, counts, totals, tiles);
         k_scan_tiles<<<kDigits, 1024, 0, s>>>(counts, tiles);
-        k_scatter<<<(unsigned)tiles, kThreads, 0, s>>>(ck, cv, dk, dv, n, shift, clamp, counts, totals, tiles);
+        k_scatter<DB><<<(unsigned)tiles, kThreads, 0, s>>>(ck, cv, dk, dv, n, shift, clamp, counts, totals, tiles);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         ck = dk;
@@ -310,6 +311,32 @@ cudaError_t radix_sort_pairs(cudaStream_t s, const uint32_t* kin, const uint32_t
     *kout = const_cast<uint32_t*>(ck);
     *vout = const_cast<uint32_t*>(cv);
     return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t radix_sort_pairs(cudaStream_t s, const uint32_t* kin, const uint32_t* vin, int64_t n, int bits,
+                             uint32_t clamp, void* scratch, uint32_t** kout, uint32_t** vout)
+{
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    char* p = (char*)scratch;
+    const size_t nb = sort_align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    uint32_t* ka = (uint32_t*)p; p += nb;
+    uint32_t* va = (uint32_t*)p; p += nb;
+    uint32_t* kb = (uint32_t*)p; p += nb;
+    uint32_t* vb = (uint32_t*)p; p += nb;
+    uint32_t* counts = (uint32_t*)p;
+    p += sort_align256(sizeof(uint32_t) * kSortMaxDigits * (size_t)(tiles > 0 ? tiles : 1));
+    uint32_t* totals = (uint32_t*)p;
+    if (n <= 0) {
+        *kout = ka;
+        *vout = va;
+        return cudaSuccess;
+    }
+    // 9-bit digits when they save a pass (26-bit keys: 3 passes instead of 4)
+    const int p8 = bits <= 0 ? 1 : (bits + 7) / 8, p9 = bits <= 0 ? 1 : (bits + 8) / 9;
+    if (p9 < p8) return sort_passes<9>(s, kin, vin, n, bits, clamp, ka, va, kb, vb, counts, totals, kout, vout);
+    return sort_passes<8>(s, kin, vin, n, bits, clamp, ka, va, kb, vb, counts, totals, kout, vout);
 }
 
 cudaError_t inclusive_scan_f32(cudaStream_t s, const float* in, float* out, int64_t n, void* scratch)
