@@ -26,9 +26,8 @@ constexpr int kMaxBoxes = 1024;
 constexpr float kShadowOffset = 1e-4f;
 constexpr float kShadowTmax = 0.9999f;
 
-// Node bounds record, 64 bytes. The descent reads the records of both
-// children of an internal node i from pairs[2i], pairs[2i+1]: one aligned
-// 128-byte line per level.
+// Node bounds record, 64 bytes (every node: export, uniform in-cluster
+// choice, split-collapse).
 struct __align__(16) NodeRec {
     float bmin[3];
     float bmax[3];
@@ -41,10 +40,10 @@ struct __align__(16) NodeRec {
 };
 static_assert(sizeof(NodeRec) == 64, "NodeRec must be 64 bytes");
 
-// Descent record of one child, 64 bytes: the constants of the importance
+// Descent record of one child, 48 bytes: the constants of the importance
 // bound precomputed (binary32, same operations as on the fly). The records
-// of both children of internal node i are pairs[2i], pairs[2i+1]: one
-// aligned 128-byte line per descent level.
+// of both children of internal node i are pairs[2i], pairs[2i+1]: 96
+// contiguous bytes (three 32-byte sectors) per descent level.
 struct __align__(16) DescRec {
     float c[3];      // AABB centre
     float r2;        // squared half diagonal
@@ -54,9 +53,8 @@ struct __align__(16) DescRec {
     float cos_t;     // cone cos(theta)
     float sin_t;     // cone sin(theta)
     uint32_t id;     // node id
-    uint32_t pad[4];
 };
-static_assert(sizeof(DescRec) == 64, "DescRec must be 64 bytes");
+static_assert(sizeof(DescRec) == 48, "DescRec must be 48 bytes");
 
 // Sorted light, 64 bytes.
 struct __align__(16) LightRec {
@@ -205,7 +203,6 @@ __device__ __forceinline__ DescRec make_desc(const NodeRec& n)
     d.cos_t = n.cos_t;
     d.sin_t = fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(n.cos_t, n.cos_t))));
     d.id = n.id;
-    d.pad[0] = d.pad[1] = d.pad[2] = d.pad[3] = 0u;
     return d;
 }
 

@@ -5,8 +5,8 @@
 // in shared memory once per block. Per sample:
 //   hash lookup / lazy insert of the (jittered) 5-d cell   (64-bit CAS)
 //   binary search of the cell's C for the cluster s        (log2 m loads of one row)
-//   in-cluster choice: bound-driven descent (two child records = one 128-byte
-//   line per level) or a uniform pick over the cluster's lights
+//   in-cluster choice: bound-driven descent (two 48-byte child records, 96
+//   contiguous bytes per level) or a uniform pick over the cluster's lights
 //   uniform point on the light triangle, contribution, shadow segment vs boxes
 //   estimate accumulation and one learning record (key, |c|).
 // The decisions (cell, branch, visibility) are exact binary32 formulas; the

@@ -79,7 +79,7 @@ __device__ __forceinline__ DescRec load_desc(const DescRec* p)
     const float4* s = reinterpret_cast<const float4*>(p);
     float4* d = reinterpret_cast<float4*>(&r);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) d[k] = __ldg(s + k);
+    for (int k = 0; k < 3; ++k) d[k] = __ldg(s + k);
     return r;
 }
 
@@ -145,17 +145,17 @@ __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1,
     const float inv_d = rsqrtf(d2);
     const float cx = fmaxf(0.0f, (n0 * wx + n1 * wy + n2 * wz) * inv_d);
     const float cl = fmaxf(0.0f, -(L.n[0] * wx + L.n[1] * wy + L.n[2] * wz) * inv_d);
-    const float geo = (occluded || !(d2 > 0.0f)) ? 0.0f : cx * cl / d2;
+    const float geo = (occluded || !(d2 > 0.0f)) ? 0.0f : __fdividef(cx * cl, d2);
     const float f = albedo * 0.31830988618379067f;
     const float c0 = f * L.le[0] * geo, c1 = f * L.le[1] * geo, c2 = f * L.le[2] * geo;
     // a zero contribution is zero whatever its pdf (a long-unrewarded
     // cluster's probability may underflow binary32)
-    const float w = geo > 0.0f ? (L.area / p_cut) / p_in : 0.0f;
+    const float w = geo > 0.0f ? __fdividef(__fdividef(L.area, p_cut), p_in) : 0.0f;
     o.est[0] = c0 * w;
     o.est[1] = c1 * w;
     o.est[2] = c2 * w;
     const float lum = 0.2126f * c0 + 0.7152f * c1 + 0.0722f * c2;
-    o.reward = !(lum > 0.0f) ? 0.0f : (reward_mode == RLL_REWARD_CLUSTER ? lum * L.area / p_in : lum * L.area);
+    o.reward = !(lum > 0.0f) ? 0.0f : (reward_mode == RLL_REWARD_CLUSTER ? __fdividef(lum * L.area, p_in) : lum * L.area);
     return o;
 }
 
@@ -261,7 +261,7 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
                 float ratio;
                 if (ssum > 0.0f) {
                     left = __fmaf_rn(ud, ssum, -wl) < 0.0f;
-                    ratio = (left ? wl : wr) / (wl + wr);
+                    ratio = __fdividef(left ? wl : wr, wl + wr);  // continuous: pdf only
                 } else {
                     left = ud < 0.5f;
                     ratio = 0.5f;

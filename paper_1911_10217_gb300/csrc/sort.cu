@@ -125,6 +125,12 @@ __device__ __forceinline__ void block_excl_scan_owned(const uint32_t* in, uint32
     }
 }
 
+// Stable scatter of one tile. Warp w ranks items w*256 .. w*256+255 of the
+// tile (8 rounds of 32 consecutive items) with private per-digit counters
+// (match_any groups equal digits; the group's first lane advances the
+// counter), so no block barrier is needed per round. Then per digit the
+// warps' counts are prefix-summed, items are reordered by digit in shared
+// memory, and every digit's run is written contiguously.
 template <int DB>
 __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t* __restrict__ kin,
                                                       const uint32_t* __restrict__ vin,
@@ -135,21 +141,27 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t* __restrict
 {
     constexpr int kDigits = 1 << DB;
     constexpr int DPT = kDigits / kThreads;
-    __shared__ uint32_t s_base[kDigits];
-    __shared__ uint32_t s_start[kDigits];
+    constexpr int kPerWarp = kTile / kWarps;  // 256 consecutive items per warp
+    __shared__ uint32_t s_wc[kWarps][kDigits];  // per-warp counts, then per-warp offsets
     __shared__ uint32_t s_cnt[kDigits];
-    __shared__ uint32_t s_run[kDigits];
-    __shared__ uint32_t s_wc[kWarps][kDigits];
+    __shared__ uint32_t s_start[kDigits];
+    __shared__ uint32_t s_base[kDigits];
     __shared__ uint32_t s_k[kTile];
     __shared__ uint32_t s_v[kTile];
     __shared__ uint32_t s_scan[kWarps];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t base = (int64_t)blockIdx.x * kTile;
-    uint32_t k[kItems], v[kItems], d[kItems];
+    for (int w = 0; w < kWarps; ++w)
+        for (int q = t; q < kDigits; q += kThreads) s_wc[w][q] = 0;
+    for (int q = t; q < kDigits; q += kThreads) s_base[q] = totals[q];
+    __syncthreads();
+    const uint32_t lt = lanemask_lt();
+    uint32_t k[kItems], v[kItems], d[kItems], r[kItems];
+    uint32_t* wc = s_wc[warp];
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const int64_t i = base + j * kThreads + t;
+        const int64_t i = base + warp * kPerWarp + j * 32 + lane;
         if (i < n) {
             k[j] = kin[i];
             v[j] = vin[i];
@@ -159,42 +171,38 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t* __restrict
             v[j] = 0u;
             d[j] = kDigits - 1;  // padding ranks after every real item of the tile
         }
-    }
-    for (int q = t; q < kDigits; q += kThreads) {
-        s_cnt[q] = 0;
-        s_run[q] = 0;
-        s_base[q] = totals[q];
+        const uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader) {
+            old = wc[d[j]];
+            wc[d[j]] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        r[j] = old + __popc(peers & lt);
+        __syncwarp();
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kItems; ++j)
-        if (base + j * kThreads + t < n) atomicAdd(&s_cnt[d[j]], 1u);
+    // per digit: exclusive prefix over warps; tile count
+    for (int q = t; q < kDigits; q += kThreads) {
+        uint32_t run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = s_wc[w][q];
+            s_wc[w][q] = run;
+            run += c;
+        }
+        s_cnt[q] = run;
+    }
     __syncthreads();
     block_excl_scan_owned<DPT>(s_cnt, s_start, s_scan);  // tile-local digit starts
-    block_excl_scan_owned<DPT>(s_base, s_base, s_scan);  // global digit starts (in place: own entries only)
+    block_excl_scan_owned<DPT>(s_base, s_base, s_scan);  // global digit starts
     __syncthreads();
     for (int q = t; q < kDigits; q += kThreads) s_base[q] += counts[(int64_t)q * tiles + blockIdx.x];
-    const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        for (int w = 0; w < kWarps; ++w)
-            for (int q = t; q < kDigits; q += kThreads) s_wc[w][q] = 0;
-        __syncthreads();
-        const uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
-        const uint32_t rank_w = __popc(peers & lt);
-        if (rank_w == 0) s_wc[warp][d[j]] = __popc(peers);
-        __syncthreads();
-        uint32_t off = s_run[d[j]] + rank_w;
-        for (int w = 0; w < warp; ++w) off += s_wc[w][d[j]];
-        const uint32_t pos = s_start[d[j]] + off;
+        const uint32_t pos = s_start[d[j]] + s_wc[warp][d[j]] + r[j];
         s_k[pos] = k[j];
         s_v[pos] = v[j];
-        __syncthreads();
-        for (int q = t; q < kDigits; q += kThreads) {
-            uint32_t add = 0;
-            for (int w = 0; w < kWarps; ++w) add += s_wc[w][q];
-            s_run[q] += add;
-        }
     }
     __syncthreads();
     const int64_t valid = min((int64_t)kTile, n - base);
