@@ -73,8 +73,7 @@ def lib():
             L.orc_fmix64.restype = ctypes.c_uint64
             L.orc_lookup_insert.argtypes = [ctypes.POINTER(_Grid), ctypes.c_uint64]
             L.orc_lookup_insert.restype = ctypes.c_int64
-            L.orc_importance32.argtypes = [P, P, P]
-            L.orc_importance32.restype = ctypes.c_float
+            L.orc_importance32.argtypes = [P, P, P, P, P]
             L.orc_sample_frame.argtypes = [ctypes.POINTER(_Tree), P, P, ctypes.c_int, P,
                                            ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P,
                                            ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
@@ -153,8 +152,11 @@ class Tree:
         return node >= self.n - 1
 
     def importance(self, node, x, nrm):
-        return lib().orc_importance32(_p(np.ascontiguousarray(self.rec[node])), _p(_f32(x)),
-                                      _p(_f32(nrm)))
+        """The descent bound of a node at (x, nrm): num / den (binary32 parts)."""
+        num, den = ctypes.c_float(), ctypes.c_float()
+        lib().orc_importance32(_p(np.ascontiguousarray(self.rec[node])), _p(_f32(x)), _p(_f32(nrm)),
+                               ctypes.byref(num), ctypes.byref(den))
+        return float(num.value) / float(den.value)
 
 
 def cdf(q, eps=0.01, precision="fp32"):

@@ -607,11 +607,13 @@ int64_t orc_lookup_insert(orc_grid* g, uint64_t key)
 /*   within the node's cone (axis, half angle theta); a point inside the      */
 /*   bounding sphere gets I = phi / r^2. Angle sums by the addition formulas; */
 /*   every cosine and sine is carried multiplied by |d| so that only         */
-/*   sqrt(d^2 - r^2) and two more square roots and one division are needed.   */
+/*   sqrt(d^2 - r^2) and two more square roots are needed; the bound is kept */
+/*   as num / den = (phi A B) / d^6 and two bounds are compared by cross      */
+/*   multiplication, without a division.                                    */
 /*   Node constants (centre, r^2, r, sin theta) are binary32 values of the    */
 /*   node record, computed with the same operations on both sides.           */
 /* ------------------------------------------------------------------------ */
-float orc_importance32(const float* r, const float x[3], const float n[3])
+void orc_importance32(const float* r, const float x[3], const float n[3], float* num, float* den)
 {
     float cx = (r[0] + r[3]) * 0.5f, cy = (r[1] + r[4]) * 0.5f, cz = (r[2] + r[5]) * 0.5f;
     float ex = r[3] - r[0], ey = r[4] - r[1], ez = r[5] - r[2];
@@ -622,7 +624,11 @@ float orc_importance32(const float* r, const float x[3], const float n[3])
     float phi = r[6];
     float dx = cx - x[0], dy = cy - x[1], dz = cz - x[2];
     float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    if (d2 <= r2) return phi / fmaxf(r2, 1e-30f);
+    if (d2 <= r2) {
+        *num = phi;
+        *den = fmaxf(r2, 1e-30f);
+        return;
+    }
     float cb = sqrtf(d2 - r2);                              /* |d| cos(beta)        */
     float nd = fmaf(n[2], dz, fmaf(n[1], dy, n[0] * dx));   /* |d| cos(gamma)       */
     float A;                                                /* |d|^2 Brecv          */
@@ -634,8 +640,25 @@ float orc_importance32(const float* r, const float x[3], const float n[3])
     float B;                                                /* |d|^2 Bemit          */
     if (sphi <= 0.0f || cphi <= ad) B = d2;
     else B = fmaxf(0.0f, fmaf(ad, cphi, sqrtf(fmaxf(0.0f, fmaf(-ad, ad, d2))) * sphi));
-    float inv = 1.0f / d2;
-    return ((phi * (A * inv)) * (B * inv)) * inv;
+    *num = (phi * A) * B;
+    *den = (d2 * d2) * d2;
+}
+
+/* Branch weights of the two children a, c of a descent step: the bounds
+ * I = num / den compared without a division, w_a = num_a den_c and
+ * w_c = num_c den_a (binary32); if both are zero, the children's powers. */
+static void orc_branch_weights(const float* ra, const float* rc, const float x[3], const float n[3],
+                               float* wa, float* wc)
+{
+    float na, da, nc, dc;
+    orc_importance32(ra, x, n, &na, &da);
+    orc_importance32(rc, x, n, &nc, &dc);
+    *wa = na * dc;
+    *wc = nc * da;
+    if (!((*wa + *wc) > 0.0f)) {
+        *wa = ra[6];
+        *wc = rc[6];
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -711,15 +734,9 @@ static int64_t orc_descend(const orc_scene* sc, int mode, int32_t node, const fl
     uint32_t level = 0;
     while (node < nl - 1) {
         int32_t a = t->left[node], c = t->right[node];
-        float ia = orc_importance32(REC(t, a), x, n);
-        float ic = orc_importance32(REC(t, c), x, n);
-        float s = ia + ic;
-        float wa = ia, wc = ic;
-        if (!(s > 0.0f)) {
-            wa = REC(t, a)[6];
-            wc = REC(t, c)[6];
-            s = wa + wc;
-        }
+        float wa, wc;
+        orc_branch_weights(REC(t, a), REC(t, c), x, n, &wa, &wc);
+        float s = wa + wc;
         float u = orc_draw(rs, ORC_DRAW_DESCENT + level);
         ++level;
         double ratio_left;
@@ -972,10 +989,8 @@ double orc_light_pdf(const orc_tree* t, int mode, int m, const int32_t* cut, con
     if (mode == ORC_MODE_UNIFORM) return p / (double)(t->end[node] - t->begin[node]);
     while (node < nl - 1) {
         int32_t a = t->left[node], c = t->right[node];
-        float ia = orc_importance32(REC(t, a), x, n);
-        float ic = orc_importance32(REC(t, c), x, n);
-        float wa = ia, wc = ic;
-        if (!((ia + ic) > 0.0f)) { wa = REC(t, a)[6]; wc = REC(t, c)[6]; }
+        float wa, wc;
+        orc_branch_weights(REC(t, a), REC(t, c), x, n, &wa, &wc);
         double ratio = ((double)wa + (double)wc) > 0.0 ? (double)wa / ((double)wa + (double)wc) : 0.5;
         if ((uint32_t)l < t->end[a]) { p *= ratio; node = a; }
         else { p *= 1.0 - ratio; node = c; }

@@ -207,15 +207,20 @@ __device__ __forceinline__ DescRec make_desc(const NodeRec& n)
 }
 
 // Unoccluded importance of a node seen from (x, n): power times the receiver
-// and emitter cosine bounds over the node's bounding sphere, over distance^2.
-// Cosines and sines are carried multiplied by |d| (2-3 square roots, one
+// and emitter cosine bounds over the node's bounding sphere, over distance^2,
+// kept as num / den = (phi A B) / d^6 with A = d^2 Brecv, B = d^2 Bemit.
+// Cosines and sines are carried multiplied by |d| (2-3 square roots, no
 // division).
-__device__ __forceinline__ float importance(const DescRec& r, float x0, float x1, float x2, float n0,
-                                            float n1, float n2)
+struct Bound {
+    float num, den;
+};
+
+__device__ __forceinline__ Bound importance(const DescRec& r, float x0, float x1, float x2, float n0, float n1,
+                                            float n2)
 {
     const float dx = fsub(r.c[0], x0), dy = fsub(r.c[1], x1), dz = fsub(r.c[2], x2);
     const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, fmul(dx, dx)));
-    if (d2 <= r.r2) return fdiv(r.phi, fmaxf(r.r2, 1e-30f));
+    if (d2 <= r.r2) return Bound{r.phi, fmaxf(r.r2, 1e-30f)};
     const float cb = fsqrt(fsub(d2, r.r2));
     const float nd = __fmaf_rn(n2, dz, __fmaf_rn(n1, dy, fmul(n0, dx)));
     float A = d2;
@@ -226,8 +231,7 @@ __device__ __forceinline__ float importance(const DescRec& r, float x0, float x1
     float B = d2;
     if (!(sphi <= 0.0f || cphi <= ad))
         B = fmaxf(0.0f, __fmaf_rn(ad, cphi, fmul(fsqrt(fmaxf(0.0f, __fmaf_rn(-ad, ad, d2))), sphi)));
-    const float inv = fdiv(1.0f, d2);
-    return fmul(fmul(fmul(r.phi, fmul(A, inv)), fmul(B, inv)), inv);
+    return Bound{fmul(fmul(r.phi, A), B), fmul(fmul(d2, d2), d2)};
 }
 
 // ---------------------------------------------------------------- storage

@@ -246,10 +246,12 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
                     if ((int64_t)L.id < nl1) prefetch_l1(a.pairs + 2 * (int64_t)L.id);
                     if ((int64_t)R.id < nl1) prefetch_l1(a.pairs + 2 * (int64_t)R.id);
                 }
-                const float il = importance(L, x0, x1, x2, n0, n1, n2);
-                const float ir = importance(R, x0, x1, x2, n0, n1, n2);
-                float wl = il, wr = ir;
-                float ssum = fadd(il, ir);
+                // the two bounds compared without a division: w_L = num_L den_R,
+                // w_R = num_R den_L; powers if both vanish
+                const Bound bl = importance(L, x0, x1, x2, n0, n1, n2);
+                const Bound br = importance(R, x0, x1, x2, n0, n1, n2);
+                float wl = fmul(bl.num, br.den), wr = fmul(br.num, bl.den);
+                float ssum = fadd(wl, wr);
                 if (!(ssum > 0.0f)) {
                     wl = L.phi;
                     wr = R.phi;
