@@ -204,8 +204,7 @@ def run_batched(args):
                  alb=T(s.albedo))
         tree = rll.Tree(ctx, d["tri"], d["em"])
         g = s.grid
-        grid = rll.Grid(ctx, tree, rll.grid_params(g.table_size, g.cut_size, g.origin, g.cell_size, g.normal_bins,
-                                                   g.jitter, q_init=g.q_init))
+        grid = rll.Grid(ctx, tree, rll.grid_params_for(g))
         objs.append(dict(s=s, d=d, tree=tree, grid=grid, rgb=torch.zeros(3, s.n_points, device=dev)))
     items = [dict(grid=o["grid"], tree=o["tree"], pos=o["d"]["pos"], nrm=o["d"]["nrm"], albedo=o["d"]["alb"],
                   boxes=o["d"]["boxes"], seed=o["s"].seed, frame=0, spp=o["s"].spp, rgb=o["rgb"]) for o in objs]
@@ -374,8 +373,7 @@ def run_dynamic(args):
     results = {}
     frames = args.dynamic_frames
     for prec in ("fp32", "fp16", "bf16"):
-        grid = rll.Grid(ctx, tree, rll.grid_params(g.table_size, g.cut_size, g.origin, g.cell_size, g.normal_bins,
-                                                   g.jitter, precision=prec, q_init=g.q_init))
+        grid = rll.Grid(ctx, tree, rll.grid_params_for(g, precision=prec))
         ms = []
         for f in range(frames):
             set_emission(f)
@@ -476,8 +474,7 @@ def main():
     P, S = scene.n_points, scene.spp
     tree = rll.Tree(ctx, tri, em)
     g = scene.grid
-    params = rll.grid_params(g.table_size, g.cut_size, g.origin, g.cell_size, g.normal_bins, g.jitter,
-                             q_init=g.q_init)
+    params = rll.grid_params_for(g)
     grid = rll.Grid(ctx, tree, params)
     rgb = torch.empty(3, P, device=dev)
     key = torch.empty(P * S, dtype=torch.int32, device=dev)

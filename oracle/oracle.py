@@ -172,7 +172,7 @@ class Grid:
 
     def __init__(self, tree: Tree, table_size, cut_size, origin=(0, 0, 0), cell_size=1.0,
                  normal_bins=1, jitter=False, mode="descent", reward="cluster", precision="fp32",
-                 alpha=0.1, T=2.0, eps=0.01, q_init=1.0):
+                 alpha=0.03, T=2.0, eps=0.02, q_init=1e-3):
         self.tree = tree
         H, M = int(table_size), int(cut_size)
         assert H & (H - 1) == 0
@@ -200,7 +200,7 @@ class Grid:
         g = scene.grid
         args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin,
                     cell_size=g.cell_size, normal_bins=g.normal_bins, jitter=g.jitter,
-                    q_init=g.q_init)
+                    q_init=g.q_init, alpha=g.alpha, eps=g.eps, T=g.threshold)
         args.update(kw)
         return cls(tree, **args)
 

@@ -236,11 +236,21 @@ class Tree:
 
 
 def grid_params(table_size, cut_size, origin=(0.0, 0.0, 0.0), cell_size=1.0, normal_bins=1,
-                jitter=False, precision="fp32", mode="descent", reward="cluster", alpha=0.1,
-                threshold=2.0, eps=0.01, q_init=1.0) -> GridParams:
+                jitter=False, precision="fp32", mode="descent", reward="cluster", alpha=0.03,
+                threshold=2.0, eps=0.02, q_init=1e-3) -> GridParams:
     return GridParams(int(table_size), int(cut_size), (ctypes.c_float * 3)(*origin), float(cell_size),
                       int(normal_bins), int(bool(jitter)), PREC[precision], MODE[mode], REWARD[reward],
                       float(alpha), float(threshold), float(eps), float(q_init))
+
+
+def grid_params_for(grid_config, **overrides) -> GridParams:
+    """GridParams of a scene's grid configuration (scenes.GridConfig)."""
+    g = grid_config
+    args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin, cell_size=g.cell_size,
+                normal_bins=g.normal_bins, jitter=g.jitter, q_init=g.q_init, alpha=g.alpha, eps=g.eps,
+                threshold=g.threshold)
+    args.update(overrides)
+    return grid_params(**args)
 
 
 class Grid:

@@ -35,6 +35,9 @@ class GridConfig:
     normal_bins: int         # quantisation bins per octahedral axis
     jitter: bool
     q_init: float = 1e-3     # Q of a new cell's leaves (below the reward scale of these scenes)
+    alpha: float = 0.03      # Eq. 1 learning rate
+    eps: float = 0.02        # Eq. 2 floor
+    threshold: float = 2.0   # split-collapse T
 
 
 @dataclasses.dataclass

@@ -169,9 +169,7 @@ class GpuExecutor:
                  pos=T(scene.pos), nrm=T(scene.nrm), alb=T(scene.albedo))
         tree = rll.Tree(self.admin, d["tri"], d["em"])
         g = scene.grid
-        grid = rll.Grid(self.admin, tree, rll.grid_params(g.table_size, g.cut_size, g.origin, g.cell_size,
-                                                          g.normal_bins, g.jitter, precision=precision,
-                                                          q_init=g.q_init))
+        grid = rll.Grid(self.admin, tree, rll.grid_params_for(g, precision=precision))
         del d["tri"], d["em"]
         rgb = torch.zeros(3, scene.n_points, device=dev)
         torch.cuda.synchronize(dev)

@@ -16,11 +16,7 @@ def device_scene(scene, dev, emission=None):
 
 
 def params_for(rll, scene, **kw):
-    g = scene.grid
-    args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin, cell_size=g.cell_size,
-                normal_bins=g.normal_bins, jitter=g.jitter, q_init=g.q_init)
-    args.update(kw)
-    return rll.grid_params(**args)
+    return rll.grid_params_for(scene.grid, **kw)
 
 
 def run_sample(rll, ctx, grid, tree, d, seed, frame, spp):
