@@ -423,7 +423,6 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
-    ap.add_argument("--sample-prefetch", type=int, default=0)
     ap.add_argument("--workload", default="frame", choices=["frame", "batched", "serving", "dynamic"])
     ap.add_argument("--dynamic-scale", type=float, default=1.0)
     ap.add_argument("--dynamic-frames", type=int, default=120)
@@ -464,7 +463,6 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ctx = rll.Context(local, stream)
     ctx.set_option("sample_min_blocks", args.sample_min_blocks)
-    ctx.set_option("sample_prefetch", args.sample_prefetch)
 
     def T(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)

@@ -87,9 +87,7 @@ int rll_ctx_create(rll_ctx** out, int device, void* cuda_stream);
 int rll_ctx_set_stream(rll_ctx* ctx, void* cuda_stream);
 /* Launch tuning of this context (no effect on results):
  *   "sample_min_blocks" 3 | 4 -- resident 256-thread blocks per SM the
- *   sampling kernel's registers are held to (default 4);
- *   "sample_prefetch" 0 | 1 -- prefetch the next descent lines and the
- *   cell's rows into L1 (default 0). */
+ *   sampling kernel's registers are held to (default 4). */
 int rll_ctx_set_option(rll_ctx* ctx, const char* name, int64_t value);
 int rll_ctx_destroy(rll_ctx* ctx);
 /* Message of the last failing call on this context ("" if none). */

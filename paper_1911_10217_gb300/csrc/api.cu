@@ -200,11 +200,6 @@ int rll_ctx_set_option(rll_ctx* ctx, const char* name, int64_t value)
         ctx->sample_min_blocks = (int)value;
         return RLL_OK;
     }
-    if (n == "sample_prefetch") {
-        if (value != 0 && value != 1) return fail(ctx, RLL_E_INVALID, "sample_prefetch must be 0 or 1");
-        ctx->sample_prefetch = (int)value;
-        return RLL_OK;
-    }
     return fail(ctx, RLL_E_INVALID, "unknown option " + n);
 }
 

@@ -446,7 +446,6 @@ int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items,
         a.rec_key = b->rec_key + rec_off;
         a.rec_val = b->rec_val + rec_off;
         a.status = b->status;
-        a.prefetch = 0;
         a.key_cells = 1;
         a.cell_base = cell_pre[i];
         d.Q = g->Q;

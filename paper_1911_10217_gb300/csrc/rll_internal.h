@@ -28,7 +28,6 @@ struct rll_ctx {
     size_t stage_bytes = 0;
     // launch tuning (rll_ctx_set_option)
     int sample_min_blocks = 4;
-    int sample_prefetch = 0;
 };
 
 struct rll_tree {

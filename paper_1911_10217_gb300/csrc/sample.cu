@@ -11,6 +11,7 @@
 //   estimate accumulation and one learning record (key, |c|).
 // The decisions (cell, branch, visibility) are exact binary32 formulas; the
 // cdf and descent comparisons u * total < c are made exactly with one fma.
+
 #include <cuda_runtime.h>
 
 #include "rll_device.cuh"
@@ -61,7 +62,8 @@ __global__ void __launch_bounds__(kThreads) k_sample_power(SampleArgs a, int32_t
         }
         const float pl = a.nodes[nl - 1 + lo].phi / total;
         const LightRec Lr = load_light(a.lights + lo);
-        const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, pl, 1.0f, rs, s_box, a.n_boxes, 0);
+        const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, pl, 1.0f, rs.draw(kDrawTriA), rs.draw(kDrawTriB),
+                                 s_box, a.n_boxes, 0);
         acc0 += o.est[0];
         acc1 += o.est[1];
         acc2 += o.est[2];
@@ -135,7 +137,6 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
     a.rec_key = rec_key;
     a.rec_val = rec_val;
     a.status = ctx->d_status;
-    a.prefetch = ctx->sample_prefetch;
     const bool use_dbg = dbg && (dbg->light || dbg->p_cut || dbg->p_in);
     if (use_dbg) {
         a.dbg_light = dbg->light;
@@ -144,10 +145,11 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
     }
     cudaError_t e;
     const int minb = ctx->sample_min_blocks;
+    const int mode = g->p.in_cluster_mode;
     switch (g->p.precision) {
-    case RLL_PREC_FP16: e = launch_p<RLL_PREC_FP16>(a, g->p.in_cluster_mode, use_dbg, minb, ctx->stream); break;
-    case RLL_PREC_BF16: e = launch_p<RLL_PREC_BF16>(a, g->p.in_cluster_mode, use_dbg, minb, ctx->stream); break;
-    default: e = launch_p<RLL_PREC_FP32>(a, g->p.in_cluster_mode, use_dbg, minb, ctx->stream);
+    case RLL_PREC_FP16: e = launch_p<RLL_PREC_FP16>(a, mode, use_dbg, minb, ctx->stream); break;
+    case RLL_PREC_BF16: e = launch_p<RLL_PREC_BF16>(a, mode, use_dbg, minb, ctx->stream); break;
+    default: e = launch_p<RLL_PREC_FP32>(a, mode, use_dbg, minb, ctx->stream);
     }
     return check_cuda(ctx, e, "sample_and_shade");
 }

@@ -46,17 +46,11 @@ struct SampleArgs {
     float* dbg_pcut;
     float* dbg_pin;
     uint32_t* status;
-    int prefetch;  // 1: prefetch the next descent lines and the cell's rows into L1
     // record key encoding: 0 -> slot * M + cluster (one grid); 1 -> ((cell_base
     // + slot) << kBatchClusterBits) | cluster (many grids sorted together)
     uint32_t key_cells;
     uint32_t cell_base;
 };
-
-__device__ __forceinline__ void prefetch_l1(const void* p)
-{
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 
 __device__ __forceinline__ int64_t lookup_insert(unsigned long long* keys, uint32_t H, unsigned long long key)
 {
@@ -100,10 +94,9 @@ struct ShadeOut {
 
 // light point, shadow test, contribution (x, n: shading point and normal)
 __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1, float x2, float n0, float n1,
-                                          float n2, float albedo, float p_cut, float p_in, SampleStream& rs,
+                                          float n2, float albedo, float p_cut, float p_in, float ua, float ub,
                                           const float4* s_box, int n_boxes, uint32_t reward_mode)
 {
-    const float ua = rs.draw(kDrawTriA), ub = rs.draw(kDrawTriB);
     const float su = fsqrt(ua);
     const float b0 = fsub(1.0f, su), b1 = fmul(ub, su), b2 = fsub(su, b1);
     const float y0 = fadd(fadd(fmul(b0, L.v0[0]), fmul(b1, L.v1[0])), fmul(b2, L.v2[0]));
@@ -172,63 +165,114 @@ __device__ __forceinline__ void stage_boxes(float4* s_box, const float* boxes, i
     }
 }
 
-// All samples of shading point p (s_box: the point's boxes, see stage_boxes).
+// Cell, cluster and triangle draws of one sample (draws 0-2 and 4-8).
+struct Setup {
+    uint32_t node;   // cut node of the chosen cluster
+    float p_cut;     // its probability under the cell's cdf
+    float ua, ub;    // triangle point draws
+    uint32_t rec;    // learning record key (kInvalidRecord if the table is full)
+    int64_t slot;
+    uint32_t s;
+};
+
+template <int P>
+__device__ __forceinline__ Setup setup_sample(const SampleArgs& a, SampleStream& rs, float x0, float x1, float x2,
+                                              float n0, float n1, float n2)
+{
+    using T = typename Store<P>::T;
+    const T* Ctab = static_cast<const T*>(a.C);
+    const T* Cdef = static_cast<const T*>(a.def_C);
+    const uint32_t m = a.m;
+    float jit[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (a.jitter) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) jit[k] = rs.draw(kDrawJit + k);
+    }
+    const unsigned long long key = cell_key(x0, x1, x2, n0, n1, n2, a.origin, a.h, a.nb, a.jitter != 0, jit);
+    const int64_t slot = lookup_insert(a.keys, a.H, key);
+    const T* crow;
+    const uint32_t* cutrow;
+    if (slot >= 0) {
+        crow = Ctab + slot * a.M;
+        cutrow = a.cut + slot * a.M;
+    } else {
+        crow = Cdef;
+        cutrow = a.def_cut;
+        atomicOr(a.status, (uint32_t)RLL_E_TABLE_FULL);
+    }
+    // cluster: first s with C(s) > u * C(m-1)
+    const float u = rs.draw(kDrawCut);
+    const float total = Store<P>::load(crow[m - 1]);
+    uint32_t lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__fmaf_rn(-u, total, Store<P>::load(crow[mid])) > 0.0f) hi = mid;
+        else lo = mid + 1;
+    }
+    Setup o;
+    o.s = lo;
+    o.slot = slot;
+    const float cprev = lo > 0 ? Store<P>::load(crow[lo - 1]) : 0.0f;
+    o.p_cut = (Store<P>::load(crow[lo]) - cprev) / total;
+    o.node = cutrow[lo];
+    if ((int64_t)o.node >= 2 * a.n_lights - 1) {  // corrupt cut row: flag, sample from the root
+        atomicOr(a.status, (uint32_t)RLL_E_DEVICE);
+        o.node = 0;
+    }
+    o.ua = rs.draw(kDrawTriA);
+    o.ub = rs.draw(kDrawTriB);
+    o.rec = slot < 0 ? kInvalidRecord
+                     : (a.key_cells ? ((a.cell_base + (uint32_t)slot) << kBatchClusterBits) | lo
+                                    : (uint32_t)slot * a.M + lo);
+    return o;
+}
+
+// One level of the bound-driven descent below internal node `node` (ud: the
+// level's draw). The two children's bounds are compared without a division:
+// w_L = num_L den_R, w_R = num_R den_L; their powers if both vanish.
+__device__ __forceinline__ void descent_step(const SampleArgs& a, uint32_t& node, float& p_in, float ud, float x0,
+                                             float x1, float x2, float n0, float n1, float n2)
+{
+    const DescRec L = load_desc(a.pairs + 2 * (int64_t)node);
+    const DescRec R = load_desc(a.pairs + 2 * (int64_t)node + 1);
+    const Bound bl = importance(L, x0, x1, x2, n0, n1, n2);
+    const Bound br = importance(R, x0, x1, x2, n0, n1, n2);
+    float wl = fmul(bl.num, br.den), wr = fmul(br.num, bl.den);
+    float ssum = fadd(wl, wr);
+    if (!(ssum > 0.0f)) {
+        wl = L.phi;
+        wr = R.phi;
+        ssum = fadd(wl, wr);
+    }
+    bool left;
+    float ratio;
+    if (ssum > 0.0f) {
+        left = __fmaf_rn(ud, ssum, -wl) < 0.0f;
+        ratio = __fdividef(left ? wl : wr, wl + wr);  // continuous: pdf only
+    } else {
+        left = ud < 0.5f;
+        ratio = 0.5f;
+    }
+    p_in *= ratio;
+    node = left ? L.id : R.id;
+}
+
+// All samples of shading point p, one thread (s_box: see stage_boxes).
 template <int P, int MODE, bool DBG>
 __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, const float4* s_box)
 {
-    using T = typename Store<P>::T;
     const int64_t np = a.n_points;
     const float x0 = a.pos[p], x1 = a.pos[np + p], x2 = a.pos[2 * np + p];
     const float n0 = a.nrm[p], n1 = a.nrm[np + p], n2 = a.nrm[2 * np + p];
     const float alb = a.albedo[p];
-    const T* Ctab = static_cast<const T*>(a.C);
-    const T* Cdef = static_cast<const T*>(a.def_C);
-    const uint32_t m = a.m;
     const int64_t nl1 = a.n_lights - 1;
     float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
     for (int j = 0; j < a.spp; ++j) {
         const uint32_t sid = (uint32_t)(p * a.spp + j);
         SampleStream rs;
         rs.init(a.seed, sid, a.frame);
-        float jit[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (a.jitter) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) jit[k] = rs.draw(kDrawJit + k);
-        }
-        const unsigned long long key =
-            cell_key(x0, x1, x2, n0, n1, n2, a.origin, a.h, a.nb, a.jitter != 0, jit);
-        const int64_t slot = lookup_insert(a.keys, a.H, key);
-        const T* crow;
-        const uint32_t* cutrow;
-        if (slot >= 0) {
-            crow = Ctab + slot * a.M;
-            cutrow = a.cut + slot * a.M;
-        } else {
-            crow = Cdef;
-            cutrow = a.def_cut;
-            atomicOr(a.status, (uint32_t)RLL_E_TABLE_FULL);
-        }
-        if (a.prefetch) {
-            prefetch_l1(crow + (m - 1));
-            prefetch_l1(crow);
-        }
-        // cluster: first s with C(s) > u * C(m-1)
-        const float u = rs.draw(kDrawCut);
-        const float total = Store<P>::load(crow[m - 1]);
-        uint32_t lo = 0, hi = m - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (__fmaf_rn(-u, total, Store<P>::load(crow[mid])) > 0.0f) hi = mid;
-            else lo = mid + 1;
-        }
-        const uint32_t s = lo;
-        const float cprev = s > 0 ? Store<P>::load(crow[s - 1]) : 0.0f;
-        const float p_cut = (Store<P>::load(crow[s]) - cprev) / total;
-        uint32_t node = cutrow[s];
-        if ((int64_t)node >= 2 * a.n_lights - 1) {  // corrupt cut row: flag, sample from the root
-            atomicOr(a.status, (uint32_t)RLL_E_DEVICE);
-            node = 0;
-        }
+        const Setup su = setup_sample<P>(a, rs, x0, x1, x2, n0, n1, n2);
+        uint32_t node = su.node;
         float p_in = 1.0f;
         int64_t light;
         if (MODE == RLL_MODE_UNIFORM) {
@@ -238,56 +282,23 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
             light = (int64_t)r.begin + (int64_t)(((unsigned long long)u24v * w) >> 24);
             p_in = 1.0f / (float)w;
         } else {
-            uint32_t level = 0;
-            while ((int64_t)node < nl1) {
-                const DescRec L = load_desc(a.pairs + 2 * (int64_t)node);
-                const DescRec R = load_desc(a.pairs + 2 * (int64_t)node + 1);
-                if (a.prefetch) {  // both possible next lines, while this level's bounds are computed
-                    if ((int64_t)L.id < nl1) prefetch_l1(a.pairs + 2 * (int64_t)L.id);
-                    if ((int64_t)R.id < nl1) prefetch_l1(a.pairs + 2 * (int64_t)R.id);
-                }
-                // the two bounds compared without a division: w_L = num_L den_R,
-                // w_R = num_R den_L; powers if both vanish
-                const Bound bl = importance(L, x0, x1, x2, n0, n1, n2);
-                const Bound br = importance(R, x0, x1, x2, n0, n1, n2);
-                float wl = fmul(bl.num, br.den), wr = fmul(br.num, bl.den);
-                float ssum = fadd(wl, wr);
-                if (!(ssum > 0.0f)) {
-                    wl = L.phi;
-                    wr = R.phi;
-                    ssum = fadd(wl, wr);
-                }
-                const float ud = rs.draw(kDrawDescent + level);
-                ++level;
-                bool left;
-                float ratio;
-                if (ssum > 0.0f) {
-                    left = __fmaf_rn(ud, ssum, -wl) < 0.0f;
-                    ratio = __fdividef(left ? wl : wr, wl + wr);  // continuous: pdf only
-                } else {
-                    left = ud < 0.5f;
-                    ratio = 0.5f;
-                }
-                p_in *= ratio;
-                node = left ? L.id : R.id;
-            }
+            for (uint32_t level = 0; (int64_t)node < nl1; ++level)
+                descent_step(a, node, p_in, rs.draw(kDrawDescent + level), x0, x1, x2, n0, n1, n2);
             light = (int64_t)node - nl1;
         }
         const LightRec Lr = load_light(a.lights + light);
-        const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, p_cut, p_in, rs, s_box, a.n_boxes,
+        const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, su.p_cut, p_in, su.ua, su.ub, s_box, a.n_boxes,
                                  a.reward_mode);
         acc0 += o.est[0];
         acc1 += o.est[1];
         acc2 += o.est[2];
         if (a.rec_key) {
-            a.rec_key[sid] = slot < 0 ? kInvalidRecord
-                                      : (a.key_cells ? ((a.cell_base + (uint32_t)slot) << kBatchClusterBits) | s
-                                                     : (uint32_t)slot * a.M + s);
+            a.rec_key[sid] = su.rec;
             a.rec_val[sid] = o.reward;
         }
         if (DBG) {
             if (a.dbg_light) a.dbg_light[sid] = (int32_t)light;
-            if (a.dbg_pcut) a.dbg_pcut[sid] = p_cut;
+            if (a.dbg_pcut) a.dbg_pcut[sid] = su.p_cut;
             if (a.dbg_pin) a.dbg_pin[sid] = p_in;
         }
     }
