@@ -56,7 +56,7 @@ def workload_config(scene):
             "points": scene.n_points, "lights": scene.n_lights, "boxes": int(scene.boxes.shape[0]),
             "spp": scene.spp, "cut_size": g.cut_size, "table_size": g.table_size,
             "cell_size": g.cell_size, "normal_bins": g.normal_bins, "jitter": g.jitter,
-            "table_precision": "fp32", "in_cluster": "descent",
+            "table_precision": "fp32", "in_cluster": "descent", "split_iterations": g.split_iterations,
             "l2": "flushed between timed steps (512 MB write, untimed)"}
 
 
@@ -413,6 +413,68 @@ def run_dynamic(args):
     return 0
 
 
+def leaf_spread(grid):
+    """How unequal the learned leaf weights of the occupied cells are: mean
+    over cells of max Q / mean Q of the cut's leaves (1 = all equal)."""
+    st = grid.export()
+    occ = st["keys"] != np.uint64(0xFFFFFFFFFFFFFFFF)
+    q = st["q"][occ, :grid.m].astype(np.float64)
+    r = q.max(axis=1) / np.maximum(q.mean(axis=1), 1e-300)
+    return {"cells": int(occ.sum()), "mean_max_over_mean": float(r.mean()),
+            "median_max_over_mean": float(np.median(r))}
+
+
+def run_split(args):
+    """Iterated split-collapse: the frame workload learned for a number of
+    passes with split-collapse repeated up to K steps per cell and pass, for
+    several K; per K the pass time (split-collapse separately), how far the
+    cuts have equalised the leaf weights after 1, 4, 16, ... passes, and the
+    1-spp MSE at the end."""
+    import torch
+    from paper_1911_10217_gb300 import rll, scenes
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    ctx = rll.Context(0, stream)
+    s = scenes.frame_scene()
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    tri, em, boxes = T(s.tris.reshape(-1, 9)), T(s.emission), T(s.boxes)
+    pos, nrm, alb = T(s.pos), T(s.nrm), T(s.albedo)
+    tree = rll.Tree(ctx, tri, em)
+    P = s.n_points
+    rgb = torch.empty(3, P, device=dev)
+    key = torch.empty(P, dtype=torch.int32, device=dev)
+    val = torch.empty(P, device=dev)
+    checkpoints = {1, 4, 16, 64, 256, 1024}
+    results = {}
+    for K in [int(k) for k in args.split_sweep.split(",")]:
+        grid = rll.Grid(ctx, tree, rll.grid_params_for(s.grid, split_iterations=K))
+        ev, spread = [], {}
+        for f in range(args.split_passes):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, s.seed, f, 1, rgb, key, val)
+            rll.learn_update(ctx, grid, key, val)
+            e[1].record(stream)
+            rll.split_collapse(ctx, grid, tree)
+            e[2].record(stream)
+            ev.append(e)
+            if f + 1 in checkpoints:
+                torch.cuda.synchronize()
+                spread[f + 1] = leaf_spread(grid)
+        torch.cuda.synchronize()
+        t_pass = [a.elapsed_time(c) for a, _, c in ev][3:]
+        t_split = [b.elapsed_time(c) for _, b, c in ev][3:]
+        results[K] = {"ms_per_pass": statistics.mean(t_pass), "split_ms": statistics.mean(t_split),
+                      "samples_per_s": P / (statistics.mean(t_pass) * 1e-3), "leaf_spread": spread,
+                      "mse_equal_spp": quality(rll, ctx, grid, tree, s, pos, nrm, alb, boxes, dev)}
+        grid.close()
+    line = {"metric": METRIC, "workload": "split", "unit": UNIT, "n_gpus": 1, "data": "synthetic",
+            "config": dict(workload_config(s), split_iterations="swept", passes=args.split_passes),
+            "split_iterations": results, "device_status": ctx.sync_status()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,7 +485,10 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
-    ap.add_argument("--workload", default="frame", choices=["frame", "batched", "serving", "dynamic"])
+    ap.add_argument("--workload", default="frame", choices=["frame", "batched", "serving", "dynamic", "split"])
+    ap.add_argument("--split-iterations", type=int, default=1)
+    ap.add_argument("--split-sweep", default="1,2,4,16,64")
+    ap.add_argument("--split-passes", type=int, default=64)
     ap.add_argument("--dynamic-scale", type=float, default=1.0)
     ap.add_argument("--dynamic-frames", type=int, default=120)
     ap.add_argument("--serving-sessions", type=int, default=64)
@@ -442,11 +507,14 @@ def main():
         return run_serving(args)
     if args.workload == "dynamic":
         return run_dynamic(args)
+    if args.workload == "split":
+        return run_split(args)
     from paper_1911_10217_gb300 import scenes
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     scene = scenes.frame_scene(seed=1 + rank)
+    scene.grid.split_iterations = args.split_iterations
     if args.impl == "reference":
         return run_reference(args, scene)
 

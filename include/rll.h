@@ -69,6 +69,9 @@ typedef struct rll_grid_params {
     float threshold;           /* split-collapse T (> 0) */
     float eps;                 /* Eq. 2 floor: eps * sum(Q) / m added to each leaf, >= 0 */
     float q_init;              /* Q of a new cell's leaves, > 0 */
+    uint32_t split_iterations; /* split-collapse steps per cell and call, 1 .. 256 (0 reads as 1):
+                                  1 is the basic algorithm; more repeat it until a step
+                                  changes nothing (Section 3) */
 } rll_grid_params;
 
 /* Per-sample diagnostics (optional outputs of rll_sample_and_shade_ex), each

@@ -80,7 +80,8 @@ def lib():
                                            P, P, P, P, P, P, P, P, P, ctypes.c_int64, ctypes.c_int64]
             L.orc_learn.argtypes = [ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P, P]
             L.orc_split_collapse_cell.argtypes = [ctypes.POINTER(_Tree), ctypes.c_int, P, P,
-                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                  ctypes.c_int, P]
             L.orc_split_collapse_cell.restype = ctypes.c_int
             L.orc_light_pdf.argtypes = [ctypes.POINTER(_Tree), ctypes.c_int, ctypes.c_int, P, P,
                                         P, P, ctypes.c_int64]
@@ -172,7 +173,7 @@ class Grid:
 
     def __init__(self, tree: Tree, table_size, cut_size, origin=(0, 0, 0), cell_size=1.0,
                  normal_bins=1, jitter=False, mode="descent", reward="cluster", precision="fp32",
-                 alpha=0.03, T=2.0, eps=0.02, q_init=1e-3):
+                 alpha=0.03, T=2.0, eps=0.02, q_init=1e-3, split_iterations=1):
         self.tree = tree
         H, M = int(table_size), int(cut_size)
         assert H & (H - 1) == 0
@@ -189,7 +190,8 @@ class Grid:
         self.params = dict(origin=tuple(float(o) for o in origin), cell_size=float(cell_size),
                            normal_bins=int(normal_bins), jitter=bool(jitter), mode=mode,
                            reward=reward, precision=precision, alpha=float(alpha), T=float(T),
-                           eps=float(eps), q_init=float(q_init))
+                           eps=float(eps), q_init=float(q_init),
+                           split_iterations=int(split_iterations))
         self._s = _Grid(H, M, m, (ctypes.c_float * 3)(*origin), float(cell_size), int(normal_bins),
                         int(bool(jitter)), MODE[mode], REWARD[reward], PREC[precision],
                         float(alpha), float(T), float(eps), _p(self.keys), _p(self.cut),
@@ -200,7 +202,8 @@ class Grid:
         g = scene.grid
         args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin,
                     cell_size=g.cell_size, normal_bins=g.normal_bins, jitter=g.jitter,
-                    q_init=g.q_init, alpha=g.alpha, eps=g.eps, T=g.threshold)
+                    q_init=g.q_init, alpha=g.alpha, eps=g.eps, T=g.threshold,
+                    split_iterations=g.split_iterations)
         args.update(kw)
         return cls(tree, **args)
 
@@ -246,15 +249,18 @@ class Grid:
         return touched.astype(bool)
 
     def split_collapse(self, touched):
-        """Split-collapse every touched cell; returns the number changed."""
+        """Split-collapse every touched cell (up to split_iterations steps
+        each); returns the number of cells changed."""
         changed = 0
         c_out = np.zeros(self.m)
         for slot in np.nonzero(touched)[0]:
             cut = np.ascontiguousarray(self.cut[slot, :self.m])
             q = np.ascontiguousarray(self.Q[slot, :self.m])
-            changed += lib().orc_split_collapse_cell(ctypes.byref(self.tree._s), self.m, _p(cut),
-                                                     _p(q), self.params["T"], self.params["eps"],
-                                                     PREC[self.precision], _p(c_out))
+            steps = lib().orc_split_collapse_cell(ctypes.byref(self.tree._s), self.m, _p(cut), _p(q),
+                                                  self.params["T"], self.params["eps"],
+                                                  PREC[self.precision], self.params["split_iterations"],
+                                                  _p(c_out))
+            changed += steps > 0
             self.cut[slot, :self.m] = cut
             self.Q[slot, :self.m] = q
             self.C[slot, :self.m] = c_out
@@ -268,13 +274,15 @@ class Grid:
                                    _p(_f32(nrm)), int(light))
 
 
-def split_collapse_cell(tree: Tree, cut, q, T=2.0, eps=0.01, precision="fp32"):
+def split_collapse_cell(tree: Tree, cut, q, T=2.0, eps=0.01, precision="fp32", max_iter=1):
+    """Split-collapse of one cut row, at most max_iter steps; returns the new
+    cut, Q, C and the number of steps that changed the cut."""
     cut = np.ascontiguousarray(cut, np.int32).copy()
     q = np.ascontiguousarray(q, np.float64).copy()
     c = np.zeros(len(cut))
-    changed = lib().orc_split_collapse_cell(ctypes.byref(tree._s), len(cut), _p(cut), _p(q),
-                                            float(T), float(eps), PREC[precision], _p(c))
-    return cut, q, c, bool(changed)
+    steps = lib().orc_split_collapse_cell(ctypes.byref(tree._s), len(cut), _p(cut), _p(q),
+                                          float(T), float(eps), PREC[precision], int(max_iter), _p(c))
+    return cut, q, c, int(steps)
 
 
 def sample_power(tree: Tree, scene_arrays, seed, frame, spp, first=0, count=-1, emission=None):

@@ -915,14 +915,15 @@ int orc_learn(orc_grid* g, int64_t nrec, const int64_t* slot, const int32_t* s, 
 /* leaves (reading: collapsing any other parent would change the cut size;   */
 /* with Q >= 0 a minimiser over all parents is always such a node). Ties go  */
 /* to the smaller range begin. If Q(l_max) > T Q(p_min), l_max is replaced by */
-/* its children (Q split in proportion to their power, reading) and p_min's  */
-/* children by p_min (Q summed). Decisions in binary32 on the stored Q.      */
-/* Returns 1 if the cut changed.                                             */
+/* its children and p_min's children by p_min. Decisions in binary32 on the  */
+/* stored Q. New Q values (reading): l_max's Q times f = phi_a / (phi_a +    */
+/* phi_c) and times 1 - f (children's stored binary32 power), p_min's Q the  */
+/* sum of its children's; binary32 arithmetic like the decisions that later  */
+/* read them, then rounded to the table precision.                          */
+/* One step; returns 1 if the cut changed.                                  */
 /* ------------------------------------------------------------------------ */
-int orc_split_collapse_cell(const orc_tree* t, int m, int32_t* cut, double* q, double T, double eps,
-                            int precision, double* c_out)
+static int orc_split_collapse_step(const orc_tree* t, int m, int32_t* cut, double* q, double T, int precision)
 {
-    int64_t nl = t->n;
     int lmax = -1;
     float qmax = 0.0f;
     for (int i = 0; i < m; ++i) {
@@ -938,35 +939,45 @@ int orc_split_collapse_cell(const orc_tree* t, int m, int32_t* cut, double* q, d
         float v = (float)q[i] + (float)q[i + 1];
         if (pmin < 0 || v < qmin) { pmin = i; qmin = v; }
     }
-    int changed = 0;
-    if (lmax >= 0 && pmin >= 0 && lmax != pmin && lmax != pmin + 1 && qmax > (float)T * qmin) {
-        int32_t nc[1024];
-        double nq[1024];
-        int k = 0;
-        for (int i = 0; i < m; ++i) {
-            if (i == lmax) {
-                int32_t node = cut[i];
-                int32_t a = t->left[node], c = t->right[node];
-                double pa = t->phi64[a], pc = t->phi64[c];
-                double fa = (pa + pc) > 0.0 ? pa / (pa + pc) : 0.5;
-                nc[k] = a; nq[k] = q[i] * fa; ++k;
-                nc[k] = c; nq[k] = q[i] * (1.0 - fa); ++k;
-            } else if (i == pmin) {
-                nc[k] = t->parent[cut[i]]; nq[k] = q[i] + q[i + 1]; ++k;
-                ++i;
-            } else {
-                nc[k] = cut[i]; nq[k] = q[i]; ++k;
-            }
+    if (!(lmax >= 0 && pmin >= 0 && lmax != pmin && lmax != pmin + 1 && qmax > (float)T * qmin)) return 0;
+    int32_t nc[1024];
+    double nq[1024];
+    int k = 0;
+    for (int i = 0; i < m; ++i) {
+        if (i == lmax) {
+            int32_t node = cut[i];
+            int32_t a = t->left[node], c = t->right[node];
+            float pa = REC(t, a)[6], pc = REC(t, c)[6];
+            float sum = pa + pc;
+            float fa = sum > 0.0f ? pa / sum : 0.5f;
+            float qi = (float)q[i];
+            nc[k] = a; nq[k] = (double)(qi * fa); ++k;
+            nc[k] = c; nq[k] = (double)(qi * (1.0f - fa)); ++k;
+        } else if (i == pmin) {
+            nc[k] = t->parent[cut[i]]; nq[k] = (double)((float)q[i] + (float)q[i + 1]); ++k;
+            ++i;
+        } else {
+            nc[k] = cut[i]; nq[k] = q[i]; ++k;
         }
-        for (int i = 0; i < m; ++i) {
-            cut[i] = nc[i];
-            q[i] = orc_round_storage(nq[i], precision);
-        }
-        changed = 1;
     }
-    (void)nl;
+    for (int i = 0; i < m; ++i) {
+        cut[i] = nc[i];
+        q[i] = orc_round_storage(nq[i], precision);
+    }
+    return 1;
+}
+
+/* Split-collapse of one cell, repeated until a step changes nothing or      */
+/* max_iter steps were taken (Section 3: the basic algorithm is one step;    */
+/* the paper notes it may be repeated until no pair of nodes is touched).    */
+/* Then Eq. 2. Returns the number of steps that changed the cut.            */
+int orc_split_collapse_cell(const orc_tree* t, int m, int32_t* cut, double* q, double T, double eps,
+                            int precision, int max_iter, double* c_out)
+{
+    int steps = 0;
+    while (steps < max_iter && orc_split_collapse_step(t, m, cut, q, T, precision)) ++steps;
     orc_cdf(m, q, eps, precision, c_out);
-    return changed;
+    return steps;
 }
 
 /* ------------------------------------------------------------------------ */

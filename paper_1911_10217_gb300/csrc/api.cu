@@ -114,6 +114,8 @@ int check_params(rll_ctx* ctx, const rll_grid_params* p)
     if (!(p->threshold > 0.0f) || !std::isfinite(p->threshold)) return fail(ctx, RLL_E_INVALID, "threshold must be > 0");
     if (!(p->eps >= 0.0f) || !std::isfinite(p->eps)) return fail(ctx, RLL_E_INVALID, "eps must be >= 0");
     if (!(p->q_init > 0.0f) || !std::isfinite(p->q_init)) return fail(ctx, RLL_E_INVALID, "q_init must be > 0");
+    if (p->split_iterations > kMaxSplitIterations)
+        return fail(ctx, RLL_E_INVALID, "split_iterations must be in [0, 256]");
     return RLL_OK;
 }
 

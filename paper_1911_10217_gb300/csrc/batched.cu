@@ -44,6 +44,7 @@ struct BatchItemDev {
     const int32_t* right;
     int64_t n_nodes;
     float alpha, eps, T;
+    uint32_t split_iters;    // split-collapse steps per cell
     uint32_t cell_base;      // first global cell of the item
 };
 
@@ -151,8 +152,8 @@ k_split_batched(const BatchItemDev* __restrict__ items, int n_items, const uint3
         const BatchItemDev& it = items[item_of_cell(cell_prefix, n_items, cell)];
         const int64_t row = (int64_t)(cell - it.cell_base) * it.s.M;
         split_one_cell<P>(it.cut + row, (T*)it.Q + row, (T*)it.C + row, it.s.m, it.nodes, it.parent, it.left,
-                          it.right, it.T, it.eps, it.n_nodes, status, s_q[warp], s_c[warp], s_cut[warp], s_nc[warp],
-                          s_b[warp]);
+                          it.right, it.T, it.eps, it.split_iters, it.n_nodes, status, s_q[warp], s_c[warp],
+                          s_cut[warp], s_nc[warp], s_b[warp]);
     }
 }
 
@@ -459,6 +460,7 @@ int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items,
         d.alpha = g->p.alpha;
         d.eps = g->p.eps;
         d.T = g->p.threshold;
+        d.split_iters = split_steps(g->p);
         d.cell_base = cell_pre[i];
         cell_pre[i + 1] = cell_pre[i] + g->H;
         rec_off += (uint64_t)it.n_points * it.spp;

@@ -208,7 +208,7 @@ k_split(uint32_t M, uint32_t m, const uint32_t* __restrict__ touched, const uint
         uint32_t* __restrict__ cut, typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C,
         const NodeRec* __restrict__ nodes, const int32_t* __restrict__ parent,
         const int32_t* __restrict__ left, const int32_t* __restrict__ right, float T, float eps,
-        int64_t n_nodes, uint32_t* __restrict__ status)
+        uint32_t max_iter, int64_t n_nodes, uint32_t* __restrict__ status)
 {
     __shared__ float s_q[kWarpsPerBlock][kMaxCut];
     __shared__ float s_c[kWarpsPerBlock][kMaxCut];
@@ -219,8 +219,8 @@ k_split(uint32_t M, uint32_t m, const uint32_t* __restrict__ touched, const uint
     const uint32_t total = *n_touched;
     for (uint32_t w = blockIdx.x * kWarpsPerBlock + warp; w < total; w += gridDim.x * kWarpsPerBlock) {
         const int64_t row = (int64_t)touched[w] * M;
-        split_one_cell<P>(cut + row, Q + row, C + row, m, nodes, parent, left, right, T, eps, n_nodes, status,
-                          s_q[warp], s_c[warp], s_cut[warp], s_nc[warp], s_b[warp]);
+        split_one_cell<P>(cut + row, Q + row, C + row, m, nodes, parent, left, right, T, eps, max_iter, n_nodes,
+                          status, s_q[warp], s_c[warp], s_cut[warp], s_nc[warp], s_b[warp]);
     }
 }
 
@@ -255,8 +255,8 @@ int split_t(rll_ctx* ctx, rll_grid* g, const rll_tree* t)
     const int blocks = device_sm_count(g->device) * 8;
     k_split<P><<<blocks, kWarpsPerBlock * 32, 0, ctx->stream>>>(g->M, g->m, g->touched, g->n_touched, g->cut,
                                                                   (T*)g->Q, (T*)g->C, t->nodes, t->parent, t->left,
-                                                                  t->right, g->p.threshold, g->p.eps, 2 * t->n - 1,
-                                                                  ctx->d_status);
+                                                                  t->right, g->p.threshold, g->p.eps,
+                                                                  split_steps(g->p), 2 * t->n - 1, ctx->d_status);
     return check_cuda(ctx, cudaGetLastError(), "split kernel");
 }
 

@@ -159,13 +159,17 @@ __device__ void learn_one_cell(const uint32_t* __restrict__ sk, const uint32_t* 
     warp_rebuild_cdf<P>(q, (int)m, eps, crow, c, bits);
 }
 
-// Split-collapse of one cell (cut row crow, Q row qrow, cdf row ccrow).
+// Split-collapse of one cell (cut row crow, Q row qrow, cdf row ccrow),
+// repeated until a step changes nothing or max_iter steps were taken. New Q
+// values in correctly rounded binary32, then rounded to the table precision:
+// l_max's Q times f = phi_a / (phi_a + phi_c) and times 1 - f (children's
+// power), p_min's Q the sum of its children's.
 template <int P>
 __device__ void split_one_cell(uint32_t* crow, typename Store<P>::T* qrow, typename Store<P>::T* ccrow, uint32_t m,
                                const NodeRec* __restrict__ nodes, const int32_t* __restrict__ parent,
                                const int32_t* __restrict__ left, const int32_t* __restrict__ right, float T,
-                               float eps, int64_t n_nodes, uint32_t* status, float* q, float* c, uint32_t* cs,
-                               uint32_t* nc, uint16_t* bits)
+                               float eps, uint32_t max_iter, int64_t n_nodes, uint32_t* status, float* q, float* c,
+                               uint32_t* cs, uint32_t* nc, uint16_t* bits)
 {
     const int lane = threadIdx.x & 31;
     bool bad = false;
@@ -179,65 +183,70 @@ __device__ void split_one_cell(uint32_t* crow, typename Store<P>::T* qrow, typen
         return;
     }
     __syncwarp();
-    ArgBest hi{0.0f, 0xFFFFFFFFu}, lo{0.0f, 0xFFFFFFFFu};
     const uint32_t n_internal = (uint32_t)((n_nodes - 1) / 2);  // ids below are internal nodes
-    for (uint32_t s = lane; s < m; s += 32) {
-        if (cs[s] < n_internal && (hi.i == 0xFFFFFFFFu || q[s] > hi.v)) {
-            hi.v = q[s];
-            hi.i = s;
-        }
-        if (s + 1 < m) {
-            const int32_t pa = parent[cs[s]];
-            if (pa >= 0 && pa == parent[cs[s + 1]]) {
-                const float v = fadd(q[s], q[s + 1]);
-                if (lo.i == 0xFFFFFFFFu || v < lo.v) {
-                    lo.v = v;
-                    lo.i = s;
+    uint32_t steps = 0;
+    for (; steps < max_iter; ++steps) {
+        ArgBest hi{0.0f, 0xFFFFFFFFu}, lo{0.0f, 0xFFFFFFFFu};
+        for (uint32_t s = lane; s < m; s += 32) {
+            if (cs[s] < n_internal && (hi.i == 0xFFFFFFFFu || q[s] > hi.v)) {
+                hi.v = q[s];
+                hi.i = s;
+            }
+            if (s + 1 < m) {
+                const int32_t pa = parent[cs[s]];
+                if (pa >= 0 && pa == parent[cs[s + 1]]) {
+                    const float v = fadd(q[s], q[s + 1]);
+                    if (lo.i == 0xFFFFFFFFu || v < lo.v) {
+                        lo.v = v;
+                        lo.i = s;
+                    }
                 }
             }
         }
-    }
-    hi = warp_argmax(hi);
-    lo = warp_argmin(lo);
-    const bool apply = hi.i != 0xFFFFFFFFu && lo.i != 0xFFFFFFFFu && hi.i != lo.i && hi.i != lo.i + 1 &&
-                       hi.v > fmul(T, lo.v);
-    if (!apply) return;
-    // one lane emits the new row into the shared scratch rows
-    if (lane == 0) {
-        float* nq = c;
-        uint32_t k = 0;
-        for (uint32_t i = 0; i < m; ++i) {
-            if (i == hi.i) {
-                const uint32_t node = cs[i];
-                const uint32_t a = (uint32_t)left[node], cc = (uint32_t)right[node];
-                const float pa = nodes[a].phi, pc = nodes[cc].phi;
-                const float sum = pa + pc;
-                const float fa = sum > 0.0f ? pa / sum : 0.5f;
-                const float fc = sum > 0.0f ? pc / sum : 0.5f;
-                nc[k] = a; nq[k] = q[i] * fa; ++k;
-                nc[k] = cc; nq[k] = q[i] * fc; ++k;
-            } else if (i == lo.i) {
-                nc[k] = (uint32_t)parent[cs[i]];
-                nq[k] = q[i] + q[i + 1];
-                ++k;
-                ++i;
-            } else {
-                nc[k] = cs[i];
-                nq[k] = q[i];
-                ++k;
+        hi = warp_argmax(hi);
+        lo = warp_argmin(lo);
+        const bool apply = hi.i != 0xFFFFFFFFu && lo.i != 0xFFFFFFFFu && hi.i != lo.i && hi.i != lo.i + 1 &&
+                           hi.v > fmul(T, lo.v);
+        if (!apply) break;
+        // one lane emits the new row into the scratch rows nc / c
+        if (lane == 0) {
+            float* nq = c;
+            uint32_t k = 0;
+            for (uint32_t i = 0; i < m; ++i) {
+                if (i == hi.i) {
+                    const uint32_t node = cs[i];
+                    const uint32_t a = (uint32_t)left[node], cc = (uint32_t)right[node];
+                    const float pa = nodes[a].phi, pc = nodes[cc].phi;
+                    const float sum = fadd(pa, pc);
+                    const float fa = sum > 0.0f ? fdiv(pa, sum) : 0.5f;
+                    nc[k] = a;
+                    nq[k] = Store<P>::load(Store<P>::store(fmul(q[i], fa)));
+                    ++k;
+                    nc[k] = cc;
+                    nq[k] = Store<P>::load(Store<P>::store(fmul(q[i], fsub(1.0f, fa))));
+                    ++k;
+                } else if (i == lo.i) {
+                    nc[k] = (uint32_t)parent[cs[i]];
+                    nq[k] = Store<P>::load(Store<P>::store(fadd(q[i], q[i + 1])));
+                    ++k;
+                    ++i;
+                } else {
+                    nc[k] = cs[i];
+                    nq[k] = q[i];
+                    ++k;
+                }
+            }
+            for (uint32_t i = 0; i < m; ++i) {
+                cs[i] = nc[i];
+                q[i] = nq[i];
             }
         }
-        for (uint32_t i = 0; i < m; ++i) {
-            cs[i] = nc[i];
-            q[i] = nq[i];
-        }
+        __syncwarp();
     }
-    __syncwarp();
+    if (steps == 0) return;
     for (uint32_t s = lane; s < m; s += 32) {
         crow[s] = cs[s];
-        const typename Store<P>::T st = Store<P>::store(q[s]);
-        qrow[s] = st;
-        q[s] = Store<P>::load(st);
+        qrow[s] = Store<P>::store(q[s]);  // exact: q holds table values
     }
     __syncwarp();
     warp_rebuild_cdf<P>(q, (int)m, eps, ccrow, c, bits);

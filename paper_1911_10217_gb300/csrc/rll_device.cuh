@@ -23,6 +23,7 @@ constexpr uint32_t kInvalidRecord = 0xFFFFFFFFu;
 constexpr int kMaxProbes = 64;
 constexpr int kMaxCut = 256;
 constexpr int kMaxBoxes = 1024;
+constexpr uint32_t kMaxSplitIterations = 256;
 constexpr float kShadowOffset = 1e-4f;
 constexpr float kShadowTmax = 0.9999f;
 

@@ -104,6 +104,8 @@ void launch_cell_heads(cudaStream_t s, const uint32_t* sk, int64_t n, uint32_t H
                        uint32_t* touched_start, uint32_t* n_touched);
 int key_bits(uint64_t hm_plus_one);
 int device_sm_count(int device);
+// split-collapse steps per cell and call (0 reads as 1)
+inline uint32_t split_steps(const rll_grid_params& p) { return p.split_iterations ? p.split_iterations : 1u; }
 int learn_update(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n);
 int split_collapse(rll_ctx* ctx, rll_grid* g, const rll_tree* t);
 // learn_update with the sort buffers in caller-provided device scratch

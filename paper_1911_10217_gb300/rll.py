@@ -47,7 +47,8 @@ class GridParams(ctypes.Structure):
                 ("normal_bins", ctypes.c_uint32), ("jitter", ctypes.c_uint32),
                 ("precision", ctypes.c_uint32), ("in_cluster_mode", ctypes.c_uint32),
                 ("reward_mode", ctypes.c_uint32), ("alpha", ctypes.c_float),
-                ("threshold", ctypes.c_float), ("eps", ctypes.c_float), ("q_init", ctypes.c_float)]
+                ("threshold", ctypes.c_float), ("eps", ctypes.c_float), ("q_init", ctypes.c_float),
+                ("split_iterations", ctypes.c_uint32)]
 
 
 class BatchItem(ctypes.Structure):
@@ -237,10 +238,10 @@ class Tree:
 
 def grid_params(table_size, cut_size, origin=(0.0, 0.0, 0.0), cell_size=1.0, normal_bins=1,
                 jitter=False, precision="fp32", mode="descent", reward="cluster", alpha=0.03,
-                threshold=2.0, eps=0.02, q_init=1e-3) -> GridParams:
+                threshold=2.0, eps=0.02, q_init=1e-3, split_iterations=1) -> GridParams:
     return GridParams(int(table_size), int(cut_size), (ctypes.c_float * 3)(*origin), float(cell_size),
                       int(normal_bins), int(bool(jitter)), PREC[precision], MODE[mode], REWARD[reward],
-                      float(alpha), float(threshold), float(eps), float(q_init))
+                      float(alpha), float(threshold), float(eps), float(q_init), int(split_iterations))
 
 
 def grid_params_for(grid_config, **overrides) -> GridParams:
@@ -248,7 +249,7 @@ def grid_params_for(grid_config, **overrides) -> GridParams:
     g = grid_config
     args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin, cell_size=g.cell_size,
                 normal_bins=g.normal_bins, jitter=g.jitter, q_init=g.q_init, alpha=g.alpha, eps=g.eps,
-                threshold=g.threshold)
+                threshold=g.threshold, split_iterations=g.split_iterations)
     args.update(overrides)
     return grid_params(**args)
 

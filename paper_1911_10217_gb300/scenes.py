@@ -38,6 +38,7 @@ class GridConfig:
     alpha: float = 0.03      # Eq. 1 learning rate
     eps: float = 0.02        # Eq. 2 floor
     threshold: float = 2.0   # split-collapse T
+    split_iterations: int = 1  # split-collapse steps per cell and pass (1: the basic algorithm)
 
 
 @dataclasses.dataclass

@@ -96,6 +96,7 @@ def clone_oracle_grid(O, og):
     p = og.params
     g2 = O.Grid(og.tree, og.H, og.M, origin=p["origin"], cell_size=p["cell_size"],
                 normal_bins=p["normal_bins"], jitter=p["jitter"], mode=p["mode"], reward=p["reward"],
-                precision=p["precision"], alpha=p["alpha"], T=p["T"], eps=p["eps"], q_init=p["q_init"])
+                precision=p["precision"], alpha=p["alpha"], T=p["T"], eps=p["eps"], q_init=p["q_init"],
+                split_iterations=p["split_iterations"])
     g2.copy_state_from(og.keys, og.cut, og.Q, og.C)
     return g2

@@ -60,8 +60,8 @@ def test_context_without_device_fails_cleanly(lib):
 
 def test_grid_params_layout_matches_header(lib):
     from paper_1911_10217_gb300 import rll
-    # 2 u32 + 3 f32 + f32 + 5 u32 + 4 f32 = 15 words
-    assert ctypes.sizeof(rll.GridParams) == 60
+    # 2 u32 + 3 f32 + f32 + 5 u32 + 4 f32 + u32 = 16 words
+    assert ctypes.sizeof(rll.GridParams) == 64
     assert ctypes.sizeof(rll.SampleDebug) == 3 * ctypes.sizeof(ctypes.c_void_p)
 
 

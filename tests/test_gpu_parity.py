@@ -54,6 +54,8 @@ def test_tree_matches_oracle_bit_exact(env, maker):
     dict(precision="bf16"),
     dict(jitter=True),
     dict(reward="literal", cut_size=8),
+    dict(split_iterations=4),
+    dict(split_iterations=16, precision="bf16"),
 ])
 def test_lockstep_learning_tiny(env, variant):
     """Eight passes of the tiny scene. At each pass the oracle's state is
@@ -61,7 +63,8 @@ def test_lockstep_learning_tiny(env, variant):
     O, rll, ctx = env["O"], env["rll"], env["ctx"]
     s = scenes.tiny_scene(jitter=variant.get("jitter", False))
     ot, dt, d = _trees(env, s)
-    okw = {k: v for k, v in variant.items() if k in ("mode", "precision", "reward", "cut_size")}
+    okw = {k: v for k, v in variant.items()
+           if k in ("mode", "precision", "reward", "cut_size", "split_iterations")}
     og = O.Grid.for_scene(ot, s, **okw)
     dkw = dict(okw)
     dg = rll.Grid(ctx, dt, params_for(rll, s, **dkw))

@@ -145,9 +145,10 @@ def test_split_collapse_figure_example(oracle_mod):
     A = cut[0]
     parent_cd = tree.parent[cut[2]]
     assert new_cut.tolist() == [tree.left[A], tree.right[A], cut[1], parent_cd]
-    # Q of A split in proportion to its children's power (equal up to float32
-    # rounding of the triangle areas); the collapsed parent sums its leaves
-    pa, pc = tree.phi64[tree.left[A]], tree.phi64[tree.right[A]]
+    # Q of A split in proportion to its children's stored (binary32) power
+    # (equal up to float32 rounding of the triangle areas); the collapsed
+    # parent sums its leaves
+    pa, pc = float(tree.rec[tree.left[A], 6]), float(tree.rec[tree.right[A], 6])
     assert new_q[0] == pytest.approx(10.0 * pa / (pa + pc), rel=1e-7)
     assert new_q[1] == pytest.approx(10.0 * pc / (pa + pc), rel=1e-7)
     assert new_q[0] == pytest.approx(5.0, rel=1e-5)
@@ -213,3 +214,76 @@ def test_split_collapse_invariants_random(oracle_mod):
                 assert len(collapsed) == 1
                 assert np.float32(internal[collapsed[0]]) <= min(internal.values()) * (1 + 1e-6)
             cut, q = new_cut, new_q * rng.uniform(0.5, 2.0, size=len(new_q))
+
+
+def _line_lights():
+    """16 equal lights on a 4 x 2 x 2 grid: a balanced tree of depth 4."""
+    tris = []
+    for x in (0.125, 0.375, 0.625, 0.875):
+        for y in (0.25, 0.75):
+            for z in (0.25, 0.75):
+                c = np.array([x, y, z])
+                tris.append([c + [-0.01, 0, -0.01], c + [0.02, 0, -0.01], c + [-0.01, 0, 0.02]])
+    t = np.asarray(tris, np.float32)
+    return t, np.ones((t.shape[0], 3), np.float32)
+
+
+def test_split_collapse_iterated_by_hand(oracle_mod):
+    """Repeating split-collapse until no pair is touched (Section 3). Cut
+    [A1, A2, B, C, D1, D2] of a balanced 16-light tree (A1, A2, D1, D2: two
+    lights; B, C: four), Q = [8, 8, 1, 0.3, 0.1, 0.1], T = 2, equal powers.
+    Step 1: l_max = A1 (tie with A2, smaller begin), p_min = D (0.2); 8 > 0.4
+    -> [a0, a1, A2, B, C, D] with Q [4, 4, 8, 1, 0.3, 0.2].
+    Step 2: l_max = A2 (8), p_min = parent(C, D) (0.5); 8 > 1
+    -> [a0, a1, a2, a3, B, parent(C, D)] with Q [4, 4, 4, 4, 1, 0.5].
+    Step 3: l_max = B (1), p_min = A1 (8): 1 > 16 fails, a fixed point."""
+    tris, em = _line_lights()
+    tree = oracle_mod.Tree(tris, em)
+    rng = lambda node: (int(tree.begin[node]), int(tree.end[node]))  # noqa: E731
+    root = 0
+    L, R = tree.left[root], tree.right[root]
+    A, B = tree.left[L], tree.right[L]
+    C, D = tree.left[R], tree.right[R]
+    assert [rng(x) for x in (A, B, C, D)] == [(0, 4), (4, 8), (8, 12), (12, 16)]
+    cut = np.array([tree.left[A], tree.right[A], B, C, tree.left[D], tree.right[D]], np.int32)
+    q = np.array([8.0, 8.0, 1.0, 0.3, 0.1, 0.1])
+    q = np.array([float(np.float32(v)) for v in q])  # table values are binary32
+    c1, q1, _, steps = oracle_mod.split_collapse_cell(tree, cut, q, T=2.0, max_iter=1)
+    assert steps == 1
+    assert [rng(x) for x in c1] == [(0, 1), (1, 2), (2, 4), (4, 8), (8, 12), (12, 16)]
+    assert q1 == pytest.approx([4, 4, 8, 1, 0.3, 0.2], rel=1e-6)
+    c2, q2, c, steps = oracle_mod.split_collapse_cell(tree, cut, q, T=2.0, max_iter=8)
+    assert steps == 2
+    assert [rng(x) for x in c2] == [(0, 1), (1, 2), (2, 3), (3, 4), (4, 8), (8, 16)]
+    assert q2 == pytest.approx([4, 4, 4, 4, 1, 0.5], rel=1e-6)
+    assert q2.sum() == pytest.approx(q.sum(), rel=1e-7)
+    # a fixed point stays put
+    _, _, _, steps = oracle_mod.split_collapse_cell(tree, c2, q2, T=2.0, max_iter=8)
+    assert steps == 0
+
+
+def test_split_collapse_iterated_reaches_fixed_point(oracle_mod):
+    """Repeated steps keep size, partition and total Q; the result is either
+    a fixed point of one more step or the step limit was reached."""
+    rng = np.random.default_rng(11)
+    s = scenes.small_frame_scene()
+    tree = oracle_mod.Tree(s.tris, s.emission)
+    hit_fixed = 0
+    for trial in range(40):
+        cut = tree.initial_cut(16)
+        q = rng.exponential(size=len(cut)) ** 3
+        new_cut, new_q, c, steps = oracle_mod.split_collapse_cell(tree, cut, q, T=1.5, eps=0.01, max_iter=32)
+        b, e = tree.begin[new_cut], tree.end[new_cut]
+        assert len(new_cut) == len(cut)
+        assert b[0] == 0 and e[-1] == tree.n and np.all(b[1:] == e[:-1])
+        assert new_q.sum() == pytest.approx(q.sum(), rel=1e-6)
+        _, _, _, more = oracle_mod.split_collapse_cell(tree, new_cut, new_q, T=1.5, max_iter=1)
+        assert steps == 32 or more == 0
+        hit_fixed += steps < 32
+        # k single steps give the same cut as one call of k steps
+        c1, q1 = cut, q
+        for _ in range(steps):
+            c1, q1, _, one = oracle_mod.split_collapse_cell(tree, c1, q1, T=1.5, max_iter=1)
+            assert one == 1
+        assert c1.tolist() == new_cut.tolist() and np.array_equal(q1, new_q)
+    assert hit_fixed > 0
