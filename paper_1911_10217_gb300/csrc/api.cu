@@ -90,7 +90,10 @@ void free_grid(rll_grid* g)
     cudaFree(g->def_C);
     cudaFree(g->touched);
     cudaFree(g->touched_start);
+    cudaFree(g->touched_len);
     cudaFree(g->n_touched);
+    cudaFree(g->cursor);
+    cudaFree(g->big);
     delete g;
 }
 
@@ -341,9 +344,13 @@ int rll_create_grid(rll_ctx* ctx, const rll_tree* tree, const rll_grid_params* p
     if (e == cudaSuccess) e = cudaMalloc(&g->def_C, eb * g->m);
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->touched, 4 * (size_t)g->H);
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->touched_start, 4 * (size_t)g->H);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&g->n_touched, 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->touched_len, 4 * (size_t)g->H);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->n_touched, 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->cursor, 4 * (size_t)g->H);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->big, 4 * (size_t)g->H);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->keys, 0xFF, 8 * (size_t)g->H, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->n_touched, 0, 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->n_touched, 0, 16, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->cursor, 0, 4 * (size_t)g->H, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->def_cut, cut.data(), 4 * g->m, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) {

@@ -1,18 +1,33 @@
 // End-of-pass learning (Section 3, Eq. 1 and Eq. 2) and split-collapse
 // (Section 3, Fig. "TreeCuts"; Section 3.1).
 //
-// learn_update:
-//   1. stable radix sort of the records by key = slot * M + cluster (records
-//      arrive in sample order, so each key's records stay in sample order);
-//   2. one thread per sorted record marks the first record of every cell and
-//      appends (cell, first record) to the touched-cell list;
-//   3. one warp per touched cell walks its records 32 at a time: a segmented
-//      inclusive scan (by cluster) composes the affine maps
-//      q -> (1 - alpha) q + alpha |c| of Eq. 1 in sample order, and the last
-//      lane of each segment applies the composite to the cluster's Q held in
-//      shared memory; the row is then stored in the table precision and its
-//      cdf rebuilt (Eq. 2 with the floor, prefix sum across the warp).
-// The result is independent of thread scheduling: deterministic.
+// learn_update (records bucketed by cell, then sorted per cell):
+//   1. count: one thread per record; the lanes of a warp that hold the same
+//      cell add their count with one atomic on the cell's cursor, and the
+//      first adder of a cell appends it to the touched-cell list;
+//   2. claim: every touched cell takes a contiguous bucket of its record
+//      count (one atomic per warp) and its cursor becomes the bucket start;
+//   3. scatter: every record writes its sample id at its cell's cursor (a
+//      warp's peers take consecutive places);
+//   4. one warp per touched cell orders its bucket in shared memory: a
+//      counting sort by cluster, then each record's rank by sample id inside
+//      its cluster group (groups are small), which gives (cluster, sample)
+//      order; it then walks the records 32 at a time: a segmented inclusive
+//      scan (by cluster) composes the affine maps q -> (1 - alpha) q +
+//      alpha |c| of Eq. 1 in sample order, and the last lane of each segment
+//      applies the composite to the cluster's Q held in shared memory; the
+//      row is then stored in the table precision and its cdf rebuilt (Eq. 2
+//      with the floor, prefix sum across the warp). Cells with more records
+//      than a warp's buffer are ordered the same way by a whole block, or,
+//      when larger still, sorted in place in global memory by a bitonic
+//      network.
+// The order inside a bucket depends on thread scheduling; the per-cell sort
+// restores sample order, so the result is deterministic.
+//
+// learn_update_with_scratch (the allocation-free entry point) keeps the
+// earlier form: a stable radix sort of all records by key = slot * M +
+// cluster, then the first record of every cell is marked (k_cell_heads) and
+// one warp per cell composes the same way.
 //
 // split_collapse: one warp per touched cell (the paper uses one thread group
 // per cell): warp arg-max over the leaves that are not single lights, warp
@@ -225,27 +240,395 @@ k_split(uint32_t M, uint32_t m, const uint32_t* __restrict__ touched, const uint
 }
 
 
+// ---------------------------------------------------------------- bucketed learning
+// counters (rll_grid::n_touched): [0] touched cells, [1] bucket space claimed,
+// [2] unused, [3] cells for the block path (listed in rll_grid::big)
+constexpr int kBucketThreads = 256;
+constexpr int kTilesPerWarp = 4;         // 32-record tiles one warp counts / scatters
+constexpr uint32_t kWarpBucket = 240;    // records of a cell one warp orders in shared memory
+constexpr uint32_t kBlockBucket = 2048;  // records of a cell one block orders in shared memory
+constexpr int kBigThreads = 256;
+
+// 1. record counts per cell; the first adder appends the cell to the touched
+// list. Each warp takes kTilesPerWarp tiles of 32 consecutive records.
+__global__ void __launch_bounds__(kBucketThreads)
+k_bucket_count(const uint32_t* __restrict__ rec_key, int64_t n, uint32_t HM, uint32_t M, uint32_t* __restrict__ cursor,
+               uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t tile0 = ((int64_t)blockIdx.x * (kBucketThreads / 32) + (threadIdx.x >> 5)) * kTilesPerWarp;
+    uint32_t slot[kTilesPerWarp], peers[kTilesPerWarp], old[kTilesPerWarp];
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        const int64_t i = (tile0 + u) * 32 + lane;
+        const uint32_t key = i < n ? __ldg(rec_key + i) : 0xFFFFFFFFu;
+        slot[u] = key < HM ? key / M : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) peers[u] = __match_any_sync(0xffffffffu, slot[u]);
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        old[u] = 1u;
+        if (slot[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
+            old[u] = atomicAdd(cursor + slot[u], (uint32_t)__popc(peers[u]));
+    }
+    // cells this lane saw first: one append per warp for all of them
+    uint32_t fresh = 0;
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) fresh += old[u] == 0u;
+    uint32_t x = fresh;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    uint32_t base = 0;
+    if (lane == 31 && x) base = atomicAdd(ctr, x);
+    base = __shfl_sync(0xffffffffu, base, 31) + x - fresh;
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u)
+        if (old[u] == 0u) touched[base++] = slot[u];
+}
+
+// 2. one contiguous bucket per touched cell (one atomic per warp)
+__global__ void __launch_bounds__(kBucketThreads)
+k_bucket_claim(const uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr, uint32_t* __restrict__ cursor,
+               uint32_t* __restrict__ start, uint32_t* __restrict__ len)
+{
+    const uint32_t total = *(volatile uint32_t*)ctr;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < total; w += warps) {
+        const uint32_t c = w * 32 + lane;
+        const uint32_t slot = c < total ? touched[c] : 0u;
+        const uint32_t cnt = c < total ? cursor[slot] : 0u;
+        uint32_t x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t base = 0;
+        if (lane == 31) base = atomicAdd(ctr + 1, x);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (c < total) {
+            start[c] = base + x - cnt;
+            len[c] = cnt;
+            cursor[slot] = base + x - cnt;
+        }
+    }
+}
+
+// 3. every record to its cell's bucket: sample id, cluster and reward (a
+// warp's lanes that share a cell take consecutive places; the order inside a
+// bucket depends on scheduling and is restored by the per-cell ordering)
+// Bucket entry of a record: sample id, cluster, reward bits (three arrays)
+struct Bucket {
+    uint32_t* sid;
+    uint8_t* s;
+    uint32_t* val;
+};
+
+__global__ void __launch_bounds__(kBucketThreads)
+k_bucket_scatter(const uint32_t* __restrict__ rec_key, const float* __restrict__ rec_val, int64_t n, uint32_t HM,
+                 uint32_t M, uint32_t* __restrict__ cursor, Bucket bucket)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t tile0 = ((int64_t)blockIdx.x * (kBucketThreads / 32) + (threadIdx.x >> 5)) * kTilesPerWarp;
+    uint32_t slot[kTilesPerWarp], clus[kTilesPerWarp], val[kTilesPerWarp], peers[kTilesPerWarp],
+        base[kTilesPerWarp];
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        const int64_t i = (tile0 + u) * 32 + lane;
+        const uint32_t key = i < n ? __ldg(rec_key + i) : 0xFFFFFFFFu;
+        val[u] = i < n ? __float_as_uint(__ldg(rec_val + i)) : 0u;
+        slot[u] = key < HM ? key / M : 0xFFFFFFFFu;
+        clus[u] = key < HM ? key % M : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) peers[u] = __match_any_sync(0xffffffffu, slot[u]);
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        base[u] = 0u;
+        if (slot[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
+            base[u] = atomicAdd(cursor + slot[u], (uint32_t)__popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        const uint32_t b = __shfl_sync(0xffffffffu, base[u], __ffs(peers[u]) - 1);
+        if (slot[u] != 0xFFFFFFFFu) {
+            const uint32_t d = b + __popc(peers[u] & lanemask_lt());
+            bucket.sid[d] = (uint32_t)((tile0 + u) * 32 + lane);
+            bucket.s[d] = (uint8_t)clus[u];
+            bucket.val[d] = val[u];
+        }
+    }
+}
+
+// Shared arrays of one team (a warp or a block) ordering one cell's records:
+// A = bucket order, then (cluster, sample) order; B = grouped by cluster,
+// then the cdf scratch.
+template <uint32_t CAP>
+struct CellOrder {
+    uint32_t a_sid[CAP];
+    uint32_t a_val[CAP];
+    uint32_t b_sid[CAP];
+    uint32_t b_val[CAP];
+    uint8_t a_s[CAP];
+    uint8_t b_s[CAP];
+    uint32_t start[kMaxCut];  // first position of each cluster in B
+    uint32_t cur[kMaxCut];    // scatter cursors, then one past the last position
+    float q[kMaxCut];
+};
+
+// A team orders one cell; its first warp (lead()) also scans and composes.
+struct WarpTeam {
+    __device__ __forceinline__ uint32_t tid() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ uint32_t size() const { return 32; }
+    __device__ __forceinline__ bool lead() const { return true; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+struct BlockTeam {
+    __device__ __forceinline__ uint32_t tid() const { return threadIdx.x; }
+    __device__ __forceinline__ uint32_t size() const { return blockDim.x; }
+    __device__ __forceinline__ bool lead() const { return threadIdx.x < 32; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+template <int P>
+__device__ __forceinline__ void load_q_row(const typename Store<P>::T* qrow, uint32_t m, float* q)
+{
+    for (uint32_t s = threadIdx.x & 31; s < m; s += 32) q[s] = Store<P>::load(qrow[s]);
+}
+
+template <int P>
+__device__ __forceinline__ void store_q_row(typename Store<P>::T* qrow, uint32_t m, float* q)
+{
+    for (uint32_t s = threadIdx.x & 31; s < m; s += 32) {
+        const typename Store<P>::T st = Store<P>::store(q[s]);
+        qrow[s] = st;
+        q[s] = Store<P>::load(st);
+    }
+}
+
+// Eq. 1 + Eq. 2 of one cell from its bucket of nr <= CAP records: grouped
+// by cluster (counting sort, any order inside a group), then each record's
+// rank by sample id inside its group is counted, which puts them in
+// (cluster, sample) order; warp 0 of the team composes, stores Q and
+// rebuilds C. Called by every thread of the team.
+template <int P, uint32_t CAP, class Team>
+__device__ void learn_cell_grouped(Team team, CellOrder<CAP>& o, const uint32_t* __restrict__ bsid,
+                                   const uint8_t* __restrict__ bs, const uint32_t* __restrict__ bval, uint32_t nr,
+                                   uint32_t M, uint32_t m, float alpha, float eps, typename Store<P>::T* qrow,
+                                   typename Store<P>::T* crow, uint32_t* status)
+{
+    const uint32_t t = team.tid(), T = team.size();
+    const int lane = threadIdx.x & 31;
+    const bool w0 = team.lead();
+    for (uint32_t s = t; s < M; s += T) o.start[s] = 0u;
+    if (w0) load_q_row<P>(qrow, m, o.q);
+    team.sync();
+    for (uint32_t k = t; k < nr; k += T) {
+        const uint32_t s = bs[k];
+        o.a_sid[k] = bsid[k];
+        o.a_val[k] = bval[k];
+        o.a_s[k] = (uint8_t)s;
+        atomicAdd(&o.start[s], 1u);
+    }
+    team.sync();
+    if (w0) {  // cluster starts: exclusive scan over M bins, ipl consecutive bins a lane
+        const uint32_t ipl = (M + 31) >> 5, lo = lane * ipl, hi = min(M, lo + ipl);
+        uint32_t sum = 0;
+        for (uint32_t s = lo; s < hi; ++s) sum += o.start[s];
+        uint32_t y = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, y, d);
+            if (lane >= d) y += v;
+        }
+        uint32_t run = y - sum;
+        for (uint32_t s = lo; s < hi; ++s) {
+            const uint32_t c = o.start[s];
+            o.start[s] = run;
+            o.cur[s] = run;
+            run += c;
+        }
+    }
+    team.sync();
+    for (uint32_t k = t; k < nr; k += T) {
+        const uint32_t s = o.a_s[k];
+        const uint32_t d = atomicAdd(&o.cur[s], 1u);
+        if (d >= nr) {  // impossible unless the counts are corrupt: flag, skip the write
+            atomicOr(status, (uint32_t)RLL_E_DEVICE);
+            continue;
+        }
+        o.b_sid[d] = o.a_sid[k];
+        o.b_val[d] = o.a_val[k];
+        o.b_s[d] = (uint8_t)s;
+    }
+    team.sync();
+    for (uint32_t k = t; k < nr; k += T) {
+        const uint32_t s = o.b_s[k], sid = o.b_sid[k];
+        const uint32_t lo = o.start[s], hi = o.cur[s];
+        const uint32_t end = min(hi, nr);
+        uint32_t rank = 0, j = lo;
+        for (; j + 4 <= end; j += 4) {
+            const uint32_t x0 = o.b_sid[j], x1 = o.b_sid[j + 1], x2 = o.b_sid[j + 2], x3 = o.b_sid[j + 3];
+            rank += (x0 < sid) + (x1 < sid) + (x2 < sid) + (x3 < sid);
+        }
+        for (; j < end; ++j) rank += o.b_sid[j] < sid;
+        if (lo + rank >= nr) {
+            atomicOr(status, (uint32_t)RLL_E_DEVICE);
+            continue;
+        }
+        o.a_s[lo + rank] = (uint8_t)s;
+        o.a_val[lo + rank] = o.b_val[k];
+    }
+    team.sync();
+    if (T == 32) {
+        learn_records<P>([&](uint32_t j) { return make_uint2(o.a_s[j], o.a_val[j]); }, nr, m, alpha, o.q);
+    } else {  // a block: warp w composes the groups of clusters w, w + warps, ...
+        const uint32_t warps = T >> 5;
+        for (uint32_t s = threadIdx.x >> 5; s < M; s += warps) {
+            const uint32_t lo = o.start[s], hi = o.cur[s];
+            if (hi > lo)
+                learn_records<P>([&](uint32_t j) { return make_uint2(o.a_s[lo + j], o.a_val[lo + j]); }, hi - lo,
+                                 m, alpha, o.q);
+        }
+        team.sync();
+    }
+    if (w0) {
+        store_q_row<P>(qrow, m, o.q);
+        __syncwarp();
+        warp_rebuild_cdf<P>(o.q, (int)m, eps, crow, reinterpret_cast<float*>(o.b_sid),
+                            reinterpret_cast<uint16_t*>(o.b_val));
+    }
+}
+
+// 4. one warp per cell of a list (list == nullptr: every touched cell) with
+// at most CAP records; a larger cell is appended to the next list (`next`,
+// its count at *next_count) for the block path.
+template <int P, uint32_t CAP, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+k_learn_tier(const Bucket bucket, const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count,
+             uint32_t* __restrict__ next, uint32_t* __restrict__ next_count, const uint32_t* __restrict__ touched,
+             const uint32_t* __restrict__ start, const uint32_t* __restrict__ len, uint32_t* __restrict__ cursor,
+             uint32_t M, uint32_t m, typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C,
+             float alpha, float eps, uint32_t* __restrict__ status)
+{
+    __shared__ CellOrder<CAP> rows[WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t total = *(volatile const uint32_t*)list_count;
+    for (uint32_t i = blockIdx.x * WARPS + warp; i < total; i += gridDim.x * WARPS) {
+        const uint32_t w = list ? list[i] : i;
+        const uint32_t slot = touched[w], nr = len[w];
+        if (nr > CAP) {
+            if (lane == 0) next[atomicAdd(next_count, 1u)] = w;
+            continue;
+        }
+        const int64_t row = (int64_t)slot * M;
+        const uint32_t b0 = start[w];
+        learn_cell_grouped<P>(WarpTeam{}, rows[warp], bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, M, m,
+                              alpha, eps, Q + row, C + row, status);
+        if (lane == 0) cursor[slot] = 0u;
+    }
+}
+
+// 5. one block per remaining cell: the same ordering with the whole block
+// (up to kBlockBucket records), or, for larger cells, (cluster << 32 |
+// sample id) sorted in place in global scratch by a bitonic network
+template <int P>
+__global__ void __launch_bounds__(kBigThreads)
+k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const float* __restrict__ rec_val,
+            const uint32_t* __restrict__ ctr,
+            const uint32_t* __restrict__ touched, const uint32_t* __restrict__ start,
+            const uint32_t* __restrict__ len, const uint32_t* __restrict__ big, uint32_t* __restrict__ cursor,
+            uint32_t M, uint32_t m, typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C,
+            float alpha, float eps, uint32_t* __restrict__ status)
+{
+    __shared__ CellOrder<kBlockBucket> o;
+    const uint32_t n_big = *(volatile const uint32_t*)(ctr + 3);
+    for (uint32_t bi = blockIdx.x; bi < n_big; bi += gridDim.x) {
+        const uint32_t w = big[bi];
+        const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
+        const int64_t row = (int64_t)slot * M;
+        if (nr <= kBlockBucket) {
+            learn_cell_grouped<P>(BlockTeam{}, o, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, M, m, alpha,
+                                  eps, Q + row, C + row, status);
+        } else {
+            unsigned long long* rec = wide + b0;
+            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x)
+                rec[k] = ((unsigned long long)bucket.s[b0 + k] << 32) | bucket.sid[b0 + k];
+            __syncthreads();
+            bitonic_sort_u64(rec, nr, threadIdx.x, blockDim.x, BlockSync{});
+            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x) {
+                const unsigned long long e = rec[k];
+                rec[k] = (e & 0xFFFFFFFF00000000ull) | __float_as_uint(__ldg(rec_val + (uint32_t)e));
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                load_q_row<P>(Q + row, m, o.q);
+                __syncwarp();
+                learn_records<P>([&](uint32_t j) {
+                    const unsigned long long e = rec[j];
+                    return make_uint2((uint32_t)(e >> 32), (uint32_t)e);
+                }, nr, m, alpha, o.q);
+                store_q_row<P>(Q + row, m, o.q);
+                __syncwarp();
+                warp_rebuild_cdf<P>(o.q, (int)m, eps, C + row, reinterpret_cast<float*>(o.b_sid),
+                                    reinterpret_cast<uint16_t*>(o.b_val));
+            }
+        }
+        if (threadIdx.x == 0) cursor[slot] = 0u;
+        __syncthreads();
+    }
+}
+
 template <int P>
 int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n)
 {
     cudaStream_t s = ctx->stream;
-    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return check_cuda(ctx, e, "memset touched");
     if (n <= 0) return RLL_OK;
+    if (n > 0xFFFFFFFFll) return fail(ctx, RLL_E_INVALID, "more than 2^32 - 1 records");
+    if (g->cursor_dirty) {
+        e = cudaMemsetAsync(g->cursor, 0, 4 * (size_t)g->H, s);
+        if (e != cudaSuccess) return check_cuda(ctx, e, "memset cursors");
+        g->cursor_dirty = false;
+    }
     const uint32_t HM = g->H * g->M;
-    void* ws = ws_get(ctx, radix_sort_scratch_bytes(n));
+    // scratch per record: bucket sample id (4 B), reward (4 B), cluster (1 B),
+    // and the block path's in-place sort buffer (8 B, used only by cells
+    // above kBlockBucket records)
+    const size_t n4 = ((size_t)n * 4 + 255) & ~(size_t)255, n1 = ((size_t)n + 255) & ~(size_t)255;
+    char* ws = static_cast<char*>(ws_get(ctx, 2 * n4 + n1 + 8 * (size_t)n));
     if (!ws) return RLL_E_NOMEM;
-    uint32_t *sk, *sv;
-    e = radix_sort_pairs(s, rec_key, reinterpret_cast<const uint32_t*>(rec_val), n, key_bits((uint64_t)HM + 1), HM,
-                         ws, &sk, &sv);
-    if (e != cudaSuccess) return check_cuda(ctx, e, "radix sort (records)");
-    k_cell_heads<<<(unsigned)((n + 256 * kHeadItems - 1) / (256 * kHeadItems)), 256, 0, s>>>(
-        sk, n, HM, g->M, g->touched, g->touched_start, g->n_touched);
-    const int blocks = device_sm_count(g->device) * 8;
+    Bucket bucket{reinterpret_cast<uint32_t*>(ws), reinterpret_cast<uint8_t*>(ws + 2 * n4),
+                  reinterpret_cast<uint32_t*>(ws + n4)};
+    auto* wide = reinterpret_cast<unsigned long long*>(ws + 2 * n4 + n1);
+    const int64_t per_block = (int64_t)kBucketThreads * kTilesPerWarp;
+    const unsigned rblocks = (unsigned)((n + per_block - 1) / per_block);
+    const int sms = device_sm_count(g->device);
     using T = typename Store<P>::T;
-    k_learn_cells<P><<<blocks, kWarpsPerBlock * 32, 0, s>>>(sk, sv, n, HM, g->M, g->m, g->touched, g->touched_start,
-                                                             g->n_touched, (T*)g->Q, (T*)g->C, g->p.alpha, g->p.eps);
-    return check_cuda(ctx, cudaGetLastError(), "learn kernels");
+    g->cursor_dirty = true;
+    k_bucket_count<<<rblocks, kBucketThreads, 0, s>>>(rec_key, n, HM, g->M, g->cursor, g->touched, g->n_touched);
+    k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(g->touched, g->n_touched, g->cursor, g->touched_start,
+                                                     g->touched_len);
+    k_bucket_scatter<<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, HM, g->M, g->cursor, bucket);
+    k_learn_tier<P, kWarpBucket, 6, 5><<<sms * 5, 6 * 32, 0, s>>>(
+        bucket, nullptr, g->n_touched, g->big, g->n_touched + 3, g->touched, g->touched_start, g->touched_len,
+        g->cursor, g->M, g->m, (T*)g->Q, (T*)g->C, g->p.alpha, g->p.eps, ctx->d_status);
+    k_learn_big<P><<<sms * 4, kBigThreads, 0, s>>>(bucket, wide, rec_val, g->n_touched, g->touched, g->touched_start,
+                                                    g->touched_len, g->big, g->cursor, g->M, g->m, (T*)g->Q,
+                                                    (T*)g->C, g->p.alpha, g->p.eps, ctx->d_status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(ctx, e, "learn kernels");
+    g->cursor_dirty = false;
+    return RLL_OK;
 }
 
 template <int P>
@@ -384,7 +767,7 @@ template <int P>
 int learn_scratch_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n, void* scratch)
 {
     cudaStream_t s = ctx->stream;
-    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return check_cuda(ctx, e, "memset touched");
     if (n <= 0) return RLL_OK;
     const uint32_t HM = g->H * g->M;

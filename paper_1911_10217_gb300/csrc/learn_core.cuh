@@ -159,6 +159,85 @@ __device__ void learn_one_cell(const uint32_t* __restrict__ sk, const uint32_t* 
     warp_rebuild_cdf<P>(q, (int)m, eps, crow, c, bits);
 }
 
+// ---------------------------------------------------------------- per-cell sort
+// Ascending sort of a[0..n) by a bitonic network in which every comparator
+// puts the minimum at the lower index: per merge size k, first the mirror
+// step (i against i ^ (k - 1)), then half-cleaners (i against i + j). The
+// array is padded virtually to the next power of two with +infinity; a
+// comparator that reaches a padded position would leave it unchanged, so it
+// is skipped. `tid`/`nthreads` split the comparators; `sync` is the barrier
+// of the participating threads (__syncwarp or __syncthreads).
+__device__ __forceinline__ void cmp_swap(unsigned long long* a, uint32_t i, uint32_t p)
+{
+    const unsigned long long x = a[i], y = a[p];
+    if (y < x) {
+        a[i] = y;
+        a[p] = x;
+    }
+}
+
+template <class Sync>
+__device__ __forceinline__ void bitonic_sort_u64(unsigned long long* a, uint32_t n, uint32_t tid, uint32_t nthreads,
+                                                 Sync sync)
+{
+    if (n < 2) return;
+    uint32_t lg = 0;
+    while ((1u << lg) < n) ++lg;
+    const uint32_t half_len = 1u << (lg - 1);
+    for (uint32_t lk = 1; lk <= lg; ++lk) {
+        const uint32_t k = 1u << lk;
+        for (uint32_t t = tid; t < half_len; t += nthreads) {
+            const uint32_t i = ((t >> (lk - 1)) << lk) | (t & ((k >> 1) - 1));
+            const uint32_t p = i ^ (k - 1);
+            if (p < n) cmp_swap(a, i, p);
+        }
+        sync();
+        for (uint32_t lj = lk - 1; lj-- > 0;) {
+            const uint32_t j = 1u << lj;
+            for (uint32_t t = tid; t < half_len; t += nthreads) {
+                const uint32_t i = ((t >> lj) << (lj + 1)) | (t & (j - 1));
+                const uint32_t p = i + j;
+                if (p < n) cmp_swap(a, i, p);
+            }
+            sync();
+        }
+    }
+}
+
+// Eq. 1 for one cell whose records are given in (cluster, sample id) order:
+// get(j) = (cluster, reward bits) of record j < len. The records are
+// composed 32 at a time exactly as learn_one_cell does (segmented scan of the
+// affine maps, in sample order per cluster), so both give the same bits.
+// q: the warp's shared Q row. Does not store the row. All 32 lanes call it.
+template <int P, class Get>
+__device__ void learn_records(Get get, uint32_t len, uint32_t m, float alpha, float* q)
+{
+    const int lane = threadIdx.x & 31;
+    const float a1 = 1.0f - alpha;
+    for (uint32_t pos = 0; pos < len; pos += 32) {
+        const uint32_t j = pos + lane;
+        const bool valid = j < len;
+        const uint2 e = valid ? get(j) : make_uint2(0xFFFFFFFFu, 0u);
+        const uint32_t s = e.x;
+        float A = valid ? a1 : 1.0f;
+        float B = valid ? alpha * __uint_as_float(e.y) : 0.0f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float Ao = __shfl_up_sync(0xffffffffu, A, o);
+            const float Bo = __shfl_up_sync(0xffffffffu, B, o);
+            const uint32_t so = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o && so == s) {
+                B = A * Bo + B;
+                A = A * Ao;
+            }
+        }
+        const uint32_t s_next = __shfl_down_sync(0xffffffffu, s, 1);
+        const bool last = valid && (lane == 31 || s_next != s);
+        if (last && s < m) q[s] = A * q[s] + B;
+        __syncwarp();
+    }
+}
+
 // Split-collapse of one cell (cut row crow, Q row qrow, cdf row ccrow),
 // repeated until a step changes nothing or max_iter steps were taken. New Q
 // values in correctly rounded binary32, then rounded to the table precision:

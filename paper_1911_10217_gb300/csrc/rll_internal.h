@@ -56,8 +56,12 @@ struct rll_grid {
     void* def_Q = nullptr;               // [m]
     void* def_C = nullptr;               // [m]
     uint32_t* touched = nullptr;         // [H] cells touched by the last learn_update
-    uint32_t* touched_start = nullptr;   // [H] first sorted record of each touched cell
-    uint32_t* n_touched = nullptr;       // [1]
+    uint32_t* touched_start = nullptr;   // [H] first record of each touched cell (sorted / bucketed)
+    uint32_t* touched_len = nullptr;     // [H] records of each touched cell (bucketed learning)
+    uint32_t* n_touched = nullptr;       // [4]: touched cells, bucket space claimed, unused, block-path cells
+    uint32_t* cursor = nullptr;          // [H] per-slot record count / scatter cursor, all zero between calls
+    uint32_t* big = nullptr;             // [H] touched-cell indices whose records exceed a warp's buffer
+    bool cursor_dirty = false;           // a learning call stopped before the cursors were cleared
 };
 
 namespace rll {

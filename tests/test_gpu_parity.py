@@ -311,3 +311,50 @@ def test_long_run_stays_finite(env):
         assert np.isfinite(q).all() and np.isfinite(c).all()
         assert np.all(np.diff(c, axis=1) > 0) and np.all(c[:, 0] > 0)
         assert ctx.sync_status() == 0
+
+
+@pytest.mark.parametrize("maker,kw,spp", [
+    ("small_frame", dict(), 2),                       # buckets sorted by one warp
+    ("tiny", dict(cell_size=0.25), 4),                 # ~1K records per cell: one block, shared memory
+    ("tiny", dict(cell_size=0.5), 4),                  # ~4K records per cell: one block, in place
+    ("tiny", dict(cell_size=0.25, precision="fp16"), 4),
+    ("tiny", dict(cell_size=4.0), 8),                  # one cell of 32K records: one block, in place
+])
+def test_bucketed_learning_matches_sorted_path(env, maker, kw, spp):
+    """rll_learn_update groups records by cell with atomics and sorts each
+    cell's records in shared (or global) memory; the allocation-free entry
+    point sorts all records by key with a radix sort. Both must give the same
+    tables. The single-cell case is also checked against the oracle."""
+    O, rll, ctx = env["O"], env["rll"], env["ctx"]
+    lib = rll.load()
+    s = getattr(scenes, maker + "_scene")()
+    ot, dt, d = _trees(env, s)
+    A = rll.Grid(ctx, dt, params_for(rll, s, **kw))
+    B = rll.Grid(ctx, dt, params_for(rll, s, **kw))
+    prec = kw.get("precision", "fp32")
+    for frame in range(2):
+        out = run_sample(rll, ctx, A, dt, d, s.seed, frame, spp)
+        st = A.export()
+        B.import_state(st["keys"], st["cut"], st["q"], st["c"])
+        rll.learn_update(ctx, A, out["key"], out["val"])
+        rc = lib.rll_learn_update_noalloc(ctx.h, B.h, out["key"].data_ptr(), out["val"].data_ptr(),
+                                          out["key"].shape[0])
+        assert rc == 0, lib.rll_last_error(ctx.h).decode()
+        assert ctx.sync_status() == 0
+        a, b = A.export(), B.export()
+        assert np.array_equal(a["keys"], b["keys"]) and np.array_equal(a["cut"], b["cut"])
+        assert np.allclose(a["q"], b["q"], rtol=1e-6, atol=0), "Q differs between the two learning paths"
+        assert np.allclose(a["c"], b["c"], rtol=1e-6, atol=0), "C differs between the two learning paths"
+        rll.split_collapse(ctx, A, dt)
+        rll.split_collapse(ctx, B, dt)
+    if kw.get("cell_size") == 4.0:
+        og = O.Grid.for_scene(ot, s, cell_size=4.0)
+        A2 = rll.Grid(ctx, dt, params_for(rll, s, cell_size=4.0))
+        g = to_host(run_sample(rll, ctx, A2, dt, d, s.seed, 0, spp))
+        o = og.sample_frame(O.scene_arrays(s), s.seed, 0, spp)
+        compare_samples(g, o, A2.export()["keys"], og.keys, A2.M)
+        rll.learn_update(ctx, A2, env["torch"].from_numpy(g["key"]).to(env["dev"]),
+                         env["torch"].from_numpy(g["val"]).to(env["dev"]))
+        og.learn(o["slot"], o["s"], o["reward"])
+        compare_tables(A2.export(), oracle_state(og), og.m, RTOL[prec])
+        assert ctx.sync_status() == 0
