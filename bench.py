@@ -520,6 +520,100 @@ def run_split(args):
     return 0
 
 
+def run_sky(args):
+    """Sky-dome interior (the situation of the paper's "Arch interior" scene,
+    Section 4): a closed room lit through small windows and skylights by a
+    2048-triangle sky dome and a small bright distant quad; 1920 x 1080 floor
+    points (--sky-sun 1 adds a small bright distant quad for a directional
+    light). For each combination of the swept in-cluster modes, learning
+    rates, floors, cut sizes, split thresholds and reward modes: learns for
+    --sky-passes passes (each timed: sample + Eq. 1/2 + split-collapse), then
+    reports the MSE of the learned sampler and of the energy sampler at 1, 4
+    and 8 spp against a common reference (the energy sampler at
+    --sky-ref-spp spp), and the MSE of a fresh grid at 1 spp."""
+    import torch
+    from paper_1911_10217_gb300 import rll, scenes
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    ctx = rll.Context(0, stream)
+    s = scenes.sky_scene(sun=bool(args.sky_sun))
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    tri, em, boxes = T(s.tris.reshape(-1, 9)), T(s.emission), T(s.boxes)
+    pos, nrm, alb = T(s.pos), T(s.nrm), T(s.albedo)
+    tree = rll.Tree(ctx, tri, em)
+    P = s.n_points
+    rgb = torch.empty(3, P, device=dev)
+    key = torch.empty(P, dtype=torch.int32, device=dev)
+    val = torch.empty(P, device=dev)
+    ref = torch.zeros(3, P, device=dev, dtype=torch.float64)
+    batches = max(1, args.sky_ref_spp // 32)
+    for i in range(batches):
+        rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 4242, 200000 + i, 32, rgb)
+        ref += rgb.double()
+    ref /= batches
+
+    def mse_of(fn, spp, reps=4):
+        acc = 0.0
+        for r in range(reps):
+            fn(spp, 70000 + 17 * r)
+            acc += float(((rgb.double() - ref) ** 2).mean())
+        return acc / reps
+
+    def power_pass(spp, frame):
+        rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 31337, frame, spp, rgb)
+
+    energy = {f"{spp}spp": mse_of(power_pass, spp) for spp in (1, 4, 8)}
+    runs = []
+    combos = [(mode, float(a), float(e), int(m), float(t), rw) for mode in args.sky_modes.split(",")
+              for a in args.sky_alphas.split(",") for e in args.sky_eps.split(",")
+              for m in args.sky_cuts.split(",") for t in args.sky_thresholds.split(",")
+              for rw in args.sky_rewards.split(",")]
+    for mode, alpha, eps, cut, thr, reward in combos:
+        if True:
+            params = rll.grid_params_for(s.grid, mode=mode, alpha=alpha, eps=eps, cut_size=cut, threshold=thr,
+                                         reward=reward)
+            grid = rll.Grid(ctx, tree, params)
+            fresh = rll.Grid(ctx, tree, params)
+            ev = []
+            for f in range(args.sky_passes):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                e[0].record(stream)
+                rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, s.seed, f, 1, rgb, key, val)
+                rll.learn_update(ctx, grid, key, val)
+                rll.split_collapse(ctx, grid, tree)
+                e[1].record(stream)
+                ev.append(e)
+            torch.cuda.synchronize()
+            t_pass = [x.elapsed_time(y) for x, y in ev][3:]
+
+            def rll_pass(spp, frame, g=grid):
+                rll.sample_and_shade(ctx, g, tree, pos, nrm, alb, boxes, 31337, frame, spp, rgb)
+
+            mse = {}
+            for spp in (1, 4, 8):
+                m = mse_of(rll_pass, spp)
+                mse[f"{spp}spp"] = {"rll": m, "energy_sampler": energy[f"{spp}spp"],
+                                    "energy_over_rll": energy[f"{spp}spp"] / m}
+            mse["fresh_grid_1spp"] = mse_of(lambda k, fr: rll_pass(k, fr, fresh), 1, reps=2)
+            runs.append({"in_cluster": mode, "alpha": alpha, "eps": eps, "cut_size": cut, "threshold": thr,
+                         "reward": reward,
+                         "ms_per_pass": statistics.mean(t_pass),
+                         "samples_per_s": P / (statistics.mean(t_pass) * 1e-3), "mse": mse})
+            grid.close()
+            fresh.close()
+    line = {"metric": METRIC, "workload": "sky", "unit": UNIT, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "sky-dome interior, 1920x1080 floor points, 2048 dome triangles"
+                                   + (" + 2 sun triangles" if args.sky_sun else "") + ", "
+                                   f"{int(s.boxes.shape[0])} occluder boxes (walls with 16 windows, 2 skylights), "
+                                   "one learning pass per step", "points": P, "lights": s.n_lights,
+                       "boxes": int(s.boxes.shape[0]), "cut_size": s.grid.cut_size,
+                       "table_size": s.grid.table_size, "cell_size": s.grid.cell_size, "passes": args.sky_passes},
+            "runs": runs, "reference": f"energy sampler, {batches * 32} spp",
+            "device_status": ctx.sync_status()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -530,7 +624,17 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
-    ap.add_argument("--workload", default="frame", choices=["frame", "batched", "serving", "dynamic", "split"])
+    ap.add_argument("--workload", default="frame",
+                    choices=["frame", "batched", "serving", "dynamic", "split", "sky"])
+    ap.add_argument("--sky-passes", type=int, default=256)
+    ap.add_argument("--sky-modes", default="descent")
+    ap.add_argument("--sky-alphas", default="0.003,0.01,0.03")
+    ap.add_argument("--sky-ref-spp", type=int, default=4096)
+    ap.add_argument("--sky-sun", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--sky-eps", default="0.02")
+    ap.add_argument("--sky-cuts", default="32,128")
+    ap.add_argument("--sky-thresholds", default="2")
+    ap.add_argument("--sky-rewards", default="cluster")
     ap.add_argument("--split-iterations", type=int, default=1)
     ap.add_argument("--split-sweep", default="1,2,4,16,64")
     ap.add_argument("--split-passes", type=int, default=64)
@@ -552,6 +656,8 @@ def main():
         return run_serving(args)
     if args.workload == "dynamic":
         return run_dynamic(args)
+    if args.workload == "sky":
+        return run_sky(args)
     if args.workload == "split":
         return run_split(args)
     from paper_1911_10217_gb300 import scenes

@@ -332,3 +332,126 @@ def batched_scenes(seed: int = 4, n_scenes: int = 256, light_range=(1 << 10, 1 <
         s.name = f"batched{i}"
         out.append(s)
     return out
+
+
+def _wall_boxes(axis, side, openings, t=0.02):
+    """Boxes of one wall of the unit room with rectangular openings.
+
+    axis: 0 -> wall plane x = side (u = z), 2 -> z = side (u = x),
+    1 -> ceiling y = 1 (u = x, v = z). The wall lies outside the room
+    (thickness t). openings: list of (u0, u1, v0, v1) in the wall's (u, v)
+    coordinates (v = y for side walls), all in one band v0..v1 per row of
+    openings; rows are given as separate lists of openings sharing v0, v1."""
+    boxes = []
+
+    def put(u0, u1, v0, v1):
+        if u1 <= u0 or v1 <= v0:
+            return
+        if axis == 1:
+            boxes.append(_box((u0, 1.0, v0), (u1, 1.0 + t, v1)))
+        elif axis == 0:
+            x0 = side - t if side <= 0.0 else side
+            boxes.append(_box((x0, v0, u0), (x0 + t, v1, u1)))
+        else:
+            z0 = side - t if side <= 0.0 else side
+            boxes.append(_box((u0, v0, z0), (u1, v1, z0 + t)))
+
+    lo_u, hi_u = -t, 1.0 + t
+    v_prev = 0.0 if axis != 1 else -t
+    for row in openings:
+        v0, v1 = row[0][2], row[0][3]
+        put(lo_u, hi_u, v_prev, v0)             # solid band below the row
+        u_prev = lo_u
+        for (u0, u1, _, _) in sorted(row):
+            put(u_prev, u0, v0, v1)             # pier between openings
+            u_prev = u1
+        put(u_prev, hi_u, v0, v1)
+        v_prev = v1
+    put(lo_u, hi_u, v_prev, 1.0 if axis != 1 else 1.0 + t)  # solid band above
+    return boxes
+
+
+def _sky_dome(center, radius, rings, segments, max_elev_deg=88.0):
+    """Hemisphere of rings x segments quads (2 triangles each) from the horizon
+    up to max_elev_deg, wound so that every normal points to the centre."""
+    el = np.radians(np.linspace(0.0, max_elev_deg, rings + 1))
+    az = np.linspace(0.0, 2.0 * math.pi, segments + 1)
+    E, A = np.meshgrid(el, az, indexing="ij")
+    P = np.stack([np.cos(E) * np.cos(A), np.sin(E), np.cos(E) * np.sin(A)], axis=-1) * radius
+    P = P + np.asarray(center, np.float64)
+    a, b = P[:-1, :-1], P[1:, :-1]
+    c, d = P[1:, 1:], P[:-1, 1:]
+    # (b - a) x (d - a) points outward for increasing elevation / azimuth;
+    # the order (a, d, b) flips it inward
+    t1 = np.stack([a, d, b], axis=2)
+    t2 = np.stack([b, d, c], axis=2)
+    return np.stack([t1, t2], axis=2).reshape(-1, 3, 3)
+
+
+def sky_scene(seed: int = 5, width: int = 1920, height: int = 1080, rings: int = 32, segments: int = 32,
+              table_size: int = 1 << 15, cut_size: int = 32, cell_size: float = 1.0 / 64.0, spp: int = 1,
+              frames: int = 64, windows_per_wall: int = 4, sun: bool = False) -> Scene:
+    """Interior lit only through small openings (the situation of the paper's
+    "Arch interior" scene, Section 4, where a uniform sky is the only light):
+    a closed unit room whose four walls each have a row of windows_per_wall
+    small windows and whose ceiling has two skylights, a few blocks inside;
+    outside, a sky dome of 2 * rings * segments inward-facing triangles with
+    uniform radiance. With sun=True a small, very bright, distant quad (two
+    triangles) stands in for a directional light. Shading points: a
+    width x height grid over the floor (normal +y, albedo U[0.2, 0.9]).
+    Cells of cell_size, one normal bin."""
+    rng = np.random.default_rng(seed)
+    boxes = []
+    k = windows_per_wall
+    for axis, side in ((0, 0.0), (0, 1.0), (2, 0.0), (2, 1.0)):
+        sill = rng.uniform(0.35, 0.5)
+        row = []
+        for i in range(k):
+            cu = (i + 0.5) / k + rng.uniform(-0.05, 0.05) / k
+            w = rng.uniform(0.05, 0.09)
+            row.append((cu - w / 2, cu + w / 2, sill, sill + rng.uniform(0.1, 0.16)))
+        v0, v1 = min(r[2] for r in row), max(r[3] for r in row)
+        row = [(u0, u1, v0, v1) for (u0, u1, _, _) in row]
+        boxes += _wall_boxes(axis, side, [row])
+    sky_row = [(0.25, 0.37, 0.3, 0.42), (0.6, 0.72, 0.3, 0.42)]
+    boxes += _wall_boxes(1, 1.0, [sky_row])
+    for _ in range(6):  # blocks inside the room
+        sx, sy, sz = rng.uniform(0.06, 0.16), rng.uniform(0.15, 0.5), rng.uniform(0.06, 0.16)
+        x0, z0 = rng.uniform(0.1, 0.9 - sx), rng.uniform(0.1, 0.9 - sz)
+        boxes.append(_box((x0, 0.0, z0), (x0 + sx, sy, z0 + sz)))
+    center = np.array([0.5, 0.0, 0.5])
+    dome = _sky_dome(center, 20.0, rings, segments)
+    sky_le = np.array([0.5, 0.65, 1.0])
+    # "sun": a 0.6 x 0.6 quad at distance 18, elevation 50 deg, facing the room
+    el, az = math.radians(50.0), math.radians(30.0)
+    d = np.array([math.cos(el) * math.cos(az), math.sin(el), math.cos(el) * math.sin(az)])
+    u, v = _orthonormal(-d)
+    sun_tris = _quad_patch(center + 18.0 * d, u * 0.6, v * 0.6, 1, 1, rng)
+    sun_le = np.array([2000.0, 1800.0, 1500.0])
+    if not sun:
+        sun_tris = sun_tris[:0]
+    tris = np.concatenate([dome, sun_tris]).astype(np.float32)
+    emission = np.concatenate([np.tile(sky_le, (dome.shape[0], 1)),
+                               np.tile(sun_le, (sun_tris.shape[0], 1))]).astype(np.float32)
+    gx = (np.arange(width) + 0.5) / width
+    gz = (np.arange(height) + 0.5) / height
+    X, Z = np.meshgrid(gx, gz, indexing="xy")
+    P = width * height
+    pos = np.stack([X.ravel(), np.zeros(P), Z.ravel()]).astype(np.float32)
+    nrm = np.stack([np.zeros(P), np.ones(P), np.zeros(P)]).astype(np.float32)
+    albedo = rng.uniform(0.2, 0.9, size=P).astype(np.float32)
+    grid = GridConfig(table_size=table_size, cut_size=cut_size, origin=(0.0, 0.0, 0.0),
+                      cell_size=cell_size, normal_bins=1, jitter=True)
+    return Scene("sky", tris, emission, np.asarray(boxes, np.float32), pos, nrm, albedo, grid, spp=spp,
+                 frames=frames, seed=seed, width=width, height=height)
+
+
+def tiny_sky_scene(seed: int = 6, jitter: bool = False, sun: bool = True) -> Scene:
+    """The sky scene small enough for the oracle: 64 x 64 floor points, a
+    dome of 8 x 8 quads (128 triangles) plus (by default) the 2-triangle sun,
+    cells of 1/8, cut size 16, 4 samples per point, 8 learning passes."""
+    s = sky_scene(seed=seed, width=64, height=64, rings=8, segments=8, table_size=1024, cut_size=16,
+                  cell_size=0.125, spp=4, frames=8, sun=sun)
+    s.name = "tiny_sky"
+    s.grid.jitter = jitter
+    return s

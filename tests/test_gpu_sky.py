@@ -1,0 +1,89 @@
+"""Sky-dome scene on the GPU (marked gpu): a room lit only through small
+windows and skylights by a triangulated sky dome and a small distant bright
+quad (the situation of the paper's "Arch interior" scene, Section 4).
+Lockstep parity with the oracle (every pass starts from the oracle's state)
+and unbiasedness against brute-force direct lighting."""
+import numpy as np
+import pytest
+
+from paper_1911_10217_gb300 import scenes
+
+from .gpu_common import (RTOL, clone_oracle_grid, compare_samples, compare_tables, device_scene,
+                         oracle_state, params_for, run_sample, to_host)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import oracle as O
+    from paper_1911_10217_gb300 import rll
+    dev = torch.device("cuda:0")
+    ctx = rll.Context(0, torch.cuda.current_stream(dev))
+    return dict(torch=torch, O=O, rll=rll, dev=dev, ctx=ctx)
+
+
+@pytest.mark.parametrize("variant", [dict(), dict(jitter=True, precision="bf16")])
+def test_sky_lockstep(env, variant):
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    ctx.sync_status()
+    s = scenes.tiny_sky_scene(jitter=variant.get("jitter", False))
+    d = device_scene(s, env["dev"])
+    ot = O.Tree(s.tris, s.emission)
+    dt = rll.Tree(ctx, d["tri"], d["em"])
+    ex = dt.export()
+    assert np.array_equal(ex["rec"].view(np.uint32), ot.rec.view(np.uint32)), "tree differs"
+    okw = {k: v for k, v in variant.items() if k == "precision"}
+    og = O.Grid.for_scene(ot, s, **okw)
+    dg = rll.Grid(ctx, dt, params_for(rll, s, **okw))
+    rtol = RTOL[variant.get("precision", "fp32")]
+    A = O.scene_arrays(s)
+    for f in range(4):
+        dg.import_state(og.keys, og.cut, og.Q, og.C)
+        g = to_host(run_sample(rll, ctx, dg, dt, d, s.seed, f, s.spp))
+        o = og.sample_frame(A, s.seed, f, s.spp)
+        mism = compare_samples(g, o, dg.export()["keys"], og.keys, dg.M)
+        rll.learn_update(ctx, dg, torch.from_numpy(g["key"]).to(env["dev"]),
+                         torch.from_numpy(g["val"]).to(env["dev"]))
+        touched = og.learn(o["slot"], o["s"], o["reward"])
+        if mism == 0:
+            compare_tables(dg.export(), oracle_state(og), og.m, rtol)
+        dg.import_state(og.keys, og.cut, og.Q, og.C)
+        rll.split_collapse(ctx, dg, dt)
+        o2 = clone_oracle_grid(O, og)
+        o2.split_collapse(og.keys != np.uint64(0xFFFFFFFFFFFFFFFF))
+        compare_tables(dg.export(), oracle_state(o2), og.m, max(rtol, 1e-5))
+        og.split_collapse(touched)
+    assert ctx.sync_status() == 0
+
+
+def test_sky_unbiased(env):
+    """After learning, the mean of 2^20 device samples at a floor point equals
+    the oracle's brute-force direct lighting within 5 standard errors."""
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    ctx.sync_status()
+    s = scenes.tiny_sky_scene()
+    d = device_scene(s, env["dev"])
+    dt = rll.Tree(ctx, d["tri"], d["em"])
+    dg = rll.Grid(ctx, dt, params_for(rll, s))
+    for f in range(6):
+        g = run_sample(rll, ctx, dg, dt, d, s.seed, f, s.spp)
+        rll.learn_update(ctx, dg, g["key"], g["val"])
+        rll.split_collapse(ctx, dg, dt)
+    R = 1 << 20
+    for idx in (64 * 10 + 10, 64 * 50 + 20):
+        pos = d["pos"][:, idx:idx + 1].repeat(1, R).contiguous()
+        nrm = d["nrm"][:, idx:idx + 1].repeat(1, R).contiguous()
+        alb = d["alb"][idx:idx + 1].repeat(R).contiguous()
+        rgb = torch.empty(3, R, device=env["dev"])
+        rll.sample_and_shade(ctx, dg, dt, pos, nrm, alb, d["boxes"], 123, 500, 1, rgb)
+        v = rgb.double().cpu().numpy()
+        ref = O.direct_bruteforce(s.pos[:, idx], s.nrm[:, idx], s.albedo[idx], s.tris, s.emission, s.boxes,
+                                  level=7)
+        for k in range(3):
+            m, se = v[k].mean(), v[k].std() / np.sqrt(R)
+            assert abs(m - ref[k]) <= 5 * se + 2e-3 * ref[k], (idx, k, m, ref[k], se)
+    assert ctx.sync_status() == 0

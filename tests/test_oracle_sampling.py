@@ -201,3 +201,21 @@ def test_learning_reduces_error(oracle_mod):
     mse_power = float(np.mean((rgb_p - ref) ** 2))
     assert mse_learned < 0.5 * mse0, (mse_learned, mse0)
     assert mse_learned < 0.5 * mse_power, (mse_learned, mse_power)
+
+
+def test_estimator_unbiased_sky_dome(oracle_mod):
+    """The sky-dome interior (far, large, inward-facing dome triangles and a
+    small bright distant quad, light entering only through small openings):
+    the learned estimator's mean equals brute-force direct lighting."""
+    s = scenes.tiny_sky_scene()
+    tree = oracle_mod.Tree(s.tris, s.emission)
+    g = _learned_grid(oracle_mod, s, tree, iters=4)
+    R = 100_000
+    for idx in (64 * 10 + 10, 64 * 50 + 20):
+        pos, nrm, alb = _repeat_point(s, idx, R)
+        out = g.sample_frame(_arrays(s, pos, nrm, alb), 13, 1000, 1)
+        ref = oracle_mod.direct_bruteforce(s.pos[:, idx], s.nrm[:, idx], s.albedo[idx],
+                                           s.tris, s.emission, s.boxes, level=7)
+        for k in range(3):
+            m, se = _mean_and_se(out["rgb"][k])
+            assert abs(m - ref[k]) < 5 * se + 3e-3 * ref[k] + 1e-9, (idx, k, m, ref[k], se)
