@@ -51,7 +51,7 @@ class _Grid(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("T", ctypes.c_double), ("eps", ctypes.c_double),
                 ("keys", ctypes.c_void_p), ("cut", ctypes.c_void_p), ("Q", ctypes.c_void_p),
                 ("C", ctypes.c_void_p), ("def_cut", ctypes.c_void_p), ("def_Q", ctypes.c_void_p),
-                ("def_C", ctypes.c_void_p)]
+                ("def_C", ctypes.c_void_p), ("levels", ctypes.c_uint32), ("Hl", ctypes.c_uint32)]
 
 
 def lib():
@@ -75,9 +75,13 @@ def lib():
             L.orc_lookup_insert.restype = ctypes.c_int64
             L.orc_importance32.argtypes = [P, P, P, P, P]
             L.orc_sample_frame.argtypes = [ctypes.POINTER(_Tree), P, P, ctypes.c_int, P,
-                                           ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P,
+                                           ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P, P,
                                            ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                            P, P, P, P, P, P, P, P, P, ctypes.c_int64, ctypes.c_int64]
+            L.orc_footprint_level.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_uint32]
+            L.orc_footprint_level.restype = ctypes.c_uint32
+            L.orc_cell_key_level.argtypes = [ctypes.POINTER(_Grid), ctypes.c_uint32, P, P, P]
+            L.orc_cell_key_level.restype = ctypes.c_uint64
             L.orc_learn.argtypes = [ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P, P]
             L.orc_split_collapse_cell.argtypes = [ctypes.POINTER(_Tree), ctypes.c_int, P, P,
                                                   ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -160,6 +164,12 @@ class Tree:
         return float(num.value) / float(den.value)
 
 
+def footprint_level(footprint, cell_size, levels):
+    """Resolution level of a point with this footprint (binary32)."""
+    return int(lib().orc_footprint_level(float(np.float32(footprint)), float(np.float32(cell_size)),
+                                         int(levels)))
+
+
 def cdf(q, eps=0.01, precision="fp32"):
     q = np.ascontiguousarray(q, np.float64)
     out = np.zeros_like(q)
@@ -169,14 +179,19 @@ def cdf(q, eps=0.01, precision="fp32"):
 
 class Grid:
     """The oracle's hash grid: H slots of (key, cut[M], Q[M], C[M]); Q and C
-    hold table-precision values in double."""
+    hold table-precision values in double. With levels > 1 the grid is
+    multi-resolution: levels tables of table_size slots (H = levels *
+    table_size), level l of cell size cell_size * 2^l, chosen per point from
+    its footprint (sample_frame's footprint argument)."""
 
     def __init__(self, tree: Tree, table_size, cut_size, origin=(0, 0, 0), cell_size=1.0,
                  normal_bins=1, jitter=False, mode="descent", reward="cluster", precision="fp32",
-                 alpha=0.03, T=2.0, eps=0.02, q_init=1e-3, split_iterations=1):
+                 alpha=0.03, T=2.0, eps=0.02, q_init=1e-3, split_iterations=1, levels=1):
         self.tree = tree
-        H, M = int(table_size), int(cut_size)
-        assert H & (H - 1) == 0
+        Hl, M = int(table_size), int(cut_size)
+        assert Hl & (Hl - 1) == 0
+        levels = max(1, int(levels))
+        H = Hl * levels
         self.def_cut = tree.initial_cut(M)
         m = len(self.def_cut)
         self.def_Q = np.array([round_storage(q_init, precision)] * m, np.float64)
@@ -191,11 +206,13 @@ class Grid:
                            normal_bins=int(normal_bins), jitter=bool(jitter), mode=mode,
                            reward=reward, precision=precision, alpha=float(alpha), T=float(T),
                            eps=float(eps), q_init=float(q_init),
-                           split_iterations=int(split_iterations))
+                           split_iterations=int(split_iterations), levels=levels)
+        self.levels, self.Hl = levels, Hl
         self._s = _Grid(H, M, m, (ctypes.c_float * 3)(*origin), float(cell_size), int(normal_bins),
                         int(bool(jitter)), MODE[mode], REWARD[reward], PREC[precision],
                         float(alpha), float(T), float(eps), _p(self.keys), _p(self.cut),
-                        _p(self.Q), _p(self.C), _p(self.def_cut), _p(self.def_Q), _p(self.def_C))
+                        _p(self.Q), _p(self.C), _p(self.def_cut), _p(self.def_Q), _p(self.def_C),
+                        levels, Hl)
 
     @classmethod
     def for_scene(cls, tree, scene, **kw):
@@ -203,7 +220,7 @@ class Grid:
         args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin,
                     cell_size=g.cell_size, normal_bins=g.normal_bins, jitter=g.jitter,
                     q_init=g.q_init, alpha=g.alpha, eps=g.eps, T=g.threshold,
-                    split_iterations=g.split_iterations)
+                    split_iterations=g.split_iterations, levels=g.levels)
         args.update(kw)
         return cls(tree, **args)
 
@@ -217,10 +234,15 @@ class Grid:
         return lib().orc_cell_key(ctypes.byref(self._s), _p(_f32(x)), _p(_f32(nrm)),
                                   _p(_f32(jit)))
 
+    def cell_key_level(self, level, x, nrm, jit=(0, 0, 0, 0, 0)):
+        return lib().orc_cell_key_level(ctypes.byref(self._s), int(level), _p(_f32(x)), _p(_f32(nrm)),
+                                        _p(_f32(jit)))
+
     def lookup_insert(self, key):
         return lib().orc_lookup_insert(ctypes.byref(self._s), int(key))
 
-    def sample_frame(self, scene_arrays, seed, frame, spp, first=0, count=-1, emission=None):
+    def sample_frame(self, scene_arrays, seed, frame, spp, first=0, count=-1, emission=None,
+                     footprint=None):
         tris, emis, boxes, pos, nrm, albedo = scene_arrays
         if emission is not None:
             emis = emission
@@ -234,6 +256,7 @@ class Grid:
         lib().orc_sample_frame(ctypes.byref(self.tree._s), _p(_f32(tris)), _p(_f32(emis)),
                                int(boxes.shape[0]), _p(_f32(boxes)), ctypes.byref(self._s),
                                npts, _p(_f32(pos)), _p(_f32(nrm)), _p(_f32(albedo)),
+                               None if footprint is None else _p(_f32(footprint)),
                                int(seed), int(frame), int(spp), _p(out["rgb"]),
                                _p(out["light"]), _p(out["slot"]), _p(out["s"]),
                                _p(out["reward"]), _p(out["p_cut"]), _p(out["p_in"]),

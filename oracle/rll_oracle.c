@@ -503,6 +503,13 @@ int orc_initial_cut(const orc_tree* t, int M, int32_t* cut)
 /* lookup; 16-bit position fields biased by 2^15, 8-bit normal fields.       */
 /* All quantisation arithmetic is binary32.                                  */
 /* ------------------------------------------------------------------------ */
+/* Multi-resolution reading of the footprint-sized cells (Section 3: cells  */
+/* sized from the ray footprint of each path vertex, coarser on later        */
+/* bounces): `levels` tables of Hl slots each (H = levels * Hl); level l has  */
+/* cell size h * 2^l and its own slot range [l * Hl, (l + 1) * Hl). A point   */
+/* with footprint f uses the smallest level whose cell is at least f wide:   */
+/* l = ceil(log2(f / h)) clamped to [0, levels - 1], from the binary32       */
+/* quotient; points without a footprint use level 0.                        */
 typedef struct {
     uint32_t H, M, m;
     float origin[3];
@@ -516,7 +523,22 @@ typedef struct {
     const int32_t* def_cut;  /* [m] */
     const double* def_Q;     /* [m] */
     const double* def_C;     /* [m] */
+    uint32_t levels;  /* resolution levels (1: a single grid of cell size h) */
+    uint32_t Hl;      /* slots per level (H / levels) */
 } orc_grid;
+
+/* level of a point with footprint f (see orc_grid) */
+uint32_t orc_footprint_level(float f, float h, uint32_t levels)
+{
+    float r = f / h;
+    if (!(r > 1.0f)) return 0;
+    uint32_t b;
+    memcpy(&b, &r, sizeof b);
+    uint32_t e = ((b >> 23) & 0xFFu) - 127u;       /* r > 1: biased exponent >= 127 */
+    uint32_t l = e + ((b & 0x7FFFFFu) != 0u);      /* ceil(log2 r) */
+    uint32_t top = levels > 0 ? levels - 1 : 0;
+    return l < top ? l : top;
+}
 
 static int32_t orc_qpos(float p, float o, float h, int jit, float u)
 {
@@ -538,12 +560,14 @@ static uint32_t orc_qnrm(float a, uint32_t nb, int jit, float u)
     return (uint32_t)f;
 }
 
-uint64_t orc_cell_key(const orc_grid* g, const float p[3], const float nrm[3], const float jit[5])
+/* key of the cell of cell size h_cell (h * 2^level) */
+static uint64_t orc_cell_key_h(const orc_grid* g, float h_cell, const float p[3], const float nrm[3],
+                               const float jit[5])
 {
     int j = g->jitter != 0;
-    uint32_t fx = (uint32_t)orc_qpos(p[0], g->origin[0], g->h, j, j ? jit[0] : 0.0f);
-    uint32_t fy = (uint32_t)orc_qpos(p[1], g->origin[1], g->h, j, j ? jit[1] : 0.0f);
-    uint32_t fz = (uint32_t)orc_qpos(p[2], g->origin[2], g->h, j, j ? jit[2] : 0.0f);
+    uint32_t fx = (uint32_t)orc_qpos(p[0], g->origin[0], h_cell, j, j ? jit[0] : 0.0f);
+    uint32_t fy = (uint32_t)orc_qpos(p[1], g->origin[1], h_cell, j, j ? jit[1] : 0.0f);
+    uint32_t fz = (uint32_t)orc_qpos(p[2], g->origin[2], h_cell, j, j ? jit[2] : 0.0f);
     float ax = fabsf(nrm[0]), ay = fabsf(nrm[1]), az = fabsf(nrm[2]);
     float s = (ax + ay) + az;
     float a = 0.0f, b = 0.0f;
@@ -564,6 +588,18 @@ uint64_t orc_cell_key(const orc_grid* g, const float p[3], const float nrm[3], c
            ((uint64_t)iv << 56);
 }
 
+uint64_t orc_cell_key(const orc_grid* g, const float p[3], const float nrm[3], const float jit[5])
+{
+    return orc_cell_key_h(g, g->h, p, nrm, jit);
+}
+
+/* key at a level: cell size h * 2^level (exact in binary32) */
+uint64_t orc_cell_key_level(const orc_grid* g, uint32_t level, const float p[3], const float nrm[3],
+                            const float jit[5])
+{
+    return orc_cell_key_h(g, ldexpf(g->h, (int)level), p, nrm, jit);
+}
+
 /* MurmurHash3 64-bit finaliser (Appleby), slot = hash mod H */
 uint64_t orc_fmix64(uint64_t k)
 {
@@ -578,11 +614,12 @@ uint64_t orc_fmix64(uint64_t k)
 /* Lookup with lazy creation (Section 3: the initial cut is copied into a cell
  * the first time it is used): linear probing from fmix64(key) mod H for at most
  * 64 slots. Returns the slot, or -1 when the probe limit is reached. */
-int64_t orc_lookup_insert(orc_grid* g, uint64_t key)
+static int64_t orc_lookup_insert_level(orc_grid* g, uint32_t level, uint64_t key)
 {
     uint64_t h = orc_fmix64(key);
+    uint32_t hl = g->Hl ? g->Hl : g->H;
     for (uint32_t i = 0; i < ORC_MAX_PROBES; ++i) {
-        uint64_t slot = (h + i) & (uint64_t)(g->H - 1);
+        uint64_t slot = (uint64_t)level * hl + ((h + i) & (uint64_t)(hl - 1));
         if (g->keys[slot] == key) return (int64_t)slot;
         if (g->keys[slot] == ORC_EMPTY) {
             g->keys[slot] = key;
@@ -596,6 +633,8 @@ int64_t orc_lookup_insert(orc_grid* g, uint64_t key)
     }
     return -1;
 }
+
+int64_t orc_lookup_insert(orc_grid* g, uint64_t key) { return orc_lookup_insert_level(g, 0, key); }
 
 /* ------------------------------------------------------------------------ */
 /* Node importance for the stochastic descent below a cut node (binary32).   */
@@ -812,15 +851,15 @@ static void orc_shade(const orc_scene* sc, int64_t l, const float x[3], const fl
 }
 
 static void orc_one_sample(const orc_scene* sc, orc_grid* g, const float x[3], const float n[3],
-                           float albedo, uint64_t seed, uint32_t sample_id, uint32_t frame,
-                           orc_sample_out* o)
+                           float albedo, uint32_t level, uint64_t seed, uint32_t sample_id,
+                           uint32_t frame, orc_sample_out* o)
 {
     orc_stream rs;
     orc_stream_init(&rs, seed, sample_id, frame);
     float jit[5];
     for (int k = 0; k < 5; ++k) jit[k] = orc_draw(&rs, ORC_DRAW_JIT + (uint32_t)k);
-    uint64_t key = orc_cell_key(g, x, n, jit);
-    int64_t slot = orc_lookup_insert(g, key);
+    uint64_t key = orc_cell_key_level(g, level, x, n, jit);
+    int64_t slot = orc_lookup_insert_level(g, level, key);
     const int32_t* cut = slot >= 0 ? g->cut + (size_t)slot * g->M : g->def_cut;
     const double* C = slot >= 0 ? g->C + (size_t)slot * g->M : g->def_C;
     uint32_t m = g->m;
@@ -846,22 +885,23 @@ static void orc_one_sample(const orc_scene* sc, orc_grid* g, const float x[3], c
  * the end of the pass, Section 3). Outputs per sample and the per-point mean. */
 int orc_sample_frame(const orc_tree* tree, const float* tri, const float* emis, int nbox,
                      const float* boxes, orc_grid* g, int64_t npts, const float* pos,
-                     const float* nrm, const float* albedo, uint64_t seed, uint32_t frame, int spp,
-                     double* rgb, int64_t* out_light, int64_t* out_slot, int32_t* out_s,
-                     double* out_reward, double* out_pcut, double* out_pin, double* out_margin,
-                     int32_t* out_visible, int64_t first, int64_t count)
+                     const float* nrm, const float* albedo, const float* footprint, uint64_t seed,
+                     uint32_t frame, int spp, double* rgb, int64_t* out_light, int64_t* out_slot,
+                     int32_t* out_s, double* out_reward, double* out_pcut, double* out_pin,
+                     double* out_margin, int32_t* out_visible, int64_t first, int64_t count)
 {
     orc_scene sc = {tree, tri, emis, nbox, boxes};
     if (count < 0) count = npts - first;
     for (int64_t i = first; i < first + count; ++i) {
         float x[3] = {pos[i], pos[npts + i], pos[2 * npts + i]};
         float n[3] = {nrm[i], nrm[npts + i], nrm[2 * npts + i]};
+        uint32_t level = footprint ? orc_footprint_level(footprint[i], g->h, g->levels) : 0;
         double acc[3] = {0, 0, 0};
         for (int j = 0; j < spp; ++j) {
             uint32_t sid = (uint32_t)(i * spp + j);
             orc_sample_out o;
             memset(&o, 0, sizeof(o));
-            orc_one_sample(&sc, g, x, n, albedo[i], seed, sid, frame, &o);
+            orc_one_sample(&sc, g, x, n, albedo[i], level, seed, sid, frame, &o);
             for (int k = 0; k < 3; ++k) acc[k] += o.est[k];
             int64_t r = (i - first) * spp + j;
             if (out_light) out_light[r] = o.light;

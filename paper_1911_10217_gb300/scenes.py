@@ -39,6 +39,7 @@ class GridConfig:
     eps: float = 0.02        # Eq. 2 floor
     threshold: float = 2.0   # split-collapse T
     split_iterations: int = 1  # split-collapse steps per cell and pass (1: the basic algorithm)
+    levels: int = 1          # resolution levels (cell size * 2^l); > 1 with per-point footprints
 
 
 @dataclasses.dataclass
