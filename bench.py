@@ -614,6 +614,90 @@ def run_sky(args):
     return 0
 
 
+def run_paths(args):
+    """Path vertices with footprint-sized cells (Section 3: cells sized from
+    the ray footprint of each path vertex, coarser on later bounces): the
+    frame workload's 1920 x 1080 primary points (finest level) and one diffuse
+    bounce vertex each, footprint (N_t p_A)^(-1/2) for each N_t of
+    --paths-tiles. For each N_t a grid of --paths-levels levels, and once a
+    single-level grid, learn for --paths-passes passes; the pass time, the
+    cells per level and the 1-spp MSE at the primary and at the bounce
+    vertices after each of --paths-checkpoints passes are reported, beside
+    the energy sampler, against the energy sampler at --paths-ref-spp spp."""
+    import torch
+    from paper_1911_10217_gb300 import rll, scenes
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    ctx = rll.Context(0, stream)
+    base = scenes.frame_scene()
+    s = scenes.path_scene(base, levels=args.paths_levels, paths_per_tile=1.0)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    tri, em, boxes = T(s.tris.reshape(-1, 9)), T(s.emission), T(s.boxes)
+    pos, nrm, alb, fp1 = T(s.pos), T(s.nrm), T(s.albedo), T(s.footprint)
+    tree = rll.Tree(ctx, tri, em)
+    P, P0 = s.n_points, base.n_points
+    rgb = torch.empty(3, P, device=dev)
+    key = torch.empty(P, dtype=torch.int32, device=dev)
+    val = torch.empty(P, device=dev)
+    ref = torch.zeros(3, P, device=dev, dtype=torch.float64)
+    batches = max(1, args.paths_ref_spp // 32)
+    for i in range(batches):
+        rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 4242, 300000 + i, 32, rgb)
+        ref += rgb.double()
+    ref /= batches
+
+    def mse_split(fn, reps=2):
+        a = b = 0.0
+        for r in range(reps):
+            fn(80000 + 13 * r)
+            e = (rgb.double() - ref) ** 2
+            a += float(e[:, :P0].mean())
+            b += float(e[:, P0:].mean())
+        return {"primary": a / reps, "bounce": b / reps}
+
+    out = {"energy_sampler_mse_1spp": mse_split(
+        lambda fr: rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 31337, fr, 1, rgb))}
+    checkpoints = sorted(int(c) for c in args.paths_checkpoints.split(","))
+    configs = [("single_level", 1, 1 << 20, None, None)]
+    for nt in (float(x) for x in args.paths_tiles.split(",")):
+        fp = fp1.clone()
+        fp[P0:] /= float(np.sqrt(nt))
+        configs.append((f"levels{args.paths_levels}_Nt{nt:g}", args.paths_levels, args.paths_table, fp, nt))
+    for name, levels, table, fp, nt in configs:
+        grid = rll.Grid(ctx, tree, rll.grid_params_for(s.grid, levels=levels, table_size=table))
+        ev, curve = [], {}
+        for f in range(checkpoints[-1]):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, s.seed, f, 1, rgb, key, val, footprint=fp)
+            rll.learn_update(ctx, grid, key, val)
+            rll.split_collapse(ctx, grid, tree)
+            e[1].record(stream)
+            ev.append(e)
+            if f + 1 in checkpoints:
+                curve[f + 1] = mse_split(lambda fr, g=grid, fa=fp: rll.sample_and_shade(
+                    ctx, g, tree, pos, nrm, alb, boxes, 31337, fr, 1, rgb, footprint=fa))
+        torch.cuda.synchronize()
+        t = [x.elapsed_time(y) for x, y in ev[3:]]
+        st = grid.export()
+        occ = st["keys"] != np.uint64(0xFFFFFFFFFFFFFFFF)
+        cells = np.bincount(np.nonzero(occ)[0] // table, minlength=levels).tolist()
+        last = curve[checkpoints[-1]]
+        out[name] = {"levels": levels, "paths_per_tile": nt, "table_size_per_level": table,
+                     "ms_per_pass": statistics.median(t), "samples_per_s": P / (statistics.median(t) * 1e-3),
+                     "cells_per_level": cells, "mse_1spp_after_passes": curve,
+                     "energy_over_rll_at_end": {k: out["energy_sampler_mse_1spp"][k] / last[k] for k in last}}
+        grid.close()
+    line = {"metric": METRIC, "workload": "paths", "unit": UNIT, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "frame-scale scene, 1920x1080 primary points + one diffuse bounce vertex each, "
+                                   "footprint-sized cells", "points": P, "primary_points": P0,
+                       "lights": s.n_lights, "boxes": int(s.boxes.shape[0]), "cut_size": s.grid.cut_size,
+                       "cell_size": s.grid.cell_size, "passes": checkpoints[-1]},
+            "results": out, "reference": f"energy sampler, {batches * 32} spp", "device_status": ctx.sync_status()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -625,7 +709,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
     ap.add_argument("--workload", default="frame",
-                    choices=["frame", "batched", "serving", "dynamic", "split", "sky"])
+                    choices=["frame", "batched", "serving", "dynamic", "split", "sky", "paths"])
+    ap.add_argument("--paths-checkpoints", default="1,4,16,64,128")
+    ap.add_argument("--paths-tiles", default="100,1000")
+    ap.add_argument("--paths-levels", type=int, default=8)
+    ap.add_argument("--paths-table", type=int, default=1 << 19)
+    ap.add_argument("--paths-ref-spp", type=int, default=1024)
     ap.add_argument("--sky-passes", type=int, default=256)
     ap.add_argument("--sky-modes", default="descent")
     ap.add_argument("--sky-alphas", default="0.003,0.01,0.03")
@@ -658,6 +747,8 @@ def main():
         return run_dynamic(args)
     if args.workload == "sky":
         return run_sky(args)
+    if args.workload == "paths":
+        return run_paths(args)
     if args.workload == "split":
         return run_split(args)
     from paper_1911_10217_gb300 import scenes

@@ -72,6 +72,16 @@ typedef struct rll_grid_params {
     uint32_t split_iterations; /* split-collapse steps per cell and call, 1 .. 256 (0 reads as 1):
                                   1 is the basic algorithm; more repeat it until a step
                                   changes nothing (Section 3) */
+    uint32_t levels;           /* resolution levels, 1 .. 16 (0 reads as 1). Section 3 sizes the
+                                  cells of a path vertex from its ray footprint (coarser for later
+                                  bounces); here level l has cell size cell_size * 2^l and a table of
+                                  its own of table_size slots (levels * table_size in all, at most
+                                  2^27, and that times cut_size at most 2^31). A point with footprint
+                                  f (rll_sample_and_shade_fp) uses the smallest level whose cell is
+                                  at least f wide: l = ceil(log2(f / cell_size)) from the binary32
+                                  quotient, clamped to [0, levels - 1]; f <= cell_size, NaN or no
+                                  footprint give level 0. Slots of level l are l * table_size ..
+                                  (l + 1) * table_size - 1 in record keys and exports. */
 } rll_grid_params;
 
 /* Per-sample diagnostics (optional outputs of rll_sample_and_shade_ex), each
@@ -169,6 +179,16 @@ int rll_sample_and_shade_ex(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, 
                             const float* boxes, int32_t n_boxes, uint64_t seed, uint32_t frame,
                             int32_t spp, float* rgb, uint32_t* rec_key, float* rec_val,
                             const rll_sample_debug* dbg);
+
+/* Same, with a footprint per point (footprint: [P] float, world units; NULL
+ * = level 0 for every point): the point's samples use the grid level its
+ * footprint selects (rll_grid_params.levels). Everything else as
+ * rll_sample_and_shade_ex. */
+int rll_sample_and_shade_fp(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos,
+                            const float* nrm, const float* albedo, const float* footprint,
+                            int64_t n_points, const float* boxes, int32_t n_boxes, uint64_t seed,
+                            uint32_t frame, int32_t spp, float* rgb, uint32_t* rec_key,
+                            float* rec_val, const rll_sample_debug* dbg);
 
 /* Energy-based baseline (Section 4): lights chosen in proportion to their
  * emitted power by inversion of one global cdf; same shading, same Philox

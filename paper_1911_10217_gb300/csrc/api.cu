@@ -104,7 +104,11 @@ int check_params(rll_ctx* ctx, const rll_grid_params* p)
     if (H < 16 || H > (1u << 26) || (H & (H - 1)) != 0)
         return fail(ctx, RLL_E_INVALID, "table_size must be a power of two in [16, 2^26]");
     if (p->cut_size < 1 || p->cut_size > (uint32_t)kMaxCut) return fail(ctx, RLL_E_INVALID, "cut_size must be in [1, 256]");
-    if ((uint64_t)H * p->cut_size > (1ull << 31)) return fail(ctx, RLL_E_INVALID, "table_size * cut_size must be <= 2^31");
+    if (p->levels > 16) return fail(ctx, RLL_E_INVALID, "levels must be in [0, 16]");
+    const uint64_t total = (uint64_t)H * (p->levels ? p->levels : 1u);
+    if (total > (1ull << 27)) return fail(ctx, RLL_E_INVALID, "levels * table_size must be <= 2^27");
+    if (total * p->cut_size > (1ull << 31))
+        return fail(ctx, RLL_E_INVALID, "levels * table_size * cut_size must be <= 2^31");
     if (!(p->cell_size > 0.0f) || !std::isfinite(p->cell_size)) return fail(ctx, RLL_E_INVALID, "cell_size must be > 0");
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(p->origin[k])) return fail(ctx, RLL_E_INVALID, "origin must be finite");
@@ -323,7 +327,9 @@ int rll_create_grid(rll_ctx* ctx, const rll_tree* tree, const rll_grid_params* p
     if (!g) return fail(ctx, RLL_E_NOMEM, "host allocation");
     g->device = ctx->device;
     g->p = *params;
-    g->H = params->table_size;
+    g->Hl = params->table_size;
+    g->levels = params->levels ? params->levels : 1u;
+    g->H = g->Hl * g->levels;
     g->M = params->cut_size;
     g->n_lights = tree->n;
     std::vector<uint32_t> cut;
@@ -347,7 +353,7 @@ int rll_create_grid(rll_ctx* ctx, const rll_tree* tree, const rll_grid_params* p
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->touched_len, 4 * (size_t)g->H);
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->n_touched, 16);
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->cursor, 4 * (size_t)g->H);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&g->big, 4 * (size_t)g->H);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->big, 8 * (size_t)g->H);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->keys, 0xFF, 8 * (size_t)g->H, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->n_touched, 0, 16, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->cursor, 0, 4 * (size_t)g->H, ctx->stream);
@@ -436,18 +442,27 @@ static int check_pass_args(rll_ctx* ctx, const rll_grid* grid, const rll_tree* t
     return RLL_OK;
 }
 
-int rll_sample_and_shade_ex(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos, const float* nrm,
-                            const float* albedo, int64_t n_points, const float* boxes, int32_t n_boxes,
-                            uint64_t seed, uint32_t frame, int32_t spp, float* rgb, uint32_t* rec_key,
-                            float* rec_val, const rll_sample_debug* dbg)
+int rll_sample_and_shade_fp(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos, const float* nrm,
+                            const float* albedo, const float* footprint, int64_t n_points, const float* boxes,
+                            int32_t n_boxes, uint64_t seed, uint32_t frame, int32_t spp, float* rgb,
+                            uint32_t* rec_key, float* rec_val, const rll_sample_debug* dbg)
 {
     if (!ctx) return RLL_E_INVALID;
     int rc = check_pass_args(ctx, grid, tree, pos, nrm, albedo, n_points, boxes, n_boxes, spp, rgb);
     if (rc != RLL_OK) return rc;
     if ((rec_key == nullptr) != (rec_val == nullptr)) return fail(ctx, RLL_E_INVALID, "rec_key and rec_val go together");
     DeviceGuard g(ctx->device);
-    return sample_and_shade(ctx, grid, tree, pos, nrm, albedo, n_points, boxes, n_boxes, seed, frame, spp, rgb,
-                            rec_key, rec_val, dbg);
+    return sample_and_shade(ctx, grid, tree, pos, nrm, albedo, footprint, n_points, boxes, n_boxes, seed, frame, spp,
+                            rgb, rec_key, rec_val, dbg);
+}
+
+int rll_sample_and_shade_ex(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos, const float* nrm,
+                            const float* albedo, int64_t n_points, const float* boxes, int32_t n_boxes,
+                            uint64_t seed, uint32_t frame, int32_t spp, float* rgb, uint32_t* rec_key,
+                            float* rec_val, const rll_sample_debug* dbg)
+{
+    return rll_sample_and_shade_fp(ctx, grid, tree, pos, nrm, albedo, nullptr, n_points, boxes, n_boxes, seed, frame,
+                                   spp, rgb, rec_key, rec_val, dbg);
 }
 
 int rll_sample_and_shade(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos, const float* nrm,
@@ -527,7 +542,7 @@ int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, con
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_alb, albedo, 4 * P, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n_boxes > 0) e = cudaMemcpyAsync(d_box, boxes, 24 * (size_t)n_boxes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return check_cuda(ctx, e, "render_pass_host: upload");
-    rc = sample_and_shade(ctx, grid, tree, d_pos, d_nrm, d_alb, P, d_box, n_boxes, seed, frame, spp, d_rgb, d_key,
+    rc = sample_and_shade(ctx, grid, tree, d_pos, d_nrm, d_alb, nullptr, P, d_box, n_boxes, seed, frame, spp, d_rgb, d_key,
                           d_val, nullptr);
     if (rc == RLL_OK) rc = learn_update(ctx, grid, d_key, d_val, S);
     if (rc == RLL_OK && do_split) rc = split_collapse(ctx, grid, tree);

@@ -425,7 +425,9 @@ int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items,
         a.keys = g->keys;
         a.cut = g->cut;
         a.C = g->C;
-        a.H = g->H;
+        a.Hl = g->Hl;
+        a.levels = g->levels;
+        a.footprint = nullptr;
         a.M = g->M;
         a.m = g->m;
         a.def_cut = g->def_cut;

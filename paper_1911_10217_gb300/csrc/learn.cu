@@ -18,9 +18,10 @@
 //      applies the composite to the cluster's Q held in shared memory; the
 //      row is then stored in the table precision and its cdf rebuilt (Eq. 2
 //      with the floor, prefix sum across the warp). Cells with more records
-//      than a warp's buffer are ordered the same way by a whole block, or,
-//      when larger still, sorted in place in global memory by a bitonic
-//      network.
+//      than a warp's buffer go to one block each: (cluster, sample id, index)
+//      keys sorted by a bitonic network in shared memory (up to 8192
+//      records; in place in global memory above that), then warps compose
+//      different clusters in parallel.
 // The order inside a bucket depends on thread scheduling; the per-cell sort
 // restores sample order, so the result is deterministic.
 //
@@ -34,6 +35,8 @@
 // arg-min over parents whose two children are both cut leaves, the
 // threshold test, then one lane emits the new cut and the cdf is rebuilt.
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "learn_core.cuh"
 #include "rll_device.cuh"
@@ -242,12 +245,16 @@ k_split(uint32_t M, uint32_t m, const uint32_t* __restrict__ touched, const uint
 
 // ---------------------------------------------------------------- bucketed learning
 // counters (rll_grid::n_touched): [0] touched cells, [1] bucket space claimed,
-// [2] unused, [3] cells for the block path (listed in rll_grid::big)
+// [2] cells for the sorting block path, [3] cells for the grouping block path;
+// rll_grid::big lists the latter, rll_grid::big + H the former
 constexpr int kBucketThreads = 256;
 constexpr int kTilesPerWarp = 4;         // 32-record tiles one warp counts / scatters
 constexpr uint32_t kWarpBucket = 240;    // records of a cell one warp orders in shared memory
-constexpr uint32_t kBlockBucket = 2048;  // records of a cell one block orders in shared memory
-constexpr int kBigThreads = 256;
+constexpr uint32_t kBlockGroup = 1024;   // records of a cell one block orders by grouping and ranking
+constexpr int kGroupThreads = 256;
+constexpr uint32_t kBlockSort = 8192;    // records of a cell one block sorts in shared memory (power of 2)
+constexpr size_t kBigSmem = kBlockSort * (sizeof(unsigned long long) + sizeof(uint32_t));
+constexpr int kBigThreads = 512;
 
 // 1. record counts per cell; the first adder appends the cell to the touched
 // list. Each warp takes kTilesPerWarp tiles of 32 consecutive records.
@@ -537,9 +544,64 @@ k_learn_tier(const Bucket bucket, const uint32_t* __restrict__ list, const uint3
     }
 }
 
-// 5. one block per remaining cell: the same ordering with the whole block
-// (up to kBlockBucket records), or, for larger cells, (cluster << 32 |
-// sample id) sorted in place in global scratch by a bitonic network
+// Eq. 1 of one cell whose records are sorted by (cluster, sample id), by a
+// whole block: cluster s occupies positions gs[s] .. ge[s]; cls(j) is the
+// cluster and val(j) the reward bits of record j. Warp w composes clusters
+// w, w + warps, ... (disjoint Q entries). All threads of the block call it.
+template <int P, class Cls, class Val>
+__device__ void compose_sorted_block(Cls cls, Val val, uint32_t nr, uint32_t M, uint32_t m, float alpha, float* q,
+                                     uint32_t* gs, uint32_t* ge)
+{
+    for (uint32_t s = threadIdx.x; s < M; s += blockDim.x) gs[s] = ge[s] = 0u;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < nr; j += blockDim.x) {
+        const uint32_t s = cls(j);
+        if (s >= M) continue;
+        if (j == 0 || cls(j - 1) != s) gs[s] = j;
+        if (j + 1 == nr || cls(j + 1) != s) ge[s] = j + 1;
+    }
+    __syncthreads();
+    const uint32_t warps = blockDim.x >> 5;
+    for (uint32_t s = threadIdx.x >> 5; s < M; s += warps) {
+        const uint32_t lo = gs[s], hi = ge[s];
+        if (hi > lo) learn_records<P>([&](uint32_t j) { return make_uint2(s, val(lo + j)); }, hi - lo, m, alpha, q);
+    }
+    __syncthreads();
+}
+
+// 5a. one block per cell of the grouping list (up to kBlockGroup records):
+// the ordering of the warp path done by the whole block, warps composing
+// different clusters in parallel; larger cells go to the sorting list.
+template <int P>
+__global__ void __launch_bounds__(kGroupThreads)
+k_learn_group(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t* __restrict__ touched,
+              const uint32_t* __restrict__ start, const uint32_t* __restrict__ len, const uint32_t* __restrict__ list,
+              uint32_t* __restrict__ next, uint32_t* __restrict__ cursor, uint32_t M, uint32_t m,
+              typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C, float alpha, float eps,
+              uint32_t* __restrict__ status)
+{
+    __shared__ CellOrder<kBlockGroup> o;
+    const uint32_t n = *(volatile const uint32_t*)(ctr + 3);
+    for (uint32_t bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const uint32_t w = list[bi];
+        const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
+        if (nr > kBlockGroup) {
+            if (threadIdx.x == 0) next[atomicAdd(ctr + 2, 1u)] = w;
+            continue;  // uniform across the block
+        }
+        const int64_t row = (int64_t)slot * M;
+        learn_cell_grouped<P>(BlockTeam{}, o, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, M, m, alpha, eps,
+                              Q + row, C + row, status);
+        if (threadIdx.x == 0) cursor[slot] = 0u;
+        __syncthreads();
+    }
+}
+
+// 5b. one block per cell of the sorting list. Up to kBlockSort records: keys
+// cluster << 45 | sample id << 13 | bucket index sorted by a bitonic network
+// in shared memory, rewards gathered in that order. Larger cells: (cluster
+// << 32 | sample id) sorted in place in global scratch, rewards read by
+// sample id. Then Eq. 1 (warps composing different clusters) and Eq. 2.
 template <int P>
 __global__ void __launch_bounds__(kBigThreads)
 k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const float* __restrict__ rec_val,
@@ -549,15 +611,28 @@ k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const fl
             uint32_t M, uint32_t m, typename Store<P>::T* __restrict__ Q, typename Store<P>::T* __restrict__ C,
             float alpha, float eps, uint32_t* __restrict__ status)
 {
-    __shared__ CellOrder<kBlockBucket> o;
-    const uint32_t n_big = *(volatile const uint32_t*)(ctr + 3);
+    extern __shared__ unsigned long long s_key[];      // kBlockSort keys, then kBlockSort rewards (u32)
+    uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kBlockSort);
+    __shared__ float s_q[kMaxCut], s_c[kMaxCut];
+    __shared__ uint16_t s_b[kMaxCut];
+    __shared__ uint32_t s_gs[kMaxCut], s_ge[kMaxCut];
+    const uint32_t n_big = *(volatile const uint32_t*)(ctr + 2);
     for (uint32_t bi = blockIdx.x; bi < n_big; bi += gridDim.x) {
         const uint32_t w = big[bi];
         const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
         const int64_t row = (int64_t)slot * M;
-        if (nr <= kBlockBucket) {
-            learn_cell_grouped<P>(BlockTeam{}, o, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, M, m, alpha,
-                                  eps, Q + row, C + row, status);
+        if (threadIdx.x < 32) load_q_row<P>(Q + row, m, s_q);
+        if (nr <= kBlockSort) {
+            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x)
+                s_key[k] = ((unsigned long long)bucket.s[b0 + k] << 45) |
+                           ((unsigned long long)bucket.sid[b0 + k] << 13) | k;
+            __syncthreads();
+            bitonic_sort_u64(s_key, nr, threadIdx.x, blockDim.x, BlockSync{});
+            for (uint32_t j = threadIdx.x; j < nr; j += blockDim.x)
+                s_val[j] = bucket.val[b0 + (uint32_t)(s_key[j] & (kBlockSort - 1))];
+            __syncthreads();
+            compose_sorted_block<P>([&](uint32_t j) { return (uint32_t)(s_key[j] >> 45); },
+                                    [&](uint32_t j) { return s_val[j]; }, nr, M, m, alpha, s_q, s_gs, s_ge);
         } else {
             unsigned long long* rec = wide + b0;
             for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x)
@@ -569,22 +644,32 @@ k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const fl
                 rec[k] = (e & 0xFFFFFFFF00000000ull) | __float_as_uint(__ldg(rec_val + (uint32_t)e));
             }
             __syncthreads();
-            if (threadIdx.x < 32) {
-                load_q_row<P>(Q + row, m, o.q);
-                __syncwarp();
-                learn_records<P>([&](uint32_t j) {
-                    const unsigned long long e = rec[j];
-                    return make_uint2((uint32_t)(e >> 32), (uint32_t)e);
-                }, nr, m, alpha, o.q);
-                store_q_row<P>(Q + row, m, o.q);
-                __syncwarp();
-                warp_rebuild_cdf<P>(o.q, (int)m, eps, C + row, reinterpret_cast<float*>(o.b_sid),
-                                    reinterpret_cast<uint16_t*>(o.b_val));
-            }
+            compose_sorted_block<P>([&](uint32_t j) { return (uint32_t)(rec[j] >> 32); },
+                                    [&](uint32_t j) { return (uint32_t)rec[j]; }, nr, M, m, alpha, s_q, s_gs, s_ge);
         }
-        if (threadIdx.x == 0) cursor[slot] = 0u;
+        if (threadIdx.x < 32) {
+            store_q_row<P>(Q + row, m, s_q);
+            __syncwarp();
+            warp_rebuild_cdf<P>(s_q, (int)m, eps, C + row, s_c, s_b);
+            if (threadIdx.x == 0) cursor[slot] = 0u;
+        }
         __syncthreads();
     }
+}
+
+// k_learn_big's shared-memory opt-in (above the 48 KB default), once per
+// device and precision
+template <int P>
+cudaError_t big_smem_attribute(int device)
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (device >= 0 && device < 64 && done[device]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_learn_big<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kBigSmem);
+    if (e == cudaSuccess && device >= 0 && device < 64) done[device] = true;
+    return e;
 }
 
 template <int P>
@@ -603,7 +688,7 @@ int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec
     const uint32_t HM = g->H * g->M;
     // scratch per record: bucket sample id (4 B), reward (4 B), cluster (1 B),
     // and the block path's in-place sort buffer (8 B, used only by cells
-    // above kBlockBucket records)
+    // above kBlockSort records)
     const size_t n4 = ((size_t)n * 4 + 255) & ~(size_t)255, n1 = ((size_t)n + 255) & ~(size_t)255;
     char* ws = static_cast<char*>(ws_get(ctx, 2 * n4 + n1 + 8 * (size_t)n));
     if (!ws) return RLL_E_NOMEM;
@@ -619,12 +704,20 @@ int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec
     k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(g->touched, g->n_touched, g->cursor, g->touched_start,
                                                      g->touched_len);
     k_bucket_scatter<<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, HM, g->M, g->cursor, bucket);
+    uint32_t* group_list = g->big;
+    uint32_t* sort_list = g->big + g->H;
     k_learn_tier<P, kWarpBucket, 6, 5><<<sms * 5, 6 * 32, 0, s>>>(
-        bucket, nullptr, g->n_touched, g->big, g->n_touched + 3, g->touched, g->touched_start, g->touched_len,
+        bucket, nullptr, g->n_touched, group_list, g->n_touched + 3, g->touched, g->touched_start, g->touched_len,
         g->cursor, g->M, g->m, (T*)g->Q, (T*)g->C, g->p.alpha, g->p.eps, ctx->d_status);
-    k_learn_big<P><<<sms * 4, kBigThreads, 0, s>>>(bucket, wide, rec_val, g->n_touched, g->touched, g->touched_start,
-                                                    g->touched_len, g->big, g->cursor, g->M, g->m, (T*)g->Q,
-                                                    (T*)g->C, g->p.alpha, g->p.eps, ctx->d_status);
+    k_learn_group<P><<<sms * 4, kGroupThreads, 0, s>>>(bucket, g->n_touched, g->touched, g->touched_start,
+                                                        g->touched_len, group_list, sort_list, g->cursor, g->M, g->m,
+                                                        (T*)g->Q, (T*)g->C, g->p.alpha, g->p.eps, ctx->d_status);
+    e = big_smem_attribute<P>(g->device);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "learn: shared memory opt-in");
+    k_learn_big<P><<<sms * 2, kBigThreads, kBigSmem, s>>>(bucket, wide, rec_val, g->n_touched, g->touched,
+                                                          g->touched_start, g->touched_len, sort_list, g->cursor,
+                                                          g->M, g->m, (T*)g->Q, (T*)g->C, g->p.alpha, g->p.eps,
+                                                          ctx->d_status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(ctx, e, "learn kernels");
     g->cursor_dirty = false;

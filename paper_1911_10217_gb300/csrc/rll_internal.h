@@ -46,7 +46,8 @@ struct rll_tree {
 struct rll_grid {
     int device = 0;
     rll_grid_params p{};
-    uint32_t H = 0, M = 0, m = 0;
+    uint32_t H = 0, M = 0, m = 0;   // H: slots of all levels (levels * Hl)
+    uint32_t Hl = 0, levels = 1;    // slots per resolution level, levels
     int64_t n_lights = 0;
     unsigned long long* keys = nullptr;  // [H]
     uint32_t* cut = nullptr;             // [H*M]
@@ -58,9 +59,9 @@ struct rll_grid {
     uint32_t* touched = nullptr;         // [H] cells touched by the last learn_update
     uint32_t* touched_start = nullptr;   // [H] first record of each touched cell (sorted / bucketed)
     uint32_t* touched_len = nullptr;     // [H] records of each touched cell (bucketed learning)
-    uint32_t* n_touched = nullptr;       // [4]: touched cells, bucket space claimed, unused, block-path cells
+    uint32_t* n_touched = nullptr;       // [4]: touched cells, bucket space claimed, sorting- and grouping-path cells
     uint32_t* cursor = nullptr;          // [H] per-slot record count / scatter cursor, all zero between calls
-    uint32_t* big = nullptr;             // [H] touched-cell indices whose records exceed a warp's buffer
+    uint32_t* big = nullptr;             // [2H] touched-cell indices for the grouping, then the sorting block path
     bool cursor_dirty = false;           // a learning call stopped before the cursors were cleared
 };
 
@@ -118,7 +119,7 @@ int learn_update_with_scratch(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key
 
 // ---- sample.cu
 int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* pos, const float* nrm,
-                     const float* albedo, int64_t n_points, const float* boxes, int n_boxes,
+                     const float* albedo, const float* footprint, int64_t n_points, const float* boxes, int n_boxes,
                      uint64_t seed, uint32_t frame, int spp, float* rgb, uint32_t* rec_key,
                      float* rec_val, const rll_sample_debug* dbg);
 int sample_power(rll_ctx* ctx, const rll_tree* t, const float* pos, const float* nrm,

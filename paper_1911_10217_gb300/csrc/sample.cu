@@ -100,7 +100,8 @@ cudaError_t launch_p(const SampleArgs& a, int mode, bool dbg, int minb, cudaStre
 }  // namespace
 
 int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* pos, const float* nrm,
-                     const float* albedo, int64_t n_points, const float* boxes, int n_boxes, uint64_t seed,
+                     const float* albedo, const float* footprint, int64_t n_points, const float* boxes, int n_boxes,
+                     uint64_t seed,
                      uint32_t frame, int spp, float* rgb, uint32_t* rec_key, float* rec_val,
                      const rll_sample_debug* dbg)
 {
@@ -115,7 +116,9 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
     a.keys = g->keys;
     a.cut = g->cut;
     a.C = g->C;
-    a.H = g->H;
+    a.Hl = g->Hl;
+    a.levels = g->levels;
+    a.footprint = footprint;
     a.M = g->M;
     a.m = g->m;
     a.def_cut = g->def_cut;

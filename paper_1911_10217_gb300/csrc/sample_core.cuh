@@ -23,7 +23,9 @@ struct SampleArgs {
     unsigned long long* keys;
     const uint32_t* cut;
     const void* C;
-    uint32_t H, M, m;
+    uint32_t Hl, M, m;        // slots per resolution level, cut size, cut length
+    uint32_t levels;          // resolution levels (cell size * 2^l)
+    const float* footprint;   // [P] or nullptr (every point at level 0)
     const uint32_t* def_cut;
     const void* def_C;
     float origin[3];
@@ -52,11 +54,26 @@ struct SampleArgs {
     uint32_t cell_base;
 };
 
-__device__ __forceinline__ int64_t lookup_insert(unsigned long long* keys, uint32_t H, unsigned long long key)
+// Level of a point with footprint f: the smallest l with h * 2^l >= f, i.e.
+// ceil(log2(f / h)) from the binary32 quotient (exponent and mantissa bits),
+// clamped to [0, levels - 1]; f <= h and NaN give 0.
+__device__ __forceinline__ uint32_t footprint_level(float f, float h, uint32_t levels)
+{
+    const float r = fdiv(f, h);
+    if (!(r > 1.0f)) return 0u;
+    const uint32_t b = __float_as_uint(r);
+    const uint32_t l = ((b >> 23) & 0xFFu) - 127u + ((b & 0x7FFFFFu) != 0u);
+    return min(l, levels - 1u);
+}
+
+// Lookup with lazy creation in the slot range of one level: linear probing
+// from level * Hl + (fmix64(key) mod Hl) for at most kMaxProbes slots.
+__device__ __forceinline__ int64_t lookup_insert(unsigned long long* keys, uint32_t Hl, uint32_t level,
+                                                 unsigned long long key)
 {
     const unsigned long long h = fmix64(key);
     for (int i = 0; i < kMaxProbes; ++i) {
-        const uint32_t slot = (uint32_t)((h + (unsigned long long)i) & (unsigned long long)(H - 1));
+        const uint32_t slot = level * Hl + (uint32_t)((h + (unsigned long long)i) & (unsigned long long)(Hl - 1));
         const unsigned long long k = __ldcg(keys + slot);
         if (k == key) return slot;
         if (k == kEmptyKey) {
@@ -177,7 +194,7 @@ struct Setup {
 
 template <int P>
 __device__ __forceinline__ Setup setup_sample(const SampleArgs& a, SampleStream& rs, float x0, float x1, float x2,
-                                              float n0, float n1, float n2)
+                                              float n0, float n1, float n2, uint32_t level)
 {
     using T = typename Store<P>::T;
     const T* Ctab = static_cast<const T*>(a.C);
@@ -188,8 +205,9 @@ __device__ __forceinline__ Setup setup_sample(const SampleArgs& a, SampleStream&
 #pragma unroll
         for (int k = 0; k < 5; ++k) jit[k] = rs.draw(kDrawJit + k);
     }
-    const unsigned long long key = cell_key(x0, x1, x2, n0, n1, n2, a.origin, a.h, a.nb, a.jitter != 0, jit);
-    const int64_t slot = lookup_insert(a.keys, a.H, key);
+    const float h_cell = fmul(a.h, (float)(1u << level));  // exact: a power of two
+    const unsigned long long key = cell_key(x0, x1, x2, n0, n1, n2, a.origin, h_cell, a.nb, a.jitter != 0, jit);
+    const int64_t slot = lookup_insert(a.keys, a.Hl, level, key);
     const T* crow;
     const uint32_t* cutrow;
     if (slot >= 0) {
@@ -265,13 +283,14 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
     const float x0 = a.pos[p], x1 = a.pos[np + p], x2 = a.pos[2 * np + p];
     const float n0 = a.nrm[p], n1 = a.nrm[np + p], n2 = a.nrm[2 * np + p];
     const float alb = a.albedo[p];
+    const uint32_t level = a.footprint ? footprint_level(__ldg(a.footprint + p), a.h, a.levels) : 0u;
     const int64_t nl1 = a.n_lights - 1;
     float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
     for (int j = 0; j < a.spp; ++j) {
         const uint32_t sid = (uint32_t)(p * a.spp + j);
         SampleStream rs;
         rs.init(a.seed, sid, a.frame);
-        const Setup su = setup_sample<P>(a, rs, x0, x1, x2, n0, n1, n2);
+        const Setup su = setup_sample<P>(a, rs, x0, x1, x2, n0, n1, n2, level);
         uint32_t node = su.node;
         float p_in = 1.0f;
         int64_t light;

@@ -28,7 +28,8 @@ EXPORTS = [
     "rll_ctx_create", "rll_ctx_set_stream", "rll_ctx_set_option", "rll_ctx_destroy", "rll_last_error", "rll_sync_status",
     "rll_build_light_tree", "rll_tree_update_emission", "rll_tree_num_lights", "rll_tree_export",
     "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_export", "rll_grid_import",
-    "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_power",
+    "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_and_shade_fp",
+    "rll_sample_power",
     "rll_learn_update", "rll_learn_update_noalloc", "rll_split_collapse", "rll_render_pass_host",
     "rll_batch_reserve", "rll_batch_set_items", "rll_batch_create", "rll_batch_set_config", "rll_batch_tune", "rll_batch_run", "rll_batch_capture",
     "rll_batch_launch", "rll_batch_destroy",
@@ -48,7 +49,7 @@ class GridParams(ctypes.Structure):
                 ("precision", ctypes.c_uint32), ("in_cluster_mode", ctypes.c_uint32),
                 ("reward_mode", ctypes.c_uint32), ("alpha", ctypes.c_float),
                 ("threshold", ctypes.c_float), ("eps", ctypes.c_float), ("q_init", ctypes.c_float),
-                ("split_iterations", ctypes.c_uint32)]
+                ("split_iterations", ctypes.c_uint32), ("levels", ctypes.c_uint32)]
 
 
 class BatchItem(ctypes.Structure):
@@ -104,6 +105,7 @@ def load(build_if_missing: bool = True):
     L.rll_sample_and_shade.argtypes = [P, P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P, P]
     L.rll_sample_and_shade_ex.argtypes = [P, P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P, P,
                                           ctypes.POINTER(SampleDebug)]
+    L.rll_sample_and_shade_fp.argtypes = [P, P, P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P, P, P]
     L.rll_sample_power.argtypes = [P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P]
     L.rll_learn_update.argtypes = [P, P, P, P, I64]
     L.rll_learn_update_noalloc.argtypes = [P, P, P, P, I64]
@@ -238,10 +240,11 @@ class Tree:
 
 def grid_params(table_size, cut_size, origin=(0.0, 0.0, 0.0), cell_size=1.0, normal_bins=1,
                 jitter=False, precision="fp32", mode="descent", reward="cluster", alpha=0.03,
-                threshold=2.0, eps=0.02, q_init=1e-3, split_iterations=1) -> GridParams:
+                threshold=2.0, eps=0.02, q_init=1e-3, split_iterations=1, levels=1) -> GridParams:
     return GridParams(int(table_size), int(cut_size), (ctypes.c_float * 3)(*origin), float(cell_size),
                       int(normal_bins), int(bool(jitter)), PREC[precision], MODE[mode], REWARD[reward],
-                      float(alpha), float(threshold), float(eps), float(q_init), int(split_iterations))
+                      float(alpha), float(threshold), float(eps), float(q_init), int(split_iterations),
+                      int(levels))
 
 
 def grid_params_for(grid_config, **overrides) -> GridParams:
@@ -249,7 +252,7 @@ def grid_params_for(grid_config, **overrides) -> GridParams:
     g = grid_config
     args = dict(table_size=g.table_size, cut_size=g.cut_size, origin=g.origin, cell_size=g.cell_size,
                 normal_bins=g.normal_bins, jitter=g.jitter, q_init=g.q_init, alpha=g.alpha, eps=g.eps,
-                threshold=g.threshold, split_iterations=g.split_iterations)
+                threshold=g.threshold, split_iterations=g.split_iterations, levels=g.levels)
     args.update(overrides)
     return grid_params(**args)
 
@@ -261,7 +264,8 @@ class Grid:
         h = ctypes.c_void_p()
         ctx._check(ctx.lib.rll_create_grid(ctx.h, tree.h, ctypes.byref(params), ctypes.byref(h)))
         self.ctx, self.h, self.tree, self.params = ctx, h, tree, params
-        self.H, self.M = int(params.table_size), int(params.cut_size)
+        self.levels = max(1, int(params.levels))
+        self.H, self.M = int(params.table_size) * self.levels, int(params.cut_size)
         self.m = int(ctx.lib.rll_grid_cut_len(h))
 
     def export(self):
@@ -294,13 +298,20 @@ class Grid:
 
 
 def sample_and_shade(ctx: Context, grid: Grid, tree: Tree, pos, nrm, albedo, boxes, seed, frame, spp,
-                     rgb, rec_key=None, rec_val=None, dbg_light=None, dbg_pcut=None, dbg_pin=None):
+                     rgb, rec_key=None, rec_val=None, dbg_light=None, dbg_pcut=None, dbg_pin=None,
+                     footprint=None):
     for t, d in ((pos, "float32"), (nrm, "float32"), (albedo, "float32"), (boxes, "float32"),
-                 (rgb, "float32"), (rec_key, "int32"), (rec_val, "float32")):
+                 (rgb, "float32"), (rec_key, "int32"), (rec_val, "float32"), (footprint, "float32")):
         _check_tensor(t, d)
     n = int(albedo.shape[0])
     k = int(boxes.shape[0]) if boxes is not None else 0
-    if dbg_light is None and dbg_pcut is None and dbg_pin is None:
+    if footprint is not None:
+        dbg = SampleDebug(_ptr(dbg_light), _ptr(dbg_pcut), _ptr(dbg_pin))
+        ctx._check(ctx.lib.rll_sample_and_shade_fp(ctx.h, grid.h, tree.h, _ptr(pos), _ptr(nrm),
+                                                   _ptr(albedo), _ptr(footprint), n, _ptr(boxes), k,
+                                                   int(seed), int(frame), int(spp), _ptr(rgb),
+                                                   _ptr(rec_key), _ptr(rec_val), ctypes.byref(dbg)))
+    elif dbg_light is None and dbg_pcut is None and dbg_pin is None:
         ctx._check(ctx.lib.rll_sample_and_shade(ctx.h, grid.h, tree.h, _ptr(pos), _ptr(nrm),
                                                 _ptr(albedo), n, _ptr(boxes), k, int(seed),
                                                 int(frame), int(spp), _ptr(rgb), _ptr(rec_key),

@@ -11,8 +11,11 @@ RTOL = {"fp32": 1e-4, "fp16": 2.5e-3, "bf16": 2e-2}
 def device_scene(scene, dev, emission=None):
     import torch
     t = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
-    return dict(tri=t(scene.tris.reshape(-1, 9)), em=t(scene.emission if emission is None else emission),
-                boxes=t(scene.boxes), pos=t(scene.pos), nrm=t(scene.nrm), alb=t(scene.albedo))
+    d = dict(tri=t(scene.tris.reshape(-1, 9)), em=t(scene.emission if emission is None else emission),
+             boxes=t(scene.boxes), pos=t(scene.pos), nrm=t(scene.nrm), alb=t(scene.albedo))
+    if scene.footprint is not None:
+        d["fp"] = t(scene.footprint)
+    return d
 
 
 def params_for(rll, scene, **kw):
@@ -30,7 +33,7 @@ def run_sample(rll, ctx, grid, tree, d, seed, frame, spp):
                pcut=torch.empty(P * spp, device=dev), pin=torch.empty(P * spp, device=dev))
     rll.sample_and_shade(ctx, grid, tree, d["pos"], d["nrm"], d["alb"], d["boxes"], seed, frame, spp,
                          out["rgb"], out["key"], out["val"], dbg_light=out["light"],
-                         dbg_pcut=out["pcut"], dbg_pin=out["pin"])
+                         dbg_pcut=out["pcut"], dbg_pin=out["pin"], footprint=d.get("fp"))
     return out
 
 
@@ -68,24 +71,29 @@ def compare_samples(gpu, orc, gpu_keys, orc_keys, M, rtol=1e-4):
     return int(mism.sum())
 
 
-def rows_by_key(keys, *tables):
+def rows_by_key(keys, *tables, Hl=None):
+    """Occupied rows by cell key (by (level, key) when Hl, the slots per
+    resolution level, is given: keys of different levels may coincide)."""
     occ = np.nonzero(keys != np.uint64(0xFFFFFFFFFFFFFFFF))[0]
-    return {int(keys[i]): tuple(t[i] for t in tables) for i in occ}
+    if Hl is None:
+        return {int(keys[i]): tuple(t[i] for t in tables) for i in occ}
+    return {(int(i) // Hl, int(keys[i])): tuple(t[i] for t in tables) for i in occ}
 
 
-def compare_tables(gstate, ostate, m, rtol, check_cut=True, only=None):
-    """Compare two grid states cell by cell (matched by key)."""
-    g = rows_by_key(gstate["keys"], gstate["cut"], gstate["q"], gstate["c"])
-    o = rows_by_key(ostate["keys"], ostate["cut"], ostate["q"], ostate["c"])
+def compare_tables(gstate, ostate, m, rtol, check_cut=True, only=None, Hl=None):
+    """Compare two grid states cell by cell (matched by key, or by level and
+    key for a multi-resolution grid)."""
+    g = rows_by_key(gstate["keys"], gstate["cut"], gstate["q"], gstate["c"], Hl=Hl)
+    o = rows_by_key(ostate["keys"], ostate["cut"], ostate["q"], ostate["c"], Hl=Hl)
     assert set(g) == set(o), f"cell sets differ: {len(set(g) ^ set(o))}"
     keys = o.keys() if only is None else only
     for k in keys:
         gc, gq, gcc = g[k]
         oc, oq, occ = o[k]
         if check_cut:
-            assert np.array_equal(gc[:m], oc[:m]), f"cut differs in cell {k:#x}"
-        assert np.allclose(gq[:m], oq[:m], rtol=rtol, atol=1e-12), f"Q differs in cell {k:#x}"
-        assert np.allclose(gcc[:m], occ[:m], rtol=rtol, atol=1e-12), f"C differs in cell {k:#x}"
+            assert np.array_equal(gc[:m], oc[:m]), f"cut differs in cell {k}"
+        assert np.allclose(gq[:m], oq[:m], rtol=rtol, atol=1e-12), f"Q differs in cell {k}"
+        assert np.allclose(gcc[:m], occ[:m], rtol=rtol, atol=1e-12), f"C differs in cell {k}"
 
 
 def oracle_state(og):

@@ -3,6 +3,7 @@ include/rll.h declares, and its host-side argument checks answer without a
 GPU (no compute is launched here)."""
 import ctypes
 import os
+import subprocess
 import re
 
 import pytest
@@ -58,11 +59,24 @@ def test_context_without_device_fails_cleanly(lib):
     assert rc == 3 and not h.value  # RLL_E_CUDA, no handle
 
 
-def test_grid_params_layout_matches_header(lib):
+def test_grid_params_layout_matches_header(lib, tmp_path):
     from paper_1911_10217_gb300 import rll
-    # 2 u32 + 3 f32 + f32 + 5 u32 + 4 f32 + u32 = 16 words
-    assert ctypes.sizeof(rll.GridParams) == 64
+    # 2 u32 + 3 f32 + f32 + 5 u32 + 4 f32 + 2 u32 = 17 words
+    assert ctypes.sizeof(rll.GridParams) == 68
     assert ctypes.sizeof(rll.SampleDebug) == 3 * ctypes.sizeof(ctypes.c_void_p)
+    # the C compiler's view of the header agrees, field by field
+    prog = tmp_path / "layout.c"
+    fields = [f for f, _ in rll.GridParams._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rll.h"', "int main(void) {",
+             'printf("%zu\\n", sizeof(rll_grid_params));']
+    lines += [f'printf("%zu\\n", offsetof(rll_grid_params, {f}));' for f in fields]
+    lines += ["return 0; }"]
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    out = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert out[0] == ctypes.sizeof(rll.GridParams)
+    assert out[1:] == [getattr(rll.GridParams, f).offset for f in fields]
 
 
 def test_oracle_builds_independently():

@@ -1,0 +1,112 @@
+"""Footprint-sized cells on path vertices (Section 3: cells sized from the
+ray footprint of each path vertex, coarser on later bounces), on the GPU
+(marked gpu): primary points of a reduced frame scene at the finest level and
+one diffuse bounce vertex each, whose footprint picks one of 8 levels. Lockstep
+parity with the oracle: level, cell (level and key), cluster and light of every
+sample exact, estimates and learned tables within tolerance."""
+import numpy as np
+import pytest
+
+from paper_1911_10217_gb300 import scenes
+
+from .gpu_common import (RTOL, clone_oracle_grid, compare_tables, device_scene, oracle_state, params_for,
+                         run_sample, to_host)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import oracle as O
+    from paper_1911_10217_gb300 import rll
+    dev = torch.device("cuda:0")
+    ctx = rll.Context(0, torch.cuda.current_stream(dev))
+    return dict(torch=torch, O=O, rll=rll, dev=dev, ctx=ctx)
+
+
+def _compare(g, o, gkeys, okeys, Hl, M):
+    light_g = g["light"].astype(np.int64)
+    mism = light_g != o["light"]
+    near = o["margin"] < 1e-6
+    assert not np.any(mism & ~near)
+    assert mism.sum() <= max(1, int(1e-5 * light_g.size))
+    ok = ~mism
+    kg = g["key"].view(np.uint32).astype(np.int64)
+    slot_g = np.where(kg == 0xFFFFFFFF, -1, kg // M)
+    assert np.array_equal(slot_g // Hl, o["slot"] // Hl), "levels differ"
+    cg = np.where(slot_g >= 0, gkeys[np.maximum(slot_g, 0)], np.uint64(0))
+    co = np.where(o["slot"] >= 0, okeys[np.maximum(o["slot"], 0)], np.uint64(0))
+    assert np.array_equal(cg[ok], co[ok]), "cell keys differ"
+    assert np.array_equal((kg % M)[ok], o["s"][ok])
+    assert np.allclose(g["val"][ok], o["reward"][ok], rtol=1e-4,
+                       atol=1e-7 * max(1.0, np.abs(o["reward"]).max()))
+    if mism.sum() == 0:
+        assert np.allclose(g["rgb"], o["rgb"], rtol=1e-4, atol=1e-7 * max(1.0, np.abs(o["rgb"]).max()))
+    return int(mism.sum())
+
+
+@pytest.mark.parametrize("variant", [dict(), dict(jitter=False, precision="fp16")])
+def test_path_vertices_lockstep(env, variant):
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    ctx.sync_status()
+    base = scenes.small_frame_scene()
+    s = scenes.path_scene(base, levels=8, paths_per_tile=1.0)  # spread over many levels
+    if "jitter" in variant:
+        s.grid.jitter = variant["jitter"]
+    d = device_scene(s, env["dev"])
+    ot = O.Tree(s.tris, s.emission)
+    dt = rll.Tree(ctx, d["tri"], d["em"])
+    okw = {k: v for k, v in variant.items() if k == "precision"}
+    og = O.Grid.for_scene(ot, s, **okw)
+    dg = rll.Grid(ctx, dt, params_for(rll, s, **okw))
+    assert dg.H == og.H == 8 * s.grid.table_size
+    Hl = s.grid.table_size
+    rtol = RTOL[variant.get("precision", "fp32")]
+    A = O.scene_arrays(s)
+    levels_seen = set()
+    for f in range(3):
+        dg.import_state(og.keys, og.cut, og.Q, og.C)
+        g = to_host(run_sample(rll, ctx, dg, dt, d, s.seed, f, s.spp))
+        o = og.sample_frame(A, s.seed, f, s.spp, footprint=s.footprint)
+        levels_seen |= set(np.unique(o["slot"][o["slot"] >= 0] // Hl).tolist())
+        mism = _compare(g, o, dg.export()["keys"], og.keys, Hl, dg.M)
+        rll.learn_update(ctx, dg, torch.from_numpy(g["key"]).to(env["dev"]),
+                         torch.from_numpy(g["val"]).to(env["dev"]))
+        touched = og.learn(o["slot"], o["s"], o["reward"])
+        if mism == 0:
+            compare_tables(dg.export(), oracle_state(og), og.m, rtol, Hl=Hl)
+        dg.import_state(og.keys, og.cut, og.Q, og.C)
+        rll.split_collapse(ctx, dg, dt)
+        o2 = clone_oracle_grid(O, og)
+        o2.split_collapse(og.keys != np.uint64(0xFFFFFFFFFFFFFFFF))
+        compare_tables(dg.export(), oracle_state(o2), og.m, max(rtol, 1e-5), Hl=Hl)
+        og.split_collapse(touched)
+    assert len(levels_seen) >= 4
+    assert ctx.sync_status() == 0
+
+
+def test_levels_without_footprints_use_level_zero(env):
+    """A multi-level grid sampled without footprints behaves as the single
+    grid: the same records (slots in level 0) and estimates."""
+    rll, ctx, torch = env["rll"], env["ctx"], env["torch"]
+    s = scenes.small_frame_scene()
+    d = device_scene(s, env["dev"])
+    dt = rll.Tree(ctx, d["tri"], d["em"])
+    one = rll.Grid(ctx, dt, params_for(rll, s))
+    multi = rll.Grid(ctx, dt, params_for(rll, s, levels=5))
+    a = to_host(run_sample(rll, ctx, one, dt, d, s.seed, 0, s.spp))
+    b = to_host(run_sample(rll, ctx, multi, dt, d, s.seed, 0, s.spp))
+    for k in ("rgb", "val", "light", "pcut", "pin"):
+        assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32)), k
+    # slots may differ (concurrent inserts race for probe slots); cells and clusters may not
+    ka, kb = a["key"].view(np.uint32).astype(np.int64), b["key"].view(np.uint32).astype(np.int64)
+    M, Hl = one.M, s.grid.table_size
+    assert np.all(kb // M < Hl)  # level 0 only
+    ea, eb = one.export()["keys"], multi.export()["keys"]
+    assert np.array_equal(ea[ka // M], eb[kb // M]) and np.array_equal(ka % M, kb % M)
+    with pytest.raises(rll.RllError):
+        rll.Grid(ctx, dt, params_for(rll, s, levels=17))
+    assert ctx.sync_status() == 0
