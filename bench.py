@@ -36,6 +36,10 @@ METRIC = ("light samples/sec (sample+shade+shadow+learn) at 1 GB300; MSE at equa
 UNIT = "light samples/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 SM_COUNT = 152
+# DRAM bytes (read + write) of one k_sample launch on this workload, from the ncu capture summarised
+# in profiles/k_sample_frame1080p.md (77.2 MB + 15.8 MB); to be set to None whenever the sampling
+# kernel changes until it is captured again
+K_SAMPLE_DRAM_BYTES = 93.04e6
 FP32_LANES_PER_SM = 128
 
 
@@ -871,14 +875,17 @@ def main():
         hbm_ach = bytes_per_sample() * n_sample / t_s / 1e9
         learn_bytes = 8 * n_sample  # records read once (keys + rewards)
         t_l = statistics.mean(t_learn) * 1e-3
-        launches_per_step = 1 + 3 * math.ceil(math.ceil(math.log2(g.table_size * g.cut_size + 1)) / 8) + 2 + 1
+        # our kernels per step: sampling 1; learning: count, claim, scatter, warp tier, grouping block
+        # tier, sorting block tier = 6; split-collapse 1 (the launch list of profiles/ shows them)
+        launches_per_step = 1 + 6 + 1
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": workload_config(scene),
                "roofline": {"kernel": "k_sample (sample_and_shade)", "bound": "alu",
                             "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                            "frac": achieved / alu_peak, "traffic": None,
+                            "frac": achieved / alu_peak, "traffic": K_SAMPLE_DRAM_BYTES,
+                            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                             "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                            f"{sm_clock:.0f} MHz ({peak_kind} sm_max_mhz)",
                             "ops_per_sample": ops / n_sample,
