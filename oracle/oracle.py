@@ -23,6 +23,7 @@ EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
 MODE = {"descent": 0, "uniform": 1}
 REWARD = {"cluster": 0, "literal": 1}
+BUILDER = {"lbvh": 0, "saoh": 1}
 
 
 def build(force: bool = False) -> str:
@@ -62,6 +63,7 @@ def lib():
             P = ctypes.c_void_p
             L.orc_philox4x32_10.argtypes = [P, P, P]
             L.orc_build_tree.argtypes = [ctypes.c_int64, P, P, ctypes.POINTER(_Tree)]
+            L.orc_build_tree_ex.argtypes = [ctypes.c_int64, P, P, ctypes.POINTER(_Tree), ctypes.c_int]
             L.orc_initial_cut.argtypes = [ctypes.POINTER(_Tree), ctypes.c_int, P]
             L.orc_initial_cut.restype = ctypes.c_int
             L.orc_cdf.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P]
@@ -124,7 +126,7 @@ class Tree:
     """The oracle's light tree (node numbering: internal 0..n-2, leaf of
     sorted light l is n-1+l, root 0)."""
 
-    def __init__(self, tris, emission):
+    def __init__(self, tris, emission, builder="lbvh"):
         tris = _f32(tris).reshape(-1, 9)
         emission = _f32(emission).reshape(-1, 3)
         n = tris.shape[0]
@@ -144,7 +146,8 @@ class Tree:
         self._s = _Tree(n, _p(self.perm), _p(self.code), _p(self.left), _p(self.right),
                         _p(self.parent), _p(self.begin), _p(self.end), _p(self.rec),
                         _p(self.phi64))
-        rc = lib().orc_build_tree(n, _p(tris), _p(emission), ctypes.byref(self._s))
+        self.builder = builder
+        rc = lib().orc_build_tree_ex(n, _p(tris), _p(emission), ctypes.byref(self._s), BUILDER[builder])
         if rc != 0:
             raise RuntimeError("oracle tree build failed")
 

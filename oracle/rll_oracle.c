@@ -333,7 +333,137 @@ static void orc_bounds_rec(const orc_tree* t, int32_t id, const float* tri, cons
     r[6] = a[6] + c[6];
 }
 
-int orc_build_tree(int64_t n, const float* tri, const float* emis, orc_tree* t)
+/* ------------------------------------------------------------------------ */
+/* Surface-area-orientation split positions (Section 3.1 leaves a hierarchy   */
+/* that considers light orientations and a surface area heuristic as future  */
+/* work). Reading: the lights keep their Morton order, so every node is still */
+/* a contiguous range; only the split position of each node changes. For a   */
+/* range of m lights the candidates are every position when m <= 17, else    */
+/* the 15 positions b + floor(m j / 16) (j = 1..15) and the Morton split; the */
+/* chosen one minimises cost(L) + cost(R) (ties: the smallest position),     */
+/* with cost(S) = phi(S) * SA(box(S)) * (2 - |sum_S c_i| / sum_S |c_i|),     */
+/* c_i the winding cross product of light i (twice its area times its unit  */
+/* normal), SA the box's surface area. phi, |c| and c are summed exactly in  */
+/* 64-bit fixed point (scale 2^(30 - e), e the exponent of the largest       */
+/* value), so that any summation order gives the same sums; the cost is     */
+/* then evaluated in binary32 from the sums converted to float. Internal    */
+/* node ids are (split position - split position of the root) mod (n - 1),  */
+/* so the root is 0; leaves keep n - 1 + l.                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    orc_tree* t;
+    const uint64_t* keys;
+    int64_t n;
+    const int64_t* pphi;   /* [n+1] prefix sums, fixed point */
+    const int64_t* parea;  /* [n+1] */
+    const int64_t* pc;     /* [3][n+1] */
+    const float* lbox;     /* [n][6] light boxes */
+    int64_t groot;
+} orc_saoh_ctx;
+
+static int orc_exponent(double v)
+{
+    int e = 0;
+    frexp(v, &e);
+    return e;
+}
+
+static float orc_box_area(const float b[6])
+{
+    float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+    return 2.0f * ((dx * dy + dy * dz) + dz * dx);
+}
+
+static float orc_saoh_cost(const orc_saoh_ctx* x, int64_t lo, int64_t hi, const float box[6])
+{
+    float phi = (float)(x->pphi[hi] - x->pphi[lo]);
+    float area = (float)(x->parea[hi] - x->parea[lo]);
+    float cx = (float)(x->pc[hi] - x->pc[lo]);
+    float cy = (float)(x->pc[(x->n + 1) + hi] - x->pc[(x->n + 1) + lo]);
+    float cz = (float)(x->pc[2 * (x->n + 1) + hi] - x->pc[2 * (x->n + 1) + lo]);
+    float om = 1.0f;
+    if (area > 0.0f) om = 2.0f - sqrtf((cx * cx + cy * cy) + cz * cz) / area;
+    return (phi * orc_box_area(box)) * om;
+}
+
+/* Morton split of [lo, hi] (inclusive): last g with a longer common prefix with lo than hi has */
+static int64_t orc_morton_split(const uint64_t* keys, int64_t lo, int64_t hi)
+{
+    int prefix = orc_clz64(keys[lo] ^ keys[hi]);
+    int64_t g = lo;
+    for (int64_t j = lo; j < hi; ++j)
+        if (orc_clz64(keys[lo] ^ keys[j]) > prefix) g = j;
+    return g;
+}
+
+/* split position k (first index of the right child) of the range [b, e) */
+int64_t orc_saoh_split(const orc_saoh_ctx* x, int64_t b, int64_t e)
+{
+    int64_t m = e - b;
+    int64_t cand[17];
+    int nc = 0;
+    if (m <= 17) {
+        for (int64_t k = b + 1; k < e; ++k) cand[nc++] = k;
+    } else {
+        int64_t km = orc_morton_split(x->keys, b, e - 1) + 1;
+        int dup = 0;
+        for (int j = 1; j <= 15; ++j) {
+            cand[nc++] = b + (m * j) / 16;
+            dup |= cand[nc - 1] == km;
+        }
+        if (!dup) cand[nc++] = km;
+    }
+    float best = INFINITY;
+    int64_t bk = b + 1;
+    for (int c = 0; c < nc; ++c) {
+        int64_t k = cand[c];
+        float lb[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        float rb[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int64_t l = b; l < e; ++l) {
+            float* bb = l < k ? lb : rb;
+            for (int q = 0; q < 3; ++q) {
+                bb[q] = fminf(bb[q], x->lbox[l * 6 + q]);
+                bb[3 + q] = fmaxf(bb[3 + q], x->lbox[l * 6 + 3 + q]);
+            }
+        }
+        float cst = orc_saoh_cost(x, b, k, lb) + orc_saoh_cost(x, k, e, rb);
+        if (cst < best || (cst == best && k < bk)) {
+            best = cst;
+            bk = k;
+        }
+    }
+    return bk;
+}
+
+static int32_t orc_saoh_id(const orc_saoh_ctx* x, int64_t g)
+{
+    int64_t nm1 = x->n - 1;
+    return (int32_t)(((g - x->groot) % nm1 + nm1) % nm1);
+}
+
+/* node [b, e) with split k; returns its id, fills the arrays below it */
+static int32_t orc_saoh_rec(orc_saoh_ctx* x, int64_t b, int64_t e, int32_t parent)
+{
+    orc_tree* t = x->t;
+    if (e - b == 1) {
+        int32_t id = (int32_t)(x->n - 1 + b);
+        t->parent[id] = parent;
+        t->begin[id] = (uint32_t)b;
+        t->end[id] = (uint32_t)e;
+        return id;
+    }
+    int64_t k = orc_saoh_split(x, b, e);
+    if (parent < 0) x->groot = k - 1;
+    int32_t id = orc_saoh_id(x, k - 1);
+    t->parent[id] = parent;
+    t->begin[id] = (uint32_t)b;
+    t->end[id] = (uint32_t)e;
+    t->left[id] = orc_saoh_rec(x, b, k, id);
+    t->right[id] = orc_saoh_rec(x, k, e, id);
+    return id;
+}
+
+static int orc_build_tree_with(int64_t n, const float* tri, const float* emis, orc_tree* t, int builder)
 {
     if (n <= 0) return -1;
     t->n = n;
@@ -368,8 +498,49 @@ int orc_build_tree(int64_t n, const float* tri, const float* emis, orc_tree* t)
         t->perm[l] = (uint32_t)(keys[l] & 0xFFFFFFFFu);
         t->code[l] = (uint32_t)(keys[l] >> 32);
     }
-    orc_build_ctx b = {t, keys, n};
-    orc_build_rec(&b, 0, n - 1, 0, -1);
+    if (builder == 0 || n < 2) {
+        orc_build_ctx b = {t, keys, n};
+        orc_build_rec(&b, 0, n - 1, 0, -1);
+    } else {
+        /* fixed-point prefix sums of power, |c| and c over the sorted lights */
+        int64_t* pphi = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));
+        int64_t* parea = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));
+        int64_t* pc = (int64_t*)calloc((size_t)(3 * (n + 1)), sizeof(int64_t));
+        float* lbox = (float*)malloc(sizeof(float) * 6 * (size_t)n);
+        float* phi = (float*)malloc(sizeof(float) * (size_t)n);
+        float* cr = (float*)malloc(sizeof(float) * 4 * (size_t)n);
+        double mphi = 0.0, mc = 0.0;
+        for (int64_t l = 0; l < n; ++l) {
+            const float* v = tri + (size_t)t->perm[l] * 9;
+            float c[3], len;
+            orc_cross32(v, c, &len);
+            for (int k = 0; k < 3; ++k) {
+                lbox[l * 6 + k] = fminf(fminf(v[k], v[3 + k]), v[6 + k]);
+                lbox[l * 6 + 3 + k] = fmaxf(fmaxf(v[k], v[3 + k]), v[6 + k]);
+                cr[l * 4 + k] = c[k];
+                if (fabs((double)c[k]) > mc) mc = fabs((double)c[k]);
+            }
+            cr[l * 4 + 3] = len;
+            if ((double)len > mc) mc = len;
+            phi[l] = orc_lum32(emis + (size_t)t->perm[l] * 3) * (0.5f * len);
+            if ((double)phi[l] > mphi) mphi = phi[l];
+        }
+        int sp = 30 - orc_exponent(mphi), sc = 30 - orc_exponent(mc);
+        for (int64_t l = 0; l < n; ++l) {
+            pphi[l + 1] = pphi[l] + llrint(ldexp((double)phi[l], sp));
+            parea[l + 1] = parea[l] + llrint(ldexp((double)cr[l * 4 + 3], sc));
+            for (int k = 0; k < 3; ++k)
+                pc[k * (n + 1) + l + 1] = pc[k * (n + 1) + l] + llrint(ldexp((double)cr[l * 4 + k], sc));
+        }
+        orc_saoh_ctx x = {t, keys, n, pphi, parea, pc, lbox, 0};
+        orc_saoh_rec(&x, 0, n, -1);
+        free(pphi);
+        free(parea);
+        free(pc);
+        free(lbox);
+        free(phi);
+        free(cr);
+    }
 
     float s[3];
     orc_bounds_rec(t, 0, tri, emis, s);
@@ -453,6 +624,18 @@ int orc_build_tree(int64_t n, const float* tri, const float* emis, orc_tree* t)
     free(cen);
     free(keys);
     return 0;
+}
+
+int orc_build_tree(int64_t n, const float* tri, const float* emis, orc_tree* t)
+{
+    return orc_build_tree_with(n, tri, emis, t, 0);
+}
+
+/* builder 0: the radix tree of the Morton codes (Section 3.1); 1: the
+ * surface-area-orientation split positions above */
+int orc_build_tree_ex(int64_t n, const float* tri, const float* emis, orc_tree* t, int builder)
+{
+    return orc_build_tree_with(n, tri, emis, t, builder);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -170,3 +170,64 @@ def test_importance_bounds_are_conservative(oracle_mod):
         assert val.max() <= bound * (1 + 1e-4) + 1e-6, (node, val.max(), bound)
         checked += 1
     assert checked > 100
+
+
+# ---- surface-area-orientation split positions (Section 3.1 names such a
+# hierarchy as future work); reading: Morton order kept, split positions by
+# cost phi * SA(box) * (2 - |sum c| / sum |c|) among fixed candidates
+
+def _line_lights(xs, up):
+    """Small triangles at x positions along a line; facing +y (up) or -y."""
+    tris = []
+    for x, u in zip(xs, up):
+        a, b, c = [x, 0.0, 0.0], [x + 0.01, 0.0, 0.0], [x, 0.0, 0.01]
+        tris.append([a, c, b] if u else [a, b, c])   # winding normal +y or -y
+    tris = np.asarray(tris, np.float32)
+    return tris, np.ones((len(xs), 3), np.float32)
+
+
+def test_saoh_tree_is_a_binary_tree_over_ranges(oracle_mod):
+    for maker in ("tiny", "small_frame"):
+        s = getattr(scenes, maker + "_scene")()
+        a = oracle_mod.Tree(s.tris, s.emission)
+        t = oracle_mod.Tree(s.tris, s.emission, builder="saoh")
+        n = t.n
+        assert np.array_equal(t.perm, a.perm)           # same light order
+        assert t.parent[0] == -1 and t.begin[0] == 0 and t.end[0] == n
+        seen = np.zeros(2 * n - 1, int)
+        for i in range(n - 1):
+            l, r = t.left[i], t.right[i]
+            seen[l] += 1
+            seen[r] += 1
+            assert t.parent[l] == i and t.parent[r] == i
+            assert t.begin[l] == t.begin[i] and t.end[l] == t.begin[r] and t.end[r] == t.end[i]
+            # id rule: (split position - the root's) mod (n - 1)
+            g_root = int(t.begin[t.right[0]]) - 1
+            assert i == ((int(t.begin[r]) - 1) - g_root) % (n - 1)
+        assert seen[0] == 0 and np.all(seen[1:] == 1)
+        for l in range(n):
+            assert t.begin[n - 1 + l] == l and t.end[n - 1 + l] == l + 1
+
+
+def test_saoh_split_moves_toward_a_change_of_facing(oracle_mod):
+    # 32 equal lights evenly spaced on a line. All facing up: the power-times-
+    # area term alone is symmetric and least in the middle (k^2 + (32-k)^2),
+    # so the root splits at 16. With the last 8 facing down, every split left
+    # of the middle leaves more mixed facing on the right, so the root split
+    # moves right of 16, but not past the change of facing at 24.
+    xs = np.arange(32) / 31.0
+    tris, em = _line_lights(xs, [True] * 32)
+    assert oracle_mod.Tree(tris, em, builder="saoh").begin[
+        oracle_mod.Tree(tris, em, builder="saoh").right[0]] == 16
+    tris, em = _line_lights(xs, [True] * 24 + [False] * 8)
+    t = oracle_mod.Tree(tris, em, builder="saoh")
+    assert 16 < int(t.begin[t.right[0]]) <= 24
+
+
+def test_saoh_separates_distant_clusters(oracle_mod):
+    # 20 lights near x = 0 and 12 near x = 1: every candidate except the gap
+    # leaves one child spanning the gap
+    xs = np.concatenate([np.linspace(0.0, 0.1, 20), np.linspace(0.9, 1.0, 12)])
+    tris, em = _line_lights(xs, [True] * 32)
+    t = oracle_mod.Tree(tris, em, builder="saoh")
+    assert t.begin[t.right[0]] == 20
