@@ -52,7 +52,7 @@ def load_peaks():
         return dict(PEAKS_FALLBACK, sm_max_mhz=2070.0), "fallback"
 
 
-def workload_config(scene):
+def workload_config(scene, tree="lbvh"):
     g = scene.grid
     return {"workload": "frame-scale static walled-cells scene, 1920x1080 G-buffer on 16 planes, "
                         "64K emissive triangles in 64 patches, 64 occluder boxes, one learning pass "
@@ -61,6 +61,7 @@ def workload_config(scene):
             "spp": scene.spp, "cut_size": g.cut_size, "table_size": g.table_size,
             "cell_size": g.cell_size, "normal_bins": g.normal_bins, "jitter": g.jitter,
             "table_precision": "fp32", "in_cluster": "descent", "split_iterations": g.split_iterations,
+            "light_tree": {"lbvh": "radix tree of Morton codes", "saoh": "Morton order, SAOH split positions"}[tree],
             "l2": "flushed between timed steps (512 MB write, untimed)"}
 
 
@@ -702,6 +703,80 @@ def run_paths(args):
     return 0
 
 
+def run_trees(args):
+    """Light-tree builders at equal cost: for the frame workload and the sky
+    interior, the radix tree of the Morton codes (Section 3.1) and the
+    surface-area-orientation split positions; per builder the leaf depth,
+    the pass time (sampling, learning, split-collapse) over --trees-passes
+    learning passes, and the 1-spp MSE after them (mean of 4 frames) against
+    the energy sampler at 1024 spp (the energy sampler uses the same light
+    order for both trees)."""
+    import torch
+    from paper_1911_10217_gb300 import rll, scenes
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    ctx = rll.Context(0, stream)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    results = {}
+    for sname, s in (("frame", scenes.frame_scene()), ("sky", scenes.sky_scene())):
+        tri, em, boxes = T(s.tris.reshape(-1, 9)), T(s.emission), T(s.boxes)
+        pos, nrm, alb = T(s.pos), T(s.nrm), T(s.albedo)
+        P = s.n_points
+        rgb = torch.empty(3, P, device=dev)
+        key = torch.empty(P, dtype=torch.int32, device=dev)
+        val = torch.empty(P, device=dev)
+        ref = torch.zeros(3, P, device=dev, dtype=torch.float64)
+        tree0 = rll.Tree(ctx, tri, em)
+        for i in range(32):
+            rll.sample_power(ctx, tree0, pos, nrm, alb, boxes, 4242, 400000 + i, 32, rgb)
+            ref += rgb.double()
+        ref /= 32
+        alpha = s.grid.alpha if sname == "frame" else 0.01
+        for builder in ("lbvh", "saoh"):
+            tree = tree0 if builder == "lbvh" else rll.Tree(ctx, tri, em, builder=builder)
+            ex = tree.export()
+            n = tree.n
+            stack, d = [0], {0: 0}
+            while stack:
+                v = stack.pop()
+                if v < n - 1:
+                    for c in (ex["left"][v], ex["right"][v]):
+                        d[int(c)] = d[v] + 1
+                        stack.append(int(c))
+            leaf_depth = np.array([d[n - 1 + l] for l in range(n)])
+            grid = rll.Grid(ctx, tree, rll.grid_params_for(s.grid, alpha=alpha))
+            ev = []
+            for f in range(args.trees_passes):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                e[0].record(stream)
+                rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, s.seed, f, 1, rgb, key, val)
+                e[1].record(stream)
+                rll.learn_update(ctx, grid, key, val)
+                e[2].record(stream)
+                rll.split_collapse(ctx, grid, tree)
+                e[3].record(stream)
+                ev.append(e)
+            torch.cuda.synchronize()
+            tim = [[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in ev[3:]]
+            mse = []
+            for r in range(4):
+                rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, 31337, 90000 + r, 1, rgb)
+                mse.append(float(((rgb.double() - ref) ** 2).mean()))
+            rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 31337, 90000, 1, rgb)
+            mse_pow = float(((rgb.double() - ref) ** 2).mean())
+            results[f"{sname}/{builder}"] = {
+                "leaf_depth_mean": float(leaf_depth.mean()), "leaf_depth_max": int(leaf_depth.max()),
+                "ms_sample": statistics.mean(t[0] for t in tim), "ms_learn": statistics.mean(t[1] for t in tim),
+                "ms_split": statistics.mean(t[2] for t in tim), "mse_1spp_mean": statistics.mean(mse),
+                "mse_1spp_runs": mse, "energy_sampler_mse_1spp": mse_pow,
+                "energy_over_rll": mse_pow / statistics.mean(mse), "alpha": alpha}
+            grid.close()
+    print(json.dumps({"metric": METRIC, "workload": "trees", "unit": UNIT, "n_gpus": 1, "data": "synthetic",
+                      "passes": args.trees_passes, "results": results, "reference": "energy sampler, 1024 spp",
+                      "device_status": ctx.sync_status()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -712,8 +787,10 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
+    ap.add_argument("--tree", default="lbvh", choices=["lbvh", "saoh"])
     ap.add_argument("--workload", default="frame",
-                    choices=["frame", "batched", "serving", "dynamic", "split", "sky", "paths"])
+                    choices=["frame", "batched", "serving", "dynamic", "split", "sky", "paths", "trees"])
+    ap.add_argument("--trees-passes", type=int, default=256)
     ap.add_argument("--paths-checkpoints", default="1,4,16,64,128")
     ap.add_argument("--paths-tiles", default="100,1000")
     ap.add_argument("--paths-levels", type=int, default=8)
@@ -753,6 +830,8 @@ def main():
         return run_sky(args)
     if args.workload == "paths":
         return run_paths(args)
+    if args.workload == "trees":
+        return run_trees(args)
     if args.workload == "split":
         return run_split(args)
     from paper_1911_10217_gb300 import scenes
@@ -784,7 +863,7 @@ def main():
     tri, em, boxes = T(scene.tris.reshape(-1, 9)), T(scene.emission), T(scene.boxes)
     pos, nrm, alb = T(scene.pos), T(scene.nrm), T(scene.albedo)
     P, S = scene.n_points, scene.spp
-    tree = rll.Tree(ctx, tri, em)
+    tree = rll.Tree(ctx, tri, em, builder=args.tree)
     g = scene.grid
     params = rll.grid_params_for(g)
     grid = rll.Grid(ctx, tree, params)
@@ -881,7 +960,7 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": workload_config(scene),
+               "config": workload_config(scene, args.tree),
                "roofline": {"kernel": "k_sample (sample_and_shade)", "bound": "alu",
                             "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                             "frac": achieved / alu_peak, "traffic": K_SAMPLE_DRAM_BYTES,

@@ -121,6 +121,25 @@ int rll_sync_status(rll_ctx* ctx);
  * Triangles must have non-zero area. n in [1, 2^24]. Synchronises. */
 int rll_build_light_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
                          rll_tree** out);
+
+/* tree builders (rll_build_light_tree_ex) */
+#define RLL_TREE_LBVH 0  /* radix tree of the Morton codes (Section 3.1: a simple LBVH) */
+#define RLL_TREE_SAOH 1  /* same light order, split positions by a surface-area-orientation cost */
+
+/* Same, with a choice of builder. RLL_TREE_SAOH follows the alternative that
+ * Section 3.1 leaves as future work (a hierarchy that considers light
+ * orientations and a surface area heuristic): the lights keep their Morton
+ * order, so every node is still a contiguous range; each node's split
+ * position is, among every position (ranges of at most 17 lights) or the 15
+ * positions b + floor(m j / 16) and the Morton split, the one of least
+ * cost(L) + cost(R), ties to the smallest, where cost(S) = phi(S) *
+ * surface area of S's box * (2 - |sum of winding cross products| / sum of
+ * their lengths); power, lengths and cross products are summed in 64-bit
+ * fixed point, so the result does not depend on summation order. Internal
+ * node ids are (split position - the root's) mod (n - 1): root 0. Same
+ * output layout and export as rll_build_light_tree. Synchronises. */
+int rll_build_light_tree_ex(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
+                            int32_t builder, rll_tree** out);
 /* Replaces the radiance used for shading (emission: [n][3], input order);
  * the node power bounds keep the values given at build time. */
 int rll_tree_update_emission(rll_ctx* ctx, rll_tree* tree, const float* emission);

@@ -241,23 +241,30 @@ int rll_sync_status(rll_ctx* ctx)
     return (int)bits;
 }
 
-int rll_build_light_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, rll_tree** out)
+int rll_build_light_tree_ex(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, int32_t builder,
+                            rll_tree** out)
 {
     if (!ctx || !out) return RLL_E_INVALID;
     *out = nullptr;
     if (!tri || !emission) return fail(ctx, RLL_E_INVALID, "tri / emission is NULL");
     if (n < 1 || n > (1ll << 24)) return fail(ctx, RLL_E_INVALID, "light count must be in [1, 2^24]");
+    if (builder != RLL_TREE_LBVH && builder != RLL_TREE_SAOH) return fail(ctx, RLL_E_INVALID, "unknown builder");
     DeviceGuard g(ctx->device);
     rll_tree* t = new (std::nothrow) rll_tree();
     if (!t) return fail(ctx, RLL_E_NOMEM, "host allocation");
     t->device = ctx->device;
-    const int rc = build_tree(ctx, tri, emission, n, t);
+    const int rc = build_tree(ctx, tri, emission, n, builder, t);
     if (rc != RLL_OK) {
         free_tree(t);
         return rc;
     }
     *out = t;
     return RLL_OK;
+}
+
+int rll_build_light_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, rll_tree** out)
+{
+    return rll_build_light_tree_ex(ctx, tri, emission, n, RLL_TREE_LBVH, out);
 }
 
 int rll_tree_update_emission(rll_ctx* ctx, rll_tree* tree, const float* emission)

@@ -96,7 +96,7 @@ cudaError_t radix_sort_pairs(cudaStream_t s, const uint32_t* kin, const uint32_t
 cudaError_t inclusive_scan_f32(cudaStream_t s, const float* in, float* out, int64_t n, void* scratch);
 
 // ---- tree.cu
-int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, rll_tree* t);
+int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, int builder, rll_tree* t);
 int tree_update_emission(rll_ctx* ctx, rll_tree* t, const float* emission);
 
 // ---- learn.cu

@@ -17,6 +17,7 @@ namespace rll {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kMaxTreeDepth = 4096;  // far above either builder's depth (SAOH: < 250 levels at 2^24 lights)
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
@@ -249,7 +250,7 @@ __global__ void k_cone(int64_t n, const LightRec* __restrict__ lights, const Nod
     const float nx = lights[l].n[0], ny = lights[l].n[1], nz = lights[l].n[2];
     int64_t node = n - 1 + l;
     int guard = 0;
-    while (node >= 0 && guard++ < 128) {
+    while (node >= 0 && guard++ < kMaxTreeDepth) {
         const NodeRec& r = nodes[node];
         const float d = fadd(fadd(fmul(r.axis[0], nx), fmul(r.axis[1], ny)), fmul(r.axis[2], nz));
         atomicMin(&cosmin[node], float_to_ordered(d));
@@ -286,11 +287,259 @@ __global__ void k_update_emission(int64_t n, const uint32_t* __restrict__ perm, 
     lights[l].le[2] = emis[(int64_t)i * 3 + 2];
 }
 
+// ---------------------------------------------------------------- SAOH split positions
+// Surface-area-orientation split positions over the Morton order (Section
+// 3.1 names a hierarchy that considers orientations and a surface area
+// heuristic as future work): every node stays a contiguous range of the
+// sorted lights; its split position is the candidate (every position when
+// the range has at most 17 lights, else the 15 positions b + floor(m j /
+// 16) and the Morton split) of least cost(L) + cost(R), ties to the
+// smallest, with cost(S) = phi(S) * SA(box(S)) * (2 - |sum c| / sum |c|),
+// c the winding cross product of a light. phi, |c| and c are summed exactly
+// in 64-bit fixed point (scale 2^(30 - e), e the exponent of the largest
+// value), so the sums do not depend on the summation order; the cost is
+// binary32 from the sums converted to float. Internal node id = (split
+// position - the root's) mod (n - 1): root 0. Built one level per launch,
+// one block per node.
+
+// fixed-point values of light l: phi, |c|, c (5 int64 arrays of n + 1, entry l + 1)
+__global__ void k_saoh_max(int64_t n, const NodeRec* __restrict__ nodes, const float* __restrict__ axis_sum,
+                           int* __restrict__ mx)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float mphi = 0.0f, mc = 0.0f;
+    if (l < n) {
+        const int64_t id = n - 1 + l;
+        mphi = nodes[id].phi;
+        const float cx = axis_sum[id * 3], cy = axis_sum[id * 3 + 1], cz = axis_sum[id * 3 + 2];
+        const float len = fsqrt(fadd(fadd(fmul(cx, cx), fmul(cy, cy)), fmul(cz, cz)));
+        mc = fmaxf(fmaxf(fabsf(cx), fabsf(cy)), fmaxf(fabsf(cz), len));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mphi = fmaxf(mphi, __shfl_xor_sync(0xffffffffu, mphi, o));
+        mc = fmaxf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(mx, __float_as_int(mphi));  // non-negative floats order as integers
+        atomicMax(mx + 1, __float_as_int(mc));
+    }
+}
+
+__device__ __forceinline__ int exponent_of(float v)  // v = f * 2^e, f in [0.5, 1); 0 -> 0
+{
+    if (!(v > 0.0f)) return 0;
+    int e;
+    frexpf(v, &e);
+    return e;
+}
+
+__global__ void k_saoh_fixed(int64_t n, const NodeRec* __restrict__ nodes, const float* __restrict__ axis_sum,
+                             const int* __restrict__ mx, long long* __restrict__ fx)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l > n) return;
+    const int64_t stride = n + 1;
+    if (l == 0) {
+        for (int k = 0; k < 5; ++k) fx[k * stride] = 0;
+        return;
+    }
+    const int64_t id = n - 1 + (l - 1);
+    const int sp = 30 - exponent_of(__int_as_float(mx[0])), sc = 30 - exponent_of(__int_as_float(mx[1]));
+    const float cx = axis_sum[id * 3], cy = axis_sum[id * 3 + 1], cz = axis_sum[id * 3 + 2];
+    const float len = fsqrt(fadd(fadd(fmul(cx, cx), fmul(cy, cy)), fmul(cz, cz)));
+    fx[l] = __double2ll_rn(ldexp((double)nodes[id].phi, sp));
+    fx[stride + l] = __double2ll_rn(ldexp((double)len, sc));
+    fx[2 * stride + l] = __double2ll_rn(ldexp((double)cx, sc));
+    fx[3 * stride + l] = __double2ll_rn(ldexp((double)cy, sc));
+    fx[4 * stride + l] = __double2ll_rn(ldexp((double)cz, sc));
+}
+
+// inclusive prefix sums of the 5 arrays (n + 1 entries each), in place: one
+// block per array, chunks of 1024 carried sequentially (exact integers)
+__global__ void __launch_bounds__(1024) k_saoh_scan(int64_t n, long long* __restrict__ fx)
+{
+    __shared__ long long s_w[32];
+    long long* a = fx + (int64_t)blockIdx.x * (n + 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long carry = 0;
+    for (int64_t base = 0; base <= n; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        long long v = i <= n ? a[i] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) s_w[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            long long w = s_w[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_w[lane] = w;
+        }
+        __syncthreads();
+        const long long incl = v + (warp > 0 ? s_w[warp - 1] : 0) + carry;
+        if (i <= n) a[i] = incl;
+        carry += s_w[31];
+        __syncthreads();
+    }
+}
+
+struct SaohNode {
+    uint32_t b, e;       // range [b, e), e - b >= 2
+    int32_t parent;      // -1 at the root
+    uint32_t side;       // 0: left child of parent, 1: right
+};
+
+__device__ __forceinline__ float box_area(const float lo[3], const float hi[3])
+{
+    const float dx = fsub(hi[0], lo[0]), dy = fsub(hi[1], lo[1]), dz = fsub(hi[2], lo[2]);
+    return fmul(2.0f, fadd(fadd(fmul(dx, dy), fmul(dy, dz)), fmul(dz, dx)));
+}
+
+__device__ __forceinline__ float saoh_cost(const long long* fx, int64_t n, uint32_t lo, uint32_t hi,
+                                           const float blo[3], const float bhi[3])
+{
+    const int64_t st = n + 1;
+    const float phi = __ll2float_rn(fx[hi] - fx[lo]);
+    const float area = __ll2float_rn(fx[st + hi] - fx[st + lo]);
+    const float cx = __ll2float_rn(fx[2 * st + hi] - fx[2 * st + lo]);
+    const float cy = __ll2float_rn(fx[3 * st + hi] - fx[3 * st + lo]);
+    const float cz = __ll2float_rn(fx[4 * st + hi] - fx[4 * st + lo]);
+    float om = 1.0f;
+    if (area > 0.0f) om = fsub(2.0f, fdiv(fsqrt(fadd(fadd(fmul(cx, cx), fmul(cy, cy)), fmul(cz, cz))), area));
+    return fmul(fmul(phi, box_area(blo, bhi)), om);
+}
+
+constexpr int kSaohThreads = 128;
+constexpr int kSaohCand = 17;
+
+__global__ void __launch_bounds__(kSaohThreads)
+k_saoh_level(int64_t n, const SaohNode* __restrict__ in, uint32_t count, SaohNode* __restrict__ out,
+             uint32_t* __restrict__ out_count, const uint32_t* __restrict__ codes, const uint32_t* __restrict__ idx,
+             const NodeRec* __restrict__ nodes, const long long* __restrict__ fx, int64_t* __restrict__ groot,
+             int32_t* __restrict__ left, int32_t* __restrict__ right, int32_t* __restrict__ parent)
+{
+    __shared__ uint32_t s_bound[kSaohCand + 2];  // b, sorted candidates, e
+    __shared__ int s_nb;
+    __shared__ int s_box[kSaohCand + 1][6];      // ordered-int min xyz, max xyz per segment
+    const uint32_t w = blockIdx.x;
+    if (w >= count) return;
+    const SaohNode nd = in[w];
+    const uint32_t b = nd.b, e = nd.e, m = e - b;
+    if (threadIdx.x == 0) {
+        uint32_t c[kSaohCand];
+        int nc = 0;
+        if (m <= 17) {
+            for (uint32_t k = b + 1; k < e; ++k) c[nc++] = k;
+        } else {
+            // Morton split: last j in [b, e-2] sharing a longer prefix with b than e-1 does
+            const unsigned long long kb = ((unsigned long long)codes[b] << 32) | idx[b];
+            const unsigned long long ke = ((unsigned long long)codes[e - 1] << 32) | idx[e - 1];
+            const int prefix = __clzll((long long)(kb ^ ke));
+            uint32_t lo = b, hi = e - 2;  // invariant: lo qualifies (lo == b always does)
+            while (lo < hi) {
+                const uint32_t mid = lo + (hi - lo + 1) / 2;
+                const unsigned long long km = ((unsigned long long)codes[mid] << 32) | idx[mid];
+                if (__clzll((long long)(kb ^ km)) > prefix) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint32_t kmort = lo + 1;
+            bool dup = false;
+            for (int j = 1; j <= 15; ++j) {
+                c[nc] = b + (uint32_t)(((uint64_t)m * (uint64_t)j) / 16u);
+                dup |= c[nc] == kmort;
+                ++nc;
+            }
+            if (!dup) c[nc++] = kmort;
+            for (int i = 1; i < nc; ++i) {  // sort ascending
+                const uint32_t v = c[i];
+                int j = i - 1;
+                while (j >= 0 && c[j] > v) {
+                    c[j + 1] = c[j];
+                    --j;
+                }
+                c[j + 1] = v;
+            }
+        }
+        s_bound[0] = b;
+        for (int i = 0; i < nc; ++i) s_bound[i + 1] = c[i];
+        s_bound[nc + 1] = e;
+        s_nb = nc + 2;
+    }
+    for (int i = threadIdx.x; i < (kSaohCand + 1) * 6; i += blockDim.x)
+        s_box[i / 6][i % 6] = float_to_ordered(i % 6 < 3 ? INFINITY : -INFINITY);
+    __syncthreads();
+    const int nb = s_nb;
+    for (uint32_t l = b + threadIdx.x; l < e; l += blockDim.x) {
+        int lo = 0, hi = nb - 2;  // segment: s_bound[seg] <= l < s_bound[seg + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (s_bound[mid] <= l) lo = mid;
+            else hi = mid - 1;
+        }
+        const NodeRec& r = nodes[n - 1 + l];
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&s_box[lo][k], float_to_ordered(r.bmin[k]));
+            atomicMax(&s_box[lo][3 + k], float_to_ordered(r.bmax[k]));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const int nseg = nb - 1;
+    float best = INFINITY;
+    uint32_t bk = b + 1;
+    for (int i = 1; i < nseg; ++i) {  // candidate s_bound[i]: left = segments 0..i-1
+        float llo[3] = {INFINITY, INFINITY, INFINITY}, lhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        float rlo[3] = {INFINITY, INFINITY, INFINITY}, rhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int g = 0; g < nseg; ++g) {
+            float* lo3 = g < i ? llo : rlo;
+            float* hi3 = g < i ? lhi : rhi;
+            for (int k = 0; k < 3; ++k) {
+                lo3[k] = fminf(lo3[k], ordered_to_float(s_box[g][k]));
+                hi3[k] = fmaxf(hi3[k], ordered_to_float(s_box[g][3 + k]));
+            }
+        }
+        const uint32_t k = s_bound[i];
+        const float cst = fadd(saoh_cost(fx, n, b, k, llo, lhi), saoh_cost(fx, n, k, e, rlo, rhi));
+        if (cst < best) {  // candidates ascend: the first minimum is the smallest position
+            best = cst;
+            bk = k;
+        }
+    }
+    const int64_t g = (int64_t)bk - 1;
+    int32_t id;
+    if (nd.parent < 0) {
+        *groot = g;
+        id = 0;
+    } else {
+        const int64_t nm1 = n - 1;
+        id = (int32_t)(((g - *groot) % nm1 + nm1) % nm1);
+        if (nd.side == 0) left[nd.parent] = id;
+        else right[nd.parent] = id;
+    }
+    parent[id] = nd.parent;
+    if (bk - b == 1) {
+        left[id] = (int32_t)(n - 1 + b);
+        parent[n - 1 + b] = id;
+    } else {
+        out[atomicAdd(out_count, 1u)] = SaohNode{b, bk, id, 0u};
+    }
+    if (e - bk == 1) {
+        right[id] = (int32_t)(n - 1 + bk);
+        parent[n - 1 + bk] = id;
+    } else {
+        out[atomicAdd(out_count, 1u)] = SaohNode{bk, e, id, 1u};
+    }
+}
+
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, rll_tree* t)
+int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n, int builder, rll_tree* t)
 {
     cudaStream_t s = ctx->stream;
     const int64_t nn = 2 * n - 1;
@@ -311,8 +560,10 @@ int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
     // scratch: codes, idx, sort, begin/end (unused after build), axis sums,
     // counters, cone minima, bbox, scan sums
     const size_t sort_b = radix_sort_scratch_bytes(n);
+    const size_t saoh_b = builder == RLL_TREE_SAOH ? a256(40 * (n + 1)) + 2 * a256(sizeof(SaohNode) * n) + a256(64)
+                                                  : 0;
     const size_t need = a256(4 * n) * 2 + sort_b + a256(4 * nn) * 2 + a256(12 * nn) + a256(4 * n) +
-                        a256(4 * nn) + a256(64) + a256(4 * 4096) + a256(4 * n);
+                        a256(4 * nn) + a256(64) + a256(4 * 4096) + a256(4 * n) + saoh_b;
     char* w = (char*)ws_get(ctx, need);
     if (!w) return RLL_E_NOMEM;
     uint32_t* codes = (uint32_t*)w; w += a256(4 * n);
@@ -325,7 +576,11 @@ int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
     int* cosmin = (int*)w; w += a256(4 * nn);
     int* bbox = (int*)w; w += a256(64);
     void* scan_ws = w; w += a256(4 * 4096);
-    float* leaf_phi = (float*)w;
+    float* leaf_phi = (float*)w; w += a256(4 * n);
+    long long* fx = (long long*)w; w += builder == RLL_TREE_SAOH ? a256(40 * (n + 1)) : 0;
+    SaohNode* list_a = (SaohNode*)w; w += builder == RLL_TREE_SAOH ? a256(sizeof(SaohNode) * n) : 0;
+    SaohNode* list_b = (SaohNode*)w; w += builder == RLL_TREE_SAOH ? a256(sizeof(SaohNode) * n) : 0;
+    uint32_t* saoh_ctr = (uint32_t*)w;  // [0] next-level count, [2..3] int64 root split, [4..5] max bits
 
     k_bbox_init<<<1, 32, 0, s>>>(bbox);
     k_centroid_bbox<<<grid_for(n), kBlock, 0, s>>>(tri, n, bbox);
@@ -335,8 +590,35 @@ int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
     if (e != cudaSuccess) return check_cuda(ctx, e, "radix sort (tree)");
     e = cudaMemsetAsync(t->parent, 0xFF, sizeof(int32_t) * nn, s);
     if (e != cudaSuccess) return check_cuda(ctx, e, "memset parent");
-    if (n > 1) k_karras<<<grid_for(n - 1), kBlock, 0, s>>>(scodes, sidx, n, t->left, t->right, t->parent, begin, end);
+    if (n > 1 && builder == RLL_TREE_LBVH)
+        k_karras<<<grid_for(n - 1), kBlock, 0, s>>>(scodes, sidx, n, t->left, t->right, t->parent, begin, end);
     k_leaves<<<grid_for(n), kBlock, 0, s>>>(tri, emission, n, sidx, t->perm, t->lights, t->nodes, axis_sum);
+    if (n > 1 && builder == RLL_TREE_SAOH) {
+        int64_t* groot = reinterpret_cast<int64_t*>(saoh_ctr + 2);
+        int* mx = reinterpret_cast<int*>(saoh_ctr + 4);
+        e = cudaMemsetAsync(saoh_ctr, 0, 64, s);
+        if (e != cudaSuccess) return check_cuda(ctx, e, "memset (saoh)");
+        k_saoh_max<<<grid_for(n), kBlock, 0, s>>>(n, t->nodes, axis_sum, mx);
+        k_saoh_fixed<<<grid_for(n + 1), kBlock, 0, s>>>(n, t->nodes, axis_sum, mx, fx);
+        k_saoh_scan<<<5, 1024, 0, s>>>(n, fx);
+        const SaohNode root{0u, (uint32_t)n, -1, 0u};
+        e = cudaMemcpyAsync(list_a, &root, sizeof(root), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return check_cuda(ctx, e, "saoh root");
+        uint32_t count = 1;
+        for (int level = 0; count > 0; ++level) {
+            if (level > kMaxTreeDepth) return fail(ctx, RLL_E_DEVICE, "saoh build: too many levels");
+            e = cudaMemsetAsync(saoh_ctr, 0, sizeof(uint32_t), s);
+            if (e != cudaSuccess) return check_cuda(ctx, e, "memset (saoh level)");
+            k_saoh_level<<<count, kSaohThreads, 0, s>>>(n, list_a, count, list_b, saoh_ctr, scodes, sidx, t->nodes,
+                                                        fx, groot, t->left, t->right, t->parent);
+            e = cudaMemcpyAsync(&count, saoh_ctr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return check_cuda(ctx, e, "saoh level");
+            SaohNode* tmp = list_a;
+            list_a = list_b;
+            list_b = tmp;
+        }
+    }
     e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * n, s);
     if (e != cudaSuccess) return check_cuda(ctx, e, "memset counters");
     if (n > 1) k_bottom_up<<<grid_for(n), kBlock, 0, s>>>(n, t->left, t->right, t->parent, t->nodes, axis_sum, counters);

@@ -22,11 +22,12 @@ ERRORS = {1: "RLL_E_INVALID", 2: "RLL_E_NOMEM", 3: "RLL_E_CUDA", 4: "RLL_E_TABLE
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
 MODE = {"descent": 0, "uniform": 1}
 REWARD = {"cluster": 0, "literal": 1}
+BUILDER = {"lbvh": 0, "saoh": 1}
 
 # every symbol declared in include/rll.h
 EXPORTS = [
     "rll_ctx_create", "rll_ctx_set_stream", "rll_ctx_set_option", "rll_ctx_destroy", "rll_last_error", "rll_sync_status",
-    "rll_build_light_tree", "rll_tree_update_emission", "rll_tree_num_lights", "rll_tree_export",
+    "rll_build_light_tree", "rll_build_light_tree_ex", "rll_tree_update_emission", "rll_tree_num_lights", "rll_tree_export",
     "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_export", "rll_grid_import",
     "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_and_shade_fp",
     "rll_sample_power",
@@ -91,6 +92,7 @@ def load(build_if_missing: bool = True):
     L.rll_last_error.restype = ctypes.c_char_p
     L.rll_sync_status.argtypes = [P]
     L.rll_build_light_tree.argtypes = [P, P, P, I64, ctypes.POINTER(P)]
+    L.rll_build_light_tree_ex.argtypes = [P, P, P, I64, I32, ctypes.POINTER(P)]
     L.rll_tree_update_emission.argtypes = [P, P, P]
     L.rll_tree_num_lights.argtypes = [P]
     L.rll_tree_num_lights.restype = I64
@@ -200,15 +202,16 @@ class Context:
 
 
 class Tree:
-    """rll_tree built by rll_build_light_tree."""
+    """rll_tree built by rll_build_light_tree_ex (builder "lbvh" or "saoh")."""
 
-    def __init__(self, ctx: Context, tri, emission):
+    def __init__(self, ctx: Context, tri, emission, builder: str = "lbvh"):
         _check_tensor(tri, "float32")
         _check_tensor(emission, "float32")
         n = int(tri.shape[0])
         h = ctypes.c_void_p()
-        ctx._check(ctx.lib.rll_build_light_tree(ctx.h, _ptr(tri), _ptr(emission), n, ctypes.byref(h)))
-        self.ctx, self.h, self.n = ctx, h, n
+        ctx._check(ctx.lib.rll_build_light_tree_ex(ctx.h, _ptr(tri), _ptr(emission), n, BUILDER[builder],
+                                                   ctypes.byref(h)))
+        self.ctx, self.h, self.n, self.builder = ctx, h, n, builder
 
     def update_emission(self, emission):
         _check_tensor(emission, "float32")

@@ -28,17 +28,20 @@ def env():
     return dict(torch=torch, O=O, rll=rll, dev=dev, ctx=ctx)
 
 
-def _trees(env, scene):
+def _trees(env, scene, builder="lbvh"):
     O, rll = env["O"], env["rll"]
     env["ctx"].sync_status()  # clear device status bits left by an earlier test
     d = device_scene(scene, env["dev"])
-    return O.Tree(scene.tris, scene.emission), rll.Tree(env["ctx"], d["tri"], d["em"]), d
+    return (O.Tree(scene.tris, scene.emission, builder=builder),
+            rll.Tree(env["ctx"], d["tri"], d["em"], builder=builder), d)
 
 
-@pytest.mark.parametrize("maker", ["tiny", "small_frame", "frame"])
-def test_tree_matches_oracle_bit_exact(env, maker):
-    s = getattr(scenes, maker + "_scene")()
-    ot, dt, _ = _trees(env, s)
+@pytest.mark.parametrize("maker,builder", [("tiny", "lbvh"), ("small_frame", "lbvh"), ("frame", "lbvh"),
+                                           ("tiny", "saoh"), ("small_frame", "saoh"), ("frame", "saoh"),
+                                           ("sky", "saoh")])
+def test_tree_matches_oracle_bit_exact(env, maker, builder):
+    s = getattr(scenes, maker + "_scene")(**({"width": 64, "height": 32} if maker == "sky" else {}))
+    ot, dt, _ = _trees(env, s, builder)
     ex = dt.export()
     assert np.array_equal(ex["perm"], ot.perm)
     assert np.array_equal(ex["left"], ot.left) and np.array_equal(ex["right"], ot.right)
@@ -56,13 +59,15 @@ def test_tree_matches_oracle_bit_exact(env, maker):
     dict(reward="literal", cut_size=8),
     dict(split_iterations=4),
     dict(split_iterations=16, precision="bf16"),
+    dict(builder="saoh"),
+    dict(builder="saoh", mode="uniform", jitter=True),
 ])
 def test_lockstep_learning_tiny(env, variant):
     """Eight passes of the tiny scene. At each pass the oracle's state is
     imported; sampling, Eq. 1 + Eq. 2 and split-collapse are compared."""
     O, rll, ctx = env["O"], env["rll"], env["ctx"]
     s = scenes.tiny_scene(jitter=variant.get("jitter", False))
-    ot, dt, d = _trees(env, s)
+    ot, dt, d = _trees(env, s, variant.get("builder", "lbvh"))
     okw = {k: v for k, v in variant.items()
            if k in ("mode", "precision", "reward", "cut_size", "split_iterations")}
     og = O.Grid.for_scene(ot, s, **okw)
