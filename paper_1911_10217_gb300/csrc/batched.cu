@@ -8,9 +8,11 @@
 //      of per-item tile counts. Per point the same device code as the
 //      single-grid kernel runs (sample_core.cuh). Records of all items go to
 //      one array with keys ((cell_base_i + slot) << 6) | cluster.
-//   2. one stable radix sort of all records, one cell-head pass, then
-//      k_learn_batched: one warp per touched cell (item found by binary search
-//      over the per-item cell prefix) runs Eq. 1 + Eq. 2 (learn_core.cuh).
+//   2. the bucketed learning step of the single grid (bucket_learn.cuh) over
+//      all items' cells: records counted and scattered into one bucket per
+//      global cell, then one warp (or block) per touched cell orders its bucket
+//      by (cluster, sample) and runs Eq. 1 + Eq. 2 on the item's rows (item
+//      found by binary search over the per-item cell prefix).
 //   3. k_split_batched: split-collapse of every touched cell.
 //   4. k_advance: every item's frame counter += 1 on the device, so the pass
 //      can be recorded once as a CUDA graph and launched repeatedly.
@@ -22,6 +24,7 @@
 #include <new>
 #include <vector>
 
+#include "bucket_learn.cuh"
 #include "learn_core.cuh"
 #include "rll_device.cuh"
 #include "rll_internal.h"
@@ -104,34 +107,28 @@ __device__ __forceinline__ int item_of_cell(const uint32_t* __restrict__ cell_pr
     return lo;
 }
 
-struct CellKey {
-    uint32_t clamp, cell;
-    __device__ __forceinline__ bool same(uint32_t k) const { return k < clamp && (k >> kBatchClusterBits) == cell; }
+// record key ((cell_base + slot) << kBatchClusterBits) | cluster of many grids
+struct BatchDec {
+    uint32_t clamp;  // total cells << kBatchClusterBits
+    __device__ __forceinline__ bool valid(uint32_t k) const { return k < clamp; }
+    __device__ __forceinline__ uint32_t cell(uint32_t k) const { return k >> kBatchClusterBits; }
     __device__ __forceinline__ uint32_t cluster(uint32_t k) const { return k & ((1u << kBatchClusterBits) - 1u); }
 };
 
+// rows of a global cell: its item's table row and learning parameters
 template <int P>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_learn_batched(const BatchItemDev* __restrict__ items, int n_items, const uint32_t* __restrict__ cell_prefix,
-                const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, int64_t n, uint32_t clamp,
-                const uint32_t* __restrict__ touched, const uint32_t* __restrict__ touched_start,
-                const uint32_t* __restrict__ n_touched)
-{
-    using T = typename Store<P>::T;
-    __shared__ float s_q[kWarpsPerBlock][kMaxCut];
-    __shared__ float s_c[kWarpsPerBlock][kMaxCut];
-    __shared__ uint16_t s_b[kWarpsPerBlock][kMaxCut];
-    const int warp = threadIdx.x >> 5;
-    const uint32_t total = *n_touched;
-    for (uint32_t w = blockIdx.x * kWarpsPerBlock + warp; w < total; w += gridDim.x * kWarpsPerBlock) {
-        const uint32_t cell = touched[w];
+struct BatchRows {
+    const BatchItemDev* items;
+    int n_items;
+    const uint32_t* cell_prefix;
+    __device__ __forceinline__ RowRef<P> row(uint32_t cell) const
+    {
         const BatchItemDev& it = items[item_of_cell(cell_prefix, n_items, cell)];
-        const int64_t row = (int64_t)(cell - it.cell_base) * it.s.M;
-        const CellKey key{clamp, cell};
-        learn_one_cell<P>(sk, sv, n, touched_start[w], key, (T*)it.Q + row, (T*)it.C + row, it.s.m, it.alpha, it.eps,
-                          s_q[warp], s_c[warp], s_b[warp]);
+        const int64_t r = (int64_t)(cell - it.cell_base) * it.s.M;
+        return RowRef<P>{(typename Store<P>::T*)it.Q + r, (typename Store<P>::T*)it.C + r, it.s.M, it.s.m, it.alpha,
+                         it.eps};
     }
-}
+};
 
 template <int P>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
@@ -185,10 +182,13 @@ struct rll_batch {
     int64_t n_records = 0;
     uint32_t* rec_key = nullptr;
     float* rec_val = nullptr;
-    void* sort_ws = nullptr;
-    uint32_t* touched = nullptr;
-    uint32_t* touched_start = nullptr;
-    uint32_t* n_touched = nullptr;
+    void* learn_ws = nullptr;          // bucketed_scratch_bytes(cap_records)
+    uint32_t* cursor = nullptr;        // [cap_cells] per-cell record cursors, zero between passes
+    uint32_t* touched = nullptr;       // [cap_cells]
+    uint32_t* touched_start = nullptr; // [cap_cells]
+    uint32_t* touched_len = nullptr;   // [cap_cells]
+    uint32_t* lists = nullptr;         // [2 cap_cells] cells for the block paths
+    uint32_t* n_touched = nullptr;     // [4] learning counters
     int max_boxes = 0;
     uint32_t* status = nullptr;
     int32_t cap_items = 0;
@@ -211,9 +211,12 @@ void free_batch(rll_batch* b)
     cudaFree(b->d_work);
     cudaFree(b->rec_key);
     cudaFree(b->rec_val);
-    cudaFree(b->sort_ws);
+    cudaFree(b->learn_ws);
+    cudaFree(b->cursor);
     cudaFree(b->touched);
     cudaFree(b->touched_start);
+    cudaFree(b->touched_len);
+    cudaFree(b->lists);
     cudaFree(b->n_touched);
     delete b;
 }
@@ -274,20 +277,18 @@ cudaError_t launch_sample(rll_batch* b, cudaStream_t s)
 template <int P>
 cudaError_t launch_learn_t(rll_batch* b, cudaStream_t s, bool do_split)
 {
-    const uint32_t clamp = b->total_cells << kBatchClusterBits;
-    cudaError_t e = cudaMemsetAsync(b->n_touched, 0, sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(b->n_touched, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess || b->n_records == 0) return e;
-    uint32_t *sk, *sv;
-    e = radix_sort_pairs(s, b->rec_key, reinterpret_cast<const uint32_t*>(b->rec_val), b->n_records,
-                         key_bits((uint64_t)clamp + 1), clamp, b->sort_ws, &sk, &sv);
+    const int sms = device_sm_count(b->device);
+    e = launch_bucketed_learn<P>(s, b->device, sms, b->rec_key, b->rec_val, b->n_records,
+                                 BatchDec{b->total_cells << kBatchClusterBits},
+                                 BatchRows<P>{b->d_items, b->n, b->d_cell_prefix}, b->total_cells, b->cursor,
+                                 b->touched, b->touched_start, b->touched_len, b->n_touched, b->lists, b->learn_ws,
+                                 b->status);
     if (e != cudaSuccess) return e;
-    launch_cell_heads(s, sk, b->n_records, clamp, 1u << kBatchClusterBits, b->touched, b->touched_start, b->n_touched);
-    const int blocks = device_sm_count(b->device) * 8;
-    k_learn_batched<P><<<blocks, kWarpsPerBlock * 32, 0, s>>>(b->d_items, b->n, b->d_cell_prefix, sk, sv, b->n_records,
-                                                               clamp, b->touched, b->touched_start, b->n_touched);
     if (do_split)
-        k_split_batched<P><<<blocks, kWarpsPerBlock * 32, 0, s>>>(b->d_items, b->n, b->d_cell_prefix, b->touched,
-                                                                   b->n_touched, b->status);
+        k_split_batched<P><<<sms * 8, kWarpsPerBlock * 32, 0, s>>>(b->d_items, b->n, b->d_cell_prefix, b->touched,
+                                                                    b->n_touched, b->status);
     return cudaGetLastError();
 }
 
@@ -341,15 +342,23 @@ int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int6
     b->cap_cells = max_cells;
     cudaError_t e = cudaMalloc((void**)&b->rec_key, 4 * std::max<size_t>(max_records, 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->rec_val, 4 * std::max<size_t>(max_records, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->sort_ws, radix_sort_scratch_bytes(max_records));
+    if (e == cudaSuccess) e = cudaMalloc(&b->learn_ws, bucketed_scratch_bytes(std::max<int64_t>(max_records, 1)));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->cursor, 4 * (size_t)max_cells);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched, 4 * (size_t)max_cells);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched_start, 4 * (size_t)max_cells);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->n_touched, 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched_len, 4 * (size_t)max_cells);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->lists, 8 * (size_t)max_cells);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->n_touched, 16);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->cursor, 0, 4 * (size_t)max_cells, ctx->stream);
+    // the learning step's shared-memory opt-in, now rather than during a graph capture
+    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP32, BatchRows<RLL_PREC_FP32>>(ctx->device);
+    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP16, BatchRows<RLL_PREC_FP16>>(ctx->device);
+    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_BF16, BatchRows<RLL_PREC_BF16>>(ctx->device);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_work, 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, sizeof(BatchItemDev) * max_items);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tile_prefix, 4 * (max_items + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cell_prefix, 4 * (max_items + 1));
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->n_touched, 0, 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->n_touched, 0, 16, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         const int rc = check_cuda(ctx, e, "batch allocation");

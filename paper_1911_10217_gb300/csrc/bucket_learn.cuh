@@ -1,0 +1,499 @@
+// Learning step on records bucketed by cell (Section 3, Eq. 1 and Eq. 2),
+// shared by the single-grid entry point (learn.cu) and the batched form
+// (batched.cu). A key decoder (valid / cell / cluster of a record key) and a
+// row map (Q and C rows, cut size and length, alpha and eps of a cell) adapt
+// it to either record layout. See learn.cu for the method notes.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "learn_core.cuh"
+#include "rll_device.cuh"
+
+namespace rll {
+namespace {  // every translation unit that includes this header gets its own copies
+
+// one cell's rows and learning parameters
+template <int P>
+struct RowRef {
+    typename Store<P>::T* Q;
+    typename Store<P>::T* C;
+    uint32_t M, m;
+    float alpha, eps;
+};
+
+// ---------------------------------------------------------------- bucketed learning
+// counters ctr[4]: [0] touched cells, [1] bucket space claimed, [2] cells for
+// the sorting block path, [3] cells for the grouping block path; lists[2 *
+// cells]: the grouping list, then the sorting list
+constexpr int kBucketThreads = 256;
+constexpr int kTilesPerWarp = 4;         // 32-record tiles one warp counts / scatters
+constexpr uint32_t kWarpBucket = 240;    // records of a cell one warp orders in shared memory
+constexpr uint32_t kBlockGroup = 1024;   // records of a cell one block orders by grouping and ranking
+constexpr int kGroupThreads = 256;
+constexpr uint32_t kBlockSort = 8192;    // records of a cell one block sorts in shared memory (power of 2)
+constexpr size_t kBigSmem = kBlockSort * (sizeof(unsigned long long) + sizeof(uint32_t));
+constexpr int kBigThreads = 512;
+
+// 1. record counts per cell; the first adder appends the cell to the touched
+// list. Each warp takes kTilesPerWarp tiles of 32 consecutive records.
+template <class Dec>
+__global__ void __launch_bounds__(kBucketThreads)
+k_bucket_count(const uint32_t* __restrict__ rec_key, int64_t n, Dec dec, uint32_t* __restrict__ cursor,
+               uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t tile0 = ((int64_t)blockIdx.x * (kBucketThreads / 32) + (threadIdx.x >> 5)) * kTilesPerWarp;
+    uint32_t slot[kTilesPerWarp], peers[kTilesPerWarp], old[kTilesPerWarp];
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        const int64_t i = (tile0 + u) * 32 + lane;
+        const uint32_t key = i < n ? __ldg(rec_key + i) : 0xFFFFFFFFu;
+        slot[u] = dec.valid(key) ? dec.cell(key) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) peers[u] = __match_any_sync(0xffffffffu, slot[u]);
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        old[u] = 1u;
+        if (slot[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
+            old[u] = atomicAdd(cursor + slot[u], (uint32_t)__popc(peers[u]));
+    }
+    // cells this lane saw first: one append per warp for all of them
+    uint32_t fresh = 0;
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) fresh += old[u] == 0u;
+    uint32_t x = fresh;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    uint32_t base = 0;
+    if (lane == 31 && x) base = atomicAdd(ctr, x);
+    base = __shfl_sync(0xffffffffu, base, 31) + x - fresh;
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u)
+        if (old[u] == 0u) touched[base++] = slot[u];
+}
+
+// 2. one contiguous bucket per touched cell (one atomic per warp)
+__global__ void __launch_bounds__(kBucketThreads)
+k_bucket_claim(const uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr, uint32_t* __restrict__ cursor,
+               uint32_t* __restrict__ start, uint32_t* __restrict__ len)
+{
+    const uint32_t total = *(volatile uint32_t*)ctr;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < total; w += warps) {
+        const uint32_t c = w * 32 + lane;
+        const uint32_t slot = c < total ? touched[c] : 0u;
+        const uint32_t cnt = c < total ? cursor[slot] : 0u;
+        uint32_t x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t base = 0;
+        if (lane == 31) base = atomicAdd(ctr + 1, x);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (c < total) {
+            start[c] = base + x - cnt;
+            len[c] = cnt;
+            cursor[slot] = base + x - cnt;
+        }
+    }
+}
+
+// 3. every record to its cell's bucket: sample id, cluster and reward (a
+// warp's lanes that share a cell take consecutive places; the order inside a
+// bucket depends on scheduling and is restored by the per-cell ordering)
+// Bucket entry of a record: sample id, cluster, reward bits (three arrays)
+struct Bucket {
+    uint32_t* sid;
+    uint8_t* s;
+    uint32_t* val;
+};
+
+template <class Dec>
+__global__ void __launch_bounds__(kBucketThreads)
+k_bucket_scatter(const uint32_t* __restrict__ rec_key, const float* __restrict__ rec_val, int64_t n, Dec dec,
+                 uint32_t* __restrict__ cursor, Bucket bucket)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t tile0 = ((int64_t)blockIdx.x * (kBucketThreads / 32) + (threadIdx.x >> 5)) * kTilesPerWarp;
+    uint32_t slot[kTilesPerWarp], clus[kTilesPerWarp], val[kTilesPerWarp], peers[kTilesPerWarp],
+        base[kTilesPerWarp];
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        const int64_t i = (tile0 + u) * 32 + lane;
+        const uint32_t key = i < n ? __ldg(rec_key + i) : 0xFFFFFFFFu;
+        val[u] = i < n ? __float_as_uint(__ldg(rec_val + i)) : 0u;
+        slot[u] = dec.valid(key) ? dec.cell(key) : 0xFFFFFFFFu;
+        clus[u] = dec.valid(key) ? dec.cluster(key) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) peers[u] = __match_any_sync(0xffffffffu, slot[u]);
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        base[u] = 0u;
+        if (slot[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
+            base[u] = atomicAdd(cursor + slot[u], (uint32_t)__popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        const uint32_t b = __shfl_sync(0xffffffffu, base[u], __ffs(peers[u]) - 1);
+        if (slot[u] != 0xFFFFFFFFu) {
+            const uint32_t d = b + __popc(peers[u] & lanemask_lt());
+            bucket.sid[d] = (uint32_t)((tile0 + u) * 32 + lane);
+            bucket.s[d] = (uint8_t)clus[u];
+            bucket.val[d] = val[u];
+        }
+    }
+}
+
+// Shared arrays of one team (a warp or a block) ordering one cell's records:
+// A = bucket order, then (cluster, sample) order; B = grouped by cluster,
+// then the cdf scratch.
+template <uint32_t CAP>
+struct CellOrder {
+    uint32_t a_sid[CAP];
+    uint32_t a_val[CAP];
+    uint32_t b_sid[CAP];
+    uint32_t b_val[CAP];
+    uint8_t a_s[CAP];
+    uint8_t b_s[CAP];
+    uint32_t start[kMaxCut];  // first position of each cluster in B
+    uint32_t cur[kMaxCut];    // scatter cursors, then one past the last position
+    float q[kMaxCut];
+};
+
+// A team orders one cell; its first warp (lead()) also scans and composes.
+struct WarpTeam {
+    __device__ __forceinline__ uint32_t tid() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ uint32_t size() const { return 32; }
+    __device__ __forceinline__ bool lead() const { return true; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+struct BlockTeam {
+    __device__ __forceinline__ uint32_t tid() const { return threadIdx.x; }
+    __device__ __forceinline__ uint32_t size() const { return blockDim.x; }
+    __device__ __forceinline__ bool lead() const { return threadIdx.x < 32; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+template <int P>
+__device__ __forceinline__ void load_q_row(const typename Store<P>::T* qrow, uint32_t m, float* q)
+{
+    for (uint32_t s = threadIdx.x & 31; s < m; s += 32) q[s] = Store<P>::load(qrow[s]);
+}
+
+template <int P>
+__device__ __forceinline__ void store_q_row(typename Store<P>::T* qrow, uint32_t m, float* q)
+{
+    for (uint32_t s = threadIdx.x & 31; s < m; s += 32) {
+        const typename Store<P>::T st = Store<P>::store(q[s]);
+        qrow[s] = st;
+        q[s] = Store<P>::load(st);
+    }
+}
+
+// Eq. 1 + Eq. 2 of one cell from its bucket of nr <= CAP records: grouped
+// by cluster (counting sort, any order inside a group), then each record's
+// rank by sample id inside its group is counted, which puts them in
+// (cluster, sample) order; warp 0 of the team composes, stores Q and
+// rebuilds C. Called by every thread of the team.
+template <int P, uint32_t CAP, class Team>
+__device__ void learn_cell_grouped(Team team, CellOrder<CAP>& o, const uint32_t* __restrict__ bsid,
+                                   const uint8_t* __restrict__ bs, const uint32_t* __restrict__ bval, uint32_t nr,
+                                   uint32_t M, uint32_t m, float alpha, float eps, typename Store<P>::T* qrow,
+                                   typename Store<P>::T* crow, uint32_t* status)
+{
+    const uint32_t t = team.tid(), T = team.size();
+    const int lane = threadIdx.x & 31;
+    const bool w0 = team.lead();
+    for (uint32_t s = t; s < M; s += T) o.start[s] = 0u;
+    if (w0) load_q_row<P>(qrow, m, o.q);
+    team.sync();
+    for (uint32_t k = t; k < nr; k += T) {
+        const uint32_t s = bs[k];
+        o.a_sid[k] = bsid[k];
+        o.a_val[k] = bval[k];
+        o.a_s[k] = (uint8_t)s;
+        atomicAdd(&o.start[s], 1u);
+    }
+    team.sync();
+    if (w0) {  // cluster starts: exclusive scan over M bins, ipl consecutive bins a lane
+        const uint32_t ipl = (M + 31) >> 5, lo = lane * ipl, hi = min(M, lo + ipl);
+        uint32_t sum = 0;
+        for (uint32_t s = lo; s < hi; ++s) sum += o.start[s];
+        uint32_t y = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, y, d);
+            if (lane >= d) y += v;
+        }
+        uint32_t run = y - sum;
+        for (uint32_t s = lo; s < hi; ++s) {
+            const uint32_t c = o.start[s];
+            o.start[s] = run;
+            o.cur[s] = run;
+            run += c;
+        }
+    }
+    team.sync();
+    for (uint32_t k = t; k < nr; k += T) {
+        const uint32_t s = o.a_s[k];
+        const uint32_t d = atomicAdd(&o.cur[s], 1u);
+        if (d >= nr) {  // impossible unless the counts are corrupt: flag, skip the write
+            atomicOr(status, (uint32_t)RLL_E_DEVICE);
+            continue;
+        }
+        o.b_sid[d] = o.a_sid[k];
+        o.b_val[d] = o.a_val[k];
+        o.b_s[d] = (uint8_t)s;
+    }
+    team.sync();
+    for (uint32_t k = t; k < nr; k += T) {
+        const uint32_t s = o.b_s[k], sid = o.b_sid[k];
+        const uint32_t lo = o.start[s], hi = o.cur[s];
+        const uint32_t end = min(hi, nr);
+        uint32_t rank = 0, j = lo;
+        for (; j + 4 <= end; j += 4) {
+            const uint32_t x0 = o.b_sid[j], x1 = o.b_sid[j + 1], x2 = o.b_sid[j + 2], x3 = o.b_sid[j + 3];
+            rank += (x0 < sid) + (x1 < sid) + (x2 < sid) + (x3 < sid);
+        }
+        for (; j < end; ++j) rank += o.b_sid[j] < sid;
+        if (lo + rank >= nr) {
+            atomicOr(status, (uint32_t)RLL_E_DEVICE);
+            continue;
+        }
+        o.a_s[lo + rank] = (uint8_t)s;
+        o.a_val[lo + rank] = o.b_val[k];
+    }
+    team.sync();
+    if (T == 32) {
+        learn_records<P>([&](uint32_t j) { return make_uint2(o.a_s[j], o.a_val[j]); }, nr, m, alpha, o.q);
+    } else {  // a block: warp w composes the groups of clusters w, w + warps, ...
+        const uint32_t warps = T >> 5;
+        for (uint32_t s = threadIdx.x >> 5; s < M; s += warps) {
+            const uint32_t lo = o.start[s], hi = o.cur[s];
+            if (hi > lo)
+                learn_records<P>([&](uint32_t j) { return make_uint2(o.a_s[lo + j], o.a_val[lo + j]); }, hi - lo,
+                                 m, alpha, o.q);
+        }
+        team.sync();
+    }
+    if (w0) {
+        store_q_row<P>(qrow, m, o.q);
+        __syncwarp();
+        warp_rebuild_cdf<P>(o.q, (int)m, eps, crow, reinterpret_cast<float*>(o.b_sid),
+                            reinterpret_cast<uint16_t*>(o.b_val));
+    }
+}
+
+// 4. one warp per cell of a list (list == nullptr: every touched cell) with
+// at most CAP records; a larger cell is appended to the next list (`next`,
+// its count at *next_count) for the block path.
+template <int P, uint32_t CAP, int WARPS, int MINB, class Rows>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+k_learn_tier(const Bucket bucket, const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count,
+             uint32_t* __restrict__ next, uint32_t* __restrict__ next_count, const uint32_t* __restrict__ touched,
+             const uint32_t* __restrict__ start, const uint32_t* __restrict__ len, uint32_t* __restrict__ cursor,
+             Rows rows, uint32_t* __restrict__ status)
+{
+    __shared__ CellOrder<CAP> orders[WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t total = *(volatile const uint32_t*)list_count;
+    for (uint32_t i = blockIdx.x * WARPS + warp; i < total; i += gridDim.x * WARPS) {
+        const uint32_t w = list ? list[i] : i;
+        const uint32_t slot = touched[w], nr = len[w];
+        if (nr > CAP) {
+            if (lane == 0) next[atomicAdd(next_count, 1u)] = w;
+            continue;
+        }
+        const RowRef<P> r = rows.row(slot);
+        const uint32_t b0 = start[w];
+        learn_cell_grouped<P>(WarpTeam{}, orders[warp], bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M,
+                              r.m, r.alpha, r.eps, r.Q, r.C, status);
+        if (lane == 0) cursor[slot] = 0u;
+    }
+}
+
+// Eq. 1 of one cell whose records are sorted by (cluster, sample id), by a
+// whole block: cluster s occupies positions gs[s] .. ge[s]; cls(j) is the
+// cluster and val(j) the reward bits of record j. Warp w composes clusters
+// w, w + warps, ... (disjoint Q entries). All threads of the block call it.
+template <int P, class Cls, class Val>
+__device__ void compose_sorted_block(Cls cls, Val val, uint32_t nr, uint32_t M, uint32_t m, float alpha, float* q,
+                                     uint32_t* gs, uint32_t* ge)
+{
+    for (uint32_t s = threadIdx.x; s < M; s += blockDim.x) gs[s] = ge[s] = 0u;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < nr; j += blockDim.x) {
+        const uint32_t s = cls(j);
+        if (s >= M) continue;
+        if (j == 0 || cls(j - 1) != s) gs[s] = j;
+        if (j + 1 == nr || cls(j + 1) != s) ge[s] = j + 1;
+    }
+    __syncthreads();
+    const uint32_t warps = blockDim.x >> 5;
+    for (uint32_t s = threadIdx.x >> 5; s < M; s += warps) {
+        const uint32_t lo = gs[s], hi = ge[s];
+        if (hi > lo) learn_records<P>([&](uint32_t j) { return make_uint2(s, val(lo + j)); }, hi - lo, m, alpha, q);
+    }
+    __syncthreads();
+}
+
+// 5a. one block per cell of the grouping list (up to kBlockGroup records):
+// the ordering of the warp path done by the whole block, warps composing
+// different clusters in parallel; larger cells go to the sorting list.
+template <int P, class Rows>
+__global__ void __launch_bounds__(kGroupThreads)
+k_learn_group(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t* __restrict__ touched,
+              const uint32_t* __restrict__ start, const uint32_t* __restrict__ len, const uint32_t* __restrict__ list,
+              uint32_t* __restrict__ next, uint32_t* __restrict__ cursor, Rows rows, uint32_t* __restrict__ status)
+{
+    __shared__ CellOrder<kBlockGroup> o;
+    const uint32_t n = *(volatile const uint32_t*)(ctr + 3);
+    for (uint32_t bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const uint32_t w = list[bi];
+        const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
+        if (nr > kBlockGroup) {
+            if (threadIdx.x == 0) next[atomicAdd(ctr + 2, 1u)] = w;
+            continue;  // uniform across the block
+        }
+        const RowRef<P> r = rows.row(slot);
+        learn_cell_grouped<P>(BlockTeam{}, o, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M, r.m, r.alpha,
+                              r.eps, r.Q, r.C, status);
+        if (threadIdx.x == 0) cursor[slot] = 0u;
+        __syncthreads();
+    }
+}
+
+// 5b. one block per cell of the sorting list. Up to kBlockSort records: keys
+// cluster << 45 | sample id << 13 | bucket index sorted by a bitonic network
+// in shared memory, rewards gathered in that order. Larger cells: (cluster
+// << 32 | sample id) sorted in place in global scratch, rewards read by
+// sample id. Then Eq. 1 (warps composing different clusters) and Eq. 2.
+template <int P, class Rows>
+__global__ void __launch_bounds__(kBigThreads)
+k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const float* __restrict__ rec_val,
+            const uint32_t* __restrict__ ctr,
+            const uint32_t* __restrict__ touched, const uint32_t* __restrict__ start,
+            const uint32_t* __restrict__ len, const uint32_t* __restrict__ big, uint32_t* __restrict__ cursor,
+            Rows rows, uint32_t* __restrict__ status)
+{
+    extern __shared__ unsigned long long s_key[];      // kBlockSort keys, then kBlockSort rewards (u32)
+    uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kBlockSort);
+    __shared__ float s_q[kMaxCut], s_c[kMaxCut];
+    __shared__ uint16_t s_b[kMaxCut];
+    __shared__ uint32_t s_gs[kMaxCut], s_ge[kMaxCut];
+    const uint32_t n_big = *(volatile const uint32_t*)(ctr + 2);
+    for (uint32_t bi = blockIdx.x; bi < n_big; bi += gridDim.x) {
+        const uint32_t w = big[bi];
+        const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
+        const RowRef<P> r = rows.row(slot);
+        const uint32_t M = r.M, m = r.m;
+        const float alpha = r.alpha;
+        if (threadIdx.x < 32) load_q_row<P>(r.Q, m, s_q);
+        if (nr <= kBlockSort) {
+            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x)
+                s_key[k] = ((unsigned long long)bucket.s[b0 + k] << 45) |
+                           ((unsigned long long)bucket.sid[b0 + k] << 13) | k;
+            __syncthreads();
+            bitonic_sort_u64(s_key, nr, threadIdx.x, blockDim.x, BlockSync{});
+            for (uint32_t j = threadIdx.x; j < nr; j += blockDim.x)
+                s_val[j] = bucket.val[b0 + (uint32_t)(s_key[j] & (kBlockSort - 1))];
+            __syncthreads();
+            compose_sorted_block<P>([&](uint32_t j) { return (uint32_t)(s_key[j] >> 45); },
+                                    [&](uint32_t j) { return s_val[j]; }, nr, M, m, alpha, s_q, s_gs, s_ge);
+        } else {
+            unsigned long long* rec = wide + b0;
+            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x)
+                rec[k] = ((unsigned long long)bucket.s[b0 + k] << 32) | bucket.sid[b0 + k];
+            __syncthreads();
+            bitonic_sort_u64(rec, nr, threadIdx.x, blockDim.x, BlockSync{});
+            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x) {
+                const unsigned long long e = rec[k];
+                rec[k] = (e & 0xFFFFFFFF00000000ull) | __float_as_uint(__ldg(rec_val + (uint32_t)e));
+            }
+            __syncthreads();
+            compose_sorted_block<P>([&](uint32_t j) { return (uint32_t)(rec[j] >> 32); },
+                                    [&](uint32_t j) { return (uint32_t)rec[j]; }, nr, M, m, alpha, s_q, s_gs, s_ge);
+        }
+        if (threadIdx.x < 32) {
+            store_q_row<P>(r.Q, m, s_q);
+            __syncwarp();
+            warp_rebuild_cdf<P>(s_q, (int)m, r.eps, r.C, s_c, s_b);
+            if (threadIdx.x == 0) cursor[slot] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+// k_learn_big's shared-memory opt-in (above the 48 KB default), once per
+// device and precision
+template <int P, class Rows>
+cudaError_t big_smem_attribute(int device)
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (device >= 0 && device < 64 && done[device]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_learn_big<P, Rows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kBigSmem);
+    if (e == cudaSuccess && device >= 0 && device < 64) done[device] = true;
+    return e;
+}
+
+// scratch of launch_bucketed_learn for n records: bucket sample ids (4 B),
+// rewards (4 B), clusters (1 B) and the in-place sort buffer (8 B, used only by
+// cells above kBlockSort records)
+inline size_t bucketed_scratch_bytes(int64_t n)
+{
+    const size_t n4 = ((size_t)n * 4 + 255) & ~(size_t)255, n1 = ((size_t)n + 255) & ~(size_t)255;
+    return 2 * n4 + n1 + 8 * (size_t)n;
+}
+
+// Enqueues the whole learning step for n >= 1 records. The caller has
+// zeroed ctr[0..3] on the stream and holds `cursor` [cells] at zero (left at
+// zero again); touched, start, len [cells] and lists [2 * cells] are outputs
+// and scratch.
+template <int P, class Dec, class Rows>
+cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uint32_t* rec_key,
+                                  const float* rec_val, int64_t n, Dec dec, Rows rows, uint32_t cells,
+                                  uint32_t* cursor, uint32_t* touched, uint32_t* start, uint32_t* len,
+                                  uint32_t* ctr, uint32_t* lists, void* scratch, uint32_t* status)
+{
+    const size_t n4 = ((size_t)n * 4 + 255) & ~(size_t)255, n1 = ((size_t)n + 255) & ~(size_t)255;
+    char* ws = static_cast<char*>(scratch);
+    Bucket bucket{reinterpret_cast<uint32_t*>(ws), reinterpret_cast<uint8_t*>(ws + 2 * n4),
+                  reinterpret_cast<uint32_t*>(ws + n4)};
+    auto* wide = reinterpret_cast<unsigned long long*>(ws + 2 * n4 + n1);
+    const int64_t per_block = (int64_t)kBucketThreads * kTilesPerWarp;
+    const unsigned rblocks = (unsigned)((n + per_block - 1) / per_block);
+    uint32_t* group_list = lists;
+    uint32_t* sort_list = lists + cells;
+    k_bucket_count<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, n, dec, cursor, touched, ctr);
+    k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(touched, ctr, cursor, start, len);
+    k_bucket_scatter<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, dec, cursor, bucket);
+    k_learn_tier<P, kWarpBucket, 6, 5, Rows><<<sms * 5, 6 * 32, 0, s>>>(
+        bucket, nullptr, ctr, group_list, ctr + 3, touched, start, len, cursor, rows, status);
+    k_learn_group<P, Rows><<<sms * 4, kGroupThreads, 0, s>>>(bucket, ctr, touched, start, len, group_list, sort_list,
+                                                              cursor, rows, status);
+    cudaError_t e = big_smem_attribute<P, Rows>(device);
+    if (e != cudaSuccess) return e;
+    k_learn_big<P, Rows><<<sms * 2, kBigThreads, kBigSmem, s>>>(bucket, wide, rec_val, ctr, touched, start, len,
+                                                               sort_list, cursor, rows, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace rll

@@ -104,9 +104,6 @@ int grid_init(rll_ctx* ctx, rll_grid* g);
 int grid_to_float(rll_ctx* ctx, const rll_grid* g, float* q_out, float* c_out);   // device out
 int grid_from_float(rll_ctx* ctx, rll_grid* g, const float* q_in, const float* c_in); // device in
 int grid_mark_occupied(rll_ctx* ctx, rll_grid* g);  // touched list := every occupied slot
-// one entry (cell = key / M, first sorted record) per cell of sorted keys < HM
-void launch_cell_heads(cudaStream_t s, const uint32_t* sk, int64_t n, uint32_t HM, uint32_t M, uint32_t* touched,
-                       uint32_t* touched_start, uint32_t* n_touched);
 int key_bits(uint64_t hm_plus_one);
 int device_sm_count(int device);
 // split-collapse steps per cell and call (0 reads as 1)
