@@ -220,10 +220,12 @@ int rll_sample_power(rll_ctx* ctx, const rll_tree* tree, const float* pos, const
 
 /* Applies Eq. 1, Q(s) := (1 - alpha) Q(s) + alpha |c|, for every record, in
  * sample order per (cell, cluster) -- a deterministic segmented reduction
- * (stable radix sort by key, then one warp per touched cell composing the
- * affine updates) -- then rebuilds C of every touched cell by Eq. 2 with the
- * eps floor. Records with key 0xFFFFFFFF are skipped. Remembers the touched
- * cells for rll_split_collapse. Uses library-owned scratch memory. */
+ * (records bucketed by cell, each bucket ordered by (cluster, sample id),
+ * then the affine updates composed per cluster) -- then rebuilds C of every
+ * touched cell by Eq. 2 with the eps floor. Records with key 0xFFFFFFFF (or
+ * any key >= slots * cut_size) are skipped. Remembers the touched cells for
+ * rll_split_collapse. Uses library-owned scratch memory (17 bytes per
+ * record, grown with cudaMalloc when needed). At most 2^32 - 1 records. */
 int rll_learn_update(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key, const float* rec_val,
                      int64_t n_records);
 
