@@ -37,6 +37,7 @@
 #define ORC_PREC_BF16 2
 #define ORC_MODE_DESCENT 0
 #define ORC_MODE_UNIFORM 1
+#define ORC_MODE_DESCENT2 2
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random        */
@@ -936,6 +937,52 @@ typedef struct {
 
 static double orc_min(double a, double b) { return a < b ? a : b; }
 
+/* Two-level descent (reading of the in-cluster choice): from internal node g
+ * the candidates are the children of g's children, a child that is a single
+ * light standing for itself (2 to 4 candidates, in light order). Candidate i
+ * has weight w_i = num_i / max(den_i, 1e-30) (binary32, its descent bound);
+ * if all weights are 0 the candidates' powers are used, if those are 0 too
+ * the choice is uniform. With the binary32 prefix sums P_i = w_0 + ... + w_i
+ * (in order) and S = P_{k-1}, the chosen candidate is the first i with
+ * u S < P_i, and its probability is (P_i - P_{i-1}) / S. */
+static int orc_frontier(const orc_tree* t, int32_t g, int32_t cand[4])
+{
+    int64_t nl = t->n;
+    int k = 0;
+    int32_t kids[2] = {t->left[g], t->right[g]};
+    for (int j = 0; j < 2; ++j) {
+        int32_t x = kids[j];
+        if (x >= nl - 1) {
+            cand[k++] = x;
+        } else {
+            cand[k++] = t->left[x];
+            cand[k++] = t->right[x];
+        }
+    }
+    return k;
+}
+
+static void orc_frontier_weights(const orc_tree* t, const int32_t* cand, int k, const float x[3],
+                                 const float n[3], float w[4], int* uniform)
+{
+    float sum = 0.0f;
+    for (int i = 0; i < k; ++i) {
+        float num, den;
+        orc_importance32(REC(t, cand[i]), x, n, &num, &den);
+        w[i] = num / fmaxf(den, 1e-30f);
+        sum = sum + w[i];
+    }
+    *uniform = 0;
+    if (!(sum > 0.0f)) {
+        sum = 0.0f;
+        for (int i = 0; i < k; ++i) {
+            w[i] = REC(t, cand[i])[6];
+            sum = sum + w[i];
+        }
+        if (!(sum > 0.0f)) *uniform = 1;
+    }
+}
+
 /* descend from cut node `node` to a light; returns the light and multiplies
  * p_in; margin tracks the closest deciding draw. */
 static int64_t orc_descend(const orc_scene* sc, int mode, int32_t node, const float x[3],
@@ -954,6 +1001,38 @@ static int64_t orc_descend(const orc_scene* sc, int mode, int32_t node, const fl
     }
     *p_in = 1.0;
     uint32_t level = 0;
+    if (mode == ORC_MODE_DESCENT2) {
+        while (node < nl - 1) {
+            int32_t cand[4];
+            float w[4];
+            int uniform;
+            int k = orc_frontier(t, node, cand);
+            orc_frontier_weights(t, cand, k, x, n, w, &uniform);
+            float u = orc_draw(rs, ORC_DRAW_DESCENT + level);
+            ++level;
+            int pick = 0;
+            if (uniform) {
+                uint32_t u24 = (uint32_t)(u * 16777216.0f);
+                pick = (int)(((uint64_t)u24 * (uint64_t)k) >> 24);
+                *p_in *= 1.0 / (double)k;
+            } else {
+                float S = 0.0f, pre[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                for (int i = 0; i < k; ++i) {
+                    S = S + w[i];
+                    pre[i] = S;
+                }
+                pick = k - 1;
+                for (int i = 0; i < k; ++i)
+                    if ((double)u * (double)S < (double)pre[i]) { pick = i; break; }
+                double lo = pick > 0 ? (double)pre[pick - 1] / (double)S : 0.0;
+                double hi = (double)pre[pick] / (double)S;
+                *margin = orc_min(*margin, orc_min(fabs((double)u - lo), fabs(hi - (double)u)));
+                *p_in *= hi - lo;  /* the chosen interval of the binary32 prefix sums */
+            }
+            node = cand[pick];
+        }
+        return (int64_t)(node - (nl - 1));
+    }
     while (node < nl - 1) {
         int32_t a = t->left[node], c = t->right[node];
         float wa, wc;
@@ -1221,6 +1300,31 @@ double orc_light_pdf(const orc_tree* t, int mode, int m, const int32_t* cut, con
     double p = (C[s] - lo) / C[m - 1];
     int32_t node = cut[s];
     if (mode == ORC_MODE_UNIFORM) return p / (double)(t->end[node] - t->begin[node]);
+    if (mode == ORC_MODE_DESCENT2) {
+        while (node < nl - 1) {
+            int32_t cand[4];
+            float w[4];
+            int uniform;
+            int k = orc_frontier(t, node, cand);
+            orc_frontier_weights(t, cand, k, x, n, w, &uniform);
+            int pick = -1;
+            for (int i = 0; i < k; ++i)
+                if ((uint32_t)l >= t->begin[cand[i]] && (uint32_t)l < t->end[cand[i]]) pick = i;
+            if (uniform) {
+                p *= 1.0 / (double)k;
+            } else {
+                float S = 0.0f, pre[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                for (int i = 0; i < k; ++i) {
+                    S = S + w[i];
+                    pre[i] = S;
+                }
+                double lo = pick > 0 ? (double)pre[pick - 1] / (double)S : 0.0;
+                p *= (double)pre[pick] / (double)S - lo;
+            }
+            node = cand[pick];
+        }
+        return p;
+    }
     while (node < nl - 1) {
         int32_t a = t->left[node], c = t->right[node];
         float wa, wc;

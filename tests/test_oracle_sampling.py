@@ -48,7 +48,7 @@ def tiny(oracle_mod):
     return s, oracle_mod.Tree(s.tris, s.emission)
 
 
-@pytest.mark.parametrize("mode", ["descent", "uniform"])
+@pytest.mark.parametrize("mode", ["descent", "uniform", "descent2"])
 def test_pdf_sums_to_one(oracle_mod, tiny, mode):
     s, tree = tiny
     g = _learned_grid(oracle_mod, s, tree, iters=3, mode=mode)
@@ -61,7 +61,7 @@ def test_pdf_sums_to_one(oracle_mod, tiny, mode):
         assert np.all(p > 0)  # the floor keeps every light reachable
 
 
-@pytest.mark.parametrize("mode", ["descent", "uniform"])
+@pytest.mark.parametrize("mode", ["descent", "uniform", "descent2"])
 def test_sample_pdf_is_cut_times_descent(oracle_mod, tiny, mode):
     s, tree = tiny
     g = _learned_grid(oracle_mod, s, tree, iters=2, mode=mode)
@@ -74,9 +74,10 @@ def test_sample_pdf_is_cut_times_descent(oracle_mod, tiny, mode):
         assert out["p_cut"][r] * out["p_in"][r] == pytest.approx(p, rel=1e-12)
 
 
-def test_light_frequencies_follow_pdf(oracle_mod, tiny):
+@pytest.mark.parametrize("mode", ["descent", "descent2"])
+def test_light_frequencies_follow_pdf(oracle_mod, tiny, mode):
     s, tree = tiny
-    g = _learned_grid(oracle_mod, s, tree, iters=3)
+    g = _learned_grid(oracle_mod, s, tree, iters=3, mode=mode)
     idx = 64 * 20 + 17
     R = 200_000
     pos, nrm, alb = _repeat_point(s, idx, R)
@@ -150,13 +151,13 @@ def _mean_and_se(v):
     return v.mean(), v.std(ddof=1) / math.sqrt(v.size)
 
 
-@pytest.mark.parametrize("variant", ["fresh", "learned", "uniform", "fp16", "jitter"])
+@pytest.mark.parametrize("variant", ["fresh", "learned", "uniform", "fp16", "jitter", "descent2"])
 def test_estimator_unbiased(oracle_mod, variant):
     s = scenes.tiny_scene(jitter=(variant == "jitter"))
     tree = oracle_mod.Tree(s.tris, s.emission)
     kw = {}
-    if variant == "uniform":
-        kw["mode"] = "uniform"
+    if variant in ("uniform", "descent2"):
+        kw["mode"] = variant
     if variant == "fp16":
         kw["precision"] = "fp16"
     iters = 0 if variant == "fresh" else 4
@@ -219,3 +220,28 @@ def test_estimator_unbiased_sky_dome(oracle_mod):
         for k in range(3):
             m, se = _mean_and_se(out["rgb"][k])
             assert abs(m - ref[k]) < 5 * se + 3e-3 * ref[k] + 1e-9, (idx, k, m, ref[k], se)
+
+
+def test_two_level_step_over_two_leaves_is_the_binary_step(oracle_mod):
+    """When both children of a node are single lights the two-level step has
+    the same two candidates as the binary step, with weights in the same
+    ratio: the light pdfs of the two modes agree (to rounding)."""
+    s = scenes.tiny_scene()
+    tree = oracle_mod.Tree(s.tris, s.emission)
+    n = tree.n
+    # cut nodes whose two children are both leaves: the cut of n/2 nodes of the
+    # balanced bottom level exists when cut_size = n / 2 covers it
+    g1 = oracle_mod.Grid.for_scene(tree, s, cut_size=128, mode="descent")
+    g2 = oracle_mod.Grid.for_scene(tree, s, cut_size=128, mode="descent2")
+    cut = g1.def_cut
+    pairs = [c for c in cut if c < n - 1 and tree.left[c] >= n - 1 and tree.right[c] >= n - 1]
+    assert len(pairs) > 10
+    rng = np.random.default_rng(2)
+    for idx in rng.integers(0, s.n_points, size=4):
+        x, nn = s.pos[:, idx], s.nrm[:, idx]
+        s1 = g1.lookup_insert(g1.cell_key(x, nn))
+        s2 = g2.lookup_insert(g2.cell_key(x, nn))
+        for c in pairs[:20]:
+            for leaf in (tree.left[c], tree.right[c]):
+                l = leaf - (n - 1)
+                assert g2.light_pdf(s2, x, nn, l) == pytest.approx(g1.light_pdf(s1, x, nn, l), rel=1e-6)
