@@ -52,7 +52,7 @@ def load_peaks():
         return dict(PEAKS_FALLBACK, sm_max_mhz=2070.0), "fallback"
 
 
-def workload_config(scene, tree="lbvh"):
+def workload_config(scene, tree="lbvh", mode="descent"):
     g = scene.grid
     return {"workload": "frame-scale static walled-cells scene, 1920x1080 G-buffer on 16 planes, "
                         "64K emissive triangles in 64 patches, 64 occluder boxes, one learning pass "
@@ -60,7 +60,7 @@ def workload_config(scene, tree="lbvh"):
             "points": scene.n_points, "lights": scene.n_lights, "boxes": int(scene.boxes.shape[0]),
             "spp": scene.spp, "cut_size": g.cut_size, "table_size": g.table_size,
             "cell_size": g.cell_size, "normal_bins": g.normal_bins, "jitter": g.jitter,
-            "table_precision": "fp32", "in_cluster": "descent", "split_iterations": g.split_iterations,
+            "table_precision": "fp32", "in_cluster": mode, "split_iterations": g.split_iterations,
             "light_tree": {"lbvh": "radix tree of Morton codes", "saoh": "Morton order, SAOH split positions"}[tree],
             "l2": "flushed between timed steps (512 MB write, untimed)"}
 
@@ -788,6 +788,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
     ap.add_argument("--tree", default="lbvh", choices=["lbvh", "saoh"])
+    ap.add_argument("--mode", default="descent", choices=["descent", "descent2", "uniform"])
     ap.add_argument("--workload", default="frame",
                     choices=["frame", "batched", "serving", "dynamic", "split", "sky", "paths", "trees"])
     ap.add_argument("--trees-passes", type=int, default=256)
@@ -865,7 +866,7 @@ def main():
     P, S = scene.n_points, scene.spp
     tree = rll.Tree(ctx, tri, em, builder=args.tree)
     g = scene.grid
-    params = rll.grid_params_for(g)
+    params = rll.grid_params_for(g, mode=args.mode)
     grid = rll.Grid(ctx, tree, params)
     rgb = torch.empty(3, P, device=dev)
     key = torch.empty(P * S, dtype=torch.int32, device=dev)
@@ -960,7 +961,7 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": workload_config(scene, args.tree),
+               "config": workload_config(scene, args.tree, args.mode),
                "roofline": {"kernel": "k_sample (sample_and_shade)", "bound": "alu",
                             "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                             "frac": achieved / alu_peak, "traffic": K_SAMPLE_DRAM_BYTES,
@@ -995,9 +996,11 @@ def main():
     return 0
 
 
-def quality(rll, ctx, grid, tree, scene, pos, nrm, alb, boxes, dev):
+def quality(rll, ctx, grid, tree, scene, pos, nrm, alb, boxes, dev, frames=4):
     """MSE at 1 spp of the learned sampler and of the energy-based sampler
-    against a 256-spp energy-sampler reference (not timed)."""
+    against a 256-spp energy-sampler reference (not timed), each the mean
+    over `frames` frames (single frames are dominated by rare high-weight
+    samples)."""
     import torch
     P = scene.n_points
     ref = torch.zeros(3, P, device=dev, dtype=torch.float64)
@@ -1007,12 +1010,14 @@ def quality(rll, ctx, grid, tree, scene, pos, nrm, alb, boxes, dev):
         rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 7777, 100000 + i, 8, tmp)
         ref += tmp.double()
     ref /= n_ref
-    rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, 4242, 90000, 1, tmp)
-    mse_rll = float(((tmp.double() - ref) ** 2).mean())
-    rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 4242, 90000, 1, tmp)
-    mse_pow = float(((tmp.double() - ref) ** 2).mean())
+    mse_rll = mse_pow = 0.0
+    for f in range(frames):
+        rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, 4242, 90000 + f, 1, tmp)
+        mse_rll += float(((tmp.double() - ref) ** 2).mean()) / frames
+        rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 4242, 90000 + f, 1, tmp)
+        mse_pow += float(((tmp.double() - ref) ** 2).mean()) / frames
     return {"rll_1spp": mse_rll, "energy_sampler_1spp": mse_pow, "ratio": mse_pow / mse_rll,
-            "reference": "energy sampler, 256 spp"}
+            "reference": "energy sampler, 256 spp", "frames": frames}
 
 
 if __name__ == "__main__":

@@ -44,6 +44,10 @@ extern "C" {
 /* choice of a light inside the sampled cluster */
 #define RLL_MODE_DESCENT 0  /* stochastic descent by unoccluded bounds (default) */
 #define RLL_MODE_UNIFORM 1  /* uniform over the cluster's lights (Section 3 picks the light in the cluster at random) */
+#define RLL_MODE_DESCENT2 2 /* descent two levels at a time: from a node, one of the children of its children (a
+                               single-light child standing for itself) by their bounds (num / max(den, 1e-30));
+                               the binary32 prefix sums P_i decide: first i with u * P_last < P_i, probability
+                               (P_i - P_{i-1}) / P_last; powers, then uniform, when all bounds vanish */
 
 /* the |c| fed to Eq. 1 */
 #define RLL_REWARD_CLUSTER 0 /* luminance of c / (p_in * p_area): the cluster's contribution estimate (default) */

@@ -69,6 +69,7 @@ void free_tree(rll_tree* t)
     if (!t) return;
     cudaFree(t->nodes);
     cudaFree(t->pairs);
+    cudaFree(t->quads);
     cudaFree(t->lights);
     cudaFree(t->perm);
     cudaFree(t->left);
@@ -115,7 +116,7 @@ int check_params(rll_ctx* ctx, const rll_grid_params* p)
     if (p->normal_bins < 1 || p->normal_bins > 255) return fail(ctx, RLL_E_INVALID, "normal_bins must be in [1, 255]");
     if (p->jitter > 1) return fail(ctx, RLL_E_INVALID, "jitter must be 0 or 1");
     if (p->precision > RLL_PREC_BF16) return fail(ctx, RLL_E_INVALID, "unknown precision");
-    if (p->in_cluster_mode > RLL_MODE_UNIFORM) return fail(ctx, RLL_E_INVALID, "unknown in_cluster_mode");
+    if (p->in_cluster_mode > RLL_MODE_DESCENT2) return fail(ctx, RLL_E_INVALID, "unknown in_cluster_mode");
     if (p->reward_mode > RLL_REWARD_LITERAL) return fail(ctx, RLL_E_INVALID, "unknown reward_mode");
     if (!(p->alpha >= 0.0f && p->alpha <= 1.0f)) return fail(ctx, RLL_E_INVALID, "alpha must be in [0, 1]");
     if (!(p->threshold > 0.0f) || !std::isfinite(p->threshold)) return fail(ctx, RLL_E_INVALID, "threshold must be > 0");

@@ -261,6 +261,9 @@ cudaError_t launch_sample_p(rll_batch* b, cudaStream_t s)
     if (b->mode == RLL_MODE_UNIFORM)
         return b->min_blocks >= 4 ? launch_sample_t<P, RLL_MODE_UNIFORM, 4>(b, s)
                                   : launch_sample_t<P, RLL_MODE_UNIFORM, 3>(b, s);
+    if (b->mode == RLL_MODE_DESCENT2)
+        return b->min_blocks >= 4 ? launch_sample_t<P, RLL_MODE_DESCENT2, 4>(b, s)
+                                  : launch_sample_t<P, RLL_MODE_DESCENT2, 3>(b, s);
     return b->min_blocks >= 4 ? launch_sample_t<P, RLL_MODE_DESCENT, 4>(b, s)
                               : launch_sample_t<P, RLL_MODE_DESCENT, 3>(b, s);
 }
@@ -447,6 +450,7 @@ int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items,
         a.jitter = g->p.jitter;
         a.reward_mode = g->p.reward_mode;
         a.pairs = t->pairs;
+        a.quads = t->quads;
         a.nodes = t->nodes;
         a.lights = t->lights;
         a.light_cdf = t->light_cdf;

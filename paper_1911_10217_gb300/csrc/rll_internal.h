@@ -35,6 +35,8 @@ struct rll_tree {
     int64_t n = 0;
     rll::NodeRec* nodes = nullptr;   // [2n-1] every node
     rll::DescRec* pairs = nullptr;   // [2(n-1)] descent records of the children of internal i at 2i, 2i+1
+    rll::DescRec* quads = nullptr;   // [4(n-1)] records of the 2..4 grandchildren of internal i at 4i.. (two-level
+                                     // descent; a single-light child stands for itself; unused entries id ~0)
     rll::LightRec* lights = nullptr; // [n] sorted lights
     uint32_t* perm = nullptr;        // [n] sorted -> input index
     int32_t* left = nullptr;         // [n-1]

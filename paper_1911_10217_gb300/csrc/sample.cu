@@ -94,6 +94,7 @@ template <int P>
 cudaError_t launch_p(const SampleArgs& a, int mode, bool dbg, int minb, cudaStream_t s)
 {
     if (mode == RLL_MODE_UNIFORM) return launch_m<P, RLL_MODE_UNIFORM>(a, dbg, minb, s);
+    if (mode == RLL_MODE_DESCENT2) return launch_m<P, RLL_MODE_DESCENT2>(a, dbg, minb, s);
     return launch_m<P, RLL_MODE_DESCENT>(a, dbg, minb, s);
 }
 
@@ -129,6 +130,7 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
     a.jitter = g->p.jitter;
     a.reward_mode = g->p.reward_mode;
     a.pairs = t->pairs;
+    a.quads = t->quads;
     a.nodes = t->nodes;
     a.lights = t->lights;
     a.light_cdf = t->light_cdf;

@@ -34,6 +34,7 @@ struct SampleArgs {
     uint32_t jitter;
     uint32_t reward_mode;
     const DescRec* pairs;
+    const DescRec* quads;     // two-level descent records (4 per internal node)
     const NodeRec* nodes;
     const LightRec* lights;
     const float* light_cdf;
@@ -275,6 +276,76 @@ __device__ __forceinline__ void descent_step(const SampleArgs& a, uint32_t& node
     node = left ? L.id : R.id;
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// One step of the two-level descent below internal node `node` (ud: the
+// step's draw): candidates quads[4 node ..] (2 to 4 valid, in light order),
+// weights num / max(den, 1e-30), binary32 prefix sums in order; the first
+// prefix above u * S is chosen (exact, one fma), probability (P_i -
+// P_{i-1}) / S; powers, then uniform over the valid candidates, when all
+// weights vanish. Candidates 2 and 3 are prefetched into L1 while 0 and 1
+// are evaluated, so no registers hold them meanwhile.
+__device__ __forceinline__ void descent2_step(const SampleArgs& a, uint32_t& node, float& p_in, float ud, float x0,
+                                              float x1, float x2, float n0, float n1, float n2)
+{
+    const DescRec* q = a.quads + 4 * (int64_t)node;
+    prefetch_l1(q + 2);
+    prefetch_l1(reinterpret_cast<const char*>(q + 2) + 64);
+    float w[4];
+    bool valid3 = false, valid4 = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const DescRec A = load_desc(q + 2 * h), B = load_desc(q + 2 * h + 1);
+        const Bound ba = importance(A, x0, x1, x2, n0, n1, n2);
+        const Bound bb = importance(B, x0, x1, x2, n0, n1, n2);
+        w[2 * h] = fdiv(ba.num, fmaxf(ba.den, 1e-30f));
+        w[2 * h + 1] = fdiv(bb.num, fmaxf(bb.den, 1e-30f));
+        if (h == 1) {
+            valid3 = A.id != 0xFFFFFFFFu;
+            valid4 = B.id != 0xFFFFFFFFu;
+        }
+    }
+    const int k = 2 + valid3 + valid4;  // valid candidates come first
+    float pre[4], S = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        S = fadd(S, i < k ? w[i] : 0.0f);
+        pre[i] = S;
+    }
+    if (!(S > 0.0f)) {  // rare: the candidates' powers (read again, L1)
+        S = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            S = fadd(S, i < k ? __ldg(&q[i].phi) : 0.0f);
+            pre[i] = S;
+        }
+    }
+    int pick;
+    if (S > 0.0f) {
+        pick = k - 1;
+#pragma unroll
+        for (int i = 3; i >= 0; --i)
+            if (i < k && __fmaf_rn(ud, S, -pre[i]) < 0.0f) pick = i;
+    } else {
+        const uint32_t u24v = (uint32_t)(ud * 16777216.0f);
+        pick = (int)(((unsigned long long)u24v * (unsigned long long)k) >> 24);
+    }
+    // the chosen candidate's interval by selects (no indexed arrays), its id from L1
+    float lo = 0.0f, hi = pre[0];
+#pragma unroll
+    for (int i = 1; i < 4; ++i) {
+        if (pick == i) {
+            lo = pre[i - 1];
+            hi = pre[i];
+        }
+    }
+    p_in *= S > 0.0f ? (hi - lo) / S : 1.0f / (float)k;  // continuous: pdf only
+    node = __ldg(&q[pick].id);
+}
+
 // All samples of shading point p, one thread (s_box: see stage_boxes).
 template <int P, int MODE, bool DBG>
 __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, const float4* s_box)
@@ -300,6 +371,10 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
             const uint32_t u24v = (uint32_t)(rs.draw(kDrawUniform) * 16777216.0f);
             light = (int64_t)r.begin + (int64_t)(((unsigned long long)u24v * w) >> 24);
             p_in = 1.0f / (float)w;
+        } else if (MODE == RLL_MODE_DESCENT2) {
+            for (uint32_t level = 0; (int64_t)node < nl1; ++level)
+                descent2_step(a, node, p_in, rs.draw(kDrawDescent + level), x0, x1, x2, n0, n1, n2);
+            light = (int64_t)node - nl1;
         } else {
             for (uint32_t level = 0; (int64_t)node < nl1; ++level)
                 descent_step(a, node, p_in, rs.draw(kDrawDescent + level), x0, x1, x2, n0, n1, n2);

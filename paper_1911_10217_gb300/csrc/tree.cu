@@ -276,6 +276,32 @@ __global__ void k_pairs(int64_t n, const NodeRec* __restrict__ nodes, const int3
     if (i < n) leaf_phi[i] = nodes[n - 1 + i].phi;
 }
 
+// candidates of the two-level descent below internal node i, in light order
+__global__ void k_quads(int64_t n, const NodeRec* __restrict__ nodes, const int32_t* __restrict__ left,
+                        const int32_t* __restrict__ right, DescRec* __restrict__ quads)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int32_t cand[4];
+    int k = 0;
+    const int32_t kids[2] = {left[i], right[i]};
+    for (int j = 0; j < 2; ++j) {
+        const int32_t x = kids[j];
+        if ((int64_t)x >= n - 1) {
+            cand[k++] = x;
+        } else {
+            cand[k++] = left[x];
+            cand[k++] = right[x];
+        }
+    }
+    for (int j = 0; j < 4; ++j) {
+        DescRec d{};
+        if (j < k) d = make_desc(nodes[cand[j]]);
+        else d.id = 0xFFFFFFFFu;
+        quads[4 * i + j] = d;
+    }
+}
+
 __global__ void k_update_emission(int64_t n, const uint32_t* __restrict__ perm, const float* __restrict__ emis,
                                   LightRec* __restrict__ lights)
 {
@@ -550,6 +576,7 @@ int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
     if (e != cudaSuccess) return check_cuda(ctx, e, "cudaMalloc(tree)");
     RLL_ALLOC(t->nodes, sizeof(NodeRec) * nn);
     RLL_ALLOC(t->pairs, sizeof(DescRec) * 2 * (n - 1));
+    RLL_ALLOC(t->quads, sizeof(DescRec) * 4 * (n - 1));
     RLL_ALLOC(t->lights, sizeof(LightRec) * n);
     RLL_ALLOC(t->perm, sizeof(uint32_t) * n);
     RLL_ALLOC(t->left, sizeof(int32_t) * (n - 1));
@@ -626,6 +653,7 @@ int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
     k_cone<<<grid_for(n), kBlock, 0, s>>>(n, t->lights, t->nodes, t->parent, cosmin);
     k_finalize<<<grid_for(nn), kBlock, 0, s>>>(nn, t->nodes, cosmin);
     k_pairs<<<grid_for(n), kBlock, 0, s>>>(n, t->nodes, t->left, t->right, t->pairs, leaf_phi);
+    if (n > 1) k_quads<<<grid_for(n - 1), kBlock, 0, s>>>(n, t->nodes, t->left, t->right, t->quads);
     e = inclusive_scan_f32(s, leaf_phi, t->light_cdf, n, scan_ws);
     if (e != cudaSuccess) return check_cuda(ctx, e, "scan (light cdf)");
     e = cudaGetLastError();

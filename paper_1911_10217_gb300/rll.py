@@ -20,7 +20,7 @@ RLL_OK = 0
 ERRORS = {1: "RLL_E_INVALID", 2: "RLL_E_NOMEM", 3: "RLL_E_CUDA", 4: "RLL_E_TABLE_FULL",
           8: "RLL_E_TIMEOUT", 16: "RLL_E_DEVICE"}
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
-MODE = {"descent": 0, "uniform": 1}
+MODE = {"descent": 0, "uniform": 1, "descent2": 2}
 REWARD = {"cluster": 0, "literal": 1}
 BUILDER = {"lbvh": 0, "saoh": 1}
 

@@ -61,6 +61,8 @@ def test_tree_matches_oracle_bit_exact(env, maker, builder):
     dict(split_iterations=16, precision="bf16"),
     dict(builder="saoh"),
     dict(builder="saoh", mode="uniform", jitter=True),
+    dict(mode="descent2"),
+    dict(mode="descent2", precision="bf16", jitter=True),
 ])
 def test_lockstep_learning_tiny(env, variant):
     """Eight passes of the tiny scene. At each pass the oracle's state is
@@ -148,22 +150,23 @@ def test_unbiased_against_bruteforce(env):
             assert abs(m - ref[k]) <= 5 * se + 2e-3 * ref[k], (idx, k, m, ref[k], se)
 
 
-def test_frame_scale_parity(env):
+@pytest.mark.parametrize("mode", ["descent", "descent2"])
+def test_frame_scale_parity(env, mode):
     """1920 x 1080 frame: tree, then one pass from the empty grid. Sampled
     pixel ranges are compared one by one; learning on the oracle's full set
     of records is compared cell by cell."""
     O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
     s = scenes.frame_scene()
     ot, dt, d = _trees(env, s)
-    og = O.Grid.for_scene(ot, s)
-    dg = rll.Grid(ctx, dt, params_for(rll, s))
+    og = O.Grid.for_scene(ot, s, mode=mode)
+    dg = rll.Grid(ctx, dt, params_for(rll, s, mode=mode))
     g = to_host(run_sample(rll, ctx, dg, dt, d, s.seed, 0, s.spp))
     st = dg.export()
     A = O.scene_arrays(s)
     rng = np.random.default_rng(0)
     P = s.n_points
     for start in rng.integers(0, P - 4096, size=6):
-        sub = O.Grid.for_scene(ot, s)
+        sub = O.Grid.for_scene(ot, s, mode=mode)
         o = sub.sample_frame(A, s.seed, 0, s.spp, first=int(start), count=4096)
         sl = slice(int(start), int(start) + 4096)
         gsub = {k: (v[:, sl] if k == "rgb" else v[sl]) for k, v in g.items()}
