@@ -787,6 +787,8 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
+    ap.add_argument("--host-chunks", type=int, default=8,
+                    help="chunks of the host-buffer pass (copy/compute overlap)")
     ap.add_argument("--tree", default="lbvh", choices=["lbvh", "saoh"])
     ap.add_argument("--mode", default="descent", choices=["descent", "descent2", "uniform"])
     ap.add_argument("--workload", default="frame",
@@ -857,6 +859,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ctx = rll.Context(local, stream)
     ctx.set_option("sample_min_blocks", args.sample_min_blocks)
+    ctx.set_option("host_chunks", args.host_chunks)
 
     def T(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)

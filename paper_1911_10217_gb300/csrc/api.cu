@@ -205,6 +205,12 @@ int rll_ctx_set_option(rll_ctx* ctx, const char* name, int64_t value)
 {
     if (!ctx || !name) return RLL_E_INVALID;
     const std::string n(name);
+    if (n == "host_chunks") {
+        if (value < 1 || value > RLL_HOST_MAX_CHUNKS)
+            return fail(ctx, RLL_E_INVALID, "host_chunks must be in [1, " + std::to_string(RLL_HOST_MAX_CHUNKS) + "]");
+        ctx->host_chunks = (int)value;
+        return RLL_OK;
+    }
     if (n == "sample_min_blocks") {
         if (value != 3 && value != 4) return fail(ctx, RLL_E_INVALID, "sample_min_blocks must be 3 or 4");
         ctx->sample_min_blocks = (int)value;
@@ -221,6 +227,15 @@ int rll_ctx_destroy(rll_ctx* ctx)
     cudaFree(ctx->d_status);
     cudaFree(ctx->ws);
     cudaFree(ctx->stage);
+    if (ctx->pipe_ready) {
+        cudaStreamSynchronize(ctx->up);
+        cudaStreamSynchronize(ctx->down);
+        cudaStreamSynchronize(ctx->comp2);
+        for (cudaEvent_t ev : ctx->ev) cudaEventDestroy(ev);
+        cudaStreamDestroy(ctx->up);
+        cudaStreamDestroy(ctx->down);
+        cudaStreamDestroy(ctx->comp2);
+    }
     delete ctx;
     return RLL_OK;
 }
@@ -536,6 +551,15 @@ int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, con
         }
         ctx->stage_bytes = need;
     }
+    if (!ctx->pipe_ready) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->down, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->comp2, cudaStreamNonBlocking);
+        for (cudaEvent_t& ev : ctx->ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return check_cuda(ctx, e, "render_pass_host: streams");
+        ctx->pipe_ready = true;
+    }
     char* w = (char*)ctx->stage;
     float* d_pos = (float*)w; w += a(12 * P);
     float* d_nrm = (float*)w; w += a(12 * P);
@@ -544,19 +568,68 @@ int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, con
     float* d_box = (float*)w; w += a(24 * (size_t)std::max(n_boxes, 1));
     uint32_t* d_key = (uint32_t*)w; w += a(4 * S);
     float* d_val = (float*)w;
-    cudaStream_t s = ctx->stream;
-    cudaError_t e = cudaMemcpyAsync(d_pos, pos, 12 * P, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_nrm, nrm, 12 * P, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_alb, albedo, 4 * P, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n_boxes > 0) e = cudaMemcpyAsync(d_box, boxes, 24 * (size_t)n_boxes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return check_cuda(ctx, e, "render_pass_host: upload");
-    rc = sample_and_shade(ctx, grid, tree, d_pos, d_nrm, d_alb, nullptr, P, d_box, n_boxes, seed, frame, spp, d_rgb, d_key,
-                          d_val, nullptr);
-    if (rc == RLL_OK) rc = learn_update(ctx, grid, d_key, d_val, S);
-    if (rc == RLL_OK && do_split) rc = split_collapse(ctx, grid, tree);
+
+    // Copy/compute overlap: the points are cut into chunks; chunk k is
+    // uploaded on `up`, shaded on the main stream or comp2 (alternately, so a
+    // chunk's tail overlaps the next chunk's start) once its upload is done,
+    // and its rgb read back on `down` once it is shaded. Learning and
+    // split-collapse follow all chunks on the main stream and overlap the
+    // last read-backs. Sample ids, records and rgb are those of one launch.
+    const int64_t want = std::max<int64_t>(1, std::min<int64_t>(ctx->host_chunks, RLL_HOST_MAX_CHUNKS));
+    int64_t chunk = (P + want - 1) / want;
+    chunk = std::max<int64_t>(4096, (chunk + 255) & ~(int64_t)255);
+    const int nc = (int)((P + chunk - 1) / chunk);
+    cudaStream_t s = ctx->stream, sc[2] = {ctx->stream, ctx->comp2};
+    cudaEvent_t* ev_up = ctx->ev;
+    cudaEvent_t* ev_done = ctx->ev + RLL_HOST_MAX_CHUNKS;
+    cudaEvent_t ev_start = ctx->ev[2 * RLL_HOST_MAX_CHUNKS], ev_join = ctx->ev[2 * RLL_HOST_MAX_CHUNKS + 1],
+                ev_down = ctx->ev[2 * RLL_HOST_MAX_CHUNKS + 2];
+    // planes of [3][P] arrays: one strided copy per chunk where the pitch allows
+    auto planes = [&](float* dst, const float* src, int64_t b, int64_t n, cudaMemcpyKind kind, cudaStream_t st) {
+        const size_t pitch = 4 * (size_t)P;
+        if (pitch <= (size_t)INT32_MAX)
+            return cudaMemcpy2DAsync(dst + b, pitch, src + b, pitch, 4 * (size_t)n, 3, kind, st);
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(dst + k * P + b, src + k * P + b, 4 * (size_t)n, kind, st);
+        return e;
+    };
+    cudaError_t e = cudaEventRecord(ev_start, s);  // the grid's earlier updates come first
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->comp2, ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->down, ev_start, 0);
+    if (e == cudaSuccess && n_boxes > 0)
+        e = cudaMemcpyAsync(d_box, boxes, 24 * (size_t)n_boxes, cudaMemcpyHostToDevice, ctx->up);
+    for (int k = 0; k < nc && e == cudaSuccess && rc == RLL_OK; ++k) {
+        const int64_t b = k * chunk, n = std::min(chunk, P - b);
+        e = planes(d_pos, pos, b, n, cudaMemcpyHostToDevice, ctx->up);
+        if (e == cudaSuccess) e = planes(d_nrm, nrm, b, n, cudaMemcpyHostToDevice, ctx->up);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_alb + b, albedo + b, 4 * (size_t)n, cudaMemcpyHostToDevice, ctx->up);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_up[k], ctx->up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sc[k & 1], ev_up[k], 0);
+        if (e != cudaSuccess) break;
+        rc = rll::sample_and_shade_range(ctx, grid, tree, d_pos, d_nrm, d_alb, nullptr, P, b, b + n, d_box, n_boxes,
+                                         seed, frame, spp, d_rgb, d_key, d_val, nullptr, sc[k & 1]);
+        if (rc != RLL_OK) break;
+        e = cudaEventRecord(ev_done[k], sc[k & 1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->down, ev_done[k], 0);
+        if (e == cudaSuccess) e = planes(rgb, d_rgb, b, n, cudaMemcpyDeviceToHost, ctx->down);
+    }
+    if (e == cudaSuccess && rc == RLL_OK) {
+        e = cudaEventRecord(ev_join, ctx->comp2);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
+    }
+    if (e == cudaSuccess && rc == RLL_OK) rc = learn_update(ctx, grid, d_key, d_val, S);
+    if (e == cudaSuccess && rc == RLL_OK && do_split) rc = split_collapse(ctx, grid, tree);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_down, ctx->down);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_down, 0);
+    // every stream of the pipeline is drained before returning, also on errors
+    cudaError_t e2 = cudaStreamSynchronize(ctx->up);
+    cudaError_t e3 = cudaStreamSynchronize(ctx->comp2);
+    cudaError_t e4 = cudaStreamSynchronize(ctx->down);
+    cudaError_t e5 = cudaStreamSynchronize(s);
     if (rc != RLL_OK) return rc;
-    e = cudaMemcpyAsync(rgb, d_rgb, 12 * P, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (cudaError_t x : {e2, e3, e4, e5})
+        if (e == cudaSuccess) e = x;
     return check_cuda(ctx, e, "render_pass_host");
 }
 

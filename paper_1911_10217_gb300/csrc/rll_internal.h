@@ -15,6 +15,8 @@ struct DescRec;
 struct LightRec;
 }  // namespace rll
 
+#define RLL_HOST_MAX_CHUNKS 32
+
 struct rll_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -26,6 +28,12 @@ struct rll_ctx {
     // staging for rll_render_pass_host
     void* stage = nullptr;
     size_t stage_bytes = 0;
+    // rll_render_pass_host pipeline: upload, download and second compute
+    // streams, and its events (created on first use)
+    cudaStream_t up = nullptr, down = nullptr, comp2 = nullptr;
+    cudaEvent_t ev[2 * RLL_HOST_MAX_CHUNKS + 3] = {};
+    bool pipe_ready = false;
+    int host_chunks = 8;
     // launch tuning (rll_ctx_set_option)
     int sample_min_blocks = 4;
 };
@@ -121,6 +129,13 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
                      const float* albedo, const float* footprint, int64_t n_points, const float* boxes, int n_boxes,
                      uint64_t seed, uint32_t frame, int spp, float* rgb, uint32_t* rec_key,
                      float* rec_val, const rll_sample_debug* dbg);
+// Shades points [p_begin, p_end) of a G-buffer of n_points (the plane stride)
+// on `stream`; sample ids, records and rgb are those of the whole launch.
+int sample_and_shade_range(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* pos, const float* nrm,
+                           const float* albedo, const float* footprint, int64_t n_points, int64_t p_begin,
+                           int64_t p_end, const float* boxes, int n_boxes, uint64_t seed, uint32_t frame, int spp,
+                           float* rgb, uint32_t* rec_key, float* rec_val, const rll_sample_debug* dbg,
+                           cudaStream_t stream);
 int sample_power(rll_ctx* ctx, const rll_tree* t, const float* pos, const float* nrm,
                  const float* albedo, int64_t n_points, const float* boxes, int n_boxes, uint64_t seed,
                  uint32_t frame, int spp, float* rgb, int32_t* light_out);

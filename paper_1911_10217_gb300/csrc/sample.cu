@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sample(SampleArgs a)
     extern __shared__ float4 s_box[];
     stage_boxes(s_box, a.boxes, a.n_boxes);
     __syncthreads();
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.n_points) return;
+    const int64_t p = a.p_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.p_end) return;
     sample_point<P, MODE, DBG>(a, p, s_box);
 }
 
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kThreads) k_sample_power(SampleArgs a, int32_t
 template <int P, int MODE, bool DBG, int MINB>
 cudaError_t launch(const SampleArgs& a, cudaStream_t s)
 {
-    const unsigned blocks = (unsigned)((a.n_points + kThreads - 1) / kThreads);
+    const unsigned blocks = (unsigned)((a.p_end - a.p_begin + kThreads - 1) / kThreads);
     k_sample<P, MODE, DBG, MINB><<<blocks, kThreads, sizeof(float4) * 2 * a.n_boxes, s>>>(a);
     return cudaGetLastError();
 }
@@ -106,12 +106,24 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
                      uint32_t frame, int spp, float* rgb, uint32_t* rec_key, float* rec_val,
                      const rll_sample_debug* dbg)
 {
-    if (n_points == 0) return RLL_OK;
+    return sample_and_shade_range(ctx, g, t, pos, nrm, albedo, footprint, n_points, 0, n_points, boxes, n_boxes, seed,
+                                  frame, spp, rgb, rec_key, rec_val, dbg, ctx->stream);
+}
+
+int sample_and_shade_range(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* pos, const float* nrm,
+                           const float* albedo, const float* footprint, int64_t n_points, int64_t p_begin,
+                           int64_t p_end, const float* boxes, int n_boxes, uint64_t seed, uint32_t frame, int spp,
+                           float* rgb, uint32_t* rec_key, float* rec_val, const rll_sample_debug* dbg,
+                           cudaStream_t stream)
+{
+    if (p_end <= p_begin) return RLL_OK;
     SampleArgs a{};
     a.pos = pos;
     a.nrm = nrm;
     a.albedo = albedo;
     a.n_points = n_points;
+    a.p_begin = p_begin;
+    a.p_end = p_end;
     a.boxes = boxes;
     a.n_boxes = n_boxes;
     a.keys = g->keys;
@@ -152,9 +164,9 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
     const int minb = ctx->sample_min_blocks;
     const int mode = g->p.in_cluster_mode;
     switch (g->p.precision) {
-    case RLL_PREC_FP16: e = launch_p<RLL_PREC_FP16>(a, mode, use_dbg, minb, ctx->stream); break;
-    case RLL_PREC_BF16: e = launch_p<RLL_PREC_BF16>(a, mode, use_dbg, minb, ctx->stream); break;
-    default: e = launch_p<RLL_PREC_FP32>(a, mode, use_dbg, minb, ctx->stream);
+    case RLL_PREC_FP16: e = launch_p<RLL_PREC_FP16>(a, mode, use_dbg, minb, stream); break;
+    case RLL_PREC_BF16: e = launch_p<RLL_PREC_BF16>(a, mode, use_dbg, minb, stream); break;
+    default: e = launch_p<RLL_PREC_FP32>(a, mode, use_dbg, minb, stream);
     }
     return check_cuda(ctx, e, "sample_and_shade");
 }

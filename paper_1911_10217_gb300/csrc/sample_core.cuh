@@ -17,7 +17,8 @@ struct SampleArgs {
     const float* pos;
     const float* nrm;
     const float* albedo;
-    int64_t n_points;
+    int64_t n_points;         // plane stride of pos / nrm / rgb
+    int64_t p_begin, p_end;   // points this launch shades (k_sample)
     const float* boxes;
     int n_boxes;
     unsigned long long* keys;

@@ -274,14 +274,19 @@ def test_checkpoint_resume_is_exact(env):
         assert np.array_equal(full[k][fo], resumed[k][ro]), k
 
 
-def test_host_pass_matches_device_pass(env):
+@pytest.mark.parametrize("chunks", [1, 3, 8])
+def test_host_pass_matches_device_pass(env, chunks):
+    """The host pass (chunked uploads, shading on two streams, overlapped
+    read-back) gives the rgb and learned tables of the device pass."""
     O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
-    s = scenes.small_frame_scene()
+    s = scenes.frame_scene(width=256, height=144, n_patches=16, tris_per_patch=256, table_size=1 << 16)
+    assert s.n_points >= 8 * 4096  # 8 chunks of the smallest size
     _, dt, d = _trees(env, s)
     a = rll.Grid(ctx, dt, params_for(rll, s))
     b = rll.Grid(ctx, dt, params_for(rll, s))
     P = s.n_points
-    for f in range(2):
+    ctx.set_option("host_chunks", chunks)
+    for f in range(3):
         # the plain kernel (no per-sample diagnostics), as the host pass uses
         g = dict(rgb=torch.empty(3, P, device=env["dev"]),
                  key=torch.empty(P * s.spp, dtype=torch.int32, device=env["dev"]),
@@ -295,6 +300,11 @@ def test_host_pass_matches_device_pass(env):
                              np.ascontiguousarray(s.albedo), np.ascontiguousarray(s.boxes), s.seed, f,
                              s.spp, rgb)
         assert np.array_equal(rgb, g["rgb"].cpu().numpy())
+        ea, eb = a.export(), b.export()
+        fa, fb = np.argsort(ea["keys"]), np.argsort(eb["keys"])
+        for k in ("keys", "cut", "q", "c"):
+            assert np.array_equal(ea[k][fa], eb[k][fb]), (k, f)
+    ctx.set_option("host_chunks", 8)
 
 
 def test_long_run_stays_finite(env):
