@@ -104,7 +104,10 @@ int rll_ctx_create(rll_ctx** out, int device, void* cuda_stream);
 int rll_ctx_set_stream(rll_ctx* ctx, void* cuda_stream);
 /* Launch tuning of this context (no effect on results):
  *   "sample_min_blocks" 3 | 4 -- resident 256-thread blocks per SM the
- *   sampling kernel's registers are held to (default 4). */
+ *   sampling kernel's registers are held to (default 4);
+ *   "host_chunks" 1..32 -- chunks rll_render_pass_host cuts the points into
+ *   for copy/compute overlap (default 8; chunks of at least 4 096 points).
+ * Returns RLL_E_INVALID for an unknown name or a value out of range. */
 int rll_ctx_set_option(rll_ctx* ctx, const char* name, int64_t value);
 int rll_ctx_destroy(rll_ctx* ctx);
 /* Message of the last failing call on this context ("" if none). */
@@ -315,8 +318,14 @@ int rll_batch_destroy(rll_batch* b);
 
 /* Copies the G-buffer (HOST pos/nrm SoA [3][P], albedo [P]) and boxes (HOST
  * [K][6]) to the device, runs rll_sample_and_shade, rll_learn_update and (if
- * do_split) rll_split_collapse, and copies rgb (HOST SoA [3][P]) back.
- * Pinned host memory makes the copies asynchronous. Synchronises. */
+ * do_split) rll_split_collapse, and copies rgb (HOST SoA [3][P]) back. The
+ * points are cut into chunks ("host_chunks"): a chunk is shaded as soon as
+ * its upload ends and read back as soon as it is shaded, on streams of the
+ * context's own, while later chunks upload; results are those of one
+ * rll_sample_and_shade launch. Work enqueued earlier on the context stream
+ * comes first. Pinned host memory makes the copies asynchronous (pageable
+ * memory is correct but serialises them). Staging buffers are owned by the
+ * context. Synchronises. */
 int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos,
                          const float* nrm, const float* albedo, int64_t n_points,
                          const float* boxes, int32_t n_boxes, uint64_t seed, uint32_t frame,
