@@ -42,9 +42,8 @@ struct __align__(16) NodeRec {
 static_assert(sizeof(NodeRec) == 64, "NodeRec must be 64 bytes");
 
 // Descent record of one child, 48 bytes: the constants of the importance
-// bound precomputed (binary32, same operations as on the fly). The records
-// of both children of internal node i are pairs[2i], pairs[2i+1]: 96
-// contiguous bytes (three 32-byte sectors) per descent level.
+// bound precomputed (binary32, same operations as on the fly). The two-level
+// descent reads them four per internal node (quads).
 struct __align__(16) DescRec {
     float c[3];      // AABB centre
     float r2;        // squared half diagonal
@@ -56,6 +55,17 @@ struct __align__(16) DescRec {
     uint32_t id;     // node id
 };
 static_assert(sizeof(DescRec) == 48, "DescRec must be 48 bytes");
+
+// The DescRec fields of both children of one internal node, interleaved
+// (x: left child, y: right child) so that each 16-byte load yields two packed
+// operands of the paired bound below; 96 bytes per descent level. nr2 holds
+// -r2 (exact).
+struct __align__(16) PairRec {
+    float2 c0, c1, c2, nr2, r, phi;
+    float2 a0, a1, a2, cos_t, sin_t;
+    uint2 id;
+};
+static_assert(sizeof(PairRec) == 96, "PairRec must be 96 bytes");
 
 // Sorted light, 64 bytes.
 struct __align__(16) LightRec {
@@ -233,6 +243,65 @@ __device__ __forceinline__ Bound importance(const DescRec& r, float x0, float x1
     if (!(sphi <= 0.0f || cphi <= ad))
         B = fmaxf(0.0f, __fmaf_rn(ad, cphi, fmul(fsqrt(fmaxf(0.0f, __fmaf_rn(-ad, ad, d2))), sphi)));
     return Bound{fmul(fmul(r.phi, A), B), fmul(fmul(d2, d2), d2)};
+}
+
+// importance() of both children of a node at once, in packed binary32
+// (f32x2) arithmetic: per component the same correctly rounded operations in
+// the same order as importance(), hence bit-identical bounds. d2 - r2 is
+// computed as d2 + (-r2) and d2 <= r2 as d2 - r2 <= 0 (equal under round to
+// nearest with gradual underflow); the early return inside the bounding
+// sphere becomes a per-component select. n*: the normal broadcast to both
+// components.
+struct Bound2 {
+    float2 num, den;
+};
+
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+__device__ __forceinline__ Bound2 importance2(const PairRec& q, float x0, float x1, float x2, float2 n0, float2 n1,
+                                              float2 n2)
+{
+    const float2 dx = make_float2(fsub(q.c0.x, x0), fsub(q.c0.y, x0));
+    const float2 dy = make_float2(fsub(q.c1.x, x1), fsub(q.c1.y, x1));
+    const float2 dz = make_float2(fsub(q.c2.x, x2), fsub(q.c2.y, x2));
+    const float2 d2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    const float2 t = __fadd2_rn(d2, q.nr2);
+    const bool in_x = t.x <= 0.0f, in_y = t.y <= 0.0f;
+    const float2 cb = make_float2(fsqrt(t.x), fsqrt(t.y));
+    const float2 nd = __ffma2_rn(n2, dz, __ffma2_rn(n1, dy, __fmul2_rn(n0, dx)));
+    float2 A = d2;
+    const bool ra = nd.x < cb.x, rb = nd.y < cb.y;
+    if (ra || rb) {
+        const float2 g = __ffma2_rn(neg2(nd), nd, d2);
+        const float2 sq = make_float2(fsqrt(fmaxf(0.0f, g.x)), fsqrt(fmaxf(0.0f, g.y)));
+        const float2 v = __ffma2_rn(nd, cb, __fmul2_rn(sq, q.r));
+        if (ra) A.x = fmaxf(0.0f, v.x);
+        if (rb) A.y = fmaxf(0.0f, v.y);
+    }
+    const float2 ad = neg2(__ffma2_rn(q.a2, dz, __ffma2_rn(q.a1, dy, __fmul2_rn(q.a0, dx))));
+    const float2 sphi = __ffma2_rn(q.sin_t, cb, __fmul2_rn(q.cos_t, q.r));
+    const float2 cphi = __ffma2_rn(q.cos_t, cb, neg2(__fmul2_rn(q.sin_t, q.r)));
+    float2 B = d2;
+    const bool ea = !(sphi.x <= 0.0f || cphi.x <= ad.x), eb = !(sphi.y <= 0.0f || cphi.y <= ad.y);
+    if (ea || eb) {
+        const float2 g = __ffma2_rn(neg2(ad), ad, d2);
+        const float2 sq = make_float2(fsqrt(fmaxf(0.0f, g.x)), fsqrt(fmaxf(0.0f, g.y)));
+        const float2 v = __ffma2_rn(ad, cphi, __fmul2_rn(sq, sphi));
+        if (ea) B.x = fmaxf(0.0f, v.x);
+        if (eb) B.y = fmaxf(0.0f, v.y);
+    }
+    Bound2 o;
+    o.num = __fmul2_rn(__fmul2_rn(q.phi, A), B);
+    o.den = __fmul2_rn(__fmul2_rn(d2, d2), d2);
+    if (in_x) {
+        o.num.x = q.phi.x;
+        o.den.x = fmaxf(-q.nr2.x, 1e-30f);
+    }
+    if (in_y) {
+        o.num.y = q.phi.y;
+        o.den.y = fmaxf(-q.nr2.y, 1e-30f);
+    }
+    return o;
 }
 
 // ---------------------------------------------------------------- storage

@@ -12,6 +12,7 @@
 namespace rll {
 struct NodeRec;
 struct DescRec;
+struct PairRec;
 struct LightRec;
 }  // namespace rll
 
@@ -42,7 +43,7 @@ struct rll_tree {
     int device = 0;
     int64_t n = 0;
     rll::NodeRec* nodes = nullptr;   // [2n-1] every node
-    rll::DescRec* pairs = nullptr;   // [2(n-1)] descent records of the children of internal i at 2i, 2i+1
+    rll::PairRec* pairs = nullptr;   // [n-1] descent records of both children of internal i, interleaved
     rll::DescRec* quads = nullptr;   // [4(n-1)] records of the 2..4 grandchildren of internal i at 4i.. (two-level
                                      // descent; a single-light child stands for itself; unused entries id ~0)
     rll::LightRec* lights = nullptr; // [n] sorted lights

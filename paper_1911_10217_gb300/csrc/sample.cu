@@ -5,8 +5,9 @@
 // in shared memory once per block. Per sample:
 //   hash lookup / lazy insert of the (jittered) 5-d cell   (64-bit CAS)
 //   binary search of the cell's C for the cluster s        (log2 m loads of one row)
-//   in-cluster choice: bound-driven descent (two 48-byte child records, 96
-//   contiguous bytes per level) or a uniform pick over the cluster's lights
+//   in-cluster choice: bound-driven descent (one 96-byte record of both
+//   children per level, both bounds in packed f32x2 arithmetic) or a uniform
+//   pick over the cluster's lights
 //   uniform point on the light triangle, contribution, shadow segment vs boxes
 //   estimate accumulation and one learning record (key, |c|).
 // The decisions (cell, branch, visibility) are exact binary32 formulas; the
@@ -23,8 +24,10 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <int P, int MODE, bool DBG, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_sample(SampleArgs a)
+// THREADS x MINB: block size and the resident blocks per SM the registers are
+// held to (256 x 4: 64 registers, 256 x 3: 80).
+template <int P, int MODE, bool DBG, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_sample(SampleArgs a)
 {
     extern __shared__ float4 s_box[];
     stage_boxes(s_box, a.boxes, a.n_boxes);
@@ -75,19 +78,19 @@ __global__ void __launch_bounds__(kThreads) k_sample_power(SampleArgs a, int32_t
     a.rgb[2 * np + p] = acc2 * inv_spp;
 }
 
-template <int P, int MODE, bool DBG, int MINB>
+template <int P, int MODE, bool DBG, int THREADS, int MINB>
 cudaError_t launch(const SampleArgs& a, cudaStream_t s)
 {
-    const unsigned blocks = (unsigned)((a.p_end - a.p_begin + kThreads - 1) / kThreads);
-    k_sample<P, MODE, DBG, MINB><<<blocks, kThreads, sizeof(float4) * 2 * a.n_boxes, s>>>(a);
+    const unsigned blocks = (unsigned)((a.p_end - a.p_begin + THREADS - 1) / THREADS);
+    k_sample<P, MODE, DBG, THREADS, MINB><<<blocks, THREADS, sizeof(float4) * 2 * a.n_boxes, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int P, int MODE>
 cudaError_t launch_m(const SampleArgs& a, bool dbg, int minb, cudaStream_t s)
 {
-    if (dbg) return launch<P, MODE, true, 3>(a, s);
-    return minb >= 4 ? launch<P, MODE, false, 4>(a, s) : launch<P, MODE, false, 3>(a, s);
+    if (dbg) return launch<P, MODE, true, 256, 3>(a, s);
+    return minb == 4 ? launch<P, MODE, false, 256, 4>(a, s) : launch<P, MODE, false, 256, 3>(a, s);
 }
 
 template <int P>

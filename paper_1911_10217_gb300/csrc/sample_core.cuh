@@ -34,7 +34,7 @@ struct SampleArgs {
     uint32_t nb;
     uint32_t jitter;
     uint32_t reward_mode;
-    const DescRec* pairs;
+    const PairRec* pairs;
     const DescRec* quads;     // two-level descent records (4 per internal node)
     const NodeRec* nodes;
     const LightRec* lights;
@@ -248,20 +248,27 @@ __device__ __forceinline__ Setup setup_sample(const SampleArgs& a, SampleStream&
 }
 
 // One level of the bound-driven descent below internal node `node` (ud: the
-// level's draw). The two children's bounds are compared without a division:
-// w_L = num_L den_R, w_R = num_R den_L; their powers if both vanish.
-__device__ __forceinline__ void descent_step(const SampleArgs& a, uint32_t& node, float& p_in, float ud, float x0,
-                                             float x1, float x2, float n0, float n1, float n2)
+// level's draw; x*: the shading point, n*: its normal broadcast to both
+// components). Both children's bounds in one packed evaluation; they are
+// compared without a division: w_L = num_L den_R, w_R = num_R den_L; their
+// powers if both vanish.
+__device__ __forceinline__ void descent_step(const SampleArgs& a, uint32_t& node, float& p_in, float ud,
+                                             float x0, float x1, float x2, float2 n0, float2 n1, float2 n2)
 {
-    const DescRec L = load_desc(a.pairs + 2 * (int64_t)node);
-    const DescRec R = load_desc(a.pairs + 2 * (int64_t)node + 1);
-    const Bound bl = importance(L, x0, x1, x2, n0, n1, n2);
-    const Bound br = importance(R, x0, x1, x2, n0, n1, n2);
-    float wl = fmul(bl.num, br.den), wr = fmul(br.num, bl.den);
+    PairRec q;
+    {
+        const float4* src = reinterpret_cast<const float4*>(a.pairs + node);
+        float4* dst = reinterpret_cast<float4*>(&q);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) dst[k] = __ldg(src + k);
+    }
+    const Bound2 b = importance2(q, x0, x1, x2, n0, n1, n2);
+    const float2 w = __fmul2_rn(b.num, make_float2(b.den.y, b.den.x));
+    float wl = w.x, wr = w.y;
     float ssum = fadd(wl, wr);
     if (!(ssum > 0.0f)) {
-        wl = L.phi;
-        wr = R.phi;
+        wl = q.phi.x;
+        wr = q.phi.y;
         ssum = fadd(wl, wr);
     }
     bool left;
@@ -274,7 +281,7 @@ __device__ __forceinline__ void descent_step(const SampleArgs& a, uint32_t& node
         ratio = 0.5f;
     }
     p_in *= ratio;
-    node = left ? L.id : R.id;
+    node = left ? q.id.x : q.id.y;
 }
 
 __device__ __forceinline__ void prefetch_l1(const void* p)
@@ -377,8 +384,9 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
                 descent2_step(a, node, p_in, rs.draw(kDrawDescent + level), x0, x1, x2, n0, n1, n2);
             light = (int64_t)node - nl1;
         } else {
+            const float2 vn0 = make_float2(n0, n0), vn1 = make_float2(n1, n1), vn2 = make_float2(n2, n2);
             for (uint32_t level = 0; (int64_t)node < nl1; ++level)
-                descent_step(a, node, p_in, rs.draw(kDrawDescent + level), x0, x1, x2, n0, n1, n2);
+                descent_step(a, node, p_in, rs.draw(kDrawDescent + level), x0, x1, x2, vn0, vn1, vn2);
             light = (int64_t)node - nl1;
         }
         const LightRec Lr = load_light(a.lights + light);

@@ -266,12 +266,25 @@ __global__ void k_finalize(int64_t nn, NodeRec* __restrict__ nodes, const int* _
 }
 
 __global__ void k_pairs(int64_t n, const NodeRec* __restrict__ nodes, const int32_t* __restrict__ left,
-                        const int32_t* __restrict__ right, DescRec* __restrict__ pairs, float* __restrict__ leaf_phi)
+                        const int32_t* __restrict__ right, PairRec* __restrict__ pairs, float* __restrict__ leaf_phi)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n - 1) {
-        pairs[2 * i] = make_desc(nodes[left[i]]);
-        pairs[2 * i + 1] = make_desc(nodes[right[i]]);
+        const DescRec L = make_desc(nodes[left[i]]), R = make_desc(nodes[right[i]]);
+        PairRec q;
+        q.c0 = make_float2(L.c[0], R.c[0]);
+        q.c1 = make_float2(L.c[1], R.c[1]);
+        q.c2 = make_float2(L.c[2], R.c[2]);
+        q.nr2 = make_float2(-L.r2, -R.r2);
+        q.r = make_float2(L.r, R.r);
+        q.phi = make_float2(L.phi, R.phi);
+        q.a0 = make_float2(L.axis[0], R.axis[0]);
+        q.a1 = make_float2(L.axis[1], R.axis[1]);
+        q.a2 = make_float2(L.axis[2], R.axis[2]);
+        q.cos_t = make_float2(L.cos_t, R.cos_t);
+        q.sin_t = make_float2(L.sin_t, R.sin_t);
+        q.id = make_uint2(L.id, R.id);
+        pairs[i] = q;
     }
     if (i < n) leaf_phi[i] = nodes[n - 1 + i].phi;
 }
@@ -575,7 +588,7 @@ int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
     e = cudaMalloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 64);               \
     if (e != cudaSuccess) return check_cuda(ctx, e, "cudaMalloc(tree)");
     RLL_ALLOC(t->nodes, sizeof(NodeRec) * nn);
-    RLL_ALLOC(t->pairs, sizeof(DescRec) * 2 * (n - 1));
+    RLL_ALLOC(t->pairs, sizeof(PairRec) * (n - 1));
     RLL_ALLOC(t->quads, sizeof(DescRec) * 4 * (n - 1));
     RLL_ALLOC(t->lights, sizeof(LightRec) * n);
     RLL_ALLOC(t->perm, sizeof(uint32_t) * n);
