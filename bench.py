@@ -705,12 +705,13 @@ def run_paths(args):
 
 def run_trees(args):
     """Light-tree builders at equal cost: for the frame workload and the sky
-    interior, the radix tree of the Morton codes (Section 3.1) and the
-    surface-area-orientation split positions; per builder the leaf depth,
-    the pass time (sampling, learning, split-collapse) over --trees-passes
-    learning passes, and the 1-spp MSE after them (mean of 4 frames) against
+    interior, the radix tree of the Morton codes (Section 3.1), the
+    surface-area-orientation split positions and the median split positions;
+    per builder the leaf depth, the pass time (sampling, learning,
+    split-collapse) over --trees-passes learning passes, and the 1-spp MSE
+    after them (mean of --trees-frames frames) against
     the energy sampler at 1024 spp (the energy sampler uses the same light
-    order for both trees)."""
+    order for every tree)."""
     import torch
     from paper_1911_10217_gb300 import rll, scenes
     dev = torch.device("cuda:0")
@@ -732,7 +733,7 @@ def run_trees(args):
             ref += rgb.double()
         ref /= 32
         alpha = s.grid.alpha if sname == "frame" else 0.01
-        for builder in ("lbvh", "saoh"):
+        for builder in args.trees_builders.split(","):
             tree = tree0 if builder == "lbvh" else rll.Tree(ctx, tri, em, builder=builder)
             ex = tree.export()
             n = tree.n
@@ -759,7 +760,7 @@ def run_trees(args):
             torch.cuda.synchronize()
             tim = [[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in ev[3:]]
             mse = []
-            for r in range(4):
+            for r in range(args.trees_frames):
                 rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, 31337, 90000 + r, 1, rgb)
                 mse.append(float(((rgb.double() - ref) ** 2).mean()))
             rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 31337, 90000, 1, rgb)
@@ -789,7 +790,9 @@ def main():
     ap.add_argument("--sample-min-blocks", type=int, default=4)
     ap.add_argument("--host-chunks", type=int, default=8,
                     help="chunks of the host-buffer pass (copy/compute overlap)")
-    ap.add_argument("--tree", default="lbvh", choices=["lbvh", "saoh"])
+    ap.add_argument("--tree", default="lbvh", choices=["lbvh", "saoh", "median"])
+    ap.add_argument("--trees-builders", default="lbvh,saoh,median")
+    ap.add_argument("--trees-frames", type=int, default=16)
     ap.add_argument("--mode", default="descent", choices=["descent", "descent2", "uniform"])
     ap.add_argument("--workload", default="frame",
                     choices=["frame", "batched", "serving", "dynamic", "split", "sky", "paths", "trees"])

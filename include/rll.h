@@ -132,6 +132,7 @@ int rll_build_light_tree(rll_ctx* ctx, const float* tri, const float* emission, 
 /* tree builders (rll_build_light_tree_ex) */
 #define RLL_TREE_LBVH 0  /* radix tree of the Morton codes (Section 3.1: a simple LBVH) */
 #define RLL_TREE_SAOH 1  /* same light order, split positions by a surface-area-orientation cost */
+#define RLL_TREE_MEDIAN 2 /* same light order, every range split at its middle (balanced) */
 
 /* Same, with a choice of builder. RLL_TREE_SAOH follows the alternative that
  * Section 3.1 leaves as future work (a hierarchy that considers light
@@ -143,8 +144,11 @@ int rll_build_light_tree(rll_ctx* ctx, const float* tri, const float* emission, 
  * surface area of S's box * (2 - |sum of winding cross products| / sum of
  * their lengths); power, lengths and cross products are summed in 64-bit
  * fixed point, so the result does not depend on summation order. Internal
- * node ids are (split position - the root's) mod (n - 1): root 0. Same
- * output layout and export as rll_build_light_tree. Synchronises. */
+ * node ids are (split position - the root's) mod (n - 1): root 0.
+ * RLL_TREE_MEDIAN: same light order and id rule, every range [b, e) of at
+ * least two lights split at b + floor((e - b) / 2), so every leaf lies at
+ * depth floor(log2 n) or ceil(log2 n). Same output layout and export as
+ * rll_build_light_tree. RLL_E_INVALID for another builder. Synchronises. */
 int rll_build_light_tree_ex(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
                             int32_t builder, rll_tree** out);
 /* Replaces the radiance used for shading (emission: [n][3], input order);

@@ -23,7 +23,7 @@ EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
 MODE = {"descent": 0, "uniform": 1, "descent2": 2}
 REWARD = {"cluster": 0, "literal": 1}
-BUILDER = {"lbvh": 0, "saoh": 1}
+BUILDER = {"lbvh": 0, "saoh": 1, "median": 2}
 
 
 def build(force: bool = False) -> str:

@@ -360,6 +360,7 @@ typedef struct {
     const int64_t* pc;     /* [3][n+1] */
     const float* lbox;     /* [n][6] light boxes */
     int64_t groot;
+    int median;            /* split every range at its middle instead */
 } orc_saoh_ctx;
 
 static int orc_exponent(double v)
@@ -453,7 +454,7 @@ static int32_t orc_saoh_rec(orc_saoh_ctx* x, int64_t b, int64_t e, int32_t paren
         t->end[id] = (uint32_t)e;
         return id;
     }
-    int64_t k = orc_saoh_split(x, b, e);
+    int64_t k = x->median ? b + (e - b) / 2 : orc_saoh_split(x, b, e);
     if (parent < 0) x->groot = k - 1;
     int32_t id = orc_saoh_id(x, k - 1);
     t->parent[id] = parent;
@@ -533,7 +534,7 @@ static int orc_build_tree_with(int64_t n, const float* tri, const float* emis, o
             for (int k = 0; k < 3; ++k)
                 pc[k * (n + 1) + l + 1] = pc[k * (n + 1) + l] + llrint(ldexp((double)cr[l * 4 + k], sc));
         }
-        orc_saoh_ctx x = {t, keys, n, pphi, parea, pc, lbox, 0};
+        orc_saoh_ctx x = {t, keys, n, pphi, parea, pc, lbox, 0, builder == 2};
         orc_saoh_rec(&x, 0, n, -1);
         free(pphi);
         free(parea);
@@ -633,7 +634,8 @@ int orc_build_tree(int64_t n, const float* tri, const float* emis, orc_tree* t)
 }
 
 /* builder 0: the radix tree of the Morton codes (Section 3.1); 1: the
- * surface-area-orientation split positions above */
+ * surface-area-orientation split positions above; 2: the same light order
+ * with every range [b, e) split at b + floor((e - b) / 2) (a balanced tree) */
 int orc_build_tree_ex(int64_t n, const float* tri, const float* emis, orc_tree* t, int builder)
 {
     return orc_build_tree_with(n, tri, emis, t, builder);

@@ -264,7 +264,8 @@ int rll_build_light_tree_ex(rll_ctx* ctx, const float* tri, const float* emissio
     *out = nullptr;
     if (!tri || !emission) return fail(ctx, RLL_E_INVALID, "tri / emission is NULL");
     if (n < 1 || n > (1ll << 24)) return fail(ctx, RLL_E_INVALID, "light count must be in [1, 2^24]");
-    if (builder != RLL_TREE_LBVH && builder != RLL_TREE_SAOH) return fail(ctx, RLL_E_INVALID, "unknown builder");
+    if (builder != RLL_TREE_LBVH && builder != RLL_TREE_SAOH && builder != RLL_TREE_MEDIAN)
+        return fail(ctx, RLL_E_INVALID, "unknown builder");
     DeviceGuard g(ctx->device);
     rll_tree* t = new (std::nothrow) rll_tree();
     if (!t) return fail(ctx, RLL_E_NOMEM, "host allocation");

@@ -574,6 +574,37 @@ k_saoh_level(int64_t n, const SaohNode* __restrict__ in, uint32_t count, SaohNod
     }
 }
 
+// ---------------------------------------------------------------- median split positions
+// Every range [b, e) of at least two lights splits at k = b + floor((e - b) / 2)
+// (same light order and id rule as above). Each split position g = k - 1 is
+// owned by exactly one internal node: thread g walks down from the root to it
+// (at most ceil(log2 n) steps) and writes that node's children and their
+// parent links; a child range of one light is its leaf.
+__global__ void k_median(int64_t n, int32_t* __restrict__ left, int32_t* __restrict__ right,
+                         int32_t* __restrict__ parent)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n - 1) return;
+    const int64_t nm1 = n - 1, groot = n / 2 - 1;
+    auto id_of = [&](int64_t s) { return (int32_t)(((s - groot) % nm1 + nm1) % nm1); };
+    int64_t b = 0, e = n;
+    for (int step = 0; step < 64; ++step) {  // g always lies in [b, e - 2]
+        const int64_t k = b + (e - b) / 2;
+        if (k - 1 == g) {
+            const int32_t id = id_of(g);
+            const int32_t l = k - b == 1 ? (int32_t)(nm1 + b) : id_of(b + (k - b) / 2 - 1);
+            const int32_t r = e - k == 1 ? (int32_t)(nm1 + k) : id_of(k + (e - k) / 2 - 1);
+            left[id] = l;
+            right[id] = r;
+            parent[l] = id;
+            parent[r] = id;
+            return;
+        }
+        if (g < k - 1) e = k;
+        else b = k;
+    }
+}
+
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -632,6 +663,7 @@ int build_tree(rll_ctx* ctx, const float* tri, const float* emission, int64_t n,
     if (e != cudaSuccess) return check_cuda(ctx, e, "memset parent");
     if (n > 1 && builder == RLL_TREE_LBVH)
         k_karras<<<grid_for(n - 1), kBlock, 0, s>>>(scodes, sidx, n, t->left, t->right, t->parent, begin, end);
+    if (n > 1 && builder == RLL_TREE_MEDIAN) k_median<<<grid_for(n - 1), kBlock, 0, s>>>(n, t->left, t->right, t->parent);
     k_leaves<<<grid_for(n), kBlock, 0, s>>>(tri, emission, n, sidx, t->perm, t->lights, t->nodes, axis_sum);
     if (n > 1 && builder == RLL_TREE_SAOH) {
         int64_t* groot = reinterpret_cast<int64_t*>(saoh_ctr + 2);

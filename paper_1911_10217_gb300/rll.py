@@ -22,7 +22,7 @@ ERRORS = {1: "RLL_E_INVALID", 2: "RLL_E_NOMEM", 3: "RLL_E_CUDA", 4: "RLL_E_TABLE
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
 MODE = {"descent": 0, "uniform": 1, "descent2": 2}
 REWARD = {"cluster": 0, "literal": 1}
-BUILDER = {"lbvh": 0, "saoh": 1}
+BUILDER = {"lbvh": 0, "saoh": 1, "median": 2}
 
 # every symbol declared in include/rll.h
 EXPORTS = [
@@ -202,7 +202,7 @@ class Context:
 
 
 class Tree:
-    """rll_tree built by rll_build_light_tree_ex (builder "lbvh" or "saoh")."""
+    """rll_tree built by rll_build_light_tree_ex (builder "lbvh", "saoh" or "median")."""
 
     def __init__(self, ctx: Context, tri, emission, builder: str = "lbvh"):
         _check_tensor(tri, "float32")

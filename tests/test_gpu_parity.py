@@ -38,7 +38,8 @@ def _trees(env, scene, builder="lbvh"):
 
 @pytest.mark.parametrize("maker,builder", [("tiny", "lbvh"), ("small_frame", "lbvh"), ("frame", "lbvh"),
                                            ("tiny", "saoh"), ("small_frame", "saoh"), ("frame", "saoh"),
-                                           ("sky", "saoh")])
+                                           ("sky", "saoh"), ("tiny", "median"), ("small_frame", "median"),
+                                           ("frame", "median"), ("sky", "median")])
 def test_tree_matches_oracle_bit_exact(env, maker, builder):
     s = getattr(scenes, maker + "_scene")(**({"width": 64, "height": 32} if maker == "sky" else {}))
     ot, dt, _ = _trees(env, s, builder)
@@ -63,6 +64,8 @@ def test_tree_matches_oracle_bit_exact(env, maker, builder):
     dict(builder="saoh", mode="uniform", jitter=True),
     dict(mode="descent2"),
     dict(mode="descent2", precision="bf16", jitter=True),
+    dict(builder="median"),
+    dict(builder="median", precision="fp16", jitter=True),
 ])
 def test_lockstep_learning_tiny(env, variant):
     """Eight passes of the tiny scene. At each pass the oracle's state is
@@ -150,14 +153,14 @@ def test_unbiased_against_bruteforce(env):
             assert abs(m - ref[k]) <= 5 * se + 2e-3 * ref[k], (idx, k, m, ref[k], se)
 
 
-@pytest.mark.parametrize("mode", ["descent", "descent2"])
-def test_frame_scale_parity(env, mode):
+@pytest.mark.parametrize("mode,builder", [("descent", "lbvh"), ("descent2", "lbvh"), ("descent", "median")])
+def test_frame_scale_parity(env, mode, builder):
     """1920 x 1080 frame: tree, then one pass from the empty grid. Sampled
     pixel ranges are compared one by one; learning on the oracle's full set
     of records is compared cell by cell."""
     O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
     s = scenes.frame_scene()
-    ot, dt, d = _trees(env, s)
+    ot, dt, d = _trees(env, s, builder)
     og = O.Grid.for_scene(ot, s, mode=mode)
     dg = rll.Grid(ctx, dt, params_for(rll, s, mode=mode))
     g = to_host(run_sample(rll, ctx, dg, dt, d, s.seed, 0, s.spp))

@@ -231,3 +231,54 @@ def test_saoh_separates_distant_clusters(oracle_mod):
     tris, em = _line_lights(xs, [True] * 32)
     t = oracle_mod.Tree(tris, em, builder="saoh")
     assert t.begin[t.right[0]] == 20
+
+
+# ---- median split positions (a balanced tree over the same light order)
+
+def _ranges(t):
+    """(begin, split, end) of every internal node."""
+    return sorted((int(t.begin[i]), int(t.begin[t.right[i]]), int(t.end[i])) for i in range(t.n - 1))
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 7, 8, 13, 17, 100])
+def test_median_tree_is_balanced_over_ranges(oracle_mod, n):
+    rng = np.random.default_rng(n)
+    tris, em = _line_lights(rng.uniform(0.0, 1.0, n), [True] * n)
+    a = oracle_mod.Tree(tris, em)
+    t = oracle_mod.Tree(tris, em, builder="median")
+    assert np.array_equal(t.perm, a.perm)               # same light order
+    assert t.parent[0] == -1 and t.begin[0] == 0 and t.end[0] == n
+    seen = np.zeros(2 * n - 1, int)
+    depth = {0: 0}
+    g_root = n // 2 - 1
+    for i in range(n - 1):
+        l, r = int(t.left[i]), int(t.right[i])
+        seen[l] += 1
+        seen[r] += 1
+        assert t.parent[l] == i and t.parent[r] == i
+        b, k, e = int(t.begin[i]), int(t.begin[r]), int(t.end[i])
+        assert t.end[l] == k and t.begin[l] == b and t.end[r] == e
+        assert k == b + (e - b) // 2                    # split at the middle
+        assert i == ((k - 1) - g_root) % (n - 1)        # id rule
+    assert seen[0] == 0 and np.all(seen[1:] == 1)
+    stack = [0]
+    while stack:
+        v = stack.pop()
+        if v < n - 1:
+            for c in (int(t.left[v]), int(t.right[v])):
+                depth[c] = depth[v] + 1
+                stack.append(c)
+    leaf = np.array([depth[n - 1 + l] for l in range(n)])
+    lo, hi = int(np.floor(np.log2(n))), int(np.ceil(np.log2(n)))
+    assert leaf.min() >= lo and leaf.max() <= hi
+
+
+def test_median_tree_equals_radix_tree_on_a_complete_grid(oracle_mod):
+    # 8 x 8 x 8 lights on a regular grid: the top 3 bits of each quantised
+    # axis enumerate the 8 rows, so the 512 Morton codes differ first in 9
+    # interleaved bits that take every value once; the radix tree of those
+    # codes (Section 3.1) is the complete tree that halves every range.
+    tris, em = _grid_lights(8)
+    a = oracle_mod.Tree(tris, em)
+    t = oracle_mod.Tree(tris, em, builder="median")
+    assert _ranges(a) == _ranges(t)
