@@ -61,7 +61,8 @@ def workload_config(scene, tree="lbvh", mode="descent"):
             "spp": scene.spp, "cut_size": g.cut_size, "table_size": g.table_size,
             "cell_size": g.cell_size, "normal_bins": g.normal_bins, "jitter": g.jitter,
             "table_precision": "fp32", "in_cluster": mode, "split_iterations": g.split_iterations,
-            "light_tree": {"lbvh": "radix tree of Morton codes", "saoh": "Morton order, SAOH split positions"}[tree],
+            "light_tree": {"lbvh": "radix tree of Morton codes", "saoh": "Morton order, SAOH split positions",
+                       "median": "Morton order, median split positions"}[tree],
             "l2": "flushed between timed steps (512 MB write, untimed)"}
 
 
