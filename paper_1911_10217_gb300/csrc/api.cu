@@ -375,11 +375,11 @@ int rll_create_grid(rll_ctx* ctx, const rll_tree* tree, const rll_grid_params* p
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->touched, 4 * (size_t)g->H);
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->touched_start, 4 * (size_t)g->H);
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->touched_len, 4 * (size_t)g->H);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&g->n_touched, 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->n_touched, 8 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->cursor, 4 * (size_t)g->H);
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->big, 8 * (size_t)g->H);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->keys, 0xFF, 8 * (size_t)g->H, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->n_touched, 0, 16, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->n_touched, 0, 8 * sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->cursor, 0, 4 * (size_t)g->H, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->def_cut, cut.data(), 4 * g->m, cudaMemcpyHostToDevice, ctx->stream);

@@ -188,7 +188,7 @@ struct rll_batch {
     uint32_t* touched_start = nullptr; // [cap_cells]
     uint32_t* touched_len = nullptr;   // [cap_cells]
     uint32_t* lists = nullptr;         // [2 cap_cells] cells for the block paths
-    uint32_t* n_touched = nullptr;     // [4] learning counters
+    uint32_t* n_touched = nullptr;     // [8] learning counters
     int max_boxes = 0;
     uint32_t* status = nullptr;
     int32_t cap_items = 0;
@@ -280,7 +280,7 @@ cudaError_t launch_sample(rll_batch* b, cudaStream_t s)
 template <int P>
 cudaError_t launch_learn_t(rll_batch* b, cudaStream_t s, bool do_split)
 {
-    cudaError_t e = cudaMemsetAsync(b->n_touched, 0, 4 * sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(b->n_touched, 0, 8 * sizeof(uint32_t), s);
     if (e != cudaSuccess || b->n_records == 0) return e;
     const int sms = device_sm_count(b->device);
     e = launch_bucketed_learn<P>(s, b->device, sms, b->rec_key, b->rec_val, b->n_records,
@@ -351,7 +351,7 @@ int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int6
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched_start, 4 * (size_t)max_cells);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched_len, 4 * (size_t)max_cells);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->lists, 8 * (size_t)max_cells);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->n_touched, 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->n_touched, 8 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->cursor, 0, 4 * (size_t)max_cells, ctx->stream);
     // the learning step's shared-memory opt-in, now rather than during a graph capture
     if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP32, BatchRows<RLL_PREC_FP32>>(ctx->device);
@@ -361,7 +361,7 @@ int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int6
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, sizeof(BatchItemDev) * max_items);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tile_prefix, 4 * (max_items + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cell_prefix, 4 * (max_items + 1));
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->n_touched, 0, 16, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->n_touched, 0, 8 * sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         const int rc = check_cuda(ctx, e, "batch allocation");

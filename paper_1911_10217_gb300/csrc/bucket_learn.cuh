@@ -32,7 +32,6 @@ constexpr int kBucketThreads = 256;
 constexpr int kTilesPerWarp = 4;         // 32-record tiles one warp counts / scatters
 constexpr uint32_t kWarpBucket = 240;    // records of a cell one warp orders in shared memory
 constexpr uint32_t kBlockGroup = 1024;   // records of a cell one block orders by grouping and ranking
-constexpr int kGroupThreads = 256;
 constexpr uint32_t kBlockSort = 8192;    // records of a cell one block sorts in shared memory (power of 2)
 constexpr size_t kBigSmem = kBlockSort * (sizeof(unsigned long long) + sizeof(uint32_t));
 constexpr int kBigThreads = 512;
@@ -82,7 +81,8 @@ k_bucket_count(const uint32_t* __restrict__ rec_key, int64_t n, Dec dec, uint32_
 // 2. one contiguous bucket per touched cell (one atomic per warp)
 __global__ void __launch_bounds__(kBucketThreads)
 k_bucket_claim(const uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr, uint32_t* __restrict__ cursor,
-               uint32_t* __restrict__ start, uint32_t* __restrict__ len)
+               uint32_t* __restrict__ start, uint32_t* __restrict__ len, uint32_t* __restrict__ group_list,
+               uint32_t* __restrict__ sort_list)
 {
     const uint32_t total = *(volatile uint32_t*)ctr;
     const int lane = threadIdx.x & 31;
@@ -105,6 +105,18 @@ k_bucket_claim(const uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr,
             len[c] = cnt;
             cursor[slot] = base + x - cnt;
         }
+        // cells above one warp's capacity: to the grouping (block) or sorting list
+        const bool to_group = c < total && cnt > kWarpBucket && cnt <= kBlockGroup;
+        const bool to_sort = c < total && cnt > kBlockGroup;
+        const uint32_t gm = __ballot_sync(0xffffffffu, to_group), sm = __ballot_sync(0xffffffffu, to_sort);
+        uint32_t gb = 0, sb = 0;
+        if (lane == 0 && gm) gb = atomicAdd(ctr + 3, (uint32_t)__popc(gm));
+        if (lane == 0 && sm) sb = atomicAdd(ctr + 2, (uint32_t)__popc(sm));
+        gb = __shfl_sync(0xffffffffu, gb, 0);
+        sb = __shfl_sync(0xffffffffu, sb, 0);
+        const uint32_t below = (1u << lane) - 1u;
+        if (to_group) group_list[gb + __popc(gm & below)] = c;
+        if (to_sort) sort_list[sb + __popc(sm & below)] = c;
     }
 }
 
@@ -298,34 +310,6 @@ __device__ void learn_cell_grouped(Team team, CellOrder<CAP>& o, const uint32_t*
     }
 }
 
-// 4. one warp per cell of a list (list == nullptr: every touched cell) with
-// at most CAP records; a larger cell is appended to the next list (`next`,
-// its count at *next_count) for the block path.
-template <int P, uint32_t CAP, int WARPS, int MINB, class Rows>
-__global__ void __launch_bounds__(WARPS * 32, MINB)
-k_learn_tier(const Bucket bucket, const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count,
-             uint32_t* __restrict__ next, uint32_t* __restrict__ next_count, const uint32_t* __restrict__ touched,
-             const uint32_t* __restrict__ start, const uint32_t* __restrict__ len, uint32_t* __restrict__ cursor,
-             Rows rows, uint32_t* __restrict__ status)
-{
-    __shared__ CellOrder<CAP> orders[WARPS];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t total = *(volatile const uint32_t*)list_count;
-    for (uint32_t i = blockIdx.x * WARPS + warp; i < total; i += gridDim.x * WARPS) {
-        const uint32_t w = list ? list[i] : i;
-        const uint32_t slot = touched[w], nr = len[w];
-        if (nr > CAP) {
-            if (lane == 0) next[atomicAdd(next_count, 1u)] = w;
-            continue;
-        }
-        const RowRef<P> r = rows.row(slot);
-        const uint32_t b0 = start[w];
-        learn_cell_grouped<P>(WarpTeam{}, orders[warp], bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M,
-                              r.m, r.alpha, r.eps, r.Q, r.C, status);
-        if (lane == 0) cursor[slot] = 0u;
-    }
-}
-
 // Eq. 1 of one cell whose records are sorted by (cluster, sample id), by a
 // whole block: cluster s occupies positions gs[s] .. ge[s]; cls(j) is the
 // cluster and val(j) the reward bits of record j. Warp w composes clusters
@@ -351,29 +335,61 @@ __device__ void compose_sorted_block(Cls cls, Val val, uint32_t nr, uint32_t M, 
     __syncthreads();
 }
 
-// 5a. one block per cell of the grouping list (up to kBlockGroup records):
-// the ordering of the warp path done by the whole block, warps composing
-// different clusters in parallel; larger cells go to the sorting list.
-template <int P, class Rows>
-__global__ void __launch_bounds__(kGroupThreads)
-k_learn_group(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t* __restrict__ touched,
-              const uint32_t* __restrict__ start, const uint32_t* __restrict__ len, const uint32_t* __restrict__ list,
-              uint32_t* __restrict__ next, uint32_t* __restrict__ cursor, Rows rows, uint32_t* __restrict__ status)
+// 4. Eq. 1 + Eq. 2 of every touched cell of at most kBlockGroup records in
+// one persistent launch. Phase 1: blocks take the cells of the grouping list
+// (more than kWarpBucket records; the ordering of the warp path done by the
+// whole block, warps composing different clusters in parallel). Phase 2:
+// warps take the touched cells one by one and order those of at most
+// kWarpBucket records themselves. Both phases draw from atomic work counters
+// (ctr[4], ctr[5]), so the long cells start first and the blocks that drew
+// one join the second phase late instead of leaving a tail; a warp fetches
+// its next cell index while it works on the current one.
+template <int P, int WARPS, int MINB, class Rows>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t* __restrict__ group_list,
+                const uint32_t* __restrict__ touched, const uint32_t* __restrict__ start,
+                const uint32_t* __restrict__ len, uint32_t* __restrict__ cursor, Rows rows,
+                uint32_t* __restrict__ status)
 {
-    __shared__ CellOrder<kBlockGroup> o;
-    const uint32_t n = *(volatile const uint32_t*)(ctr + 3);
-    for (uint32_t bi = blockIdx.x; bi < n; bi += gridDim.x) {
-        const uint32_t w = list[bi];
+    __shared__ union {
+        CellOrder<kWarpBucket> warp[WARPS];
+        CellOrder<kBlockGroup> block;
+    } sm;
+    __shared__ uint32_t s_next;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t n_group = *(volatile const uint32_t*)(ctr + 3);
+    const uint32_t total = *(volatile const uint32_t*)ctr;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(ctr + 4, 1u);
+        __syncthreads();
+        const uint32_t bi = s_next;
+        __syncthreads();
+        if (bi >= n_group) break;  // uniform across the block
+        const uint32_t w = group_list[bi];
         const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
-        if (nr > kBlockGroup) {
-            if (threadIdx.x == 0) next[atomicAdd(ctr + 2, 1u)] = w;
-            continue;  // uniform across the block
-        }
         const RowRef<P> r = rows.row(slot);
-        learn_cell_grouped<P>(BlockTeam{}, o, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M, r.m, r.alpha,
-                              r.eps, r.Q, r.C, status);
+        learn_cell_grouped<P>(BlockTeam{}, sm.block, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M, r.m,
+                              r.alpha, r.eps, r.Q, r.C, status);
         if (threadIdx.x == 0) cursor[slot] = 0u;
         __syncthreads();
+    }
+    // every warp of the block has left phase 1: the shared memory is per warp now
+    uint32_t next = 0;
+    if (lane == 0) next = atomicAdd(ctr + 5, 1u);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    while (next < total) {
+        const uint32_t i = next;
+        uint32_t ahead = 0;
+        if (lane == 0) ahead = atomicAdd(ctr + 5, 1u);
+        const uint32_t slot = touched[i], nr = len[i];
+        if (nr <= kWarpBucket) {
+            const RowRef<P> r = rows.row(slot);
+            const uint32_t b0 = start[i];
+            learn_cell_grouped<P>(WarpTeam{}, sm.warp[warp], bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M,
+                                  r.m, r.alpha, r.eps, r.Q, r.C, status);
+            if (lane == 0) cursor[slot] = 0u;
+        }
+        next = __shfl_sync(0xffffffffu, ahead, 0);
     }
 }
 
@@ -463,9 +479,11 @@ inline size_t bucketed_scratch_bytes(int64_t n)
 }
 
 // Enqueues the whole learning step for n >= 1 records. The caller has
-// zeroed ctr[0..3] on the stream and holds `cursor` [cells] at zero (left at
+// zeroed ctr[0..5] on the stream and holds `cursor` [cells] at zero (left at
 // zero again); touched, start, len [cells] and lists [2 * cells] are outputs
-// and scratch.
+// and scratch. Counters: ctr[0] touched cells, [1] claimed records, [2]
+// sorting list, [3] grouping list, [4] and [5] work counters of
+// k_learn_buckets.
 template <int P, class Dec, class Rows>
 cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uint32_t* rec_key,
                                   const float* rec_val, int64_t n, Dec dec, Rows rows, uint32_t cells,
@@ -482,12 +500,10 @@ cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uin
     uint32_t* group_list = lists;
     uint32_t* sort_list = lists + cells;
     k_bucket_count<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, n, dec, cursor, touched, ctr);
-    k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(touched, ctr, cursor, start, len);
+    k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(touched, ctr, cursor, start, len, group_list, sort_list);
     k_bucket_scatter<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, dec, cursor, bucket);
-    k_learn_tier<P, kWarpBucket, 6, 5, Rows><<<sms * 5, 6 * 32, 0, s>>>(
-        bucket, nullptr, ctr, group_list, ctr + 3, touched, start, len, cursor, rows, status);
-    k_learn_group<P, Rows><<<sms * 4, kGroupThreads, 0, s>>>(bucket, ctr, touched, start, len, group_list, sort_list,
-                                                              cursor, rows, status);
+    k_learn_buckets<P, 6, 5, Rows><<<sms * 5, 6 * 32, 0, s>>>(bucket, ctr, group_list, touched, start, len, cursor,
+                                                              rows, status);
     cudaError_t e = big_smem_attribute<P, Rows>(device);
     if (e != cudaSuccess) return e;
     k_learn_big<P, Rows><<<sms * 2, kBigThreads, kBigSmem, s>>>(bucket, wide, rec_val, ctr, touched, start, len,

@@ -268,7 +268,7 @@ template <int P>
 int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n)
 {
     cudaStream_t s = ctx->stream;
-    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, 4 * sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, 8 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return check_cuda(ctx, e, "memset touched");
     if (n <= 0) return RLL_OK;
     if (n > 0xFFFFFFFFll) return fail(ctx, RLL_E_INVALID, "more than 2^32 - 1 records");
@@ -420,7 +420,7 @@ template <int P>
 int learn_scratch_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n, void* scratch)
 {
     cudaStream_t s = ctx->stream;
-    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, 4 * sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(g->n_touched, 0, 8 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return check_cuda(ctx, e, "memset touched");
     if (n <= 0) return RLL_OK;
     const uint32_t HM = g->H * g->M;

@@ -70,7 +70,8 @@ struct rll_grid {
     uint32_t* touched = nullptr;         // [H] cells touched by the last learn_update
     uint32_t* touched_start = nullptr;   // [H] first record of each touched cell (sorted / bucketed)
     uint32_t* touched_len = nullptr;     // [H] records of each touched cell (bucketed learning)
-    uint32_t* n_touched = nullptr;       // [4]: touched cells, bucket space claimed, sorting- and grouping-path cells
+    uint32_t* n_touched = nullptr;       // [8]: touched cells, bucket space claimed, sorting- and grouping-path
+                                         // cells, two work counters of the learning kernel
     uint32_t* cursor = nullptr;          // [H] per-slot record count / scatter cursor, all zero between calls
     uint32_t* big = nullptr;             // [2H] touched-cell indices for the grouping, then the sorting block path
     bool cursor_dirty = false;           // a learning call stopped before the cursors were cleared
