@@ -127,6 +127,15 @@ struct SampleStream {
         frame = fr;
         block = 0xFFFFFFFFu;
     }
+    // the four words of Philox block b (draws 4b .. 4b + 3)
+    __device__ __forceinline__ uint4 block_words(uint32_t b)
+    {
+        if (b != block) {
+            words = philox4x32_10(make_uint4(sample_id, frame, b, 0u), key);
+            block = b;
+        }
+        return words;
+    }
     __device__ __forceinline__ float draw(uint32_t i)
     {
         const uint32_t b = i >> 2;

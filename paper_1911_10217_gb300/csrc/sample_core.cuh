@@ -385,8 +385,20 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
             light = (int64_t)node - nl1;
         } else {
             const float2 vn0 = make_float2(n0, n0), vn1 = make_float2(n1, n1), vn2 = make_float2(n2, n2);
-            for (uint32_t level = 0; (int64_t)node < nl1; ++level)
-                descent_step(a, node, p_in, rs.draw(kDrawDescent + level), x0, x1, x2, vn0, vn1, vn2);
+            // level l takes draw kDrawDescent + l: words 1..3 of Philox block 2, then four levels per
+            // block, unrolled so that every word index is a constant
+            static_assert(kDrawDescent == 9, "descent draws start at word 1 of block 2");
+            uint4 w = rs.block_words(2);
+            if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.y), x0, x1, x2, vn0, vn1, vn2);
+            if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.z), x0, x1, x2, vn0, vn1, vn2);
+            if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.w), x0, x1, x2, vn0, vn1, vn2);
+            for (uint32_t b = 3; (int64_t)node < nl1; ++b) {
+                w = rs.block_words(b);
+                descent_step(a, node, p_in, u24(w.x), x0, x1, x2, vn0, vn1, vn2);
+                if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.y), x0, x1, x2, vn0, vn1, vn2);
+                if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.z), x0, x1, x2, vn0, vn1, vn2);
+                if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.w), x0, x1, x2, vn0, vn1, vn2);
+            }
             light = (int64_t)node - nl1;
         }
         const LightRec Lr = load_light(a.lights + light);

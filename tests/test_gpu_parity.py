@@ -282,8 +282,9 @@ def test_host_pass_matches_device_pass(env, chunks):
     """The host pass (chunked uploads, shading on two streams, overlapped
     read-back) gives the rgb and learned tables of the device pass."""
     O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
-    s = scenes.frame_scene(width=256, height=144, n_patches=16, tris_per_patch=256, table_size=1 << 16)
-    assert s.n_points >= 8 * 4096  # 8 chunks of the smallest size
+    # 250 x 144 points: chunks of 4 608 (8 chunks) or 12 032 (3 chunks) leave a ragged last chunk
+    s = scenes.frame_scene(width=250, height=144, n_patches=16, tris_per_patch=256, table_size=1 << 16)
+    assert s.n_points >= 8 * 4096 and s.n_points % 4608 != 0 and s.n_points % 12032 != 0
     _, dt, d = _trees(env, s)
     a = rll.Grid(ctx, dt, params_for(rll, s))
     b = rll.Grid(ctx, dt, params_for(rll, s))
