@@ -305,8 +305,10 @@ __device__ void learn_cell_grouped(Team team, CellOrder<CAP>& o, const uint32_t*
     if (w0) {
         store_q_row<P>(qrow, m, o.q);
         __syncwarp();
-        warp_rebuild_cdf<P>(o.q, (int)m, eps, crow, reinterpret_cast<float*>(o.b_sid),
-                            reinterpret_cast<uint16_t*>(o.b_val));
+        // scratch rows of kMaxCut entries (cluster starts and cursors are no longer needed); the
+        // record arrays hold only CAP entries, fewer than a cut of more than CAP leaves
+        warp_rebuild_cdf<P>(o.q, (int)m, eps, crow, reinterpret_cast<float*>(o.start),
+                            reinterpret_cast<uint16_t*>(o.cur));
     }
 }
 

@@ -66,6 +66,9 @@ def test_tree_matches_oracle_bit_exact(env, maker, builder):
     dict(mode="descent2", precision="bf16", jitter=True),
     dict(builder="median"),
     dict(builder="median", precision="fp16", jitter=True),
+    # the largest cut (every light of the tiny scene): Eq. 2 rows of 256 entries in 16-bit tables
+    dict(cut_size=256, precision="fp16"),
+    dict(cut_size=256, precision="bf16"),
 ])
 def test_lockstep_learning_tiny(env, variant):
     """Eight passes of the tiny scene. At each pass the oracle's state is
@@ -341,6 +344,9 @@ def test_long_run_stays_finite(env):
     ("tiny", dict(cell_size=0.5), 4),                  # ~4K records per cell: one block, in place
     ("tiny", dict(cell_size=0.25, precision="fp16"), 4),
     ("tiny", dict(cell_size=4.0), 8),                  # one cell of 32K records: one block, in place
+    # cuts of 256 leaves in 16-bit tables, cells of ~64 records (warp path): Eq. 2 over 256 entries
+    ("tiny", dict(cell_size=0.0625, cut_size=256, precision="fp16"), 4),
+    ("tiny", dict(cell_size=0.0625, cut_size=256, precision="bf16"), 4),
 ])
 def test_bucketed_learning_matches_sorted_path(env, maker, kw, spp):
     """rll_learn_update groups records by cell with atomics and sorts each
