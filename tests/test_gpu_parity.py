@@ -229,6 +229,21 @@ def test_edge_cases(env):
     assert torch.isfinite(out["rgb"]).all()
     rll.learn_update(ctx, gs, out["key"], out["val"])
     assert ctx.sync_status() == 0
+    # the largest occluder set (1024 boxes, 32 KB of shared memory per block): 1024 small seeded
+    # boxes inside the room
+    rng = np.random.default_rng(11)
+    lo = rng.uniform(0.05, 0.93, size=(1024, 3)).astype(np.float32)
+    big_boxes = np.concatenate([lo, lo + rng.uniform(0.005, 0.02, size=(1024, 3)).astype(np.float32)], axis=1)
+    dgb = rll.Grid(ctx, dt, params_for(rll, s))
+    db = dict(d, boxes=torch.from_numpy(np.ascontiguousarray(big_boxes)).to(dev))
+    gb = to_host(run_sample(rll, ctx, dgb, dt, db, 7, 0, 1))
+    sb = scenes.Scene("b", s.tris, s.emission, big_boxes, s.pos, s.nrm, s.albedo, s.grid, 1, 1, 7)
+    ogb = O.Grid.for_scene(ot, s)
+    ob = ogb.sample_frame(O.scene_arrays(sb), 7, 0, 1)
+    compare_samples(gb, ob, dgb.export()["keys"], ogb.keys, dgb.M)
+    with pytest.raises(rll.RllError):  # one more box is refused
+        more = torch.zeros(1025, 6, device=dev)
+        rll.sample_and_shade(ctx, dgb, dt, d["pos"], d["nrm"], d["alb"], more, 0, 0, 1, g["rgb"])
     # invalid arguments are refused without launching
     with pytest.raises(rll.RllError):
         rll.sample_and_shade(ctx, dg, dt, d["pos"], d["nrm"], d["alb"], d["boxes"], 0, 0, 0, g["rgb"])
@@ -280,8 +295,8 @@ def test_checkpoint_resume_is_exact(env):
         assert np.array_equal(full[k][fo], resumed[k][ro]), k
 
 
-@pytest.mark.parametrize("chunks", [1, 3, 8])
-def test_host_pass_matches_device_pass(env, chunks):
+@pytest.mark.parametrize("chunks,spp", [(1, 1), (3, 2), (8, 1)])
+def test_host_pass_matches_device_pass(env, chunks, spp):
     """The host pass (chunked uploads, shading on two streams, overlapped
     read-back) gives the rgb and learned tables of the device pass."""
     O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
@@ -296,16 +311,16 @@ def test_host_pass_matches_device_pass(env, chunks):
     for f in range(3):
         # the plain kernel (no per-sample diagnostics), as the host pass uses
         g = dict(rgb=torch.empty(3, P, device=env["dev"]),
-                 key=torch.empty(P * s.spp, dtype=torch.int32, device=env["dev"]),
-                 val=torch.empty(P * s.spp, device=env["dev"]))
-        rll.sample_and_shade(ctx, a, dt, d["pos"], d["nrm"], d["alb"], d["boxes"], s.seed, f, s.spp,
+                 key=torch.empty(P * spp, dtype=torch.int32, device=env["dev"]),
+                 val=torch.empty(P * spp, device=env["dev"]))
+        rll.sample_and_shade(ctx, a, dt, d["pos"], d["nrm"], d["alb"], d["boxes"], s.seed, f, spp,
                              g["rgb"], g["key"], g["val"])
         rll.learn_update(ctx, a, g["key"], g["val"])
         rll.split_collapse(ctx, a, dt)
         rgb = np.zeros((3, P), np.float32)
         rll.render_pass_host(ctx, b, dt, np.ascontiguousarray(s.pos), np.ascontiguousarray(s.nrm),
                              np.ascontiguousarray(s.albedo), np.ascontiguousarray(s.boxes), s.seed, f,
-                             s.spp, rgb)
+                             spp, rgb)
         assert np.array_equal(rgb, g["rgb"].cpu().numpy())
         ea, eb = a.export(), b.export()
         fa, fb = np.argsort(ea["keys"]), np.argsort(eb["keys"])
