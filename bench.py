@@ -789,6 +789,8 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
+    ap.add_argument("--separate-split", action="store_true",
+                    help="learning step as rll_learn_update + rll_split_collapse instead of the fused call")
     ap.add_argument("--host-chunks", type=int, default=8,
                     help="chunks of the host-buffer pass (copy/compute overlap)")
     ap.add_argument("--tree", default="lbvh", choices=["lbvh", "saoh", "median"])
@@ -886,10 +888,15 @@ def main():
         rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, scene.seed, frame, S, rgb, key, val)
         if ev:
             ev[1].record(stream)
-        rll.learn_update(ctx, grid, key, val)
-        if ev:
-            ev[2].record(stream)
-        rll.split_collapse(ctx, grid, tree)
+        if args.separate_split:
+            rll.learn_update(ctx, grid, key, val)
+            if ev:
+                ev[2].record(stream)
+            rll.split_collapse(ctx, grid, tree)
+        else:  # Eq. 1, split-collapse and Eq. 2 in the learning kernels
+            rll.learn_update_split(ctx, grid, tree, key, val)
+            if ev:
+                ev[2].record(stream)
         if ev:
             ev[3].record(stream)
 
@@ -962,9 +969,10 @@ def main():
         hbm_ach = bytes_per_sample() * n_sample / t_s / 1e9
         learn_bytes = 8 * n_sample  # records read once (keys + rewards)
         t_l = statistics.mean(t_learn) * 1e-3
-        # our kernels per step: sampling 1; learning: count, claim, scatter, warp tier, grouping block
-        # tier, sorting block tier = 6; split-collapse 1 (the launch list of profiles/ shows them)
-        launches_per_step = 1 + 6 + 1
+        # our kernels per step: sampling 1; learning: count, claim, scatter, the warp and grouping block
+        # paths (one launch), the sorting block path = 5; split-collapse 1 unless fused into learning
+        # (the launch list of profiles/ shows them)
+        launches_per_step = 1 + 5 + (1 if args.separate_split else 0)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -984,9 +992,12 @@ def main():
                        "d2h_bytes_per_step": int(12 * P)},
                "gpu_launches": args.steps * launches_per_step,
                "clocks": clk,
-               "extras": {"per_kernel_ms": {"sample_and_shade": statistics.mean(t_sample),
-                                            "learn_update": statistics.mean(t_learn),
-                                            "split_collapse": statistics.mean(t_split)},
+               "extras": {"per_kernel_ms": ({"sample_and_shade": statistics.mean(t_sample),
+                                             "learn_update": statistics.mean(t_learn),
+                                             "split_collapse": statistics.mean(t_split)}
+                                            if args.separate_split else
+                                            {"sample_and_shade": statistics.mean(t_sample),
+                                             "learn_update_split": statistics.mean(t_learn)}),
                           "p50_frame_ms": statistics.median(t_step),
                           "p99_frame_ms": float(np.percentile(t_step, 99)),
                           "learn_update_algorithmic_gbs": learn_bytes / t_l / 1e9,

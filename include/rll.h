@@ -254,6 +254,15 @@ int rll_learn_update(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key, cons
 int rll_learn_update_noalloc(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key,
                              const float* rec_val, int64_t n_records);
 
+/* rll_learn_update followed by rll_split_collapse, fused: each touched
+ * cell's Eq. 1 update, split-collapse steps (on the Q values as stored in the
+ * table precision) and one Eq. 2 rebuild run back to back in the learning
+ * kernels, so the rows are read once and C is built once. Tables, cut rows
+ * and the touched set afterwards are identical to those of the two calls.
+ * Same arguments and errors as those two calls. Enqueued on the context
+ * stream. */
+int rll_learn_update_split(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const uint32_t* rec_key,
+                           const float* rec_val, int64_t n_records);
 /* Split-collapse (Section 3, Fig. "TreeCuts"; Section 3.1: one thread group
  * per cell) on every cell touched by the last rll_learn_update: split the
  * non-single-light leaf of largest Q into its children and collapse the

@@ -521,6 +521,18 @@ int rll_learn_update(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key, cons
     return learn_update(ctx, grid, rec_key, rec_val, n_records);
 }
 
+int rll_learn_update_split(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const uint32_t* rec_key,
+                           const float* rec_val, int64_t n_records)
+{
+    if (!ctx) return RLL_E_INVALID;
+    if (!grid || !tree) return fail(ctx, RLL_E_INVALID, "grid / tree is NULL");
+    if (grid->n_lights != tree->n) return fail(ctx, RLL_E_INVALID, "grid was created for another tree");
+    if (n_records < 0 || n_records >= 0xFFFFFFFFll) return fail(ctx, RLL_E_INVALID, "n_records out of range");
+    if (n_records > 0 && (!rec_key || !rec_val)) return fail(ctx, RLL_E_INVALID, "NULL records");
+    DeviceGuard g(ctx->device);
+    return learn_update_split(ctx, grid, tree, rec_key, rec_val, n_records);
+}
+
 int rll_split_collapse(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree)
 {
     if (!ctx) return RLL_E_INVALID;
@@ -619,8 +631,8 @@ int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, con
         e = cudaEventRecord(ev_join, ctx->comp2);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
     }
-    if (e == cudaSuccess && rc == RLL_OK) rc = learn_update(ctx, grid, d_key, d_val, S);
-    if (e == cudaSuccess && rc == RLL_OK && do_split) rc = split_collapse(ctx, grid, tree);
+    if (e == cudaSuccess && rc == RLL_OK)
+        rc = do_split ? learn_update_split(ctx, grid, tree, d_key, d_val, S) : learn_update(ctx, grid, d_key, d_val, S);
     if (e == cudaSuccess) e = cudaEventRecord(ev_down, ctx->down);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_down, 0);
     // every stream of the pipeline is drained before returning, also on errors

@@ -354,9 +354,9 @@ int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int6
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->n_touched, 8 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->cursor, 0, 4 * (size_t)max_cells, ctx->stream);
     // the learning step's shared-memory opt-in, now rather than during a graph capture
-    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP32, BatchRows<RLL_PREC_FP32>>(ctx->device);
-    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP16, BatchRows<RLL_PREC_FP16>>(ctx->device);
-    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_BF16, BatchRows<RLL_PREC_BF16>>(ctx->device);
+    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP32, BatchRows<RLL_PREC_FP32>, NoSplit>(ctx->device);
+    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP16, BatchRows<RLL_PREC_FP16>, NoSplit>(ctx->device);
+    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_BF16, BatchRows<RLL_PREC_BF16>, NoSplit>(ctx->device);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_work, 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, sizeof(BatchItemDev) * max_items);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tile_prefix, 4 * (max_items + 1));

@@ -181,7 +181,37 @@ struct CellOrder {
     uint32_t start[kMaxCut];  // first position of each cluster in B
     uint32_t cur[kMaxCut];    // scatter cursors, then one past the last position
     float q[kMaxCut];
+    // Once Eq. 1 is composed, the record arrays (the first 16 CAP bytes) are
+    // dead: they give the float and 16-bit scratch rows (kMaxCut entries each)
+    // of Eq. 2 and split-collapse.
+    static_assert(16u * CAP >= 6u * (uint32_t)kMaxCut, "record arrays too small for the scratch rows");
+    __device__ __forceinline__ float* scratch_c() { return reinterpret_cast<float*>(this); }
+    __device__ __forceinline__ uint16_t* scratch_bits()
+    {
+        return reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(this) + 4 * kMaxCut);
+    }
 };
+
+// Split-collapse policy of the learning kernels: NoSplit leaves it to a
+// separate call; WithSplit runs it on each cell right after the cell's Eq. 1,
+// before the one Eq. 2 rebuild (cut rows of M entries at cut + slot M, the
+// light tree, threshold T, at most max_iter steps).
+struct SplitArgs {
+    uint32_t* cut;
+    uint32_t M;
+    const NodeRec* nodes;
+    const int32_t *parent, *left, *right;
+    float T;
+    uint32_t max_iter;
+    int64_t n_nodes;
+};
+struct NoSplit : SplitArgs {
+    static constexpr bool kOn = false;
+};
+struct WithSplit : SplitArgs {
+    static constexpr bool kOn = true;
+};
+
 
 // A team orders one cell; its first warp (lead()) also scans and composes.
 struct WarpTeam {
@@ -216,16 +246,45 @@ __device__ __forceinline__ void store_q_row(typename Store<P>::T* qrow, uint32_t
     }
 }
 
+// Last step of one cell, by one warp: Q (q, m entries) stored to the table
+// precision (q then holds the stored values); with a split policy,
+// split-collapse on those values and the rows it changed stored; then Eq. 2
+// from the final Q. Scratch rows of kMaxCut entries: cs, nc, c, bits.
+template <int P, class Split>
+__device__ void finish_cell(const Split& sp, uint32_t slot, float* q, uint32_t m, float eps,
+                            typename Store<P>::T* qrow, typename Store<P>::T* crow, uint32_t* cs, uint32_t* nc,
+                            float* c, uint16_t* bits, uint32_t* status)
+{
+    store_q_row<P>(qrow, m, q);
+    __syncwarp();
+    if constexpr (Split::kOn) {
+        const int lane = threadIdx.x & 31;
+        uint32_t* cutrow = sp.cut + (int64_t)slot * sp.M;
+        if (load_cut_row(cutrow, cs, m, sp.n_nodes, status)) {
+            const uint32_t steps = split_collapse_steps<P>(cs, q, c, nc, m, sp.nodes, sp.parent, sp.left, sp.right,
+                                                           sp.T, sp.max_iter, sp.n_nodes);
+            if (steps) {
+                for (uint32_t s = lane; s < m; s += 32) {
+                    cutrow[s] = cs[s];
+                    qrow[s] = Store<P>::store(q[s]);  // exact: q holds table values
+                }
+                __syncwarp();
+            }
+        }
+    }
+    warp_rebuild_cdf<P>(q, (int)m, eps, crow, c, bits);
+}
+
 // Eq. 1 + Eq. 2 of one cell from its bucket of nr <= CAP records: grouped
 // by cluster (counting sort, any order inside a group), then each record's
 // rank by sample id inside its group is counted, which puts them in
 // (cluster, sample) order; warp 0 of the team composes, stores Q and
 // rebuilds C. Called by every thread of the team.
-template <int P, uint32_t CAP, class Team>
+template <int P, uint32_t CAP, class Team, class Split>
 __device__ void learn_cell_grouped(Team team, CellOrder<CAP>& o, const uint32_t* __restrict__ bsid,
                                    const uint8_t* __restrict__ bs, const uint32_t* __restrict__ bval, uint32_t nr,
                                    uint32_t M, uint32_t m, float alpha, float eps, typename Store<P>::T* qrow,
-                                   typename Store<P>::T* crow, uint32_t* status)
+                                   typename Store<P>::T* crow, const Split& sp, uint32_t slot, uint32_t* status)
 {
     const uint32_t t = team.tid(), T = team.size();
     const int lane = threadIdx.x & 31;
@@ -302,14 +361,8 @@ __device__ void learn_cell_grouped(Team team, CellOrder<CAP>& o, const uint32_t*
         }
         team.sync();
     }
-    if (w0) {
-        store_q_row<P>(qrow, m, o.q);
-        __syncwarp();
-        // scratch rows of kMaxCut entries (cluster starts and cursors are no longer needed); the
-        // record arrays hold only CAP entries, fewer than a cut of more than CAP leaves
-        warp_rebuild_cdf<P>(o.q, (int)m, eps, crow, reinterpret_cast<float*>(o.start),
-                            reinterpret_cast<uint16_t*>(o.cur));
-    }
+    if (w0)  // cluster starts and cursors are dead too: the cut scratch rows
+        finish_cell<P>(sp, slot, o.q, m, eps, qrow, crow, o.start, o.cur, o.scratch_c(), o.scratch_bits(), status);
 }
 
 // Eq. 1 of one cell whose records are sorted by (cluster, sample id), by a
@@ -346,11 +399,11 @@ __device__ void compose_sorted_block(Cls cls, Val val, uint32_t nr, uint32_t M, 
 // (ctr[4], ctr[5]), so the long cells start first and the blocks that drew
 // one join the second phase late instead of leaving a tail; a warp fetches
 // its next cell index while it works on the current one.
-template <int P, int WARPS, int MINB, class Rows>
+template <int P, int WARPS, int MINB, class Rows, class Split>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
 k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t* __restrict__ group_list,
                 const uint32_t* __restrict__ touched, const uint32_t* __restrict__ start,
-                const uint32_t* __restrict__ len, uint32_t* __restrict__ cursor, Rows rows,
+                const uint32_t* __restrict__ len, uint32_t* __restrict__ cursor, Rows rows, Split sp,
                 uint32_t* __restrict__ status)
 {
     __shared__ union {
@@ -371,7 +424,7 @@ k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t*
         const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
         const RowRef<P> r = rows.row(slot);
         learn_cell_grouped<P>(BlockTeam{}, sm.block, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M, r.m,
-                              r.alpha, r.eps, r.Q, r.C, status);
+                              r.alpha, r.eps, r.Q, r.C, sp, slot, status);
         if (threadIdx.x == 0) cursor[slot] = 0u;
         __syncthreads();
     }
@@ -388,7 +441,7 @@ k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t*
             const RowRef<P> r = rows.row(slot);
             const uint32_t b0 = start[i];
             learn_cell_grouped<P>(WarpTeam{}, sm.warp[warp], bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M,
-                                  r.m, r.alpha, r.eps, r.Q, r.C, status);
+                                  r.m, r.alpha, r.eps, r.Q, r.C, sp, slot, status);
             if (lane == 0) cursor[slot] = 0u;
         }
         next = __shfl_sync(0xffffffffu, ahead, 0);
@@ -400,13 +453,13 @@ k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t*
 // in shared memory, rewards gathered in that order. Larger cells: (cluster
 // << 32 | sample id) sorted in place in global scratch, rewards read by
 // sample id. Then Eq. 1 (warps composing different clusters) and Eq. 2.
-template <int P, class Rows>
+template <int P, class Rows, class Split>
 __global__ void __launch_bounds__(kBigThreads)
 k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const float* __restrict__ rec_val,
             const uint32_t* __restrict__ ctr,
             const uint32_t* __restrict__ touched, const uint32_t* __restrict__ start,
             const uint32_t* __restrict__ len, const uint32_t* __restrict__ big, uint32_t* __restrict__ cursor,
-            Rows rows, uint32_t* __restrict__ status)
+            Rows rows, Split sp, uint32_t* __restrict__ status)
 {
     extern __shared__ unsigned long long s_key[];      // kBlockSort keys, then kBlockSort rewards (u32)
     uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kBlockSort);
@@ -446,10 +499,8 @@ k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const fl
             compose_sorted_block<P>([&](uint32_t j) { return (uint32_t)(rec[j] >> 32); },
                                     [&](uint32_t j) { return (uint32_t)rec[j]; }, nr, M, m, alpha, s_q, s_gs, s_ge);
         }
-        if (threadIdx.x < 32) {
-            store_q_row<P>(r.Q, m, s_q);
-            __syncwarp();
-            warp_rebuild_cdf<P>(s_q, (int)m, r.eps, r.C, s_c, s_b);
+        if (threadIdx.x < 32) {  // the cluster bounds are dead: the cut scratch rows
+            finish_cell<P>(sp, slot, s_q, m, r.eps, r.Q, r.C, s_gs, s_ge, s_c, s_b, status);
             if (threadIdx.x == 0) cursor[slot] = 0u;
         }
         __syncthreads();
@@ -458,14 +509,14 @@ k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const fl
 
 // k_learn_big's shared-memory opt-in (above the 48 KB default), once per
 // device and precision
-template <int P, class Rows>
+template <int P, class Rows, class Split>
 cudaError_t big_smem_attribute(int device)
 {
     static std::mutex mu;
     static bool done[64] = {};
     std::lock_guard<std::mutex> lock(mu);
     if (device >= 0 && device < 64 && done[device]) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(k_learn_big<P, Rows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const cudaError_t e = cudaFuncSetAttribute(k_learn_big<P, Rows, Split>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)kBigSmem);
     if (e == cudaSuccess && device >= 0 && device < 64) done[device] = true;
     return e;
@@ -486,11 +537,12 @@ inline size_t bucketed_scratch_bytes(int64_t n)
 // and scratch. Counters: ctr[0] touched cells, [1] claimed records, [2]
 // sorting list, [3] grouping list, [4] and [5] work counters of
 // k_learn_buckets.
-template <int P, class Dec, class Rows>
+template <int P, class Dec, class Rows, class Split = NoSplit>
 cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uint32_t* rec_key,
                                   const float* rec_val, int64_t n, Dec dec, Rows rows, uint32_t cells,
                                   uint32_t* cursor, uint32_t* touched, uint32_t* start, uint32_t* len,
-                                  uint32_t* ctr, uint32_t* lists, void* scratch, uint32_t* status)
+                                  uint32_t* ctr, uint32_t* lists, void* scratch, uint32_t* status,
+                                  Split sp = Split{})
 {
     const size_t n4 = ((size_t)n * 4 + 255) & ~(size_t)255, n1 = ((size_t)n + 255) & ~(size_t)255;
     char* ws = static_cast<char*>(scratch);
@@ -504,12 +556,12 @@ cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uin
     k_bucket_count<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, n, dec, cursor, touched, ctr);
     k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(touched, ctr, cursor, start, len, group_list, sort_list);
     k_bucket_scatter<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, dec, cursor, bucket);
-    k_learn_buckets<P, 6, 5, Rows><<<sms * 5, 6 * 32, 0, s>>>(bucket, ctr, group_list, touched, start, len, cursor,
-                                                              rows, status);
-    cudaError_t e = big_smem_attribute<P, Rows>(device);
+    k_learn_buckets<P, 6, 5, Rows, Split><<<sms * 5, 6 * 32, 0, s>>>(bucket, ctr, group_list, touched, start, len,
+                                                                     cursor, rows, sp, status);
+    cudaError_t e = big_smem_attribute<P, Rows, Split>(device);
     if (e != cudaSuccess) return e;
-    k_learn_big<P, Rows><<<sms * 2, kBigThreads, kBigSmem, s>>>(bucket, wide, rec_val, ctr, touched, start, len,
-                                                               sort_list, cursor, rows, status);
+    k_learn_big<P, Rows, Split><<<sms * 2, kBigThreads, kBigSmem, s>>>(bucket, wide, rec_val, ctr, touched, start,
+                                                                      len, sort_list, cursor, rows, sp, status);
     return cudaGetLastError();
 }
 

@@ -264,8 +264,8 @@ struct GridRows {
     }
 };
 
-template <int P>
-int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n)
+template <int P, class Split = NoSplit>
+int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n, Split sp = Split{})
 {
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaMemsetAsync(g->n_touched, 0, 8 * sizeof(uint32_t), s);
@@ -285,10 +285,28 @@ int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec
                                  GridDec{g->H * g->M, g->M},
                                  GridRows<P>{(T*)g->Q, (T*)g->C, g->M, g->m, g->p.alpha, g->p.eps}, g->H, g->cursor,
                                  g->touched, g->touched_start, g->touched_len, g->n_touched, g->big, ws,
-                                 ctx->d_status);
+                                 ctx->d_status, sp);
     if (e != cudaSuccess) return check_cuda(ctx, e, "learn kernels");
     g->cursor_dirty = false;
     return RLL_OK;
+}
+
+// Eq. 1, split-collapse and Eq. 2 of every touched cell in the learning kernels
+template <int P>
+int learn_split_t(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const uint32_t* rec_key, const float* rec_val,
+                  int64_t n)
+{
+    WithSplit sp;
+    sp.cut = g->cut;
+    sp.M = g->M;
+    sp.nodes = t->nodes;
+    sp.parent = t->parent;
+    sp.left = t->left;
+    sp.right = t->right;
+    sp.T = g->p.threshold;
+    sp.max_iter = split_steps(g->p);
+    sp.n_nodes = 2 * t->n - 1;
+    return learn_t<P>(ctx, g, rec_key, rec_val, n, sp);
 }
 
 template <int P>
@@ -394,6 +412,16 @@ int learn_update(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float
     case RLL_PREC_FP16: return learn_t<RLL_PREC_FP16>(ctx, g, rec_key, rec_val, n);
     case RLL_PREC_BF16: return learn_t<RLL_PREC_BF16>(ctx, g, rec_key, rec_val, n);
     default: return learn_t<RLL_PREC_FP32>(ctx, g, rec_key, rec_val, n);
+    }
+}
+
+int learn_update_split(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const uint32_t* rec_key, const float* rec_val,
+                       int64_t n)
+{
+    switch (g->p.precision) {
+    case RLL_PREC_FP16: return learn_split_t<RLL_PREC_FP16>(ctx, g, t, rec_key, rec_val, n);
+    case RLL_PREC_BF16: return learn_split_t<RLL_PREC_BF16>(ctx, g, t, rec_key, rec_val, n);
+    default: return learn_split_t<RLL_PREC_FP32>(ctx, g, t, rec_key, rec_val, n);
     }
 }
 

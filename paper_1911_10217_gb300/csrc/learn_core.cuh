@@ -238,30 +238,19 @@ __device__ void learn_records(Get get, uint32_t len, uint32_t m, float alpha, fl
     }
 }
 
-// Split-collapse of one cell (cut row crow, Q row qrow, cdf row ccrow),
-// repeated until a step changes nothing or max_iter steps were taken. New Q
-// values in correctly rounded binary32, then rounded to the table precision:
-// l_max's Q times f = phi_a / (phi_a + phi_c) and times 1 - f (children's
-// power), p_min's Q the sum of its children's.
+// Split-collapse steps on one cell's rows in shared memory (cut cs, Q q,
+// both of m entries; c and nc: scratch rows), repeated until a step changes
+// nothing or max_iter steps were taken; returns the number of steps taken.
+// New Q values in correctly rounded binary32, then rounded to the table
+// precision: l_max's Q times f = phi_a / (phi_a + phi_c) and times 1 - f
+// (children's power), p_min's Q the sum of its children's. One warp.
 template <int P>
-__device__ void split_one_cell(uint32_t* crow, typename Store<P>::T* qrow, typename Store<P>::T* ccrow, uint32_t m,
-                               const NodeRec* __restrict__ nodes, const int32_t* __restrict__ parent,
-                               const int32_t* __restrict__ left, const int32_t* __restrict__ right, float T,
-                               float eps, uint32_t max_iter, int64_t n_nodes, uint32_t* status, float* q, float* c,
-                               uint32_t* cs, uint32_t* nc, uint16_t* bits)
+__device__ uint32_t split_collapse_steps(uint32_t* cs, float* q, float* c, uint32_t* nc, uint32_t m,
+                                const NodeRec* __restrict__ nodes, const int32_t* __restrict__ parent,
+                                const int32_t* __restrict__ left, const int32_t* __restrict__ right, float T,
+                                uint32_t max_iter, int64_t n_nodes)
 {
     const int lane = threadIdx.x & 31;
-    bool bad = false;
-    for (uint32_t s = lane; s < m; s += 32) {
-        cs[s] = crow[s];
-        q[s] = Store<P>::load(qrow[s]);
-        bad |= (int64_t)cs[s] >= n_nodes;
-    }
-    if (__any_sync(0xffffffffu, bad)) {  // corrupt cut row: flag and leave the cell alone
-        if (lane == 0) atomicOr(status, (uint32_t)RLL_E_DEVICE);
-        return;
-    }
-    __syncwarp();
     const uint32_t n_internal = (uint32_t)((n_nodes - 1) / 2);  // ids below are internal nodes
     uint32_t steps = 0;
     for (; steps < max_iter; ++steps) {
@@ -322,6 +311,44 @@ __device__ void split_one_cell(uint32_t* crow, typename Store<P>::T* qrow, typen
         }
         __syncwarp();
     }
+    return steps;
+}
+
+// Loads cut row crow into cs (m entries); false (and RLL_E_DEVICE flagged)
+// when an entry is not a node of the tree. One warp.
+__device__ __forceinline__ bool load_cut_row(const uint32_t* crow, uint32_t* cs, uint32_t m, int64_t n_nodes,
+                                             uint32_t* status)
+{
+    const int lane = threadIdx.x & 31;
+    bool bad = false;
+    for (uint32_t s = lane; s < m; s += 32) {
+        cs[s] = crow[s];
+        bad |= (int64_t)cs[s] >= n_nodes;
+    }
+    if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) atomicOr(status, (uint32_t)RLL_E_DEVICE);
+        return false;
+    }
+    __syncwarp();
+    return true;
+}
+
+// Split-collapse of one cell (cut row crow, Q row qrow, cdf row ccrow): the
+// steps above on the rows loaded into shared memory; when a step was taken,
+// the rows are stored and C rebuilt (Eq. 2). A corrupt cut row is flagged
+// and the cell left alone. One warp; q, c, cs, nc, bits: its scratch rows.
+template <int P>
+__device__ void split_one_cell(uint32_t* crow, typename Store<P>::T* qrow, typename Store<P>::T* ccrow, uint32_t m,
+                               const NodeRec* __restrict__ nodes, const int32_t* __restrict__ parent,
+                               const int32_t* __restrict__ left, const int32_t* __restrict__ right, float T,
+                               float eps, uint32_t max_iter, int64_t n_nodes, uint32_t* status, float* q, float* c,
+                               uint32_t* cs, uint32_t* nc, uint16_t* bits)
+{
+    const int lane = threadIdx.x & 31;
+    if (!load_cut_row(crow, cs, m, n_nodes, status)) return;
+    for (uint32_t s = lane; s < m; s += 32) q[s] = Store<P>::load(qrow[s]);
+    __syncwarp();
+    const uint32_t steps = split_collapse_steps<P>(cs, q, c, nc, m, nodes, parent, left, right, T, max_iter, n_nodes);
     if (steps == 0) return;
     for (uint32_t s = lane; s < m; s += 32) {
         crow[s] = cs[s];

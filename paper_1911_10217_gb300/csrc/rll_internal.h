@@ -122,6 +122,9 @@ int device_sm_count(int device);
 inline uint32_t split_steps(const rll_grid_params& p) { return p.split_iterations ? p.split_iterations : 1u; }
 int learn_update(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n);
 int split_collapse(rll_ctx* ctx, rll_grid* g, const rll_tree* t);
+// learn_update followed by split_collapse, fused per cell (same tables)
+int learn_update_split(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const uint32_t* rec_key, const float* rec_val,
+                       int64_t n);
 // learn_update with the sort buffers in caller-provided device scratch
 int learn_update_with_scratch(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec_val, int64_t n,
                               void* scratch, size_t scratch_bytes);

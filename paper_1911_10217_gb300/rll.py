@@ -31,7 +31,8 @@ EXPORTS = [
     "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_export", "rll_grid_import",
     "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_and_shade_fp",
     "rll_sample_power",
-    "rll_learn_update", "rll_learn_update_noalloc", "rll_split_collapse", "rll_render_pass_host",
+    "rll_learn_update", "rll_learn_update_noalloc", "rll_learn_update_split", "rll_split_collapse",
+    "rll_render_pass_host",
     "rll_batch_reserve", "rll_batch_set_items", "rll_batch_create", "rll_batch_set_config", "rll_batch_tune", "rll_batch_run", "rll_batch_capture",
     "rll_batch_launch", "rll_batch_destroy",
 ]
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = True):
     L.rll_sample_power.argtypes = [P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P]
     L.rll_learn_update.argtypes = [P, P, P, P, I64]
     L.rll_learn_update_noalloc.argtypes = [P, P, P, P, I64]
+    L.rll_learn_update_split.argtypes = [P, P, P, P, P, I64]
     L.rll_split_collapse.argtypes = [P, P, P]
     L.rll_render_pass_host.argtypes = [P, P, P, P, P, P, I64, P, I32, U64, U32, I32, I32, P]
     L.rll_batch_create.argtypes = [P, ctypes.POINTER(BatchItem), I32, ctypes.POINTER(P)]
@@ -339,6 +341,12 @@ def sample_power(ctx: Context, tree: Tree, pos, nrm, albedo, boxes, seed, frame,
 def learn_update(ctx: Context, grid: Grid, rec_key, rec_val, n_records=None):
     n = int(rec_key.shape[0]) if n_records is None else int(n_records)
     ctx._check(ctx.lib.rll_learn_update(ctx.h, grid.h, _ptr(rec_key), _ptr(rec_val), n))
+
+
+def learn_update_split(ctx: Context, grid: Grid, tree: Tree, rec_key, rec_val, n_records=None):
+    """rll_learn_update_split: learn_update then split_collapse, fused per cell."""
+    n = int(rec_key.shape[0]) if n_records is None else int(n_records)
+    ctx._check(ctx.lib.rll_learn_update_split(ctx.h, grid.h, tree.h, _ptr(rec_key), _ptr(rec_val), n))
 
 
 def split_collapse(ctx: Context, grid: Grid, tree: Tree):

@@ -401,3 +401,42 @@ def test_bucketed_learning_matches_sorted_path(env, maker, kw, spp):
         og.learn(o["slot"], o["s"], o["reward"])
         compare_tables(A2.export(), oracle_state(og), og.m, RTOL[prec])
         assert ctx.sync_status() == 0
+
+
+@pytest.mark.parametrize("maker,kw,spp", [
+    ("small_frame", dict(), 2),                          # warp path
+    ("small_frame", dict(precision="bf16", split_iterations=4), 2),
+    ("tiny", dict(cell_size=0.25), 4),                    # block grouping path
+    ("tiny", dict(cell_size=0.5, precision="fp16"), 4),  # block sort in shared memory / in place
+    ("tiny", dict(cell_size=4.0), 8),                     # one cell, in-place global sort
+    # two cut entries per lane; threshold 1 so that cells split within six passes
+    ("small_frame", dict(cut_size=64, precision="fp16", split_iterations=16, threshold=1.0), 2),
+])
+def test_fused_learn_split_matches_two_calls(env, maker, kw, spp):
+    """rll_learn_update_split leaves the tables, cut rows and touched set that
+    rll_learn_update followed by rll_split_collapse leave."""
+    O, rll, ctx = env["O"], env["rll"], env["ctx"]
+    s = getattr(scenes, maker + "_scene")()
+    _, dt, d = _trees(env, s)
+    A = rll.Grid(ctx, dt, params_for(rll, s, **kw))
+    B = rll.Grid(ctx, dt, params_for(rll, s, **kw))
+    changed = 0
+    for frame in range(6):
+        out = run_sample(rll, ctx, A, dt, d, s.seed, frame, spp)
+        st = A.export()
+        B.import_state(st["keys"], st["cut"], st["q"], st["c"])
+        rll.learn_update(ctx, A, out["key"], out["val"])
+        rll.split_collapse(ctx, A, dt)
+        rll.learn_update_split(ctx, B, dt, out["key"], out["val"])
+        assert ctx.sync_status() == 0
+        a, b = A.export(), B.export()
+        for k in ("keys", "cut", "q", "c"):
+            assert np.array_equal(a[k], b[k]), (k, frame)
+        changed += int(np.sum(a["cut"] != st["cut"]))
+        # the same touched set: a second split-collapse acts on the same cells
+        rll.split_collapse(ctx, A, dt)
+        rll.split_collapse(ctx, B, dt)
+        a, b = A.export(), B.export()
+        for k in ("cut", "q", "c"):
+            assert np.array_equal(a[k], b[k]), (k, frame, "second split")
+    assert changed > 0  # split-collapse changed some cut rows
