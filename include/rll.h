@@ -106,7 +106,8 @@ int rll_ctx_set_stream(rll_ctx* ctx, void* cuda_stream);
  *   "sample_min_blocks" 3 | 4 -- resident 256-thread blocks per SM the
  *   sampling kernel's registers are held to (default 4);
  *   "host_chunks" 1..32 -- chunks rll_render_pass_host cuts the points into
- *   for copy/compute overlap (default 8; chunks of at least 4 096 points).
+ *   for copy/compute overlap (default 8; sizes growing by 3/2, at least 4 096
+ *   points each).
  * Returns RLL_E_INVALID for an unknown name or a value out of range. */
 int rll_ctx_set_option(rll_ctx* ctx, const char* name, int64_t value);
 int rll_ctx_destroy(rll_ctx* ctx);

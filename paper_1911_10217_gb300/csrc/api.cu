@@ -582,16 +582,31 @@ int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, con
     uint32_t* d_key = (uint32_t*)w; w += a(4 * S);
     float* d_val = (float*)w;
 
-    // Copy/compute overlap: the points are cut into chunks; chunk k is
+    // Copy/compute overlap: the points are cut into chunks (sizes below); chunk k is
     // uploaded on `up`, shaded on the main stream or comp2 (alternately, so a
     // chunk's tail overlaps the next chunk's start) once its upload is done,
     // and its rgb read back on `down` once it is shaded. Learning and
     // split-collapse follow all chunks on the main stream and overlap the
     // last read-backs. Sample ids, records and rgb are those of one launch.
-    const int64_t want = std::max<int64_t>(1, std::min<int64_t>(ctx->host_chunks, RLL_HOST_MAX_CHUNKS));
-    int64_t chunk = (P + want - 1) / want;
-    chunk = std::max<int64_t>(4096, (chunk + 255) & ~(int64_t)255);
-    const int nc = (int)((P + chunk - 1) / chunk);
+    // Chunk sizes grow by 3/2 (multiples of 256 points, at least 4 096): the first upload, which
+    // nothing overlaps, is short, and an upload (28 B a point) still ends before the shading of
+    // the chunk ahead of it.
+    const int want = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->host_chunks, RLL_HOST_MAX_CHUNKS));
+    int64_t bnd[RLL_HOST_MAX_CHUNKS + 1];
+    int nc = 0;
+    {
+        double wsum = 0.0, w = 1.0;
+        for (int k = 0; k < want; ++k, w *= 1.5) wsum += w;
+        int64_t b = 0;
+        w = 1.0;
+        bnd[0] = 0;
+        for (int k = 0; k < want && b < P; ++k, w *= 1.5) {
+            int64_t len = (int64_t)((double)P * w / wsum);
+            len = std::max<int64_t>(4096, (len + 255) & ~(int64_t)255);
+            b = (k == want - 1) ? P : std::min<int64_t>(P, b + len);
+            bnd[++nc] = b;
+        }
+    }
     cudaStream_t s = ctx->stream, sc[2] = {ctx->stream, ctx->comp2};
     cudaEvent_t* ev_up = ctx->ev;
     cudaEvent_t* ev_done = ctx->ev + RLL_HOST_MAX_CHUNKS;
@@ -613,7 +628,7 @@ int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, con
     if (e == cudaSuccess && n_boxes > 0)
         e = cudaMemcpyAsync(d_box, boxes, 24 * (size_t)n_boxes, cudaMemcpyHostToDevice, ctx->up);
     for (int k = 0; k < nc && e == cudaSuccess && rc == RLL_OK; ++k) {
-        const int64_t b = k * chunk, n = std::min(chunk, P - b);
+        const int64_t b = bnd[k], n = bnd[k + 1] - bnd[k];
         e = planes(d_pos, pos, b, n, cudaMemcpyHostToDevice, ctx->up);
         if (e == cudaSuccess) e = planes(d_nrm, nrm, b, n, cudaMemcpyHostToDevice, ctx->up);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_alb + b, albedo + b, 4 * (size_t)n, cudaMemcpyHostToDevice, ctx->up);

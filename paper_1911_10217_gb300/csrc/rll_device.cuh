@@ -22,6 +22,9 @@ constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint32_t kInvalidRecord = 0xFFFFFFFFu;
 constexpr int kMaxProbes = 64;
 constexpr int kMaxCut = 256;
+// Bound of every walk over the light tree: far above any builder's depth (radix tree of 64-bit
+// keys: <= 64 levels; SAOH: < 250 levels at 2^24 lights; median: ceil(log2 n)).
+constexpr int kMaxTreeDepth = 4096;
 constexpr int kMaxBoxes = 1024;
 constexpr uint32_t kMaxSplitIterations = 256;
 constexpr float kShadowOffset = 1e-4f;

@@ -354,6 +354,16 @@ __device__ __forceinline__ void descent2_step(const SampleArgs& a, uint32_t& nod
     node = __ldg(&q[pick].id);
 }
 
+// Light index of the node a descent ended on. A descent that ran into the
+// depth bound (only on a corrupt tree: no builder comes near it) is flagged
+// and takes the first light of the node it reached.
+__device__ __forceinline__ int64_t leaf_or_flag(const SampleArgs& a, uint32_t node, int64_t nl1)
+{
+    if ((int64_t)node >= nl1) return (int64_t)node - nl1;
+    atomicOr(a.status, (uint32_t)RLL_E_DEVICE);
+    return (int64_t)a.nodes[node].begin;
+}
+
 // All samples of shading point p, one thread (s_box: see stage_boxes).
 template <int P, int MODE, bool DBG>
 __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, const float4* s_box)
@@ -380,9 +390,9 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
             light = (int64_t)r.begin + (int64_t)(((unsigned long long)u24v * w) >> 24);
             p_in = 1.0f / (float)w;
         } else if (MODE == RLL_MODE_DESCENT2) {
-            for (uint32_t level = 0; (int64_t)node < nl1; ++level)
+            for (uint32_t level = 0; (int64_t)node < nl1 && level < (uint32_t)kMaxTreeDepth; ++level)
                 descent2_step(a, node, p_in, rs.draw(kDrawDescent + level), x0, x1, x2, n0, n1, n2);
-            light = (int64_t)node - nl1;
+            light = leaf_or_flag(a, node, nl1);
         } else {
             const float2 vn0 = make_float2(n0, n0), vn1 = make_float2(n1, n1), vn2 = make_float2(n2, n2);
             // level l takes draw kDrawDescent + l: words 1..3 of Philox block 2, then four levels per
@@ -392,14 +402,14 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
             if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.y), x0, x1, x2, vn0, vn1, vn2);
             if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.z), x0, x1, x2, vn0, vn1, vn2);
             if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.w), x0, x1, x2, vn0, vn1, vn2);
-            for (uint32_t b = 3; (int64_t)node < nl1; ++b) {
+            for (uint32_t b = 3; (int64_t)node < nl1 && b < (uint32_t)(kMaxTreeDepth / 4); ++b) {
                 w = rs.block_words(b);
                 descent_step(a, node, p_in, u24(w.x), x0, x1, x2, vn0, vn1, vn2);
                 if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.y), x0, x1, x2, vn0, vn1, vn2);
                 if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.z), x0, x1, x2, vn0, vn1, vn2);
                 if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.w), x0, x1, x2, vn0, vn1, vn2);
             }
-            light = (int64_t)node - nl1;
+            light = leaf_or_flag(a, node, nl1);
         }
         const LightRec Lr = load_light(a.lights + light);
         const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, su.p_cut, p_in, su.ua, su.ub, s_box, a.n_boxes,

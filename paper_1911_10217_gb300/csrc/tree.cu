@@ -17,7 +17,6 @@ namespace rll {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kMaxTreeDepth = 4096;  // far above either builder's depth (SAOH: < 250 levels at 2^24 lights)
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
