@@ -11,10 +11,10 @@
 //   2. the bucketed learning step of the single grid (bucket_learn.cuh) over
 //      all items' cells: records counted and scattered into one bucket per
 //      global cell, then one warp (or block) per touched cell orders its bucket
-//      by (cluster, sample) and runs Eq. 1 + Eq. 2 on the item's rows (item
-//      found by binary search over the per-item cell prefix).
-//   3. k_split_batched: split-collapse of every touched cell.
-//   4. k_advance: every item's frame counter += 1 on the device, so the pass
+//      by (cluster, sample) and runs Eq. 1, split-collapse (when the pass
+//      splits) and Eq. 2 on the item's rows (item found by binary search over
+//      the per-item cell prefix).
+//   3. k_advance: every item's frame counter += 1 on the device, so the pass
 //      can be recorded once as a CUDA graph and launched repeatedly.
 // The tile size and the occupancy target of step 1 come from a measured
 // search (rll_batch_tune).
@@ -130,29 +130,20 @@ struct BatchRows {
     }
 };
 
-template <int P>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_split_batched(const BatchItemDev* __restrict__ items, int n_items, const uint32_t* __restrict__ cell_prefix,
-                const uint32_t* __restrict__ touched, const uint32_t* __restrict__ n_touched,
-                uint32_t* __restrict__ status)
-{
-    using T = typename Store<P>::T;
-    __shared__ float s_q[kWarpsPerBlock][kMaxCut];
-    __shared__ float s_c[kWarpsPerBlock][kMaxCut];
-    __shared__ uint32_t s_cut[kWarpsPerBlock][kMaxCut];
-    __shared__ uint32_t s_nc[kWarpsPerBlock][kMaxCut];
-    __shared__ uint16_t s_b[kWarpsPerBlock][kMaxCut];
-    const int warp = threadIdx.x >> 5;
-    const uint32_t total = *n_touched;
-    for (uint32_t w = blockIdx.x * kWarpsPerBlock + warp; w < total; w += gridDim.x * kWarpsPerBlock) {
-        const uint32_t cell = touched[w];
+// split-collapse of a global cell, fused into the learning kernels: its
+// item's cut row, light tree, threshold and step limit
+struct BatchSplit {
+    static constexpr bool kOn = true;
+    const BatchItemDev* items;
+    int n_items;
+    const uint32_t* cell_prefix;
+    __device__ __forceinline__ SplitRow row(uint32_t cell) const
+    {
         const BatchItemDev& it = items[item_of_cell(cell_prefix, n_items, cell)];
-        const int64_t row = (int64_t)(cell - it.cell_base) * it.s.M;
-        split_one_cell<P>(it.cut + row, (T*)it.Q + row, (T*)it.C + row, it.s.m, it.nodes, it.parent, it.left,
-                          it.right, it.T, it.eps, it.split_iters, it.n_nodes, status, s_q[warp], s_c[warp],
-                          s_cut[warp], s_nc[warp], s_b[warp]);
+        return SplitRow{it.cut + (int64_t)(cell - it.cell_base) * it.s.M, it.nodes, it.parent, it.left, it.right, it.T,
+                        it.split_iters, it.n_nodes};
     }
-}
+};
 
 __global__ void k_advance(BatchItemDev* items, int n_items)
 {
@@ -283,16 +274,16 @@ cudaError_t launch_learn_t(rll_batch* b, cudaStream_t s, bool do_split)
     cudaError_t e = cudaMemsetAsync(b->n_touched, 0, 8 * sizeof(uint32_t), s);
     if (e != cudaSuccess || b->n_records == 0) return e;
     const int sms = device_sm_count(b->device);
-    e = launch_bucketed_learn<P>(s, b->device, sms, b->rec_key, b->rec_val, b->n_records,
-                                 BatchDec{b->total_cells << kBatchClusterBits},
-                                 BatchRows<P>{b->d_items, b->n, b->d_cell_prefix}, b->total_cells, b->cursor,
-                                 b->touched, b->touched_start, b->touched_len, b->n_touched, b->lists, b->learn_ws,
-                                 b->status);
-    if (e != cudaSuccess) return e;
-    if (do_split)
-        k_split_batched<P><<<sms * 8, kWarpsPerBlock * 32, 0, s>>>(b->d_items, b->n, b->d_cell_prefix, b->touched,
-                                                                    b->n_touched, b->status);
-    return cudaGetLastError();
+    const BatchDec dec{b->total_cells << kBatchClusterBits};
+    const BatchRows<P> rows{b->d_items, b->n, b->d_cell_prefix};
+    if (do_split)  // split-collapse fused into the learning kernels
+        return launch_bucketed_learn<P>(s, b->device, sms, b->rec_key, b->rec_val, b->n_records, dec, rows,
+                                        b->total_cells, b->cursor, b->touched, b->touched_start, b->touched_len,
+                                        b->n_touched, b->lists, b->learn_ws, b->status,
+                                        BatchSplit{b->d_items, b->n, b->d_cell_prefix});
+    return launch_bucketed_learn<P>(s, b->device, sms, b->rec_key, b->rec_val, b->n_records, dec, rows,
+                                    b->total_cells, b->cursor, b->touched, b->touched_start, b->touched_len,
+                                    b->n_touched, b->lists, b->learn_ws, b->status);
 }
 
 cudaError_t enqueue_pass(rll_batch* b, cudaStream_t s, bool do_split)
@@ -355,8 +346,11 @@ int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int6
     if (e == cudaSuccess) e = cudaMemsetAsync(b->cursor, 0, 4 * (size_t)max_cells, ctx->stream);
     // the learning step's shared-memory opt-in, now rather than during a graph capture
     if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP32, BatchRows<RLL_PREC_FP32>, NoSplit>(ctx->device);
+    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP32, BatchRows<RLL_PREC_FP32>, BatchSplit>(ctx->device);
     if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP16, BatchRows<RLL_PREC_FP16>, NoSplit>(ctx->device);
+    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP16, BatchRows<RLL_PREC_FP16>, BatchSplit>(ctx->device);
     if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_BF16, BatchRows<RLL_PREC_BF16>, NoSplit>(ctx->device);
+    if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_BF16, BatchRows<RLL_PREC_BF16>, BatchSplit>(ctx->device);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_work, 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, sizeof(BatchItemDev) * max_items);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tile_prefix, 4 * (max_items + 1));

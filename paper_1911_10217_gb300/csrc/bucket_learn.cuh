@@ -193,10 +193,24 @@ struct CellOrder {
 };
 
 // Split-collapse policy of the learning kernels: NoSplit leaves it to a
-// separate call; WithSplit runs it on each cell right after the cell's Eq. 1,
-// before the one Eq. 2 rebuild (cut rows of M entries at cut + slot M, the
-// light tree, threshold T, at most max_iter steps).
-struct SplitArgs {
+// separate call; a policy with kOn = true runs it on each cell right after the
+// cell's Eq. 1, before the one Eq. 2 rebuild. row(cell) gives the cell's cut
+// row, its light tree, threshold T and step limit.
+struct SplitRow {
+    uint32_t* cut;
+    const NodeRec* nodes;
+    const int32_t *parent, *left, *right;
+    float T;
+    uint32_t max_iter;
+    int64_t n_nodes;
+};
+struct NoSplit {
+    static constexpr bool kOn = false;
+    __device__ __forceinline__ SplitRow row(uint32_t) const { return SplitRow{}; }
+};
+// one grid: cut rows of M entries at cut + slot M
+struct WithSplit {
+    static constexpr bool kOn = true;
     uint32_t* cut;
     uint32_t M;
     const NodeRec* nodes;
@@ -204,12 +218,10 @@ struct SplitArgs {
     float T;
     uint32_t max_iter;
     int64_t n_nodes;
-};
-struct NoSplit : SplitArgs {
-    static constexpr bool kOn = false;
-};
-struct WithSplit : SplitArgs {
-    static constexpr bool kOn = true;
+    __device__ __forceinline__ SplitRow row(uint32_t slot) const
+    {
+        return SplitRow{cut + (int64_t)slot * M, nodes, parent, left, right, T, max_iter, n_nodes};
+    }
 };
 
 
@@ -259,13 +271,13 @@ __device__ void finish_cell(const Split& sp, uint32_t slot, float* q, uint32_t m
     __syncwarp();
     if constexpr (Split::kOn) {
         const int lane = threadIdx.x & 31;
-        uint32_t* cutrow = sp.cut + (int64_t)slot * sp.M;
-        if (load_cut_row(cutrow, cs, m, sp.n_nodes, status)) {
-            const uint32_t steps = split_collapse_steps<P>(cs, q, c, nc, m, sp.nodes, sp.parent, sp.left, sp.right,
-                                                           sp.T, sp.max_iter, sp.n_nodes);
+        const SplitRow r = sp.row(slot);
+        if (load_cut_row(r.cut, cs, m, r.n_nodes, status)) {
+            const uint32_t steps = split_collapse_steps<P>(cs, q, c, nc, m, r.nodes, r.parent, r.left, r.right, r.T,
+                                                           r.max_iter, r.n_nodes);
             if (steps) {
                 for (uint32_t s = lane; s < m; s += 32) {
-                    cutrow[s] = cs[s];
+                    r.cut[s] = cs[s];
                     qrow[s] = Store<P>::store(q[s]);  // exact: q holds table values
                 }
                 __syncwarp();
