@@ -279,11 +279,11 @@ cudaError_t launch_learn_t(rll_batch* b, cudaStream_t s, bool do_split)
     if (do_split)  // split-collapse fused into the learning kernels
         return launch_bucketed_learn<P>(s, b->device, sms, b->rec_key, b->rec_val, b->n_records, dec, rows,
                                         b->total_cells, b->cursor, b->touched, b->touched_start, b->touched_len,
-                                        b->n_touched, b->lists, b->learn_ws, b->status,
+                                        b->n_touched, b->lists, b->learn_ws, b->status, 1u << kBatchClusterBits,
                                         BatchSplit{b->d_items, b->n, b->d_cell_prefix});
     return launch_bucketed_learn<P>(s, b->device, sms, b->rec_key, b->rec_val, b->n_records, dec, rows,
                                     b->total_cells, b->cursor, b->touched, b->touched_start, b->touched_len,
-                                    b->n_touched, b->lists, b->learn_ws, b->status);
+                                    b->n_touched, b->lists, b->learn_ws, b->status, 1u << kBatchClusterBits);
 }
 
 cudaError_t enqueue_pass(rll_batch* b, cudaStream_t s, bool do_split)

@@ -167,10 +167,10 @@ k_bucket_scatter(const uint32_t* __restrict__ rec_key, const float* __restrict__
     }
 }
 
-// Shared arrays of one team (a warp or a block) ordering one cell's records:
-// A = bucket order, then (cluster, sample) order; B = grouped by cluster,
-// then the cdf scratch.
-template <uint32_t CAP>
+// Shared arrays of one team (a warp or a block) ordering one cell's records
+// (at most CAP records, cut sizes up to CLUS): A = bucket order, then
+// (cluster, sample) order; B = grouped by cluster, then the cdf scratch.
+template <uint32_t CAP, uint32_t CLUS = kMaxCut>
 struct CellOrder {
     uint32_t a_sid[CAP];
     uint32_t a_val[CAP];
@@ -178,17 +178,17 @@ struct CellOrder {
     uint32_t b_val[CAP];
     uint8_t a_s[CAP];
     uint8_t b_s[CAP];
-    uint32_t start[kMaxCut];  // first position of each cluster in B
-    uint32_t cur[kMaxCut];    // scatter cursors, then one past the last position
-    float q[kMaxCut];
+    uint32_t start[CLUS];  // first position of each cluster in B
+    uint32_t cur[CLUS];    // scatter cursors, then one past the last position
+    float q[CLUS];
     // Once Eq. 1 is composed, the record arrays (the first 16 CAP bytes) are
-    // dead: they give the float and 16-bit scratch rows (kMaxCut entries each)
+    // dead: they give the float and 16-bit scratch rows (CLUS entries each)
     // of Eq. 2 and split-collapse.
-    static_assert(16u * CAP >= 6u * (uint32_t)kMaxCut, "record arrays too small for the scratch rows");
+    static_assert(16u * CAP >= 6u * CLUS, "record arrays too small for the scratch rows");
     __device__ __forceinline__ float* scratch_c() { return reinterpret_cast<float*>(this); }
     __device__ __forceinline__ uint16_t* scratch_bits()
     {
-        return reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(this) + 4 * kMaxCut);
+        return reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(this) + 4 * CLUS);
     }
 };
 
@@ -292,8 +292,8 @@ __device__ void finish_cell(const Split& sp, uint32_t slot, float* q, uint32_t m
 // rank by sample id inside its group is counted, which puts them in
 // (cluster, sample) order; warp 0 of the team composes, stores Q and
 // rebuilds C. Called by every thread of the team.
-template <int P, uint32_t CAP, class Team, class Split>
-__device__ void learn_cell_grouped(Team team, CellOrder<CAP>& o, const uint32_t* __restrict__ bsid,
+template <int P, uint32_t CAP, uint32_t CLUS, class Team, class Split>
+__device__ void learn_cell_grouped(Team team, CellOrder<CAP, CLUS>& o, const uint32_t* __restrict__ bsid,
                                    const uint8_t* __restrict__ bs, const uint32_t* __restrict__ bval, uint32_t nr,
                                    uint32_t M, uint32_t m, float alpha, float eps, typename Store<P>::T* qrow,
                                    typename Store<P>::T* crow, const Split& sp, uint32_t slot, uint32_t* status)
@@ -411,7 +411,7 @@ __device__ void compose_sorted_block(Cls cls, Val val, uint32_t nr, uint32_t M, 
 // (ctr[4], ctr[5]), so the long cells start first and the blocks that drew
 // one join the second phase late instead of leaving a tail; a warp fetches
 // its next cell index while it works on the current one.
-template <int P, int WARPS, int MINB, class Rows, class Split>
+template <int P, int WARPS, int MINB, uint32_t CLUS, class Rows, class Split>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
 k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t* __restrict__ group_list,
                 const uint32_t* __restrict__ touched, const uint32_t* __restrict__ start,
@@ -419,8 +419,8 @@ k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t*
                 uint32_t* __restrict__ status)
 {
     __shared__ union {
-        CellOrder<kWarpBucket> warp[WARPS];
-        CellOrder<kBlockGroup> block;
+        CellOrder<kWarpBucket, CLUS> warp[WARPS];
+        CellOrder<kBlockGroup, CLUS> block;
     } sm;
     __shared__ uint32_t s_next;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -543,7 +543,8 @@ inline size_t bucketed_scratch_bytes(int64_t n)
     return 2 * n4 + n1 + 8 * (size_t)n;
 }
 
-// Enqueues the whole learning step for n >= 1 records. The caller has
+// Enqueues the whole learning step for n >= 1 records (cut sizes up to
+// max_cut). The caller has
 // zeroed ctr[0..5] on the stream and holds `cursor` [cells] at zero (left at
 // zero again); touched, start, len [cells] and lists [2 * cells] are outputs
 // and scratch. Counters: ctr[0] touched cells, [1] claimed records, [2]
@@ -554,7 +555,7 @@ cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uin
                                   const float* rec_val, int64_t n, Dec dec, Rows rows, uint32_t cells,
                                   uint32_t* cursor, uint32_t* touched, uint32_t* start, uint32_t* len,
                                   uint32_t* ctr, uint32_t* lists, void* scratch, uint32_t* status,
-                                  Split sp = Split{})
+                                  uint32_t max_cut, Split sp = Split{})
 {
     const size_t n4 = ((size_t)n * 4 + 255) & ~(size_t)255, n1 = ((size_t)n + 255) & ~(size_t)255;
     char* ws = static_cast<char*>(scratch);
@@ -568,8 +569,14 @@ cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uin
     k_bucket_count<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, n, dec, cursor, touched, ctr);
     k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(touched, ctr, cursor, start, len, group_list, sort_list);
     k_bucket_scatter<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, dec, cursor, bucket);
-    k_learn_buckets<P, 6, 5, Rows, Split><<<sms * 5, 6 * 32, 0, s>>>(bucket, ctr, group_list, touched, start, len,
-                                                                     cursor, rows, sp, status);
+    // cuts of at most 64 leaves: per-cluster arrays of 64 entries (30.5 KB of shared memory per
+    // block), 56 registers, 6 blocks per SM; larger cuts: 256 entries (44.4 KB), 5 blocks per SM
+    if (max_cut <= 64)
+        k_learn_buckets<P, 6, 6, 64, Rows, Split><<<sms * 6, 6 * 32, 0, s>>>(bucket, ctr, group_list, touched, start,
+                                                                           len, cursor, rows, sp, status);
+    else
+        k_learn_buckets<P, 6, 5, kMaxCut, Rows, Split><<<sms * 5, 6 * 32, 0, s>>>(bucket, ctr, group_list, touched,
+                                                                                start, len, cursor, rows, sp, status);
     cudaError_t e = big_smem_attribute<P, Rows, Split>(device);
     if (e != cudaSuccess) return e;
     k_learn_big<P, Rows, Split><<<sms * 2, kBigThreads, kBigSmem, s>>>(bucket, wide, rec_val, ctr, touched, start,

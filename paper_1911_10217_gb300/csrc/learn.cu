@@ -285,7 +285,7 @@ int learn_t(rll_ctx* ctx, rll_grid* g, const uint32_t* rec_key, const float* rec
                                  GridDec{g->H * g->M, g->M},
                                  GridRows<P>{(T*)g->Q, (T*)g->C, g->M, g->m, g->p.alpha, g->p.eps}, g->H, g->cursor,
                                  g->touched, g->touched_start, g->touched_len, g->n_touched, g->big, ws,
-                                 ctx->d_status, sp);
+                                 ctx->d_status, g->M, sp);
     if (e != cudaSuccess) return check_cuda(ctx, e, "learn kernels");
     g->cursor_dirty = false;
     return RLL_OK;
