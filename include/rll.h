@@ -107,7 +107,9 @@ int rll_ctx_set_stream(rll_ctx* ctx, void* cuda_stream);
  *   sampling kernel's registers are held to (default 4);
  *   "host_chunks" 1..32 -- chunks rll_render_pass_host cuts the points into
  *   for copy/compute overlap (default 8; sizes growing by 3/2, at least 4 096
- *   points each).
+ *   points each);
+ *   "host_zero_copy" 0 | 1 -- rll_render_pass_host uses mapped host buffers
+ *   in place (default 1).
  * Returns RLL_E_INVALID for an unknown name or a value out of range. */
 int rll_ctx_set_option(rll_ctx* ctx, const char* name, int64_t value);
 int rll_ctx_destroy(rll_ctx* ctx);
@@ -330,16 +332,19 @@ int rll_batch_destroy(rll_batch* b);
 
 /* ---- one whole pass from host memory ------------------------------------- */
 
-/* Copies the G-buffer (HOST pos/nrm SoA [3][P], albedo [P]) and boxes (HOST
- * [K][6]) to the device, runs rll_sample_and_shade, rll_learn_update and (if
- * do_split) rll_split_collapse, and copies rgb (HOST SoA [3][P]) back. The
- * points are cut into chunks ("host_chunks"): a chunk is shaded as soon as
- * its upload ends and read back as soon as it is shaded, on streams of the
- * context's own, while later chunks upload; results are those of one
- * rll_sample_and_shade launch. Work enqueued earlier on the context stream
- * comes first. Pinned host memory makes the copies asynchronous (pageable
- * memory is correct but serialises them). Staging buffers are owned by the
- * context. Synchronises. */
+/* One whole pass from HOST buffers: G-buffer pos/nrm SoA [3][P], albedo [P],
+ * boxes [K][6], rgb out SoA [3][P]. Runs rll_sample_and_shade, then
+ * rll_learn_update_split (do_split) or rll_learn_update. When pos, nrm,
+ * albedo and rgb are page-locked host memory mapped into the device address
+ * space (cudaHostAlloc / cudaHostRegister under unified addressing) and
+ * "host_zero_copy" is on, the sampling kernel reads and writes them in place
+ * over the host link; otherwise they are copied in chunks ("host_chunks"):
+ * a chunk is shaded as soon as its upload ends and read back as soon as it
+ * is shaded, on streams of the context's own, while later chunks upload
+ * (pageable memory is correct but serialises the copies). Either way the
+ * results are those of one rll_sample_and_shade launch on device copies.
+ * Work enqueued earlier on the context stream comes first. Staging buffers
+ * are owned by the context. Synchronises. */
 int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, const float* pos,
                          const float* nrm, const float* albedo, int64_t n_points,
                          const float* boxes, int32_t n_boxes, uint64_t seed, uint32_t frame,

@@ -205,6 +205,11 @@ int rll_ctx_set_option(rll_ctx* ctx, const char* name, int64_t value)
 {
     if (!ctx || !name) return RLL_E_INVALID;
     const std::string n(name);
+    if (n == "host_zero_copy") {
+        if (value != 0 && value != 1) return fail(ctx, RLL_E_INVALID, "host_zero_copy must be 0 or 1");
+        ctx->host_zero_copy = (int)value;
+        return RLL_OK;
+    }
     if (n == "host_chunks") {
         if (value < 1 || value > RLL_HOST_MAX_CHUNKS)
             return fail(ctx, RLL_E_INVALID, "host_chunks must be in [1, " + std::to_string(RLL_HOST_MAX_CHUNKS) + "]");
@@ -581,6 +586,35 @@ int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, con
     float* d_box = (float*)w; w += a(24 * (size_t)std::max(n_boxes, 1));
     uint32_t* d_key = (uint32_t*)w; w += a(4 * S);
     float* d_val = (float*)w;
+
+    // Host memory the device can address (page-locked and mapped, as every cudaHostAlloc /
+    // cudaHostRegister allocation is under unified addressing): the sampling kernel reads the
+    // G-buffer and writes rgb over the host link itself; only the boxes are copied.
+    auto mapped = [](const void* p) -> void* {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+    };
+    if (ctx->host_zero_copy) {
+        void *zp = mapped(pos), *zn = mapped(nrm), *za = mapped(albedo), *zr = mapped(rgb);
+        if (zp && zn && za && zr) {
+            cudaStream_t s = ctx->stream;
+            cudaError_t e = cudaSuccess;
+            if (n_boxes > 0) e = cudaMemcpyAsync(d_box, boxes, 24 * (size_t)n_boxes, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return check_cuda(ctx, e, "render_pass_host: boxes");
+            rc = sample_and_shade(ctx, grid, tree, (const float*)zp, (const float*)zn, (const float*)za, nullptr, P,
+                                  d_box, n_boxes, seed, frame, spp, (float*)zr, d_key, d_val, nullptr);
+            if (rc == RLL_OK)
+                rc = do_split ? learn_update_split(ctx, grid, tree, d_key, d_val, S)
+                              : learn_update(ctx, grid, d_key, d_val, S);
+            e = cudaStreamSynchronize(s);  // rgb is complete in host memory after this
+            if (rc != RLL_OK) return rc;
+            return check_cuda(ctx, e, "render_pass_host");
+        }
+    }
 
     // Copy/compute overlap: the points are cut into chunks (sizes below); chunk k is
     // uploaded on `up`, shaded on the main stream or comp2 (alternately, so a

@@ -35,6 +35,7 @@ struct rll_ctx {
     cudaEvent_t ev[2 * RLL_HOST_MAX_CHUNKS + 3] = {};
     bool pipe_ready = false;
     int host_chunks = 8;
+    int host_zero_copy = 1;  // rll_render_pass_host: use mapped host buffers in place
     // launch tuning (rll_ctx_set_option)
     int sample_min_blocks = 4;
 };

@@ -295,10 +295,13 @@ def test_checkpoint_resume_is_exact(env):
         assert np.array_equal(full[k][fo], resumed[k][ro]), k
 
 
-@pytest.mark.parametrize("chunks,spp", [(1, 1), (3, 2), (8, 1)])
-def test_host_pass_matches_device_pass(env, chunks, spp):
-    """The host pass (chunked uploads, shading on two streams, overlapped
-    read-back) gives the rgb and learned tables of the device pass."""
+@pytest.mark.parametrize("chunks,spp,host", [(1, 1, "numpy"), (3, 2, "numpy"), (8, 1, "numpy"),
+                                             (8, 1, "pinned"), (8, 2, "pinned"), (3, 1, "pinned-copy")])
+def test_host_pass_matches_device_pass(env, chunks, spp, host):
+    """The host pass gives the rgb and learned tables of the device pass:
+    from pageable buffers (chunked uploads, shading on two streams,
+    overlapped read-back), from pinned buffers used in place by the kernels,
+    and from pinned buffers with the chunked copies (host_zero_copy off)."""
     O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
     # 250 x 144 = 36 000 points: chunk sizes grow by 3/2 in multiples of 256 points (3 chunks:
     # 7 680, 11 520, 16 800; 8 chunks: 4 096 ... 1 440), so the last chunk is ragged
@@ -309,6 +312,13 @@ def test_host_pass_matches_device_pass(env, chunks, spp):
     b = rll.Grid(ctx, dt, params_for(rll, s))
     P = s.n_points
     ctx.set_option("host_chunks", chunks)
+    ctx.set_option("host_zero_copy", 0 if host == "pinned-copy" else 1)
+    if host == "numpy":
+        hpos, hnrm, halb = (np.ascontiguousarray(s.pos), np.ascontiguousarray(s.nrm),
+                            np.ascontiguousarray(s.albedo))
+    else:
+        hpos, hnrm, halb = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                            for a in (s.pos, s.nrm, s.albedo))
     for f in range(3):
         # the plain kernel (no per-sample diagnostics), as the host pass uses
         g = dict(rgb=torch.empty(3, P, device=env["dev"]),
@@ -318,16 +328,16 @@ def test_host_pass_matches_device_pass(env, chunks, spp):
                              g["rgb"], g["key"], g["val"])
         rll.learn_update(ctx, a, g["key"], g["val"])
         rll.split_collapse(ctx, a, dt)
-        rgb = np.zeros((3, P), np.float32)
-        rll.render_pass_host(ctx, b, dt, np.ascontiguousarray(s.pos), np.ascontiguousarray(s.nrm),
-                             np.ascontiguousarray(s.albedo), np.ascontiguousarray(s.boxes), s.seed, f,
-                             spp, rgb)
+        rgb = np.zeros((3, P), np.float32) if host == "numpy" else torch.zeros(3, P).pin_memory()
+        rll.render_pass_host(ctx, b, dt, hpos, hnrm, halb, np.ascontiguousarray(s.boxes), s.seed, f, spp, rgb)
+        rgb = rgb if host == "numpy" else rgb.numpy()
         assert np.array_equal(rgb, g["rgb"].cpu().numpy())
         ea, eb = a.export(), b.export()
         fa, fb = np.argsort(ea["keys"]), np.argsort(eb["keys"])
         for k in ("keys", "cut", "q", "c"):
             assert np.array_equal(ea[k][fa], eb[k][fb]), (k, f)
     ctx.set_option("host_chunks", 8)
+    ctx.set_option("host_zero_copy", 1)
 
 
 def test_long_run_stays_finite(env):
