@@ -284,8 +284,7 @@ def run_batched(args):
         n = s.n_points * s.spp
         rll.sample_and_shade(ctx, o["grid"], o["tree"], d["pos"], d["nrm"], d["alb"], d["boxes"], s.seed, 10**6,
                              s.spp, o["rgb"], key[:n], val[:n])
-        rll.learn_update(ctx, o["grid"], key[:n], val[:n])
-        rll.split_collapse(ctx, o["grid"], o["tree"])
+        rll.learn_update_split(ctx, o["grid"], o["tree"], key[:n], val[:n])
     e1.record(stream)
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1)
@@ -431,8 +430,7 @@ def run_dynamic(args):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, s.seed, f, s.spp, rgb, key, val)
-            rll.learn_update(ctx, grid, key, val)
-            rll.split_collapse(ctx, grid, tree)
+            rll.learn_update_split(ctx, grid, tree, key, val)
             e1.record(stream)
             ms.append((e0, e1))
         torch.cuda.synchronize()
@@ -585,8 +583,7 @@ def run_sky(args):
                 e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
                 e[0].record(stream)
                 rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, s.seed, f, 1, rgb, key, val)
-                rll.learn_update(ctx, grid, key, val)
-                rll.split_collapse(ctx, grid, tree)
+                rll.learn_update_split(ctx, grid, tree, key, val)
                 e[1].record(stream)
                 ev.append(e)
             torch.cuda.synchronize()
@@ -676,8 +673,7 @@ def run_paths(args):
             e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             e[0].record(stream)
             rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, s.seed, f, 1, rgb, key, val, footprint=fp)
-            rll.learn_update(ctx, grid, key, val)
-            rll.split_collapse(ctx, grid, tree)
+            rll.learn_update_split(ctx, grid, tree, key, val)
             e[1].record(stream)
             ev.append(e)
             if f + 1 in checkpoints:
