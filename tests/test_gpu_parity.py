@@ -247,6 +247,14 @@ def test_edge_cases(env):
     # invalid arguments are refused without launching
     with pytest.raises(rll.RllError):
         rll.sample_and_shade(ctx, dg, dt, d["pos"], d["nrm"], d["alb"], d["boxes"], 0, 0, 0, g["rgb"])
+    with pytest.raises(rll.RllError):  # a tree the grid was not created for
+        rll.learn_update_split(ctx, dg, t1, torch.empty(0, dtype=torch.int32, device=dev),
+                               torch.empty(0, device=dev))
+    for name, value in (("host_chunks", 0), ("host_chunks", 33), ("host_zero_copy", 2),
+                        ("sample_min_blocks", 5), ("no_such_option", 1)):
+        with pytest.raises(rll.RllError):
+            ctx.set_option(name, value)
+    assert ctx.sync_status() == 0
     with pytest.raises(rll.RllError):
         rll.Grid(ctx, dt, params_for(rll, s, table_size=1000))
 
