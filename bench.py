@@ -39,7 +39,7 @@ SM_COUNT = 152
 # DRAM bytes (read + write) of one k_sample launch on this workload, from the ncu capture summarised
 # in profiles/k_sample_frame1080p.md (77.33 MB + 22.50 MB); to be set to None whenever the sampling
 # kernel changes until it is captured again
-K_SAMPLE_DRAM_BYTES = 99.83e6
+K_SAMPLE_DRAM_BYTES = None
 FP32_LANES_PER_SM = 128
 
 

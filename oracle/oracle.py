@@ -76,6 +76,8 @@ def lib():
             L.orc_lookup_insert.argtypes = [ctypes.POINTER(_Grid), ctypes.c_uint64]
             L.orc_lookup_insert.restype = ctypes.c_int64
             L.orc_importance32.argtypes = [P, P, P, P, P]
+            L.orc_half_round.argtypes = [ctypes.c_float, ctypes.c_int]
+            L.orc_half_round.restype = ctypes.c_float
             L.orc_sample_frame.argtypes = [ctypes.POINTER(_Tree), P, P, ctypes.c_int, P,
                                            ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P, P,
                                            ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
@@ -165,6 +167,11 @@ class Tree:
         lib().orc_importance32(_p(np.ascontiguousarray(self.rec[node])), _p(_f32(x)), _p(_f32(nrm)),
                                ctypes.byref(num), ctypes.byref(den))
         return float(num.value) / float(den.value)
+
+
+def half_round(x, up):
+    """x rounded to binary16 toward +inf (up) or -inf, as a float."""
+    return float(lib().orc_half_round(float(x), 1 if up else 0))
 
 
 def footprint_level(footprint, cell_size, levels):

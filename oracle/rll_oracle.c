@@ -835,17 +835,39 @@ int64_t orc_lookup_insert(orc_grid* g, uint64_t key) { return orc_lookup_insert_
 /*   sqrt(d^2 - r^2) and two more square roots are needed; the bound is kept */
 /*   as num / den = (phi A B) / d^6 and two bounds are compared by cross      */
 /*   multiplication, without a division.                                    */
-/*   Node constants (centre, r^2, r, sin theta) are binary32 values of the    */
-/*   node record, computed with the same operations on both sides.           */
+/*   Node constants are binary32 values of the node record, computed with    */
+/*   the same operations on both sides, and kept compact: r = the square     */
+/*   root of the squared half diagonal rounded up by one ulp, r^2 = r r      */
+/*   (not below the box's own r^2); cos theta rounded down to binary16 (a    */
+/*   cone at least as wide), sin theta = sqrt(1 - cos^2) of that value       */
+/*   rounded up to binary16.                                                 */
 /* ------------------------------------------------------------------------ */
+
+/* x rounded to binary16 toward -inf (up = 0) or +inf (up = 1); |x| < 65504.  */
+/* The binary16 values of the binade of |x| are multiples of its ulp          */
+/* 2^(E - 10) (2^-24 below 2^-14), so the rounding is a floor or ceiling of   */
+/* x / ulp, exact in double.                                                  */
+float orc_half_round(float x, int up)
+{
+    if (x == 0.0f) return x;
+    int e = 0;
+    frexp(fabs((double)x), &e);
+    int E = e - 1;                 /* 2^E <= |x| < 2^(E+1) */
+    if (E < -14) E = -14;
+    double q = ldexp(1.0, E - 10);
+    double k = (double)x / q;
+    return (float)((up ? ceil(k) : floor(k)) * q);
+}
+
 void orc_importance32(const float* r, const float x[3], const float n[3], float* num, float* den)
 {
     float cx = (r[0] + r[3]) * 0.5f, cy = (r[1] + r[4]) * 0.5f, cz = (r[2] + r[5]) * 0.5f;
     float ex = r[3] - r[0], ey = r[4] - r[1], ez = r[5] - r[2];
-    float r2 = 0.25f * ((ex * ex + ey * ey) + ez * ez);
-    float rr = sqrtf(r2);
-    float ct = r[10];
-    float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    float rb2 = 0.25f * ((ex * ex + ey * ey) + ez * ez);
+    float rr = nextafterf(sqrtf(rb2), INFINITY);
+    float r2 = rr * rr;
+    float ct = orc_half_round(r[10], 0);
+    float st = orc_half_round(sqrtf(fmaxf(0.0f, 1.0f - ct * ct)), 1);
     float phi = r[6];
     float dx = cx - x[0], dy = cy - x[1], dz = cz - x[2];
     float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));

@@ -61,14 +61,17 @@ static_assert(sizeof(DescRec) == 48, "DescRec must be 48 bytes");
 
 // The DescRec fields of both children of one internal node, interleaved
 // (x: left child, y: right child) so that each 16-byte load yields two packed
-// operands of the paired bound below; 96 bytes per descent level. nr2 holds
-// -r2 (exact).
+// operands of the paired bound below; 80 bytes per descent level (the
+// descent is bound by how many record bytes a level pulls through L1). r2 is
+// r r, formed at use; cs holds (cos theta, sin theta) of each child as two
+// binary16 values (exactly the DescRec values).
 struct __align__(16) PairRec {
-    float2 c0, c1, c2, nr2, r, phi;
-    float2 a0, a1, a2, cos_t, sin_t;
+    float2 c0, c1, c2, r, phi;
+    float2 a0, a1, a2;
+    uint2 cs;
     uint2 id;
 };
-static_assert(sizeof(PairRec) == 96, "PairRec must be 96 bytes");
+static_assert(sizeof(PairRec) == 80, "PairRec must be 80 bytes");
 
 // Sorted light, 64 bytes.
 struct __align__(16) LightRec {
@@ -220,11 +223,15 @@ __device__ __forceinline__ DescRec make_desc(const NodeRec& n)
         d.c[k] = fmul(fadd(n.bmin[k], n.bmax[k]), 0.5f);
         d.axis[k] = n.axis[k];
     }
-    d.r2 = fmul(0.25f, fadd(fadd(fmul(ex, ex), fmul(ey, ey)), fmul(ez, ez)));
-    d.r = fsqrt(d.r2);
+    // compact constants: r rounded up one ulp and r^2 = r r (not below the box's squared half
+    // diagonal); cos theta rounded down to binary16 (a cone at least as wide) and sin theta of
+    // that cosine rounded up to binary16
+    const float rb2 = fmul(0.25f, fadd(fadd(fmul(ex, ex), fmul(ey, ey)), fmul(ez, ez)));
+    d.r = nextafterf(fsqrt(rb2), INFINITY);
+    d.r2 = fmul(d.r, d.r);
     d.phi = n.phi;
-    d.cos_t = n.cos_t;
-    d.sin_t = fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(n.cos_t, n.cos_t))));
+    d.cos_t = __half2float(__float2half_rd(n.cos_t));
+    d.sin_t = __half2float(__float2half_ru(fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(d.cos_t, d.cos_t))))));
     d.id = n.id;
     return d;
 }
@@ -273,11 +280,15 @@ __device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y
 __device__ __forceinline__ Bound2 importance2(const PairRec& q, float x0, float x1, float x2, float2 n0, float2 n1,
                                               float2 n2)
 {
+    const float2 nr2 = neg2(__fmul2_rn(q.r, q.r));
+    const float2 cl = __half22float2(*reinterpret_cast<const __half2*>(&q.cs.x));
+    const float2 cr = __half22float2(*reinterpret_cast<const __half2*>(&q.cs.y));
+    const float2 cos_t = make_float2(cl.x, cr.x), sin_t = make_float2(cl.y, cr.y);
     const float2 dx = make_float2(fsub(q.c0.x, x0), fsub(q.c0.y, x0));
     const float2 dy = make_float2(fsub(q.c1.x, x1), fsub(q.c1.y, x1));
     const float2 dz = make_float2(fsub(q.c2.x, x2), fsub(q.c2.y, x2));
     const float2 d2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-    const float2 t = __fadd2_rn(d2, q.nr2);
+    const float2 t = __fadd2_rn(d2, nr2);
     const bool in_x = t.x <= 0.0f, in_y = t.y <= 0.0f;
     const float2 cb = make_float2(fsqrt(t.x), fsqrt(t.y));
     const float2 nd = __ffma2_rn(n2, dz, __ffma2_rn(n1, dy, __fmul2_rn(n0, dx)));
@@ -291,8 +302,8 @@ __device__ __forceinline__ Bound2 importance2(const PairRec& q, float x0, float 
         if (rb) A.y = fmaxf(0.0f, v.y);
     }
     const float2 ad = neg2(__ffma2_rn(q.a2, dz, __ffma2_rn(q.a1, dy, __fmul2_rn(q.a0, dx))));
-    const float2 sphi = __ffma2_rn(q.sin_t, cb, __fmul2_rn(q.cos_t, q.r));
-    const float2 cphi = __ffma2_rn(q.cos_t, cb, neg2(__fmul2_rn(q.sin_t, q.r)));
+    const float2 sphi = __ffma2_rn(sin_t, cb, __fmul2_rn(cos_t, q.r));
+    const float2 cphi = __ffma2_rn(cos_t, cb, neg2(__fmul2_rn(sin_t, q.r)));
     float2 B = d2;
     const bool ea = !(sphi.x <= 0.0f || cphi.x <= ad.x), eb = !(sphi.y <= 0.0f || cphi.y <= ad.y);
     if (ea || eb) {
@@ -307,11 +318,11 @@ __device__ __forceinline__ Bound2 importance2(const PairRec& q, float x0, float 
     o.den = __fmul2_rn(__fmul2_rn(d2, d2), d2);
     if (in_x) {
         o.num.x = q.phi.x;
-        o.den.x = fmaxf(-q.nr2.x, 1e-30f);
+        o.den.x = fmaxf(-nr2.x, 1e-30f);
     }
     if (in_y) {
         o.num.y = q.phi.y;
-        o.den.y = fmaxf(-q.nr2.y, 1e-30f);
+        o.den.y = fmaxf(-nr2.y, 1e-30f);
     }
     return o;
 }

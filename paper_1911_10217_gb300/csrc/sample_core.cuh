@@ -260,7 +260,7 @@ __device__ __forceinline__ void descent_step(const SampleArgs& a, uint32_t& node
         const float4* src = reinterpret_cast<const float4*>(a.pairs + node);
         float4* dst = reinterpret_cast<float4*>(&q);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) dst[k] = __ldg(src + k);
+        for (int k = 0; k < 5; ++k) dst[k] = __ldg(src + k);
     }
     const Bound2 b = importance2(q, x0, x1, x2, n0, n1, n2);
     const float2 w = __fmul2_rn(b.num, make_float2(b.den.y, b.den.x));

@@ -274,14 +274,16 @@ __global__ void k_pairs(int64_t n, const NodeRec* __restrict__ nodes, const int3
         q.c0 = make_float2(L.c[0], R.c[0]);
         q.c1 = make_float2(L.c[1], R.c[1]);
         q.c2 = make_float2(L.c[2], R.c[2]);
-        q.nr2 = make_float2(-L.r2, -R.r2);
         q.r = make_float2(L.r, R.r);
         q.phi = make_float2(L.phi, R.phi);
         q.a0 = make_float2(L.axis[0], R.axis[0]);
         q.a1 = make_float2(L.axis[1], R.axis[1]);
         q.a2 = make_float2(L.axis[2], R.axis[2]);
-        q.cos_t = make_float2(L.cos_t, R.cos_t);
-        q.sin_t = make_float2(L.sin_t, R.sin_t);
+        {  // exact: both values are binary16 numbers
+            const __half2 hl = __halves2half2(__float2half_rn(L.cos_t), __float2half_rn(L.sin_t));
+            const __half2 hr = __halves2half2(__float2half_rn(R.cos_t), __float2half_rn(R.sin_t));
+            q.cs = make_uint2(*reinterpret_cast<const uint32_t*>(&hl), *reinterpret_cast<const uint32_t*>(&hr));
+        }
         q.id = make_uint2(L.id, R.id);
         pairs[i] = q;
     }

@@ -282,3 +282,27 @@ def test_median_tree_equals_radix_tree_on_a_complete_grid(oracle_mod):
     a = oracle_mod.Tree(tris, em)
     t = oracle_mod.Tree(tris, em, builder="median")
     assert _ranges(a) == _ranges(t)
+
+
+# ---- compact descent-bound constants: binary16 cone rounded outward
+
+def test_half_round_directed(oracle_mod):
+    """Rounding to binary16 toward -inf / +inf against numpy's float16: both
+    results are binary16 values, bracket x, and no binary16 value lies
+    strictly between either result and x."""
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([rng.uniform(-1.0, 1.0, 4000), rng.uniform(-1e-3, 1e-3, 500),
+                         rng.uniform(-1e-6, 1e-6, 200),
+                         [1.0, -1.0, 0.5, -0.5, 1.0 / 3.0, -1.0 / 3.0, 2.0 ** -14, -2.0 ** -14, 2.0 ** -20,
+                          0.999999, -0.999999]]).astype(np.float32)
+    inf16 = np.float16(np.inf)
+    for x in xs:
+        d, u = oracle_mod.half_round(x, False), oracle_mod.half_round(x, True)
+        assert d <= x <= u
+        assert float(np.float16(d)) == d and float(np.float16(u)) == u
+        if d < x:
+            assert float(np.nextafter(np.float16(d), inf16)) > x
+        if u > x:
+            assert float(np.nextafter(np.float16(u), -inf16)) < x
+        if float(np.float16(x)) == float(x):
+            assert d == u == x
