@@ -37,9 +37,9 @@ UNIT = "light samples/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 SM_COUNT = 152
 # DRAM bytes (read + write) of one k_sample launch on this workload, from the ncu capture summarised
-# in profiles/k_sample_frame1080p.md (77.33 MB + 22.50 MB); to be set to None whenever the sampling
+# in profiles/k_sample_frame1080p.md (76.38 MB + 21.66 MB); to be set to None whenever the sampling
 # kernel changes until it is captured again
-K_SAMPLE_DRAM_BYTES = None
+K_SAMPLE_DRAM_BYTES = 98.04e6
 FP32_LANES_PER_SM = 128
 
 
