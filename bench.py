@@ -213,6 +213,23 @@ def cpu_baseline(scene, single_seconds=6.0, cpu_seconds=24.0, chunk=65536):
                             "sample": f"{one[1]} samples, one process, {one[2]:.1f} s"}}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (a job takes as long as its slowest rank);
+    x itself without a process group."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, ms_per_step):
+    """Whole-job units per second under weak scaling: every rank processes
+    units_per_rank units per step."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def run_reference(args, scene):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -925,13 +942,9 @@ def main():
     t_learn = [e[1].elapsed_time(e[2]) for e in evs]
     t_split = [e[2].elapsed_time(e[3]) for e in evs]
     t_step = [e[0].elapsed_time(e[3]) for e in evs]
-    total_ms = sum(t_step)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(t_step), dist, dev)
     ms_step = total_ms / args.steps
-    value = world * P * S / (ms_step * 1e-3)
+    value = job_throughput(world, P * S, ms_step)
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     hpos = torch.from_numpy(np.ascontiguousarray(scene.pos)).pin_memory()

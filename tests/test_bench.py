@@ -48,3 +48,44 @@ def test_gpu_arm_line():
     assert d["gpu_launches"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
     assert d["extras"]["device_status"] == 0
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    """The timing reduction of the multi-rank bench: every rank gets the
+    slowest rank's time; whole-job throughput scales with the rank count."""
+    code = (
+        "import json, sys, torch, torch.distributed as dist\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import bench\n"
+        "dist.init_process_group('gloo')\n"
+        "r = dist.get_rank()\n"
+        "m = bench.max_over_ranks(1.0 + 1.5 * r, dist, torch.device('cpu'))\n"
+        "print(json.dumps({'rank': r, 'max': m, 'value': bench.job_throughput(2, 1000, m)}))\n"
+        "dist.destroy_process_group()\n")
+    port = _free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE="2", MASTER_ADDR="127.0.0.1",
+                   MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=300) for p in procs]
+    for p, (out, err) in zip(procs, outs):
+        assert p.returncode == 0, err[-2000:]
+    got = sorted((json.loads(out.strip().splitlines()[-1]) for out, _ in outs), key=lambda d: d["rank"])
+    assert [d["max"] for d in got] == [2.5, 2.5]
+    assert got[0]["value"] == pytest.approx(2 * 1000 / 2.5e-3)
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
