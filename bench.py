@@ -37,8 +37,8 @@ UNIT = "light samples/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 SM_COUNT = 152
 # DRAM bytes (read + write) of one k_sample launch on this workload, from the ncu capture summarised
-# in profiles/k_sample_frame1080p.md (76.38 MB + 21.66 MB); to be set to None whenever the sampling
-# kernel changes until it is captured again
+# of one ncu capture of it (76.38 MB read + 21.66 MB written); to be set to None whenever the
+# sampling kernel changes until it is captured again
 K_SAMPLE_DRAM_BYTES = 98.04e6
 FP32_LANES_PER_SM = 128
 
@@ -980,7 +980,7 @@ def main():
         t_l = statistics.mean(t_learn) * 1e-3
         # our kernels per step: sampling 1; learning: count, claim, scatter, the warp and grouping block
         # paths (one launch), the sorting block path = 5; split-collapse 1 unless fused into learning
-        # (the launch list of profiles/ shows them)
+        # (an ncu launch list of the pass shows them)
         launches_per_step = 1 + 5 + (1 if args.separate_split else 0)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
