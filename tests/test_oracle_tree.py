@@ -306,3 +306,15 @@ def test_half_round_directed(oracle_mod):
             assert float(np.nextafter(np.float16(u), -inf16)) < x
         if float(np.float16(x)) == float(x):
             assert d == u == x
+
+
+def test_radius_rounded_up_keeps_r_squared():
+    """The sphere constant of the descent bound: r = the binary32 square root
+    of the squared half diagonal, one ulp up, and r^2 = fl(r r) is never below
+    the squared half diagonal itself (binary32 throughout)."""
+    rng = np.random.default_rng(9)
+    rb2 = np.concatenate([rng.uniform(0.0, 1.0, 200000), 10.0 ** rng.uniform(-30, 10, 200000),
+                          [0.0, 1.0, 2.0, 0.25, 1e-38, 3.4e38 / 4]]).astype(np.float32)
+    r = np.nextafter(np.sqrt(rb2, dtype=np.float32), np.float32(np.inf))
+    r2 = (r * r).astype(np.float32)
+    assert r2.dtype == np.float32 and np.all(r2 >= rb2)
