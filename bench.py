@@ -39,7 +39,7 @@ SM_COUNT = 152
 # DRAM bytes (read + write) of one k_sample launch on this workload, from one ncu capture of it
 # (76.38 MB read + 21.66 MB written); to be set to None whenever the sampling kernel changes until
 # it is captured again
-K_SAMPLE_DRAM_BYTES = 98.04e6
+K_SAMPLE_DRAM_BYTES = None
 FP32_LANES_PER_SM = 128
 
 

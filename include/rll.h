@@ -103,8 +103,9 @@ typedef struct rll_sample_debug {
 int rll_ctx_create(rll_ctx** out, int device, void* cuda_stream);
 int rll_ctx_set_stream(rll_ctx* ctx, void* cuda_stream);
 /* Launch tuning of this context (no effect on results):
- *   "sample_min_blocks" 3 | 4 -- resident 256-thread blocks per SM the
- *   sampling kernel's registers are held to (default 4);
+ *   "sample_min_blocks" 3 | 4 -- register budget of the sampling kernel:
+ *   4 = 64 registers (8 resident 128-thread blocks, 32 warps per SM; the
+ *   default), 3 = 80 registers (6 blocks, 24 warps);
  *   "host_chunks" 1..32 -- chunks rll_render_pass_host cuts the points into
  *   for copy/compute overlap (default 8; sizes growing by 3/2, at least 4 096
  *   points each);
