@@ -1014,7 +1014,7 @@ def main():
                           "device_status": status}}
         if not args.no_quality:
             out["extras"]["mse_equal_spp"] = quality(rll, ctx, grid, tree, scene, pos, nrm, alb, boxes, dev)
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:  # the host baseline belongs to the one-GPU line
             out["cpu_baseline"] = cpu_baseline(scene)
         print(json.dumps(out))
     if dist:
