@@ -134,6 +134,16 @@ def bytes_per_sample():
     return 28 + 12 + 8
 
 
+def learn_step_bytes(n_records, touched_cells, cut_size, precision="fp32"):
+    """Algorithmic HBM bytes of one learning step (Eq. 1, split-collapse,
+    Eq. 2): every 8-byte record (key, reward) read once, and per touched cell
+    its rows: node ids read and written (8 B per leaf), Q read, Q and C
+    written (3 table entries per leaf) -- 20 B per leaf with binary32 tables,
+    14 B with 16-bit Q and C."""
+    per_leaf = 8 + 3 * (4 if precision == "fp32" else 2)
+    return 8 * n_records + per_leaf * cut_size * touched_cells
+
+
 def _host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -441,17 +451,23 @@ def run_dynamic(args):
     frames = args.dynamic_frames
     for prec in ("fp32", "fp16", "bf16"):
         grid = rll.Grid(ctx, tree, rll.grid_params_for(g, precision=prec))
-        ms = []
+        ms, touched = [], []
         for f in range(frames):
             set_emission(f)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
             rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, s.seed, f, s.spp, rgb, key, val)
-            rll.learn_update_split(ctx, grid, tree, key, val)
             e1.record(stream)
-            ms.append((e0, e1))
+            rll.learn_update_split(ctx, grid, tree, key, val)
+            e2.record(stream)
+            ms.append((e0, e1, e2))
+            if f >= 3 and f % 8 == 3:  # outside the event pairs: costs a host round trip only
+                touched.append(grid.touched_cells())
         torch.cuda.synchronize()
-        t = [a.elapsed_time(b) for a, b in ms][3:]
+        t = [a.elapsed_time(c) for a, b, c in ms][3:]
+        t_s = [a.elapsed_time(b) for a, b, c in ms][3:]
+        t_l = [b.elapsed_time(c) for a, b, c in ms][3:]
+        n_touched = statistics.mean(touched) if touched else float("nan")
         # reference of the last frame: energy sampler, 256 spp
         set_emission(frames - 1)
         ref = torch.zeros(3, P, device=dev, dtype=torch.float64)
@@ -465,7 +481,12 @@ def run_dynamic(args):
         rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 4242, 300000, 1, tmp)
         mse_pow = float(((tmp.double() - ref) ** 2).mean())
         e = 4 if prec == "fp32" else 2
+        lb = learn_step_bytes(P * s.spp, n_touched, g.cut_size, prec)
         results[prec] = {"ms_per_frame": statistics.mean(t), "p99_frame_ms": float(np.percentile(t, 99)),
+                         "sample_ms": statistics.mean(t_s), "learn_update_split_ms": statistics.mean(t_l),
+                         "touched_cells_per_frame": n_touched,
+                         "learn_algorithmic_bytes_per_frame": lb,
+                         "learn_algorithmic_gbs": lb / (statistics.mean(t_l) * 1e-3) / 1e9,
                          "samples_per_s": P * s.spp / (statistics.mean(t) * 1e-3),
                          "mse_1spp": mse, "energy_sampler_mse_1spp": mse_pow, "mse_ratio_vs_energy": mse_pow / mse,
                          "table_bytes": g.table_size * g.cut_size * (4 + 2 * e)}
@@ -795,8 +816,8 @@ def run_trees(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=29)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
@@ -938,6 +959,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     status = ctx.sync_status()
+    n_touched = grid.touched_cells()  # cells the last timed pass learned
     t_sample = [e[0].elapsed_time(e[1]) for e in evs]
     t_learn = [e[1].elapsed_time(e[2]) for e in evs]
     t_split = [e[2].elapsed_time(e[3]) for e in evs]
@@ -976,7 +998,7 @@ def main():
         t_s = statistics.mean(t_sample) * 1e-3
         achieved = ops / t_s / 1e12
         hbm_ach = bytes_per_sample() * n_sample / t_s / 1e9
-        learn_bytes = 8 * n_sample  # records read once (keys + rewards)
+        learn_bytes = learn_step_bytes(n_sample, n_touched, grid.M)
         t_l = statistics.mean(t_learn) * 1e-3
         # our kernels per step: sampling 1; learning: count, claim, scatter, the warp and grouping block
         # paths (one launch), the sorting block path = 5; split-collapse 1 unless fused into learning
@@ -985,7 +1007,9 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": workload_config(scene, args.tree, args.mode),
+               "config": dict(workload_config(scene, args.tree, args.mode),
+                              passes=f"passes {args.warmup}..{args.warmup + args.steps - 1} of a fresh grid timed "
+                                     f"(passes 0..{args.warmup - 1} untimed warm-up)"),
                "roofline": {"kernel": "k_sample (sample_and_shade)", "bound": "alu",
                             "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                             "frac": achieved / alu_peak, "traffic": K_SAMPLE_DRAM_BYTES,
@@ -1010,6 +1034,8 @@ def main():
                           "p50_frame_ms": statistics.median(t_step),
                           "p99_frame_ms": float(np.percentile(t_step, 99)),
                           "learn_update_algorithmic_gbs": learn_bytes / t_l / 1e9,
+                          "learn_update_algorithmic_bytes": learn_bytes,
+                          "touched_cells_last_pass": n_touched,
                           "wall_s_timed_region_incl_flush": wall,
                           "device_status": status}}
         if not args.no_quality:

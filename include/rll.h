@@ -176,6 +176,12 @@ int rll_create_grid(rll_ctx* ctx, const rll_tree* tree, const rll_grid_params* p
                     rll_grid** out);
 /* Number of leaves m = min(M, lights) in every cut. */
 uint32_t rll_grid_cut_len(const rll_grid* grid);
+/* Cells touched by the last learning call (rll_learn_update,
+ * rll_learn_update_split, rll_learn_update_noalloc; after rll_grid_import:
+ * every occupied cell), written to the HOST int64 *out. These are the cells
+ * whose Q and C rows Eq. 1 and Eq. 2 rewrote, the unit of the learning step's
+ * table traffic. Synchronises. */
+int rll_grid_touched_cells(rll_ctx* ctx, const rll_grid* grid, int64_t* out);
 /* Copies the grid to HOST arrays (any may be NULL): keys [H] (empty slots
  * 0xFFFFFFFFFFFFFFFF), cut [H][M] node ids, q and c [H][M] as float (16-bit
  * tables widened exactly). Only the first m entries of a row are meaningful.

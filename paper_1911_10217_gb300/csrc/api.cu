@@ -405,6 +405,19 @@ int rll_create_grid(rll_ctx* ctx, const rll_tree* tree, const rll_grid_params* p
 
 uint32_t rll_grid_cut_len(const rll_grid* grid) { return grid ? grid->m : 0; }
 
+int rll_grid_touched_cells(rll_ctx* ctx, const rll_grid* g, int64_t* out)
+{
+    if (!ctx) return RLL_E_INVALID;
+    if (!g || !out) return fail(ctx, RLL_E_INVALID, "grid / out is NULL");
+    DeviceGuard dg(ctx->device);
+    uint32_t n = 0;
+    cudaError_t e = cudaMemcpyAsync(&n, g->n_touched, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "grid touched cells");
+    *out = (int64_t)n;
+    return RLL_OK;
+}
+
 int rll_grid_export(rll_ctx* ctx, const rll_grid* g, uint64_t* keys, int32_t* cut, float* q, float* c)
 {
     if (!ctx || !g) return RLL_E_INVALID;

@@ -28,7 +28,7 @@ BUILDER = {"lbvh": 0, "saoh": 1, "median": 2}
 EXPORTS = [
     "rll_ctx_create", "rll_ctx_set_stream", "rll_ctx_set_option", "rll_ctx_destroy", "rll_last_error", "rll_sync_status",
     "rll_build_light_tree", "rll_build_light_tree_ex", "rll_tree_update_emission", "rll_tree_num_lights", "rll_tree_export",
-    "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_export", "rll_grid_import",
+    "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_touched_cells", "rll_grid_export", "rll_grid_import",
     "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_and_shade_fp",
     "rll_sample_power",
     "rll_learn_update", "rll_learn_update_noalloc", "rll_learn_update_split", "rll_split_collapse",
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
     L.rll_create_grid.argtypes = [P, P, ctypes.POINTER(GridParams), ctypes.POINTER(P)]
     L.rll_grid_cut_len.argtypes = [P]
     L.rll_grid_cut_len.restype = U32
+    L.rll_grid_touched_cells.argtypes = [P, P, ctypes.POINTER(I64)]
     L.rll_grid_export.argtypes = [P, P, P, P, P, P]
     L.rll_grid_import.argtypes = [P, P, P, P, P, P]
     L.rll_grid_destroy.argtypes = [P]
@@ -272,6 +273,12 @@ class Grid:
         self.levels = max(1, int(params.levels))
         self.H, self.M = int(params.table_size) * self.levels, int(params.cut_size)
         self.m = int(ctx.lib.rll_grid_cut_len(h))
+
+    def touched_cells(self) -> int:
+        """Cells rewritten by the last learning call (synchronises)."""
+        n = ctypes.c_int64()
+        self.ctx._check(self.ctx.lib.rll_grid_touched_cells(self.ctx.h, self.h, ctypes.byref(n)))
+        return int(n.value)
 
     def export(self):
         H, M = self.H, self.M
