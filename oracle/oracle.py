@@ -76,6 +76,10 @@ def lib():
             L.orc_lookup_insert.argtypes = [ctypes.POINTER(_Grid), ctypes.c_uint64]
             L.orc_lookup_insert.restype = ctypes.c_int64
             L.orc_importance32.argtypes = [P, P, P, P, P]
+            L.orc_node_consts32.argtypes = [P, P]
+            L.orc_bound64.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P,
+                                      ctypes.c_double, P, P]
+            L.orc_bound64.restype = ctypes.c_double
             L.orc_half_round.argtypes = [ctypes.c_float, ctypes.c_int]
             L.orc_half_round.restype = ctypes.c_float
             L.orc_sample_frame.argtypes = [ctypes.POINTER(_Tree), P, P, ctypes.c_int, P,
@@ -167,6 +171,23 @@ class Tree:
         lib().orc_importance32(_p(np.ascontiguousarray(self.rec[node])), _p(_f32(x)), _p(_f32(nrm)),
                                ctypes.byref(num), ctypes.byref(den))
         return float(num.value) / float(den.value)
+
+
+def node_consts(rec):
+    """Compact bound constants of a node record: centre xyz, r, r*r, cone
+    cos and sin (binary32 values)."""
+    k = np.zeros(7, np.float32)
+    lib().orc_node_consts32(_p(_f32(rec)), _p(k))
+    return k
+
+
+def bound64(centre, r, cos_t, sin_t, axis, phi, x, nrm):
+    """The descent bound written out plainly in double precision."""
+    c = np.ascontiguousarray(centre, np.float64)
+    a = np.ascontiguousarray(axis, np.float64)
+    xx = np.ascontiguousarray(x, np.float64)
+    nn = np.ascontiguousarray(nrm, np.float64)
+    return float(lib().orc_bound64(_p(c), float(r), float(cos_t), float(sin_t), _p(a), float(phi), _p(xx), _p(nn)))
 
 
 def half_round(x, up):

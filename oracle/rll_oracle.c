@@ -838,36 +838,57 @@ int64_t orc_lookup_insert(orc_grid* g, uint64_t key) { return orc_lookup_insert_
 /*   Node constants are binary32 values of the node record, computed with    */
 /*   the same operations on both sides, and kept compact: r = the square     */
 /*   root of the squared half diagonal rounded up by one ulp, r^2 = r r      */
-/*   (not below the box's own r^2); cos theta rounded down to binary16 (a    */
-/*   cone at least as wide), sin theta = sqrt(1 - cos^2) of that value       */
-/*   rounded up to binary16.                                                 */
+/*   (not below the box's own r^2); the cone as 1 - cos theta rounded up to  */
+/*   binary16 (a cone at least as wide) and sin theta of that cone rounded   */
+/*   up to binary16 (orc_node_consts32).                                     */
 /* ------------------------------------------------------------------------ */
 
 /* x rounded to binary16 toward -inf (up = 0) or +inf (up = 1); |x| < 65504.  */
 /* The binary16 values of the binade of |x| are multiples of its ulp          */
 /* 2^(E - 10) (2^-24 below 2^-14), so the rounding is a floor or ceiling of   */
 /* x / ulp, exact in double.                                                  */
-float orc_half_round(float x, int up)
+static double orc_half_round64(double x, int up)
 {
-    if (x == 0.0f) return x;
+    if (x == 0.0) return x;
     int e = 0;
-    frexp(fabs((double)x), &e);
+    frexp(fabs(x), &e);
     int E = e - 1;                 /* 2^E <= |x| < 2^(E+1) */
     if (E < -14) E = -14;
     double q = ldexp(1.0, E - 10);
-    double k = (double)x / q;
-    return (float)((up ? ceil(k) : floor(k)) * q);
+    double k = x / q;
+    return (up ? ceil(k) : floor(k)) * q;
+}
+
+float orc_half_round(float x, int up) { return (float)orc_half_round64((double)x, up); }
+
+/* The compact constants of a node's descent bound (reading of the stored
+ * bound, see above), from its record r = bmin xyz, bmax xyz, phi, cone axis
+ * xyz, cone cos: k[0..2] the box centre (binary32), k[3] the radius r
+ * (binary32 square root of the squared half diagonal, one ulp up), k[4] =
+ * r r; the cone as k[5] = cos theta' = 1 - v, where v is 1 - cos theta
+ * rounded up to binary16 (a cone at least as wide; binary16 keeps 11
+ * significant bits of v, so narrow cones stay narrow), and k[6] = sin theta'
+ * rounded up to binary16, from the exact 1 - cos^2 theta' = v (2 - v). */
+void orc_node_consts32(const float* r, float k[7])
+{
+    k[0] = (r[0] + r[3]) * 0.5f;
+    k[1] = (r[1] + r[4]) * 0.5f;
+    k[2] = (r[2] + r[5]) * 0.5f;
+    float ex = r[3] - r[0], ey = r[4] - r[1], ez = r[5] - r[2];
+    float rb2 = 0.25f * ((ex * ex + ey * ey) + ez * ez);
+    k[3] = nextafterf(sqrtf(rb2), INFINITY);
+    k[4] = k[3] * k[3];
+    double v = orc_half_round64(1.0 - (double)r[10], 1);  /* 1 - cos exact in double */
+    k[5] = (float)(1.0 - v);                             /* exact in binary32 */
+    k[6] = (float)orc_half_round64(sqrt(v * (2.0 - v)), 1);
 }
 
 void orc_importance32(const float* r, const float x[3], const float n[3], float* num, float* den)
 {
-    float cx = (r[0] + r[3]) * 0.5f, cy = (r[1] + r[4]) * 0.5f, cz = (r[2] + r[5]) * 0.5f;
-    float ex = r[3] - r[0], ey = r[4] - r[1], ez = r[5] - r[2];
-    float rb2 = 0.25f * ((ex * ex + ey * ey) + ez * ez);
-    float rr = nextafterf(sqrtf(rb2), INFINITY);
-    float r2 = rr * rr;
-    float ct = orc_half_round(r[10], 0);
-    float st = orc_half_round(sqrtf(fmaxf(0.0f, 1.0f - ct * ct)), 1);
+    float k[7];
+    orc_node_consts32(r, k);
+    float cx = k[0], cy = k[1], cz = k[2];
+    float rr = k[3], r2 = k[4], ct = k[5], st = k[6];
     float phi = r[6];
     float dx = cx - x[0], dy = cy - x[1], dz = cz - x[2];
     float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -889,6 +910,51 @@ void orc_importance32(const float* r, const float x[3], const float n[3], float*
     else B = fmaxf(0.0f, fmaf(ad, cphi, sqrtf(fmaxf(0.0f, fmaf(-ad, ad, d2))) * sphi));
     *num = (phi * A) * B;
     *den = (d2 * d2) * d2;
+}
+
+/* The same bound written out plainly in double precision, as a check of the
+ * binary32 form above (which carries the cosines multiplied by |d| and
+ * compares bounds without dividing). Inputs are the node's constants:
+ * centre c, radius r, cone cos theta and sin theta, cone axis a (unit),
+ * power phi; x the shading point, n its unit normal.
+ *   w = d / |d| with d = c - x is the direction to the centre; the sphere of
+ *   radius r subtends the half angle beta, sin beta = r / |d|.
+ *   Receiver: gamma = angle(n, w). Over directions within beta of w,
+ *   max(0, n . omega) is 1 if gamma <= beta, else max(0, cos(gamma - beta)).
+ *   Emitter: psi = angle(a, -w), the angle between the cone axis and the
+ *   direction from the node back to x. Over normals within theta of a and
+ *   directions within beta of w, max(0, -n_l . omega) is 1 if
+ *   psi <= theta + beta (or theta + beta >= pi), else
+ *   max(0, cos(psi - (theta + beta))).
+ *   I = phi * Brecv * Bemit / |d|^2; inside the sphere (|d| <= r) I = phi / r^2.
+ * The cosines of the angle differences and sums come from the addition
+ * formulas with the sines sqrt(1 - cos^2). */
+double orc_bound64(const double c[3], double r, double cos_t, double sin_t, const double a[3], double phi,
+                   const double x[3], const double n[3])
+{
+    double d[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
+    double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (d2 <= r * r) return phi / (r * r);
+    double dist = sqrt(d2);
+    double w[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+    double sin_b = r / dist;
+    double cos_b = sqrt(1.0 - sin_b * sin_b);
+
+    double cos_g = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
+    double sin_g = sqrt(fmax(0.0, 1.0 - cos_g * cos_g));
+    double recv;
+    if (cos_g >= cos_b) recv = 1.0;                          /* gamma <= beta */
+    else recv = fmax(0.0, cos_g * cos_b + sin_g * sin_b);   /* cos(gamma - beta) */
+
+    double cos_p = -(a[0] * w[0] + a[1] * w[1] + a[2] * w[2]);
+    double sin_p = sqrt(fmax(0.0, 1.0 - cos_p * cos_p));
+    double cos_tb = cos_t * cos_b - sin_t * sin_b;          /* cos(theta + beta) */
+    double sin_tb = sin_t * cos_b + cos_t * sin_b;          /* sin(theta + beta) */
+    double emit;
+    if (sin_tb <= 0.0 || cos_p >= cos_tb) emit = 1.0;         /* psi <= theta + beta */
+    else emit = fmax(0.0, cos_p * cos_tb + sin_p * sin_tb); /* cos(psi - theta - beta) */
+
+    return phi * recv * emit / d2;
 }
 
 /* Branch weights of the two children a, c of a descent step: the bounds

@@ -63,8 +63,8 @@ static_assert(sizeof(DescRec) == 48, "DescRec must be 48 bytes");
 // (x: left child, y: right child) so that each 16-byte load yields two packed
 // operands of the paired bound below; 80 bytes per descent level (the
 // descent is bound by how many record bytes a level pulls through L1). r2 is
-// r r, formed at use; cs holds (cos theta, sin theta) of each child as two
-// binary16 values (exactly the DescRec values).
+// r r, formed at use; cs holds (1 - cos theta, sin theta) of each child as two
+// binary16 values (exactly the DescRec values; cos theta = 1 - v is exact).
 struct __align__(16) PairRec {
     float2 c0, c1, c2, r, phi;
     float2 a0, a1, a2;
@@ -224,14 +224,17 @@ __device__ __forceinline__ DescRec make_desc(const NodeRec& n)
         d.axis[k] = n.axis[k];
     }
     // compact constants: r rounded up one ulp and r^2 = r r (not below the box's squared half
-    // diagonal); cos theta rounded down to binary16 (a cone at least as wide) and sin theta of
-    // that cosine rounded up to binary16
+    // diagonal); the cone as v = 1 - cos theta rounded up to binary16 (a cone at least as wide;
+    // 11 significant bits of v keep narrow cones narrow), cos = 1 - v (exact), and sin theta of
+    // that cone rounded up to binary16 from the exact 1 - cos^2 = v (2 - v). Rounding up twice
+    // (binary32, then binary16) equals rounding up once.
     const float rb2 = fmul(0.25f, fadd(fadd(fmul(ex, ex), fmul(ey, ey)), fmul(ez, ez)));
     d.r = nextafterf(fsqrt(rb2), INFINITY);
     d.r2 = fmul(d.r, d.r);
     d.phi = n.phi;
-    d.cos_t = __half2float(__float2half_rd(n.cos_t));
-    d.sin_t = __half2float(__float2half_ru(fsqrt(fmaxf(0.0f, fsub(1.0f, fmul(d.cos_t, d.cos_t))))));
+    const float v = __half2float(__float2half_ru(__fsub_ru(1.0f, n.cos_t)));
+    d.cos_t = fsub(1.0f, v);
+    d.sin_t = __half2float(__float2half_ru(__fsqrt_ru(fmul(v, fsub(2.0f, v)))));
     d.id = n.id;
     return d;
 }
@@ -283,7 +286,8 @@ __device__ __forceinline__ Bound2 importance2(const PairRec& q, float x0, float 
     const float2 nr2 = neg2(__fmul2_rn(q.r, q.r));
     const float2 cl = __half22float2(*reinterpret_cast<const __half2*>(&q.cs.x));
     const float2 cr = __half22float2(*reinterpret_cast<const __half2*>(&q.cs.y));
-    const float2 cos_t = make_float2(cl.x, cr.x), sin_t = make_float2(cl.y, cr.y);
+    const float2 cos_t = __fadd2_rn(make_float2(1.0f, 1.0f), neg2(make_float2(cl.x, cr.x)));  // exact
+    const float2 sin_t = make_float2(cl.y, cr.y);
     const float2 dx = make_float2(fsub(q.c0.x, x0), fsub(q.c0.y, x0));
     const float2 dy = make_float2(fsub(q.c1.x, x1), fsub(q.c1.y, x1));
     const float2 dz = make_float2(fsub(q.c2.x, x2), fsub(q.c2.y, x2));

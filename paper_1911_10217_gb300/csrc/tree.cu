@@ -279,9 +279,9 @@ __global__ void k_pairs(int64_t n, const NodeRec* __restrict__ nodes, const int3
         q.a0 = make_float2(L.axis[0], R.axis[0]);
         q.a1 = make_float2(L.axis[1], R.axis[1]);
         q.a2 = make_float2(L.axis[2], R.axis[2]);
-        {  // exact: both values are binary16 numbers
-            const __half2 hl = __halves2half2(__float2half_rn(L.cos_t), __float2half_rn(L.sin_t));
-            const __half2 hr = __halves2half2(__float2half_rn(R.cos_t), __float2half_rn(R.sin_t));
+        {  // exact: 1 - cos theta and sin theta are binary16 numbers
+            const __half2 hl = __halves2half2(__float2half_rn(fsub(1.0f, L.cos_t)), __float2half_rn(L.sin_t));
+            const __half2 hr = __halves2half2(__float2half_rn(fsub(1.0f, R.cos_t)), __float2half_rn(R.sin_t));
             q.cs = make_uint2(*reinterpret_cast<const uint32_t*>(&hl), *reinterpret_cast<const uint32_t*>(&hr));
         }
         q.id = make_uint2(L.id, R.id);
