@@ -449,7 +449,7 @@ def run_dynamic(args):
     g = s.grid
     results = {}
     frames = args.dynamic_frames
-    for prec in ("fp32", "fp16", "bf16"):
+    for prec in args.dynamic_precisions.split(","):
         grid = rll.Grid(ctx, tree, rll.grid_params_for(g, precision=prec))
         ms, touched = [], []
         for f in range(frames):
@@ -853,6 +853,7 @@ def main():
     ap.add_argument("--split-passes", type=int, default=64)
     ap.add_argument("--dynamic-scale", type=float, default=1.0)
     ap.add_argument("--dynamic-frames", type=int, default=120)
+    ap.add_argument("--dynamic-precisions", default="fp32,fp16,bf16")
     ap.add_argument("--serving-sessions", type=int, default=64)
     ap.add_argument("--serving-frames", type=int, default=160)
     ap.add_argument("--serving-scale", type=float, default=1.0)

@@ -258,7 +258,9 @@ int rll_learn_update(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key, cons
  * array inside the library (about 18 MB, held on every GPU that loads the
  * library until exit). At most 1048576 records per call; more returns
  * RLL_E_INVALID without launching. The first call on a device looks up the
- * array's address: make it before any stream capture. All calls share the
+ * array's address: make it before any stream capture. The address is kept
+ * for the process's life and does not survive a cudaDeviceReset of that
+ * device (do not call this entry point after one). All calls share the
  * array, so calls that overlap on the GPU race: serialise them. The paper has
  * no counterpart of this entry point. */
 int rll_learn_update_noalloc(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key,

@@ -48,20 +48,6 @@ void* ws_get(rll_ctx* ctx, size_t bytes)
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 size_t elem_bytes(uint32_t precision) { return precision == RLL_PREC_FP32 ? 4 : 2; }
 
 void free_tree(rll_tree* t)

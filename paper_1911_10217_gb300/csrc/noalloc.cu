@@ -11,7 +11,9 @@
 // size. Every GPU that loads this library holds that array until the process
 // exits. Its device address is looked up once per device (the first call of
 // the entry point on a device does that set-up, so make that first call
-// before any stream capture). All calls share the array and it keeps the
+// before any stream capture) and kept for the life of the process: it does
+// not survive a cudaDeviceReset of that device, after which this entry point
+// must not be called again in the same process. All calls share the array and it keeps the
 // previous call's contents; whatever must start at zero (the per-pass digit
 // totals, the touched-cell count) is cleared by the call itself. Calls whose
 // work overlaps on the GPU (other streams, other host threads) race on the
@@ -52,20 +54,6 @@ int scratch_for(rll_ctx* ctx, void** out)
     return RLL_OK;
 }
 
-struct CurrentDevice {
-    int prev = -1;
-    explicit CurrentDevice(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~CurrentDevice()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 }  // namespace
 
 extern "C" int rll_learn_update_noalloc(rll_ctx* ctx, rll_grid* grid, const uint32_t* rec_key, const float* rec_val,
@@ -78,7 +66,7 @@ extern "C" int rll_learn_update_noalloc(rll_ctx* ctx, rll_grid* grid, const uint
         return rll::fail(ctx, RLL_E_INVALID,
                          "rll_learn_update_noalloc takes at most 1048576 records per call (use rll_learn_update)");
     if (n_records > 0 && (!rec_key || !rec_val)) return rll::fail(ctx, RLL_E_INVALID, "NULL records");
-    CurrentDevice dev(ctx->device);
+    rll::DeviceGuard dev(ctx->device);
     void* scratch = nullptr;
     const int rc = scratch_for(ctx, &scratch);
     if (rc != RLL_OK) return rc;

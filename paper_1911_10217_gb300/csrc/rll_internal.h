@@ -80,6 +80,22 @@ struct rll_grid {
 
 namespace rll {
 
+// Makes `dev` the current device for the guard's lifetime (restores the
+// previous one).
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 // status helpers (api.cu)
 int fail(rll_ctx* ctx, int code, const std::string& msg);
 int check_cuda(rll_ctx* ctx, cudaError_t e, const char* what);

@@ -43,14 +43,17 @@ def to_host(out):
 
 def compare_samples(gpu, orc, gpu_keys, orc_keys, M, rtol=1e-4):
     """Light index bit-exact except draws within 1e-6 of a threshold (at most
-    1e-5 of the samples); the same cell key and cluster; estimates and
-    rewards within rtol."""
+    1e-5 of the samples, rounded down: none below 10^5 samples); the same cell
+    key and cluster; estimates and rewards within rtol. The estimate of every
+    point whose samples all agree is compared. Returns the set of cell keys a
+    mismatched sample fed on either side (empty when the light choices all
+    agree): the cells whose learned rows may then legitimately differ."""
     light_g = gpu["light"].astype(np.int64)
     n = light_g.size
     mism = light_g != orc["light"]
     near = orc["margin"] < 1e-6
     assert not np.any(mism & ~near), f"{int(np.sum(mism & ~near))} light choices differ away from a boundary"
-    assert mism.sum() <= max(1, int(1e-5 * n)), f"{int(mism.sum())} boundary mismatches of {n}"
+    assert mism.sum() <= int(1e-5 * n), f"{int(mism.sum())} boundary mismatches of {n}"
     ok = ~mism
     kg = gpu["key"].view(np.uint32).astype(np.int64)
     slot_g = np.where(kg == 0xFFFFFFFF, -1, kg // M)
@@ -65,10 +68,16 @@ def compare_samples(gpu, orc, gpu_keys, orc_keys, M, rtol=1e-4):
     pdf_g = gpu["pcut"].astype(np.float64) * gpu["pin"]
     pdf_o = orc["p_cut"] * orc["p_in"]
     assert np.allclose(pdf_g[ok], pdf_o[ok], rtol=rtol), "pdfs differ"
-    if mism.sum() == 0:
-        assert np.allclose(gpu["rgb"], orc["rgb"], rtol=rtol, atol=1e-7 * max(1.0, np.abs(orc["rgb"]).max())), \
-            "estimates differ"
-    return int(mism.sum())
+    P = gpu["rgb"].shape[1]
+    spp = n // max(P, 1)
+    pt_ok = ok.reshape(P, spp).all(axis=1) if P else np.zeros(0, bool)
+    assert np.allclose(gpu["rgb"][:, pt_ok], orc["rgb"][:, pt_ok], rtol=rtol,
+                       atol=1e-7 * max(1.0, np.abs(orc["rgb"]).max())), "estimates differ"
+    skip = set()
+    for i in np.nonzero(mism)[0]:
+        for c in (cell_g[i], cell_o[i]):
+            skip.add(int(c))
+    return skip
 
 
 def rows_by_key(keys, *tables, Hl=None):
@@ -80,14 +89,18 @@ def rows_by_key(keys, *tables, Hl=None):
     return {(int(i) // Hl, int(keys[i])): tuple(t[i] for t in tables) for i in occ}
 
 
-def compare_tables(gstate, ostate, m, rtol, check_cut=True, only=None, Hl=None):
+def compare_tables(gstate, ostate, m, rtol, check_cut=True, only=None, Hl=None, skip=()):
     """Compare two grid states cell by cell (matched by key, or by level and
-    key for a multi-resolution grid)."""
+    key for a multi-resolution grid). Cells in `skip` (those fed by a
+    boundary-mismatched sample) are left out; at most a handful, checked."""
     g = rows_by_key(gstate["keys"], gstate["cut"], gstate["q"], gstate["c"], Hl=Hl)
     o = rows_by_key(ostate["keys"], ostate["cut"], ostate["q"], ostate["c"], Hl=Hl)
     assert set(g) == set(o), f"cell sets differ: {len(set(g) ^ set(o))}"
     keys = o.keys() if only is None else only
+    assert len(skip) <= max(2, len(o) // 1000), f"{len(skip)} cells left out"
     for k in keys:
+        if (k[1] if isinstance(k, tuple) else k) in skip:
+            continue
         gc, gq, gcc = g[k]
         oc, oq, occ = o[k]
         if check_cut:

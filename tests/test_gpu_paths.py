@@ -28,11 +28,16 @@ def env():
 
 
 def _compare(g, o, gkeys, okeys, Hl, M):
+    """Level, cell and cluster of every sample exact (light choices may differ
+    only for draws within 1e-6 of a threshold, at most 1e-5 of the samples,
+    rounded down); rewards and the estimates of points whose samples all
+    agree within 1e-4. Returns the (level, key) cells fed by a mismatched
+    sample on either side."""
     light_g = g["light"].astype(np.int64)
     mism = light_g != o["light"]
     near = o["margin"] < 1e-6
     assert not np.any(mism & ~near)
-    assert mism.sum() <= max(1, int(1e-5 * light_g.size))
+    assert mism.sum() <= int(1e-5 * light_g.size)
     ok = ~mism
     kg = g["key"].view(np.uint32).astype(np.int64)
     slot_g = np.where(kg == 0xFFFFFFFF, -1, kg // M)
@@ -43,9 +48,11 @@ def _compare(g, o, gkeys, okeys, Hl, M):
     assert np.array_equal((kg % M)[ok], o["s"][ok])
     assert np.allclose(g["val"][ok], o["reward"][ok], rtol=1e-4,
                        atol=1e-7 * max(1.0, np.abs(o["reward"]).max()))
-    if mism.sum() == 0:
-        assert np.allclose(g["rgb"], o["rgb"], rtol=1e-4, atol=1e-7 * max(1.0, np.abs(o["rgb"]).max()))
-    return int(mism.sum())
+    P = g["rgb"].shape[1]
+    pt_ok = ok.reshape(P, -1).all(axis=1)
+    assert np.allclose(g["rgb"][:, pt_ok], o["rgb"][:, pt_ok], rtol=1e-4,
+                       atol=1e-7 * max(1.0, np.abs(o["rgb"]).max()))
+    return {int(c) for i in np.nonzero(mism)[0] for c in (cg[i], co[i])}
 
 
 @pytest.mark.parametrize("variant", [dict(), dict(jitter=False, precision="fp16")])
@@ -72,12 +79,11 @@ def test_path_vertices_lockstep(env, variant):
         g = to_host(run_sample(rll, ctx, dg, dt, d, s.seed, f, s.spp))
         o = og.sample_frame(A, s.seed, f, s.spp, footprint=s.footprint)
         levels_seen |= set(np.unique(o["slot"][o["slot"] >= 0] // Hl).tolist())
-        mism = _compare(g, o, dg.export()["keys"], og.keys, Hl, dg.M)
+        skip = _compare(g, o, dg.export()["keys"], og.keys, Hl, dg.M)
         rll.learn_update(ctx, dg, torch.from_numpy(g["key"]).to(env["dev"]),
                          torch.from_numpy(g["val"]).to(env["dev"]))
         touched = og.learn(o["slot"], o["s"], o["reward"])
-        if mism == 0:
-            compare_tables(dg.export(), oracle_state(og), og.m, rtol, Hl=Hl)
+        compare_tables(dg.export(), oracle_state(og), og.m, rtol, Hl=Hl, skip=skip)
         dg.import_state(og.keys, og.cut, og.Q, og.C)
         rll.split_collapse(ctx, dg, dt)
         o2 = clone_oracle_grid(O, og)

@@ -45,12 +45,11 @@ def test_sky_lockstep(env, variant):
         dg.import_state(og.keys, og.cut, og.Q, og.C)
         g = to_host(run_sample(rll, ctx, dg, dt, d, s.seed, f, s.spp))
         o = og.sample_frame(A, s.seed, f, s.spp)
-        mism = compare_samples(g, o, dg.export()["keys"], og.keys, dg.M)
+        skip = compare_samples(g, o, dg.export()["keys"], og.keys, dg.M)
         rll.learn_update(ctx, dg, torch.from_numpy(g["key"]).to(env["dev"]),
                          torch.from_numpy(g["val"]).to(env["dev"]))
         touched = og.learn(o["slot"], o["s"], o["reward"])
-        if mism == 0:
-            compare_tables(dg.export(), oracle_state(og), og.m, rtol)
+        compare_tables(dg.export(), oracle_state(og), og.m, rtol, skip=skip)
         dg.import_state(og.keys, og.cut, og.Q, og.C)
         rll.split_collapse(ctx, dg, dt)
         o2 = clone_oracle_grid(O, og)
