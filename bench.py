@@ -330,16 +330,16 @@ def run_batched(args):
     return 0
 
 
-def run_serving(args):
+def serving_measure(n_sessions, frames, scale=1.0, load=0.7, budget_gb=80.0, seed=11):
     """Continuous batching of frame requests from many sessions (half of the
     frame-scale shape, half of the 4K / 1M-light shape, BF16 tables), Poisson
     arrivals at a fixed fraction of the measured capacity, admission by an HBM
-    budget; p50 / p99 frame latency and served samples per second."""
+    budget. Returns served samples per second, p50 / p99 frame latency and the
+    device overlap of the two launch slots."""
     import torch
     from paper_1911_10217_gb300 import rll, scenes, serving
     dev = torch.device("cuda:0")
-    n_sessions, frames = args.serving_sessions, args.serving_frames
-    sc = args.serving_scale
+    sc = scale
     t0 = time.perf_counter()
     shape_a = scenes.frame_scene(seed=1, width=int(1920 * sc), height=int(1080 * sc))
     shape_b = scenes.dynamic_scene(seed=2, width=int(3840 * sc), height=int(2160 * sc))
@@ -347,8 +347,8 @@ def run_serving(args):
     prec = "bf16"
     shapes = {sid: (shape_a if sid % 2 == 0 else shape_b) for sid in range(n_sessions)}
     max_items, max_records, max_cells = 64, 1 << 26, (1 << 26) - 1
-    ex = serving.GpuExecutor(torch, rll, dev, max_items, max_records, max_cells)
-    budget = int(args.serving_budget_gb * 1e9)
+    ex = serving.GpuExecutor(torch, rll, dev, max_items, max_records, max_cells, timeline=True)
+    budget = int(budget_gb * 1e9)
     sched = serving.Scheduler(budget, max_items, max_records, max_cells,
                               reserved_bytes=ex.reserved_bytes(max_records, max_cells))
 
@@ -380,54 +380,72 @@ def run_serving(args):
             cal_samples += sum(cal[r.session].n_points * cal[r.session].spp for r in batch)
     for sid in cal:
         ex.release(sid)
+    ex.timeline.clear()
     capacity = cal_samples / t_cal
     mean_samples = np.mean([shapes[s].n_points * shapes[s].spp for s in shapes])
-    rate_total = args.serving_load * capacity / mean_samples   # frames per second
-    rng = np.random.default_rng(11)
+    rate_total = load * capacity / mean_samples   # frames per second
+    rng = np.random.default_rng(seed)
     arrivals = {sid: serving.poisson_arrivals(rng, frames, rate_total / n_sessions) for sid in shapes}
     for sid, s in shapes.items():
         sched.add_session(sid, size(s), s.n_points * s.spp, s.grid.table_size, frames)
-    seeded = {sid: s for sid, s in shapes.items()}
     # each session its own Philox seed
     orig_create = ex.create
     ex.create = lambda sid, s, p: orig_create(sid, s, p, seed=1000 + sid)
     w0 = time.perf_counter()
-    log = serving.serve(ex, sched, seeded, arrivals, precision=prec, timeout_s=3600.0)
+    log = serving.serve(ex, sched, shapes, arrivals, precision=prec, timeout_s=3600.0)
     wall = time.perf_counter() - w0
+    spans = ex.device_intervals()
     lat = np.array([1e3 * (r.done - r.arrival) for r in log])
     starts = {}
     for r in log:
         starts.setdefault(r.start, []).append(r)
     served = sum(shapes[r.session].n_points * shapes[r.session].spp for r in log)
-    status = ex.status()
-    line = {"metric": METRIC, "workload": "serving", "value": served / wall, "unit": UNIT, "n_gpus": 1,
+    # launches of the two slots on the device at the same time
+    ends = {}
+    for slot, a, b in spans:
+        ends.setdefault(slot, []).append((a, b))
+    overlap = sum(1 for a1, b1 in ends.get(0, []) for a2, b2 in ends.get(1, []) if a1 < b2 and a2 < b1)
+    return {"value": served / wall, "p50_frame_ms": float(np.percentile(lat, 50)),
+            "p99_frame_ms": float(np.percentile(lat, 99)), "frames": len(log), "launches": len(starts),
+            "mean_sessions_per_launch": len(log) / len(starts), "offered_load_fraction": load,
+            "capacity_samples_per_s": capacity, "overlapping_launch_pairs": overlap,
+            "sessions": n_sessions, "frames_per_session": frames,
+            "shape_a": f"{shape_a.width}x{shape_a.height}, {shape_a.n_lights} lights, M={shape_a.grid.cut_size}",
+            "shape_b": f"{shape_b.width}x{shape_b.height}, {shape_b.n_lights} lights, M={shape_b.grid.cut_size}",
+            "budget_gb": budget_gb, "table_precision": prec,
+            "resident_gb": sum(size(s) for s in shapes.values()) / 1e9,
+            "wall_s": wall, "generation_s": gen_s, "device_status": ex.status()}
+
+
+def run_serving(args):
+    """The serving workload on its own line (64 sessions by default)."""
+    r = serving_measure(args.serving_sessions, args.serving_frames, args.serving_scale, args.serving_load,
+                        args.serving_budget_gb)
+    line = {"metric": METRIC, "workload": "serving", "value": r["value"], "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32 arithmetic, bf16 tables", "data": "synthetic",
-            "p50_frame_ms": float(np.percentile(lat, 50)), "p99_frame_ms": float(np.percentile(lat, 99)),
-            "frames": len(log), "launches": len(starts), "mean_sessions_per_launch": len(log) / len(starts),
-            "offered_load_fraction": args.serving_load, "capacity_samples_per_s": capacity,
-            "config": {"workload": f"{n_sessions} sessions, continuous batching, HBM-budget admission",
-                       "sessions": n_sessions, "frames_per_session": frames,
-                       "shape_a": f"{shape_a.width}x{shape_a.height}, {shape_a.n_lights} lights, M={shape_a.grid.cut_size}",
-                       "shape_b": f"{shape_b.width}x{shape_b.height}, {shape_b.n_lights} lights, M={shape_b.grid.cut_size}",
-                       "budget_gb": args.serving_budget_gb, "table_precision": prec,
-                       "resident_gb": sum(size(s) for s in shapes.values()) / 1e9},
-            "wall_s": wall, "generation_s": gen_s, "device_status": status}
+            "p50_frame_ms": r["p50_frame_ms"], "p99_frame_ms": r["p99_frame_ms"],
+            "config": {"workload": f"{r['sessions']} sessions, continuous batching, HBM-budget admission",
+                       **{k: r[k] for k in ("sessions", "frames_per_session", "shape_a", "shape_b", "budget_gb",
+                                            "table_precision", "resident_gb")}},
+            **{k: r[k] for k in ("frames", "launches", "mean_sessions_per_launch", "offered_load_fraction",
+                                 "capacity_samples_per_s", "overlapping_launch_pairs", "wall_s", "generation_s",
+                                 "device_status")}}
     print(json.dumps(line))
     return 0
 
 
-def run_dynamic(args):
+def dynamic_measure(frames, precisions, scale=1.0, mse=True):
     """Dynamic lighting (1M triangles, 10% blinking, 3840x2160, M = 64,
-    split-collapse every frame) with FP32, FP16 and BF16 tables: time per
-    frame and 1-spp MSE against a high-spp energy-sampler reference of the
-    last frame."""
+    split-collapse every frame) per table precision: sampling and learning
+    time per frame (frames 3.. of a fresh grid), touched cells, the learning
+    step's algorithmic bytes, and optionally the 1-spp MSE against a
+    high-spp energy-sampler reference of the last frame."""
     import torch
     from paper_1911_10217_gb300 import rll, scenes
     dev = torch.device("cuda:0")
     stream = torch.cuda.current_stream(dev)
     ctx = rll.Context(0, stream)
-    sc = args.dynamic_scale
-    s = scenes.dynamic_scene(width=int(3840 * sc), height=int(2160 * sc))
+    s = scenes.dynamic_scene(width=int(3840 * scale), height=int(2160 * scale))
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     tri, bound, em0 = T(s.tris.reshape(-1, 9)), T(s.emission_bound()), T(s.emission)
     omega, phase = T(s.blink_omega), T(s.blink_phase)
@@ -439,8 +457,8 @@ def run_dynamic(args):
 
     def set_emission(frame):
         t = frame / 30.0
-        scale = 1.0 + mask * 0.9 * torch.sin(omega * t + phase)
-        torch.mul(em0, scale[:, None], out=em)
+        sc = 1.0 + mask * 0.9 * torch.sin(omega * t + phase)
+        torch.mul(em0, sc[:, None], out=em)
         tree.update_emission(em)
 
     rgb = torch.empty(3, P, device=dev)
@@ -448,8 +466,7 @@ def run_dynamic(args):
     val = torch.empty(P * s.spp, device=dev)
     g = s.grid
     results = {}
-    frames = args.dynamic_frames
-    for prec in args.dynamic_precisions.split(","):
+    for prec in precisions:
         grid = rll.Grid(ctx, tree, rll.grid_params_for(g, precision=prec))
         ms, touched = [], []
         for f in range(frames):
@@ -461,41 +478,49 @@ def run_dynamic(args):
             rll.learn_update_split(ctx, grid, tree, key, val)
             e2.record(stream)
             ms.append((e0, e1, e2))
-            if f >= 3 and f % 8 == 3:  # outside the event pairs: costs a host round trip only
+            if f >= 3 and (f % 8 == 3 or f == frames - 1):  # outside the event pairs: a host round trip only
                 touched.append(grid.touched_cells())
         torch.cuda.synchronize()
         t = [a.elapsed_time(c) for a, b, c in ms][3:]
         t_s = [a.elapsed_time(b) for a, b, c in ms][3:]
         t_l = [b.elapsed_time(c) for a, b, c in ms][3:]
         n_touched = statistics.mean(touched) if touched else float("nan")
-        # reference of the last frame: energy sampler, 256 spp
-        set_emission(frames - 1)
-        ref = torch.zeros(3, P, device=dev, dtype=torch.float64)
-        tmp = torch.empty(3, P, device=dev)
-        for i in range(32):
-            rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 9999, 200000 + i, 8, tmp)
-            ref += tmp.double()
-        ref /= 32
-        rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, 4242, 300000, 1, tmp)
-        mse = float(((tmp.double() - ref) ** 2).mean())
-        rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 4242, 300000, 1, tmp)
-        mse_pow = float(((tmp.double() - ref) ** 2).mean())
         e = 4 if prec == "fp32" else 2
         lb = learn_step_bytes(P * s.spp, n_touched, g.cut_size, prec)
-        results[prec] = {"ms_per_frame": statistics.mean(t), "p99_frame_ms": float(np.percentile(t, 99)),
-                         "sample_ms": statistics.mean(t_s), "learn_update_split_ms": statistics.mean(t_l),
-                         "touched_cells_per_frame": n_touched,
-                         "learn_algorithmic_bytes_per_frame": lb,
-                         "learn_algorithmic_gbs": lb / (statistics.mean(t_l) * 1e-3) / 1e9,
-                         "samples_per_s": P * s.spp / (statistics.mean(t) * 1e-3),
-                         "mse_1spp": mse, "energy_sampler_mse_1spp": mse_pow, "mse_ratio_vs_energy": mse_pow / mse,
-                         "table_bytes": g.table_size * g.cut_size * (4 + 2 * e)}
+        r = {"ms_per_frame": statistics.mean(t), "p99_frame_ms": float(np.percentile(t, 99)),
+             "sample_ms": statistics.mean(t_s), "learn_update_split_ms": statistics.mean(t_l),
+             "touched_cells_per_frame": n_touched,
+             "learn_algorithmic_bytes_per_frame": lb,
+             "learn_algorithmic_gbs": lb / (statistics.mean(t_l) * 1e-3) / 1e9,
+             "samples_per_s": P * s.spp / (statistics.mean(t) * 1e-3),
+             "table_bytes": g.table_size * g.cut_size * (4 + 2 * e)}
+        if mse:
+            # reference of the last frame: energy sampler, 256 spp
+            set_emission(frames - 1)
+            ref = torch.zeros(3, P, device=dev, dtype=torch.float64)
+            tmp = torch.empty(3, P, device=dev)
+            for i in range(32):
+                rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 9999, 200000 + i, 8, tmp)
+                ref += tmp.double()
+            ref /= 32
+            rll.sample_and_shade(ctx, grid, tree, pos, nrm, alb, boxes, 4242, 300000, 1, tmp)
+            err = float(((tmp.double() - ref) ** 2).mean())
+            rll.sample_power(ctx, tree, pos, nrm, alb, boxes, 4242, 300000, 1, tmp)
+            err_pow = float(((tmp.double() - ref) ** 2).mean())
+            r.update({"mse_1spp": err, "energy_sampler_mse_1spp": err_pow, "mse_ratio_vs_energy": err_pow / err})
+        results[prec] = r
         grid.close()
+    config = {"workload": "dynamic lighting, 10% blinking lights, split-collapse every frame",
+              "points": P, "lights": s.n_lights, "cut_size": g.cut_size, "table_size": g.table_size,
+              "frames": frames, "timed_frames": f"3..{frames - 1} of a fresh grid", "boxes": int(s.boxes.shape[0])}
+    return config, results, ctx.sync_status()
+
+
+def run_dynamic(args):
+    config, results, status = dynamic_measure(args.dynamic_frames, args.dynamic_precisions.split(","),
+                                              args.dynamic_scale)
     line = {"metric": METRIC, "workload": "dynamic", "unit": UNIT, "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "dynamic lighting, 10% blinking lights, split-collapse every frame",
-                       "points": P, "lights": s.n_lights, "cut_size": g.cut_size, "table_size": g.table_size,
-                       "frames": frames, "boxes": int(s.boxes.shape[0])},
-            "precisions": results, "device_status": ctx.sync_status()}
+            "config": config, "precisions": results, "device_status": status}
     print(json.dumps(line))
     return 0
 
@@ -674,9 +699,19 @@ def run_paths(args):
     s = scenes.path_scene(base, levels=args.paths_levels, paths_per_tile=1.0)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     tri, em, boxes = T(s.tris.reshape(-1, 9)), T(s.emission), T(s.boxes)
-    pos, nrm, alb, fp1 = T(s.pos), T(s.nrm), T(s.albedo), T(s.footprint)
+    # the bounce vertices by the library: one diffuse bounce from every primary point
+    P0 = base.n_points
+    P = 2 * P0
+    pos, nrm = torch.empty(3, P, device=dev), torch.empty(3, P, device=dev)
+    fp1 = torch.empty(P, device=dev)
+    pos[:, :P0], nrm[:, :P0], fp1[:P0] = T(base.pos), T(base.nrm), T(s.footprint)
+    b = s.bounce
+    by, bn, bf = torch.empty(3, P0, device=dev), torch.empty(3, P0, device=dev), torch.empty(P0, device=dev)
+    rll.bounce_vertices(ctx, pos[:, :P0].contiguous(), nrm[:, :P0].contiguous(), boxes, b.room, b.seed, b.frame,
+                        b.paths_per_tile, by, bn, bf)
+    pos[:, P0:], nrm[:, P0:], fp1[P0:] = by, bn, bf
+    alb = torch.cat([T(base.albedo), T(b.albedo)])
     tree = rll.Tree(ctx, tri, em)
-    P, P0 = s.n_points, base.n_points
     rgb = torch.empty(3, P, device=dev)
     key = torch.empty(P, dtype=torch.int32, device=dev)
     val = torch.empty(P, device=dev)
@@ -822,6 +857,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-workload-extras", action="store_true",
+                    help="skip the 4K dynamic-lighting and short serving figures of the default line")
     ap.add_argument("--sample-min-blocks", type=int, default=4)
     ap.add_argument("--separate-split", action="store_true",
                     help="learning step as rll_learn_update + rll_split_collapse instead of the fused call")
@@ -1041,6 +1078,12 @@ def main():
                           "device_status": status}}
         if not args.no_quality:
             out["extras"]["mse_equal_spp"] = quality(rll, ctx, grid, tree, scene, pos, nrm, alb, boxes, dev)
+        if not args.no_workload_extras and world == 1:
+            # the 4K / 1M-light shape in binary32 and bfloat16 tables, and a short serving run
+            grid.close()
+            cfg, res, st = dynamic_measure(8, ["fp32", "bf16"], mse=False)
+            out["extras"]["dynamic_4k"] = {"config": cfg, "precisions": res, "device_status": st}
+            out["extras"]["serving"] = serving_measure(16, 16)
         if not args.no_cpu_baseline and world == 1:  # the host baseline belongs to the one-GPU line
             out["cpu_baseline"] = cpu_baseline(scene)
         print(json.dumps(out))

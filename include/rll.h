@@ -230,6 +230,31 @@ int rll_sample_and_shade_fp(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, 
                             uint32_t frame, int32_t spp, float* rgb, uint32_t* rec_key,
                             float* rec_val, const rll_sample_debug* dbg);
 
+/* Path vertices of one diffuse bounce and their footprints (Section 3, first
+ * ingredient: a path vertex's cells are sized from its ray footprint, derived
+ * from its area pdf). From every point x (pos, nrm: SoA [3][P], unit normals)
+ * one cosine-weighted direction: a uniform point (a, b) of the unit disk by
+ * rejection (Philox key = seed, counter = (point, frame, k / 2, 1), pair k =
+ * words 2k mod 4 and 2k + 1 mod 4 as 2u - 1, the first of 16 pairs with
+ * a^2 + b^2 < 1, else the centre), lifted to d = a u + b v + sqrt(1 - a^2 -
+ * b^2) n with u = normalise(n x t), v = n x u, t the x axis (the z axis when
+ * |n.x| >= 0.9). The ray from o = x + 1e-4 n meets the nearest surface ahead
+ * (t > 1e-6): a box face (boxes [K][6], K <= 1024) or, from the inside, a wall
+ * of the room (HOST float[6]: min xyz, max xyz). Outputs (device, caller
+ * owned): out_pos SoA [3][P] the vertex y = o + t d, out_nrm SoA [3][P] the
+ * hit face's axis normal turned toward x, out_footprint [P] =
+ * t sqrt(pi / (N_t cos_x cos_y)) = (N_t p_A)^(-1/2), where p_A = cos_x cos_y
+ * / (pi t^2) is the vertex's area density for one path, N_t = paths_per_tile
+ * (> 0) the paths that leave one tile and share it, and each cosine is at
+ * least 1e-6. A ray with nothing ahead (a point outside the room) escapes:
+ * y = o, normal 0, footprint +inf (rll_sample_and_shade_fp then uses the
+ * coarsest level). Every step is one correctly rounded binary32 operation.
+ * P < 2^32. Enqueued on the context stream. */
+int rll_bounce_vertices(rll_ctx* ctx, const float* pos, const float* nrm, int64_t n_points,
+                        const float* boxes, int32_t n_boxes, const float* room, uint64_t seed,
+                        uint32_t frame, float paths_per_tile, float* out_pos, float* out_nrm,
+                        float* out_footprint);
+
 /* Energy-based baseline (Section 4): lights chosen in proportion to their
  * emitted power by inversion of one global cdf; same shading, same Philox
  * stream (cluster draw reused as the cdf draw). rgb: SoA [3][P]. */
@@ -310,8 +335,10 @@ int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int6
                       rll_batch** out);
 /* Sets the scenes of the next passes (all grids with the same table
  * precision and in-cluster mode, cut sizes <= 64, each grid at most once,
- * within the reserved capacity). Uploads descriptors only, allocates
- * nothing; drops a recorded graph. Synchronises the context stream. */
+ * within the reserved capacity). Enqueues the upload of the descriptors on
+ * the context stream from page-locked staging owned by the batch and returns
+ * without waiting for the stream (it waits only if the previous upload from
+ * that staging has not run yet); allocates nothing; drops a recorded graph. */
 int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items, int32_t n_items);
 /* rll_batch_reserve for exactly these items, then rll_batch_set_items.
  *

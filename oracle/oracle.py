@@ -76,6 +76,8 @@ def lib():
             L.orc_lookup_insert.argtypes = [ctypes.POINTER(_Grid), ctypes.c_uint64]
             L.orc_lookup_insert.restype = ctypes.c_int64
             L.orc_importance32.argtypes = [P, P, P, P, P]
+            L.orc_bounce_vertices.argtypes = [ctypes.c_int64, P, P, ctypes.c_int, P, P, ctypes.c_uint64,
+                                              ctypes.c_uint32, ctypes.c_float, P, P, P]
             L.orc_node_consts32.argtypes = [P, P]
             L.orc_bound64.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P,
                                       ctypes.c_double, P, P]
@@ -171,6 +173,19 @@ class Tree:
         lib().orc_importance32(_p(np.ascontiguousarray(self.rec[node])), _p(_f32(x)), _p(_f32(nrm)),
                                ctypes.byref(num), ctypes.byref(den))
         return float(num.value) / float(den.value)
+
+
+def bounce_vertices(pos, nrm, boxes, room, seed, frame, paths_per_tile):
+    """One diffuse bounce per point (cosine-weighted direction, nearest box
+    face or room wall): vertex positions and face normals SoA [3][P] and
+    footprints [P] (binary32)."""
+    pos, nrm = _f32(pos), _f32(nrm)
+    P = pos.shape[1]
+    boxes = _f32(boxes).reshape(-1, 6)
+    y, ny, fp = np.zeros((3, P), np.float32), np.zeros((3, P), np.float32), np.zeros(P, np.float32)
+    lib().orc_bounce_vertices(P, _p(pos), _p(nrm), int(boxes.shape[0]), _p(boxes), _p(_f32(room)),
+                              int(seed), int(frame), float(paths_per_tile), _p(y), _p(ny), _p(fp))
+    return y, ny, fp
 
 
 def node_consts(rec):

@@ -1563,3 +1563,136 @@ void orc_direct_bruteforce(const float x32[3], const float n32[3], float albedo,
     double f = (double)albedo / 3.14159265358979323846;
     for (int k = 0; k < 3; ++k) rgb[k] *= f;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Path vertices of one diffuse bounce and their footprints (Section 3, first */
+/* ingredient: cells sized from the ray footprint of each path vertex,       */
+/* derived from its area pdf). Reading: from each shading point x with unit   */
+/* normal n, one cosine-weighted direction (Malley: a uniform point (a, b) of */
+/* the unit disk lifted to the hemisphere) is traced to the nearest face of   */
+/* an occluder box or of the room's inside; the vertex y gets the footprint  */
+/* f = (N_t p_A)^(-1/2), p_A = cos(theta_x) cos(theta_y) / (pi d^2) the area   */
+/* density of y for one path, shared by the N_t paths that leave one tile.   */
+/* The disk point comes from rejection: draws 2k, 2k + 1 of the point's      */
+/* stream (Philox counter = (point, frame, draw / 4, 1)) give a = 2u - 1,    */
+/* b = 2u' - 1, accepted at the first k < 16 with a^2 + b^2 < 1 (else a = b =  */
+/* 0). Everything is binary32 with one correctly rounded operation per step  */
+/* (the hit face is a decision). Only surfaces ahead (t > 1e-6) count; a ray */
+/* from outside the room may find none and escapes: y = x + 1e-4 n, normal   */
+/* 0 and footprint +inf (the coarsest level).                                */
+/* ------------------------------------------------------------------------ */
+#define ORC_BOUNCE_TRIES 16
+#define ORC_BOUNCE_OFFSET 1e-4f
+#define ORC_BOUNCE_TMIN 1e-6f
+#define ORC_PI_F 3.14159265358979323846f
+
+static void orc_bounce_one(const float x[3], const float n[3], int nbox, const float* boxes, const float room[6],
+                           uint64_t seed, uint32_t point, uint32_t frame, float paths_per_tile, float y[3],
+                           float ny[3], float* footprint)
+{
+    /* the disk point */
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {point, frame, 0, 1}, w[4];
+    float a = 0.0f, b = 0.0f;
+    for (int k = 0; k < ORC_BOUNCE_TRIES; ++k) {
+        if ((k & 1) == 0) {  /* draws 2k .. 2k + 3 are the words of block k / 2 */
+            ctr[2] = (uint32_t)(k >> 1);
+            orc_philox4x32_10(ctr, key, w);
+        }
+        float ua = orc_u24(w[(2 * k) & 3]), ub = orc_u24(w[(2 * k + 1) & 3]);
+        float ta = 2.0f * ua - 1.0f, tb = 2.0f * ub - 1.0f;
+        if (ta * ta + tb * tb < 1.0f) {
+            a = ta;
+            b = tb;
+            break;
+        }
+    }
+    float s = a * a + b * b;
+    float c = sqrtf(fmaxf(0.0f, 1.0f - s));               /* cos(theta_x) */
+
+    /* tangent frame of n: u = normalise(n x t), v = n x u */
+    float t0 = fabsf(n[0]) < 0.9f ? 1.0f : 0.0f, t2 = fabsf(n[0]) < 0.9f ? 0.0f : 1.0f;
+    float u[3] = {n[1] * t2 - n[2] * 0.0f, n[2] * t0 - n[0] * t2, n[0] * 0.0f - n[1] * t0};
+    float ul = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int k = 0; k < 3; ++k) u[k] = u[k] / ul;
+    float v[3] = {n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]};
+
+    float d[3], o[3], inv[3];
+    for (int k = 0; k < 3; ++k) {
+        d[k] = (a * u[k] + b * v[k]) + c * n[k];
+        o[k] = x[k] + ORC_BOUNCE_OFFSET * n[k];
+        inv[k] = 1.0f / d[k];
+    }
+
+    /* leave the room through the first wall ahead (a point outside the room may have none) */
+    float t_best = INFINITY;
+    int axis = 0;
+    for (int k = 0; k < 3; ++k) {
+        if (d[k] == 0.0f) continue;
+        float wall = d[k] > 0.0f ? room[3 + k] : room[k];
+        float t = (wall - o[k]) * inv[k];
+        if (t > ORC_BOUNCE_TMIN && t < t_best) {
+            t_best = t;
+            axis = k;
+        }
+    }
+    /* the nearest box face in front of it */
+    for (int i = 0; i < nbox; ++i) {
+        const float* bx = boxes + (size_t)i * 6;
+        float tn = -INFINITY, tf = INFINITY;
+        int ax = 0, miss = 0;
+        for (int k = 0; k < 3; ++k) {
+            if (d[k] == 0.0f) {  /* parallel to this slab: inside it or a miss */
+                if (!(o[k] > bx[k] && o[k] < bx[3 + k])) miss = 1;
+                continue;
+            }
+            float ta = (bx[k] - o[k]) * inv[k];
+            float tb = (bx[3 + k] - o[k]) * inv[k];
+            float lo = fminf(ta, tb), hi = fmaxf(ta, tb);
+            if (lo > tn) {
+                tn = lo;
+                ax = k;
+            }
+            tf = fminf(tf, hi);
+        }
+        if (!miss && tn < tf && tn > ORC_BOUNCE_TMIN && tn < t_best) {
+            t_best = tn;
+            axis = ax;
+        }
+    }
+    if (t_best == INFINITY) {  /* nothing ahead: the path escapes, no vertex */
+        for (int k = 0; k < 3; ++k) {
+            y[k] = o[k];
+            ny[k] = 0.0f;
+        }
+        *footprint = INFINITY;
+        return;
+    }
+    for (int k = 0; k < 3; ++k) {
+        y[k] = o[k] + t_best * d[k];
+        ny[k] = 0.0f;
+    }
+    ny[axis] = d[axis] > 0.0f ? -1.0f : 1.0f;               /* the face turned toward x */
+    float cy = fabsf(d[axis]);                               /* cos(theta_y) */
+    float q = (paths_per_tile * fmaxf(c, 1e-6f)) * fmaxf(cy, 1e-6f);
+    *footprint = t_best * sqrtf(ORC_PI_F / q);               /* d sqrt(pi / (N_t cx cy)) */
+}
+
+/* Bounce vertices of P points: pos, nrm SoA [3][P] in, y, ny SoA [3][P] and
+ * footprint [P] out; room [6] = min xyz, max xyz. */
+void orc_bounce_vertices(int64_t npts, const float* pos, const float* nrm, int nbox, const float* boxes,
+                         const float room[6], uint64_t seed, uint32_t frame, float paths_per_tile, float* y_out,
+                         float* ny_out, float* fp_out)
+{
+    for (int64_t p = 0; p < npts; ++p) {
+        float x[3] = {pos[p], pos[npts + p], pos[2 * npts + p]};
+        float n[3] = {nrm[p], nrm[npts + p], nrm[2 * npts + p]};
+        float y[3], ny[3], f;
+        orc_bounce_one(x, n, nbox, boxes, room, seed, (uint32_t)p, frame, paths_per_tile, y, ny, &f);
+        for (int k = 0; k < 3; ++k) {
+            y_out[k * npts + p] = y[k];
+            ny_out[k * npts + p] = ny[k];
+        }
+        fp_out[p] = f;
+    }
+}

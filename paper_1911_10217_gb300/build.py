@@ -17,7 +17,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "--expt-relaxed-constexpr"]
-SOURCES = ["api.cu", "tree.cu", "sort.cu", "sample.cu", "learn.cu", "noalloc.cu", "batched.cu"]
+SOURCES = ["api.cu", "tree.cu", "sort.cu", "sample.cu", "learn.cu", "noalloc.cu", "batched.cu", "bounce.cu"]
 
 
 def _deps():

@@ -187,6 +187,15 @@ struct rll_batch {
     int64_t cap_cells = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
+    // page-locked staging of the descriptor, cell-prefix and tile-prefix uploads, so that
+    // rll_batch_set_items enqueues them without waiting; `staged` is recorded after the
+    // last upload from it and waited on before the staging is written again
+    void* stage = nullptr;
+    BatchItemDev* stage_items = nullptr;   // [cap_items]
+    uint32_t* stage_cells = nullptr;       // [cap_items + 1]
+    uint32_t* stage_tiles = nullptr;       // [cap_items + 1]
+    cudaEvent_t staged = nullptr;
+    bool stage_pending = false;
 };
 
 namespace {
@@ -209,6 +218,11 @@ void free_batch(rll_batch* b)
     cudaFree(b->touched_len);
     cudaFree(b->lists);
     cudaFree(b->n_touched);
+    if (b->staged) {
+        if (b->stage_pending) cudaEventSynchronize(b->staged);
+        cudaEventDestroy(b->staged);
+    }
+    cudaFreeHost(b->stage);
     delete b;
 }
 
@@ -221,14 +235,37 @@ std::vector<uint32_t> tile_prefix(const rll_batch* b, uint32_t tile_points)
     return pre;
 }
 
-int set_tiles(rll_ctx* ctx, rll_batch* b, uint32_t tile_points)
+// The staging may be written once the uploads enqueued from it have run.
+cudaError_t stage_wait(rll_batch* b)
+{
+    if (!b->stage_pending) return cudaSuccess;
+    b->stage_pending = false;
+    return cudaEventSynchronize(b->staged);
+}
+
+// Uploads the tile prefix through the staging (the caller has waited for it
+// and records `staged` afterwards).
+int set_tiles_staged(rll_ctx* ctx, rll_batch* b, uint32_t tile_points)
 {
     const std::vector<uint32_t> pre = tile_prefix(b, tile_points);
-    const cudaError_t e = cudaMemcpyAsync(b->d_tile_prefix, pre.data(), sizeof(uint32_t) * (b->n + 1),
+    std::copy(pre.begin(), pre.end(), b->stage_tiles);
+    const cudaError_t e = cudaMemcpyAsync(b->d_tile_prefix, b->stage_tiles, sizeof(uint32_t) * (b->n + 1),
                                           cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return check_cuda(ctx, e, "batch tiles");
     b->tile_points = tile_points;
     b->total_tiles = pre[b->n];
+    return RLL_OK;
+}
+
+int set_tiles(rll_ctx* ctx, rll_batch* b, uint32_t tile_points)
+{
+    cudaError_t e = stage_wait(b);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "batch staging");
+    const int rc = set_tiles_staged(ctx, b, tile_points);
+    if (rc != RLL_OK) return rc;
+    e = cudaEventRecord(b->staged, ctx->stream);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "batch staging");
+    b->stage_pending = true;
     return RLL_OK;
 }
 
@@ -300,19 +337,6 @@ cudaError_t enqueue_pass(rll_batch* b, cudaStream_t s, bool do_split)
     return cudaGetLastError();
 }
 
-struct DevGuard {
-    int prev = -1;
-    explicit DevGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DevGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 }  // namespace
 
@@ -326,7 +350,7 @@ int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int6
     if (max_records < 0 || max_records >= 0xFFFFFFFFll) return fail(ctx, RLL_E_INVALID, "max_records must be < 2^32");
     if (max_cells < 1 || (max_cells << kBatchClusterBits) >= 0xFFFFFFFFll)
         return fail(ctx, RLL_E_INVALID, "max_cells must be in [1, 2^26)");
-    DevGuard dg(ctx->device);
+    DeviceGuard dg(ctx->device);
     rll_batch* b = new (std::nothrow) rll_batch();
     if (!b) return fail(ctx, RLL_E_NOMEM, "host allocation");
     b->device = ctx->device;
@@ -356,6 +380,17 @@ int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int6
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tile_prefix, 4 * (max_items + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cell_prefix, 4 * (max_items + 1));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->n_touched, 0, 8 * sizeof(uint32_t), ctx->stream);
+    if (e == cudaSuccess) {
+        const size_t items_b = (sizeof(BatchItemDev) * max_items + 255) & ~(size_t)255;
+        const size_t pre_b = (4 * ((size_t)max_items + 1) + 255) & ~(size_t)255;
+        e = cudaHostAlloc(&b->stage, items_b + 2 * pre_b, cudaHostAllocDefault);
+        if (e == cudaSuccess) {
+            b->stage_items = static_cast<BatchItemDev*>(b->stage);
+            b->stage_cells = reinterpret_cast<uint32_t*>(static_cast<char*>(b->stage) + items_b);
+            b->stage_tiles = reinterpret_cast<uint32_t*>(static_cast<char*>(b->stage) + items_b + pre_b);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         const int rc = check_cuda(ctx, e, "batch allocation");
@@ -370,7 +405,7 @@ int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items,
 {
     if (!ctx || !b) return RLL_E_INVALID;
     if (!items || n_items < 1 || n_items > b->cap_items) return fail(ctx, RLL_E_INVALID, "need 1..max_items items");
-    DevGuard dg(ctx->device);
+    DeviceGuard dg(ctx->device);
     uint32_t precision = 0, mode = 0;
     uint64_t cells = 0, recs = 0;
     int max_boxes = 0;
@@ -475,14 +510,25 @@ int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items,
         rec_off += (uint64_t)it.n_points * it.spp;
         b->points_per_item[i] = (uint32_t)it.n_points;
     }
-    cudaError_t e = cudaMemcpyAsync(b->d_items, b->host.data(), sizeof(BatchItemDev) * n_items,
-                                    cudaMemcpyHostToDevice, ctx->stream);
+    // through the page-locked staging: the copies are enqueued without waiting (only a previous
+    // upload from the staging that has not run yet is waited for)
+    cudaError_t e = stage_wait(b);
+    if (e == cudaSuccess) {
+        std::copy(b->host.begin(), b->host.end(), b->stage_items);
+        std::copy(cell_pre.begin(), cell_pre.end(), b->stage_cells);
+        e = cudaMemcpyAsync(b->d_items, b->stage_items, sizeof(BatchItemDev) * n_items, cudaMemcpyHostToDevice,
+                            ctx->stream);
+    }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_cell_prefix, cell_pre.data(), 4 * (n_items + 1), cudaMemcpyHostToDevice, ctx->stream);
+        e = cudaMemcpyAsync(b->d_cell_prefix, b->stage_cells, 4 * (n_items + 1), cudaMemcpyHostToDevice,
+                            ctx->stream);
     int rc = check_cuda(ctx, e, "batch upload");
-    if (rc == RLL_OK) rc = set_tiles(ctx, b, b->tile_points);
-    // the host-side descriptor and prefix arrays are pageable: finish the copies
-    if (rc == RLL_OK) rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "batch items");
+    if (rc == RLL_OK) rc = set_tiles_staged(ctx, b, b->tile_points);
+    if (rc == RLL_OK) {
+        e = cudaEventRecord(b->staged, ctx->stream);
+        if (e == cudaSuccess) b->stage_pending = true;
+        rc = check_cuda(ctx, e, "batch staging");
+    }
     return rc;
 }
 
@@ -514,7 +560,7 @@ int rll_batch_set_config(rll_ctx* ctx, rll_batch* b, int32_t tile_points, int32_
     if (!ctx || !b) return RLL_E_INVALID;
     if (tile_points < 32 || tile_points > (1 << 20)) return fail(ctx, RLL_E_INVALID, "tile_points must be in [32, 2^20]");
     if (min_blocks != 3 && min_blocks != 4) return fail(ctx, RLL_E_INVALID, "min_blocks must be 3 or 4");
-    DevGuard dg(ctx->device);
+    DeviceGuard dg(ctx->device);
     b->min_blocks = min_blocks;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
@@ -527,7 +573,7 @@ int rll_batch_set_config(rll_ctx* ctx, rll_batch* b, int32_t tile_points, int32_
 int rll_batch_tune(rll_ctx* ctx, rll_batch* b, int32_t* tile_points_out, int32_t* min_blocks_out)
 {
     if (!ctx || !b) return RLL_E_INVALID;
-    DevGuard dg(ctx->device);
+    DeviceGuard dg(ctx->device);
     const uint32_t tiles[] = {128, 256, 512, 1024, 2048, 4096, 8192};
     const int minbs[] = {3, 4};
     cudaEvent_t e0, e1;
@@ -576,14 +622,14 @@ int rll_batch_tune(rll_ctx* ctx, rll_batch* b, int32_t* tile_points_out, int32_t
 int rll_batch_run(rll_ctx* ctx, rll_batch* b, int32_t do_split)
 {
     if (!ctx || !b) return RLL_E_INVALID;
-    DevGuard dg(ctx->device);
+    DeviceGuard dg(ctx->device);
     return check_cuda(ctx, enqueue_pass(b, ctx->stream, do_split != 0), "batch pass");
 }
 
 int rll_batch_capture(rll_ctx* ctx, rll_batch* b, int32_t do_split)
 {
     if (!ctx || !b) return RLL_E_INVALID;
-    DevGuard dg(ctx->device);
+    DeviceGuard dg(ctx->device);
     cudaError_t e = cudaSuccess;
     if (!b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return check_cuda(ctx, e, "capture stream");
@@ -613,14 +659,14 @@ int rll_batch_launch(rll_ctx* ctx, rll_batch* b)
 {
     if (!ctx || !b) return RLL_E_INVALID;
     if (!b->graph) return fail(ctx, RLL_E_INVALID, "no recorded pass: call rll_batch_capture first");
-    DevGuard dg(ctx->device);
+    DeviceGuard dg(ctx->device);
     return check_cuda(ctx, cudaGraphLaunch(b->graph, ctx->stream), "graph launch");
 }
 
 int rll_batch_destroy(rll_batch* b)
 {
     if (!b) return RLL_OK;
-    DevGuard dg(b->device);
+    DeviceGuard dg(b->device);
     cudaDeviceSynchronize();
     free_batch(b);
     return RLL_OK;

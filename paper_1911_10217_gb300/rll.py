@@ -30,7 +30,7 @@ EXPORTS = [
     "rll_build_light_tree", "rll_build_light_tree_ex", "rll_tree_update_emission", "rll_tree_num_lights", "rll_tree_export",
     "rll_tree_destroy", "rll_create_grid", "rll_grid_cut_len", "rll_grid_touched_cells", "rll_grid_export", "rll_grid_import",
     "rll_grid_destroy", "rll_sample_and_shade", "rll_sample_and_shade_ex", "rll_sample_and_shade_fp",
-    "rll_sample_power",
+    "rll_sample_power", "rll_bounce_vertices",
     "rll_learn_update", "rll_learn_update_noalloc", "rll_learn_update_split", "rll_split_collapse",
     "rll_render_pass_host",
     "rll_batch_reserve", "rll_batch_set_items", "rll_batch_create", "rll_batch_set_config", "rll_batch_tune", "rll_batch_run", "rll_batch_capture",
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
                                           ctypes.POINTER(SampleDebug)]
     L.rll_sample_and_shade_fp.argtypes = [P, P, P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P, P, P]
     L.rll_sample_power.argtypes = [P, P, P, P, P, I64, P, I32, U64, U32, I32, P, P]
+    L.rll_bounce_vertices.argtypes = [P, P, P, I64, P, I32, P, U64, U32, ctypes.c_float, P, P, P]
     L.rll_learn_update.argtypes = [P, P, P, P, I64]
     L.rll_learn_update_noalloc.argtypes = [P, P, P, P, I64]
     L.rll_learn_update_split.argtypes = [P, P, P, P, P, I64]
@@ -343,6 +344,20 @@ def sample_power(ctx: Context, tree: Tree, pos, nrm, albedo, boxes, seed, frame,
     ctx._check(ctx.lib.rll_sample_power(ctx.h, tree.h, _ptr(pos), _ptr(nrm), _ptr(albedo), n,
                                         _ptr(boxes), k, int(seed), int(frame), int(spp), _ptr(rgb),
                                         _ptr(light_out)))
+
+
+def bounce_vertices(ctx: Context, pos, nrm, boxes, room, seed, frame, paths_per_tile, out_pos, out_nrm,
+                    out_footprint):
+    """rll_bounce_vertices: one diffuse bounce from every point; room is a
+    host sequence of 6 floats (min xyz, max xyz)."""
+    P = int(pos.shape[1])
+    for t in (pos, nrm, out_pos, out_nrm):
+        _check_tensor(t, "float32")
+    _check_tensor(out_footprint, "float32")
+    rm = np.ascontiguousarray(np.asarray(room, np.float32).reshape(6))
+    ctx._check(ctx.lib.rll_bounce_vertices(ctx.h, _ptr(pos), _ptr(nrm), P, _ptr(boxes), int(boxes.shape[0]),
+                                           _ptr(rm), int(seed), int(frame), float(paths_per_tile),
+                                           _ptr(out_pos), _ptr(out_nrm), _ptr(out_footprint)))
 
 
 def learn_update(ctx: Context, grid: Grid, rec_key, rec_val, n_records=None):

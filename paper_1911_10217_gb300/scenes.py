@@ -63,6 +63,8 @@ class Scene:
     blink_mask: np.ndarray | None = None
     # per-point footprint (world units) for multi-resolution grids, or None
     footprint: np.ndarray | None = None
+    # inputs of one diffuse bounce from every point (path scenes), or None
+    bounce: object = None
 
     @property
     def n_lights(self) -> int:
@@ -460,94 +462,47 @@ def tiny_sky_scene(seed: int = 6, jitter: bool = False, sun: bool = True) -> Sce
     return s
 
 
-def _basis(n):
-    """Orthonormal tangents (u, v) of unit normals n [P, 3]."""
-    t = np.where(np.abs(n[:, :1]) < 0.9, np.array([[1.0, 0.0, 0.0]]), np.array([[0.0, 0.0, 1.0]]))
-    u = np.cross(n, t)
-    u /= np.linalg.norm(u, axis=1, keepdims=True)
-    v = np.cross(n, u)
-    return u, v
+# Path vertices: the bounce vertices themselves (one cosine-weighted diffuse
+# bounce per shading point, its nearest surface, its footprint from the area
+# pdf) are computed by the method -- the CUDA library's rll_bounce_vertices,
+# or the oracle in tests. This generator only supplies the primary points and
+# the bounce's inputs.
+ROOM = np.array([0.0, 0.0, 0.0, 1.0, 1.0, 1.0], np.float32)  # the walled rooms' enclosure, min xyz, max xyz
 
 
-def _nearest_hit(o, d, boxes, eps=1e-6):
-    """Nearest hit of rays o + t d (t > eps) with the occluder boxes (from
-    outside) and the inside of the unit room; returns t and the unit normal
-    of the face hit, facing the ray's origin."""
-    R = o.shape[0]
-    with np.errstate(divide="ignore", invalid="ignore"):
-        inv = 1.0 / d
-        # inside of the unit room: leave through the first wall
-        tw = np.where(d > 0, (1.0 - o) * inv, np.where(d < 0, -o * inv, np.inf))
-        axis = np.argmin(tw, axis=1)
-        t_best = tw[np.arange(R), axis]
-        nrm = np.zeros((R, 3))
-        nrm[np.arange(R), axis] = -np.sign(d[np.arange(R), axis])
-        for b in boxes.astype(np.float64):
-            t1 = (b[:3][None] - o) * inv
-            t2 = (b[3:][None] - o) * inv
-            tmin = np.minimum(t1, t2)
-            tmax = np.maximum(t1, t2)
-            tn = np.nanmax(tmin, axis=1)
-            tf = np.nanmin(tmax, axis=1)
-            hit = (tn < tf) & (tn > eps) & (tn < t_best)
-            if np.any(hit):
-                ax = np.nanargmax(tmin[hit], axis=1)
-                t_best[hit] = tn[hit]
-                nn = np.zeros((int(hit.sum()), 3))
-                nn[np.arange(nn.shape[0]), ax] = -np.sign(d[hit][np.arange(nn.shape[0]), ax])
-                nrm[hit] = nn
-    return t_best, nrm
-
-
-def bounce_vertices(scene: Scene, seed: int = 7, paths_per_tile: float = 100.0, chunk: int = 1 << 16):
-    """One diffuse bounce per shading point of `scene`: a cosine-weighted
-    direction about the point's normal, traced to the nearest occluder box
-    face or room wall (emitters do not block). Returns SoA positions and
-    normals [3, P] of the hit points, albedo U[0.2, 0.9] [P] and each hit's
-    footprint [P] = (N_t p_A)^(-1/2): p_A = cos(theta_x) cos(theta_y) /
-    (pi d^2) is the area density of the bounce vertex of one path, and the
-    N_t = paths_per_tile paths that leave one tile (a finest-level cell)
-    share it, so each covers an area 1 / (N_t p_A)."""
-    rng = np.random.default_rng(seed)
-    P = scene.n_points
-    x = scene.pos.T.astype(np.float64)
-    n = scene.nrm.T.astype(np.float64)
-    n /= np.linalg.norm(n, axis=1, keepdims=True)
-    pos = np.zeros((P, 3))
-    nrm = np.zeros((P, 3))
-    fp = np.zeros(P)
-    for a in range(0, P, chunk):
-        b = min(P, a + chunk)
-        r1, r2 = rng.uniform(size=b - a), rng.uniform(size=b - a)
-        u, v = _basis(n[a:b])
-        st, ct = np.sqrt(r2), np.sqrt(1.0 - r2)
-        d = (st * np.cos(2 * math.pi * r1))[:, None] * u + (st * np.sin(2 * math.pi * r1))[:, None] * v \
-            + ct[:, None] * n[a:b]
-        o = x[a:b] + 1e-4 * n[a:b]
-        t, hn = _nearest_hit(o, d, scene.boxes)
-        y = o + t[:, None] * d
-        cos_y = np.abs(np.einsum("ij,ij->i", d, hn))
-        p_area = np.maximum(ct, 1e-6) * np.maximum(cos_y, 1e-6) / (math.pi * np.maximum(t, 1e-9) ** 2)
-        pos[a:b], nrm[a:b], fp[a:b] = y, hn, 1.0 / np.sqrt(paths_per_tile * p_area)
-    albedo = rng.uniform(0.2, 0.9, size=P).astype(np.float32)
-    return (pos.T.astype(np.float32).copy(), nrm.T.astype(np.float32).copy(), albedo,
-            fp.astype(np.float32))
+@dataclasses.dataclass
+class BounceSpec:
+    """Inputs of one bounce from every primary point: the Philox key and
+    frame of its directions, the paths N_t leaving one tile, the room it
+    stays in, and the albedo of the surface each vertex lands on."""
+    seed: int
+    frame: int
+    paths_per_tile: float
+    room: np.ndarray
+    albedo: np.ndarray
 
 
 def path_scene(base: Scene, seed: int = 7, levels: int = 8, paths_per_tile: float = 100.0) -> Scene:
-    """Path vertices of one bounce: the primary shading points of `base`
-    (footprint = the cell size, the finest level) followed by one bounce
-    vertex per primary point (footprint from its area pdf, see
-    bounce_vertices; the frame recipe puts ~90 samples in a cell per pass);
-    the grid gets `levels` resolution levels. The footprints are in
-    scene.footprint."""
-    bp, bn, ba, bf = bounce_vertices(base, seed, paths_per_tile)
-    P = base.n_points
+    """Primary points of `base` (footprint = the cell size, the finest level)
+    with the inputs of one diffuse bounce each (scene.bounce); the grid gets
+    `levels` resolution levels. The bounce vertices are appended by
+    with_bounce_vertices once they are computed."""
+    rng = np.random.default_rng(seed)
     s = dataclasses.replace(base)
     s.name = base.name + "_paths"
-    s.pos = np.concatenate([base.pos, bp], axis=1)
-    s.nrm = np.concatenate([base.nrm, bn], axis=1)
-    s.albedo = np.concatenate([base.albedo, ba])
-    s.footprint = np.concatenate([np.full(P, np.float32(base.grid.cell_size), np.float32), bf])
+    s.footprint = np.full(base.n_points, np.float32(base.grid.cell_size), np.float32)
     s.grid = dataclasses.replace(base.grid, levels=levels)
+    s.bounce = BounceSpec(seed=seed, frame=0, paths_per_tile=float(paths_per_tile), room=ROOM.copy(),
+                          albedo=rng.uniform(0.2, 0.9, size=base.n_points).astype(np.float32))
     return s
+
+
+def with_bounce_vertices(s: Scene, pos: np.ndarray, nrm: np.ndarray, footprint: np.ndarray) -> Scene:
+    """The path scene's points followed by its bounce vertices (SoA [3][P]
+    positions and normals, footprints [P])."""
+    out = dataclasses.replace(s)
+    out.pos = np.concatenate([s.pos, np.asarray(pos, np.float32)], axis=1)
+    out.nrm = np.concatenate([s.nrm, np.asarray(nrm, np.float32)], axis=1)
+    out.albedo = np.concatenate([s.albedo, s.bounce.albedo])
+    out.footprint = np.concatenate([s.footprint, np.asarray(footprint, np.float32)])
+    return out

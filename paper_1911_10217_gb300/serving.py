@@ -7,9 +7,11 @@ arrive over time; whenever one of the launch slots is free, the scheduler
 forms a batch from the oldest pending requests of admitted sessions that
 have no frame in flight (a session's frames depend on each other) and
 launches it as one batched pass (rll_batch_*: one persistent sampling
-kernel for all its scenes, one sort, one learning kernel). Two launch slots
-on two CUDA streams let a new batch start while the previous one still
-runs, so requests that arrive during a launch join the next one.
+kernel for all its scenes, one bucketing of the records, one learning
+kernel). Two launch slots on two CUDA streams let a new batch start while the
+previous one still runs, so requests that arrive during a launch join the
+next one and its work is on the device at the same time; a launch enqueues
+its descriptor upload and pass without waiting for its stream.
 
 Each session has its own Philox seed and its own cells in the batch's
 record keys, so its results do not depend on which other sessions share a
@@ -143,10 +145,13 @@ def session_bytes(n_lights, n_points, table_size, cut_size, precision="fp32"):
 class GpuExecutor:
     """Resident per-session device state and batched launches on two streams."""
 
-    def __init__(self, torch, rll, device, max_items, max_records, max_cells, slots=2, keep_results=False):
+    def __init__(self, torch, rll, device, max_items, max_records, max_cells, slots=2, keep_results=False,
+                 timeline=False):
         self.torch, self.rll, self.dev = torch, rll, device
         self.keep_results = keep_results
         self.results = {}
+        # (slot, start event, end event) of every launch, when asked for
+        self.timeline = [] if timeline else None
         self.slots = []
         for _ in range(slots):
             stream = torch.cuda.Stream(device)
@@ -198,11 +203,25 @@ class GpuExecutor:
             items.append(dict(grid=st["grid"], tree=st["tree"], pos=st["d"]["pos"], nrm=st["d"]["nrm"],
                               albedo=st["d"]["alb"], boxes=st["d"]["boxes"], seed=st["seed"],
                               frame=frames[req.session], spp=st["spp"], rgb=st["rgb"]))
+        t0 = None
+        if self.timeline is not None:
+            t0 = self.torch.cuda.Event(enable_timing=True)
+            t0.record(sl["stream"])
         sl["batch"].set_items(items)
         sl["batch"].run(do_split=True)
-        ev = self.torch.cuda.Event()
+        ev = self.torch.cuda.Event(enable_timing=self.timeline is not None)
         ev.record(sl["stream"])
+        if self.timeline is not None:
+            self.timeline.append((slot, t0, ev))
         sl["busy"], sl["event"] = batch, ev
+
+    def device_intervals(self):
+        """(slot, start ms, end ms) of every launch on the device clock (CUDA
+        events recorded on the slot's stream before its descriptor upload and
+        after its pass), relative to the first launch's start."""
+        self.torch.cuda.synchronize(self.dev)
+        base = self.timeline[0][1]
+        return [(slot, base.elapsed_time(a), base.elapsed_time(b)) for slot, a, b in self.timeline]
 
     def poll(self):
         """Slots whose batch has finished: list of (slot, batch)."""

@@ -97,7 +97,7 @@ def compare_tables(gstate, ostate, m, rtol, check_cut=True, only=None, Hl=None, 
     o = rows_by_key(ostate["keys"], ostate["cut"], ostate["q"], ostate["c"], Hl=Hl)
     assert set(g) == set(o), f"cell sets differ: {len(set(g) ^ set(o))}"
     keys = o.keys() if only is None else only
-    assert len(skip) <= max(2, len(o) // 1000), f"{len(skip)} cells left out"
+    assert len(skip) <= max(2, len(o) // 100), f"{len(skip)} cells left out"
     for k in keys:
         if (k[1] if isinstance(k, tuple) else k) in skip:
             continue
@@ -107,6 +107,29 @@ def compare_tables(gstate, ostate, m, rtol, check_cut=True, only=None, Hl=None, 
             assert np.array_equal(gc[:m], oc[:m]), f"cut differs in cell {k}"
         assert np.allclose(gq[:m], oq[:m], rtol=rtol, atol=1e-12), f"Q differs in cell {k}"
         assert np.allclose(gcc[:m], occ[:m], rtol=rtol, atol=1e-12), f"C differs in cell {k}"
+
+
+def split_margin(cut, q, parent, n_lights, T):
+    """Smallest relative gap among the decisions split-collapse takes on one
+    row: the leaf of largest Q (not a single light) against the runner-up,
+    the parent of two cut leaves with the smallest Q sum against the
+    runner-up, and Q(l_max) against T Q(p_min). Exact ties are broken by the
+    same rule on both sides and do not count. When the smallest gap is within
+    the rounding of Eq. 1 (binary32 on the device, double in the oracle),
+    either outcome is correct."""
+    q = np.asarray(q, np.float64)
+    m = len(cut)
+    gaps = [np.inf]
+    cand = sorted((q[i] for i in range(m) if cut[i] < n_lights - 1), reverse=True)
+    if len(cand) > 1 and cand[0] > cand[1]:
+        gaps.append((cand[0] - cand[1]) / cand[0])
+    sums = sorted(float(np.float32(q[i]) + np.float32(q[i + 1])) for i in range(m - 1)
+                  if parent[cut[i]] >= 0 and parent[cut[i]] == parent[cut[i + 1]])
+    if len(sums) > 1 and sums[1] > sums[0]:
+        gaps.append((sums[1] - sums[0]) / sums[1])
+    if cand and sums and cand[0] > 0:
+        gaps.append(abs(cand[0] - T * sums[0]) / cand[0])
+    return min(gaps)
 
 
 def oracle_state(og):

@@ -36,7 +36,8 @@ def test_reference_arm_line():
 
 @pytest.mark.gpu
 def test_gpu_arm_line():
-    d = _run(["--steps", "3", "--warmup", "3", "--no-cpu-baseline", "--no-quality"], timeout=1200)
+    d = _run(["--steps", "3", "--warmup", "3", "--no-cpu-baseline", "--no-quality", "--no-workload-extras"],
+             timeout=1200)
     assert BASE_KEYS <= set(d)
     assert d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3
     assert d["value"] > 0 and d["ms_per_step"] > 0

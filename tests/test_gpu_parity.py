@@ -11,7 +11,7 @@ import pytest
 from paper_1911_10217_gb300 import scenes
 
 from .gpu_common import (RTOL, clone_oracle_grid, compare_samples, compare_tables, device_scene,
-                         oracle_state, params_for, run_sample, to_host)
+                         oracle_state, params_for, rows_by_key, run_sample, split_margin, to_host)
 
 pytestmark = pytest.mark.gpu
 
@@ -194,7 +194,11 @@ def test_frame_scale_learned_state_fused_step(env, precision):
     imported, and pass 3 is compared sample by sample over the whole frame;
     then the device's fused rll_learn_update_split on its own records is
     compared with the oracle's learn + split-collapse on every cell: cuts
-    exact, Q and C within the table tolerance."""
+    exact, Q and C within the table tolerance. The one allowance: a cell whose
+    split decision was within the rounding of Eq. 1 in the oracle's own state
+    (a near-tie of the largest leaf, the smallest twin-leaf parent or the
+    threshold) may take the other branch; such cells (at most 0.5 %) are
+    checked to be near-ties and left out."""
     O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
     s = scenes.frame_scene()
     ot, dt, d = _trees(env, s)
@@ -212,10 +216,22 @@ def test_frame_scale_learned_state_fused_step(env, precision):
     rll.learn_update_split(ctx, dg, dt, torch.from_numpy(g["key"]).to(env["dev"]),
                            torch.from_numpy(g["val"]).to(env["dev"]))
     touched = og.learn(o["slot"], o["s"], o["reward"])
+    m = og.m
+    pre = {int(og.keys[sl]): (og.cut[sl, :m].copy(), og.Q[sl, :m].copy()) for sl in np.nonzero(touched)[0]}
     changed = og.split_collapse(touched)
     assert dg.touched_cells() == int(touched.sum())
     assert changed > 100  # the cuts do move at this point of learning
-    compare_tables(dg.export(), oracle_state(og), og.m, RTOL[precision], check_cut=True, skip=skip)
+    # a split decision may go the other way only where the oracle's own decision was within the
+    # rounding of Eq. 1 (device binary32 against oracle double, then the table format)
+    st = dg.export()
+    g_rows = rows_by_key(st["keys"], st["cut"])
+    o_rows = rows_by_key(og.keys, og.cut)
+    flipped = {k for k in o_rows if k in g_rows and not np.array_equal(g_rows[k][0][:m], o_rows[k][0][:m])}
+    tol = {"fp32": 1e-5, "bf16": 2 * 2.0 ** -8}[precision]
+    for k in flipped:
+        assert k in pre and split_margin(*pre[k], ot.parent, ot.n, s.grid.threshold) <= tol, k
+    assert len(flipped) <= max(2, len(pre) // 200), len(flipped)
+    compare_tables(st, oracle_state(og), m, RTOL[precision], check_cut=True, skip=skip | flipped)
     assert ctx.sync_status() == 0
 
 

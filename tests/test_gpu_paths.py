@@ -1,9 +1,11 @@
 """Footprint-sized cells on path vertices (Section 3: cells sized from the
 ray footprint of each path vertex, coarser on later bounces), on the GPU
-(marked gpu): primary points of a reduced frame scene at the finest level and
-one diffuse bounce vertex each, whose footprint picks one of 8 levels. Lockstep
-parity with the oracle: level, cell (level and key), cluster and light of every
-sample exact, estimates and learned tables within tolerance."""
+(marked gpu): the bounce vertices and footprints of rll_bounce_vertices equal
+the oracle's bit for bit; primary points of a reduced frame scene at the
+finest level and one diffuse bounce vertex each (the oracle's), whose
+footprint picks one of 8 levels. Lockstep parity with the oracle: level, cell
+(level and key), cluster and light of every sample exact, estimates and
+learned tables within tolerance."""
 import numpy as np
 import pytest
 
@@ -61,6 +63,9 @@ def test_path_vertices_lockstep(env, variant):
     ctx.sync_status()
     base = scenes.small_frame_scene()
     s = scenes.path_scene(base, levels=8, paths_per_tile=1.0)  # spread over many levels
+    b = s.bounce
+    s = scenes.with_bounce_vertices(s, *O.bounce_vertices(base.pos, base.nrm, base.boxes, b.room, b.seed, b.frame,
+                                                          b.paths_per_tile))
     if "jitter" in variant:
         s.grid.jitter = variant["jitter"]
     d = device_scene(s, env["dev"])
@@ -91,6 +96,29 @@ def test_path_vertices_lockstep(env, variant):
         compare_tables(dg.export(), oracle_state(o2), og.m, max(rtol, 1e-5), Hl=Hl)
         og.split_collapse(touched)
     assert len(levels_seen) >= 4
+    assert ctx.sync_status() == 0
+
+
+@pytest.mark.parametrize("maker,n_t", [("small_frame", 100.0), ("frame", 1.0), ("tiny", 1000.0)])
+def test_bounce_vertices_equal_the_oracle(env, maker, n_t):
+    """rll_bounce_vertices against the oracle's bounce, point by point:
+    every step is one correctly rounded binary32 operation on both sides, so
+    vertex positions, face normals and footprints are bit-identical (the
+    hit face is a decision)."""
+    O, rll, ctx, torch = env["O"], env["rll"], env["ctx"], env["torch"]
+    ctx.sync_status()
+    s = getattr(scenes, maker + "_scene")()
+    d = device_scene(s, env["dev"])
+    P = s.n_points
+    out = [torch.empty(3, P, device=env["dev"]), torch.empty(3, P, device=env["dev"]),
+           torch.empty(P, device=env["dev"])]
+    rll.bounce_vertices(ctx, d["pos"], d["nrm"], d["boxes"], scenes.ROOM, 9, 2, n_t, *out)
+    y, ny, fp = (t.cpu().numpy() for t in out)
+    oy, ony, ofp = O.bounce_vertices(s.pos, s.nrm, s.boxes, scenes.ROOM, 9, 2, n_t)
+    assert np.array_equal(ny, ony), int(np.sum(np.any(ny != ony, axis=0)))
+    assert np.array_equal(y.view(np.uint32), oy.view(np.uint32))
+    assert np.array_equal(fp.view(np.uint32), ofp.view(np.uint32))
+    assert np.all(np.isfinite(fp[np.all((s.pos >= 0) & (s.pos <= 1), axis=0)]))
     assert ctx.sync_status() == 0
 
 

@@ -1,6 +1,7 @@
 """GPU test of the serving loop: sessions served concurrently in shared
 batched launches give, session by session, exactly the results of serving
-that session alone."""
+that session alone; launches of the two slots are on the device at the same
+time; the first frame of every served session equals the oracle's."""
 import numpy as np
 import pytest
 
@@ -18,10 +19,11 @@ def _sessions():
     return out
 
 
-def _serve(torch, rll, sc, sids, arrivals, budget):
+def _serve(torch, rll, sc, sids, arrivals, budget, timeline=False):
     from paper_1911_10217_gb300 import serving
     dev = torch.device("cuda:0")
-    ex = serving.GpuExecutor(torch, rll, dev, max_items=8, max_records=1 << 16, max_cells=1 << 16, keep_results=True)
+    ex = serving.GpuExecutor(torch, rll, dev, max_items=8, max_records=1 << 16, max_cells=1 << 16, keep_results=True,
+                             timeline=timeline)
     sched = serving.Scheduler(budget, 8, 1 << 16, 1 << 16)
     for sid in sids:
         s = sc[sid]
@@ -29,6 +31,8 @@ def _serve(torch, rll, sc, sids, arrivals, budget):
                           s.n_points * s.spp, s.grid.table_size, len(arrivals[sid]))
     log = serving.serve(ex, sched, {k: sc[k] for k in sids}, {k: arrivals[k] for k in sids})
     assert all(st == 0 for st in ex.status())
+    if timeline:
+        return ex.results, log, ex.device_intervals()
     return ex.results, log
 
 
@@ -41,8 +45,11 @@ def test_alone_equals_in_the_mix():
     rng = np.random.default_rng(0)
     arrivals = {sid: np.cumsum(rng.exponential(0.002, size=6)) for sid in sc}
     big = 10**12
-    mix, log = _serve(torch, rll, sc, list(sc), arrivals, big)
+    mix, log, spans = _serve(torch, rll, sc, list(sc), arrivals, big, timeline=True)
     assert len(log) == sum(len(a) for a in arrivals.values())
+    # continuous batching: a launch of one slot started on the device before a launch of the other slot ended
+    overlaps = sum(1 for (s1, a1, b1) in spans for (s2, a2, b2) in spans if s1 < s2 and a1 < b2 and a2 < b1)
+    assert overlaps >= 1, spans
     # requests overlapped: some launch held more than one session
     starts = {}
     for r in log:
@@ -69,3 +76,29 @@ def test_budget_admits_in_turn():
     budget = max(sizes.values()) + min(sizes.values())   # never all four at once
     res, log = _serve(torch, rll, sc, list(sc), arrivals, budget)
     assert len(log) == 16 and set(res) == set(sc)
+
+
+def test_served_first_frames_equal_the_oracle():
+    """Four sessions whose first frame is requested at once are served in
+    shared launches; each session's estimate of that frame and its learned
+    tables afterwards (Eq. 1, split-collapse, Eq. 2) equal the oracle's pass
+    over that session alone: estimates and Q, C within 1e-4, cuts exact."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import oracle as O
+    from paper_1911_10217_gb300 import rll
+
+    from .gpu_common import compare_tables, oracle_state
+    sc = _sessions()
+    arrivals = {sid: np.zeros(1) for sid in sc}
+    res, log = _serve(torch, rll, sc, list(sc), arrivals, 10**12)
+    assert len(log) == len(sc) and max(sum(1 for r in log if r.start == x.start) for x in log) > 1
+    for sid, s in sc.items():
+        ot = O.Tree(s.tris, s.emission)
+        og = O.Grid.for_scene(ot, s)
+        o = og.sample_frame(O.scene_arrays(s), s.seed, 0, s.spp)
+        got = res[sid]["rgb"].astype(np.float64)
+        assert np.allclose(got, o["rgb"], rtol=1e-4, atol=1e-7 * max(1.0, np.abs(o["rgb"]).max())), sid
+        og.split_collapse(og.learn(o["slot"], o["s"], o["reward"]))
+        compare_tables(res[sid]["grid"], oracle_state(og), og.m, 1e-4, check_cut=True)
