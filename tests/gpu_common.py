@@ -113,19 +113,19 @@ def split_margin(cut, q, parent, n_lights, T):
     """Smallest relative gap among the decisions split-collapse takes on one
     row: the leaf of largest Q (not a single light) against the runner-up,
     the parent of two cut leaves with the smallest Q sum against the
-    runner-up, and Q(l_max) against T Q(p_min). Exact ties are broken by the
-    same rule on both sides and do not count. When the smallest gap is within
-    the rounding of Eq. 1 (binary32 on the device, double in the oracle),
-    either outcome is correct."""
+    runner-up, and Q(l_max) against T Q(p_min). An exact tie is a gap of 0:
+    values equal in the oracle may differ by an ulp on the device. When the
+    smallest gap is within the rounding of Eq. 1 (binary32 on the device,
+    double in the oracle), either outcome is correct."""
     q = np.asarray(q, np.float64)
     m = len(cut)
     gaps = [np.inf]
     cand = sorted((q[i] for i in range(m) if cut[i] < n_lights - 1), reverse=True)
-    if len(cand) > 1 and cand[0] > cand[1]:
+    if len(cand) > 1 and cand[0] > 0:
         gaps.append((cand[0] - cand[1]) / cand[0])
     sums = sorted(float(np.float32(q[i]) + np.float32(q[i + 1])) for i in range(m - 1)
                   if parent[cut[i]] >= 0 and parent[cut[i]] == parent[cut[i + 1]])
-    if len(sums) > 1 and sums[1] > sums[0]:
+    if len(sums) > 1 and sums[1] > 0:
         gaps.append((sums[1] - sums[0]) / sums[1])
     if cand and sums and cand[0] > 0:
         gaps.append(abs(cand[0] - T * sums[0]) / cand[0])
