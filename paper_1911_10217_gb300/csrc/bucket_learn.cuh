@@ -304,12 +304,26 @@ __device__ void learn_cell_grouped(Team team, CellOrder<CAP, CLUS>& o, const uin
     for (uint32_t s = t; s < M; s += T) o.start[s] = 0u;
     if (w0) load_q_row<P>(qrow, m, o.q);
     team.sync();
-    for (uint32_t k = t; k < nr; k += T) {
-        const uint32_t s = bs[k];
-        o.a_sid[k] = bsid[k];
-        o.a_val[k] = bval[k];
-        o.a_s[k] = (uint8_t)s;
-        atomicAdd(&o.start[s], 1u);
+    // the bucket, four records a thread in flight at once
+    for (uint32_t k0 = t; k0 < nr; k0 += 4 * T) {
+        uint32_t rs[4], rsid[4], rval[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t k = k0 + u * T;
+            rs[u] = k < nr ? bs[k] : 0u;
+            rsid[u] = k < nr ? bsid[k] : 0u;
+            rval[u] = k < nr ? bval[k] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t k = k0 + u * T;
+            if (k < nr) {
+                o.a_sid[k] = rsid[u];
+                o.a_val[k] = rval[u];
+                o.a_s[k] = (uint8_t)rs[u];
+                atomicAdd(&o.start[rs[u]], 1u);
+            }
+        }
     }
     team.sync();
     if (w0) {  // cluster starts: exclusive scan over M bins, ipl consecutive bins a lane

@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include "rll_device.cuh"
 
 namespace rll {
@@ -59,16 +61,40 @@ __device__ void warp_rebuild_cdf(const float* q, int m, float eps, typename Stor
         const float total = c[m - 1];
         for (int s = lane; s < m; s += 32) bits[s] = Store<P>::bits(Store<P>::store(c[s] / total));
         __syncwarp();
-        if (lane == 0) {
-            const uint16_t one = Store<P>::bits(Store<P>::store(1.0f));
-            bits[m - 1] = one;
-            uint16_t prev = 0;
-            for (int s = 0; s < m - 1; ++s) {
-                if (bits[s] <= prev) bits[s] = (uint16_t)(prev + 1);
-                prev = bits[s];
-            }
-            for (int s = m - 2; s >= 0; --s)
-                if (bits[s] >= bits[s + 1]) bits[s] = (uint16_t)(bits[s + 1] - 1);
+        // Strictly increasing bit patterns (positive values order as their bits), last = 1.0:
+        // forward, b[s] = max(b[s], b[s-1] + 1) for s < m - 1 (b[-1] = 0); then b[m-1] = one;
+        // backward, b[s] = min(b[s], b[s+1] - 1) for s = m - 2 .. 0. Both recurrences are
+        // scans: b'[s] - s is the running maximum of b[t] - t (at least 1), and b''[s] - s the
+        // running minimum of b'[t] - t from the top, so each lane scans its `ipl` entries and
+        // the lanes combine by shuffles. The patterns stay within 1 .. one (m <= 256), so the
+        // 16-bit values never wrap and the result equals the sequential loops.
+        const int one = Store<P>::bits(Store<P>::store(1.0f));
+        int mx = INT_MIN;
+        for (int s = b; s < e && s < m - 1; ++s) mx = max(mx, (int)bits[s] - s);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, mx, o);
+            if (lane >= o) mx = max(mx, y);
+        }
+        int up = __shfl_up_sync(0xffffffffu, mx, 1);
+        up = lane == 0 ? 1 : max(up, 1);
+        for (int s = b; s < e && s < m - 1; ++s) {
+            up = max(up, (int)bits[s] - s);
+            bits[s] = (uint16_t)(s + up);
+        }
+        if (b <= m - 1 && m - 1 < e) bits[m - 1] = (uint16_t)one;
+        int mn = INT_MAX;
+        for (int s = e - 1; s >= b; --s) mn = min(mn, (int)bits[s] - s);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_down_sync(0xffffffffu, mn, o);
+            if (lane + o < 32) mn = min(mn, y);
+        }
+        int down = __shfl_down_sync(0xffffffffu, mn, 1);
+        if (lane == 31) down = INT_MAX;
+        for (int s = e - 1; s >= b; --s) {
+            down = min(down, (int)bits[s] - s);
+            bits[s] = (uint16_t)(s + down);
         }
         __syncwarp();
         for (int s = lane; s < m; s += 32) out[s] = Store<P>::from_bits(bits[s]);
@@ -276,38 +302,36 @@ __device__ uint32_t split_collapse_steps(uint32_t* cs, float* q, float* c, uint3
         const bool apply = hi.i != 0xFFFFFFFFu && lo.i != 0xFFFFFFFFu && hi.i != lo.i && hi.i != lo.i + 1 &&
                            hi.v > fmul(T, lo.v);
         if (!apply) break;
-        // one lane emits the new row into the scratch rows nc / c
-        if (lane == 0) {
-            float* nq = c;
-            uint32_t k = 0;
-            for (uint32_t i = 0; i < m; ++i) {
-                if (i == hi.i) {
-                    const uint32_t node = cs[i];
-                    const uint32_t a = (uint32_t)left[node], cc = (uint32_t)right[node];
-                    const float pa = nodes[a].phi, pc = nodes[cc].phi;
-                    const float sum = fadd(pa, pc);
-                    const float fa = sum > 0.0f ? fdiv(pa, sum) : 0.5f;
-                    nc[k] = a;
-                    nq[k] = Store<P>::load(Store<P>::store(fmul(q[i], fa)));
-                    ++k;
-                    nc[k] = cc;
-                    nq[k] = Store<P>::load(Store<P>::store(fmul(q[i], fsub(1.0f, fa))));
-                    ++k;
-                } else if (i == lo.i) {
-                    nc[k] = (uint32_t)parent[cs[i]];
-                    nq[k] = Store<P>::load(Store<P>::store(fadd(q[i], q[i + 1])));
-                    ++k;
-                    ++i;
-                } else {
-                    nc[k] = cs[i];
-                    nq[k] = q[i];
-                    ++k;
-                }
+        // the new row into the scratch rows nc / c, every lane placing its own entries: entry i
+        // moves to i + [i > hi] - [i > lo + 1] (one more before it after the split, one fewer
+        // after the merge); hi becomes its two children, lo and lo + 1 their parent
+        const uint32_t H = hi.i, L = lo.i;
+        const uint32_t node = cs[H];
+        const uint32_t a = (uint32_t)left[node], cc = (uint32_t)right[node];
+        const float pa = nodes[a].phi, pc = nodes[cc].phi;
+        const float sum = fadd(pa, pc);
+        const float fa = sum > 0.0f ? fdiv(pa, sum) : 0.5f;
+        float* nq = c;
+        for (uint32_t i = lane; i < m; i += 32) {
+            if (i == L + 1) continue;
+            const uint32_t k = i + (i > H ? 1u : 0u) - (i > L + 1 ? 1u : 0u);
+            if (i == H) {
+                nc[k] = a;
+                nq[k] = Store<P>::load(Store<P>::store(fmul(q[i], fa)));
+                nc[k + 1] = cc;
+                nq[k + 1] = Store<P>::load(Store<P>::store(fmul(q[i], fsub(1.0f, fa))));
+            } else if (i == L) {
+                nc[k] = (uint32_t)parent[cs[i]];
+                nq[k] = Store<P>::load(Store<P>::store(fadd(q[i], q[i + 1])));
+            } else {
+                nc[k] = cs[i];
+                nq[k] = q[i];
             }
-            for (uint32_t i = 0; i < m; ++i) {
-                cs[i] = nc[i];
-                q[i] = nq[i];
-            }
+        }
+        __syncwarp();
+        for (uint32_t i = lane; i < m; i += 32) {
+            cs[i] = nc[i];
+            q[i] = nq[i];
         }
         __syncwarp();
     }
