@@ -25,12 +25,15 @@ struct RowRef {
 };
 
 // ---------------------------------------------------------------- bucketed learning
-// counters ctr[4]: [0] touched cells, [1] bucket space claimed, [2] cells for
-// the sorting block path, [3] cells for the grouping block path; lists[2 *
-// cells]: the grouping list, then the sorting list
+// counters ctr[8]: [0] touched cells, [1] bucket space claimed, [2] cells for
+// the sorting block path, [3] cells for the two-warp path, [4] [5] [7] work
+// counters of the block, warp and two-warp phases, [6] cells for the grouping
+// block path; lists[2 * cells]: the grouping list (two-warp cells from the
+// front, block cells from the back), then the sorting list
 constexpr int kBucketThreads = 256;
 constexpr int kTilesPerWarp = 4;         // 32-record tiles one warp counts / scatters
 constexpr uint32_t kWarpBucket = 240;    // records of a cell one warp orders in shared memory
+constexpr uint32_t kPairBucket = 512;    // records of a cell two warps order together
 constexpr uint32_t kBlockGroup = 1024;   // records of a cell one block orders by grouping and ranking
 constexpr uint32_t kBlockSort = 8192;    // records of a cell one block sorts in shared memory (power of 2)
 constexpr size_t kBigSmem = kBlockSort * (sizeof(unsigned long long) + sizeof(uint32_t));
@@ -82,7 +85,7 @@ k_bucket_count(const uint32_t* __restrict__ rec_key, int64_t n, Dec dec, uint32_
 __global__ void __launch_bounds__(kBucketThreads)
 k_bucket_claim(const uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr, uint32_t* __restrict__ cursor,
                uint32_t* __restrict__ start, uint32_t* __restrict__ len, uint32_t* __restrict__ group_list,
-               uint32_t* __restrict__ sort_list)
+               uint32_t* __restrict__ sort_list, uint32_t cells)
 {
     const uint32_t total = *(volatile uint32_t*)ctr;
     const int lane = threadIdx.x & 31;
@@ -105,17 +108,23 @@ k_bucket_claim(const uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr,
             len[c] = cnt;
             cursor[slot] = base + x - cnt;
         }
-        // cells above one warp's capacity: to the grouping (block) or sorting list
-        const bool to_group = c < total && cnt > kWarpBucket && cnt <= kBlockGroup;
+        // cells above one warp's capacity: to the two-warp list (front of the grouping list),
+        // the block list (its back) or the sorting list
+        const bool to_pair = c < total && cnt > kWarpBucket && cnt <= kPairBucket;
+        const bool to_group = c < total && cnt > kPairBucket && cnt <= kBlockGroup;
         const bool to_sort = c < total && cnt > kBlockGroup;
+        const uint32_t pm = __ballot_sync(0xffffffffu, to_pair);
         const uint32_t gm = __ballot_sync(0xffffffffu, to_group), sm = __ballot_sync(0xffffffffu, to_sort);
-        uint32_t gb = 0, sb = 0;
-        if (lane == 0 && gm) gb = atomicAdd(ctr + 3, (uint32_t)__popc(gm));
+        uint32_t pb = 0, gb = 0, sb = 0;
+        if (lane == 0 && pm) pb = atomicAdd(ctr + 3, (uint32_t)__popc(pm));
+        if (lane == 0 && gm) gb = atomicAdd(ctr + 6, (uint32_t)__popc(gm));
         if (lane == 0 && sm) sb = atomicAdd(ctr + 2, (uint32_t)__popc(sm));
+        pb = __shfl_sync(0xffffffffu, pb, 0);
         gb = __shfl_sync(0xffffffffu, gb, 0);
         sb = __shfl_sync(0xffffffffu, sb, 0);
         const uint32_t below = (1u << lane) - 1u;
-        if (to_group) group_list[gb + __popc(gm & below)] = c;
+        if (to_pair) group_list[pb + __popc(pm & below)] = c;
+        if (to_group) group_list[cells - 1u - (gb + __popc(gm & below))] = c;
         if (to_sort) sort_list[sb + __popc(sm & below)] = c;
     }
 }
@@ -237,6 +246,21 @@ struct BlockTeam {
     __device__ __forceinline__ uint32_t size() const { return blockDim.x; }
     __device__ __forceinline__ bool lead() const { return threadIdx.x < 32; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+// warps 2p and 2p + 1 of a block; named barrier 1 + p (0 is __syncthreads)
+struct PairTeam {
+    __device__ __forceinline__ uint32_t tid() const { return threadIdx.x & 63u; }
+    __device__ __forceinline__ uint32_t size() const { return 64; }
+    __device__ __forceinline__ bool lead() const { return (threadIdx.x & 63u) < 32u; }
+    // immediate barrier ids (a register id would reserve all 16 barriers of the block)
+    __device__ __forceinline__ void sync() const
+    {
+        switch (threadIdx.x >> 6) {
+        case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+        case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+        default: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+        }
+    }
 };
 struct BlockSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
@@ -377,9 +401,9 @@ __device__ void learn_cell_grouped(Team team, CellOrder<CAP, CLUS>& o, const uin
     team.sync();
     if (T == 32) {
         learn_records<P>([&](uint32_t j) { return make_uint2(o.a_s[j], o.a_val[j]); }, nr, m, alpha, o.q);
-    } else {  // a block: warp w composes the groups of clusters w, w + warps, ...
+    } else {  // a block or a pair: warp w of the team composes the groups of clusters w, w + warps, ...
         const uint32_t warps = T >> 5;
-        for (uint32_t s = threadIdx.x >> 5; s < M; s += warps) {
+        for (uint32_t s = t >> 5; s < M; s += warps) {
             const uint32_t lo = o.start[s], hi = o.cur[s];
             if (hi > lo)
                 learn_records<P>([&](uint32_t j) { return make_uint2(o.a_s[lo + j], o.a_val[lo + j]); }, hi - lo,
@@ -417,44 +441,77 @@ __device__ void compose_sorted_block(Cls cls, Val val, uint32_t nr, uint32_t M, 
 }
 
 // 4. Eq. 1 + Eq. 2 of every touched cell of at most kBlockGroup records in
-// one persistent launch. Phase 1: blocks take the cells of the grouping list
-// (more than kWarpBucket records; the ordering of the warp path done by the
-// whole block, warps composing different clusters in parallel). Phase 2:
-// warps take the touched cells one by one and order those of at most
-// kWarpBucket records themselves. Both phases draw from atomic work counters
-// (ctr[4], ctr[5]), so the long cells start first and the blocks that drew
-// one join the second phase late instead of leaving a tail; a warp fetches
-// its next cell index while it works on the current one.
+// one persistent launch. Phase 1: blocks take the cells of the block list
+// (more than kPairBucket records; the ordering of the warp path done by the
+// whole block, warps composing different clusters in parallel). Phase 2: the
+// block's warp pairs take the cells of the two-warp list (kWarpBucket ..
+// kPairBucket records), three cells per block at a time. Phase 3: warps take
+// the touched cells one by one and order those of at most kWarpBucket records
+// themselves. Every phase draws from an atomic work counter (ctr[4], ctr[7],
+// ctr[5]), so the long cells start first and the teams that drew one join the
+// next phase late instead of leaving a tail; a warp fetches its next cell
+// index while it works on the current one. Shared memory: one slab per warp;
+// a pair's arrays lie in its two warps' slabs, the block's across all.
+template <uint32_t CLUS>
+struct LearnSmem {
+    static constexpr size_t kWarp = sizeof(CellOrder<kWarpBucket, CLUS>);
+    static constexpr size_t kPairHalf = (sizeof(CellOrder<kPairBucket, CLUS>) + 1) / 2;
+    static constexpr size_t kSlab = ((kWarp > kPairHalf ? kWarp : kPairHalf) + 15) & ~(size_t)15;
+};
+
 template <int P, int WARPS, int MINB, uint32_t CLUS, class Rows, class Split>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
 k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t* __restrict__ group_list,
                 const uint32_t* __restrict__ touched, const uint32_t* __restrict__ start,
                 const uint32_t* __restrict__ len, uint32_t* __restrict__ cursor, Rows rows, Split sp,
-                uint32_t* __restrict__ status)
+                uint32_t* __restrict__ status, uint32_t cells)
 {
-    __shared__ union {
-        CellOrder<kWarpBucket, CLUS> warp[WARPS];
-        CellOrder<kBlockGroup, CLUS> block;
-    } sm;
-    __shared__ uint32_t s_next;
+    static_assert(WARPS == 6, "three warp pairs, named barriers 1 .. 3");
+    using L = LearnSmem<CLUS>;
+    static_assert(sizeof(CellOrder<kBlockGroup, CLUS>) <= WARPS * L::kSlab, "block arrays exceed the slabs");
+    __shared__ __align__(16) unsigned char smem[WARPS * L::kSlab];
+    __shared__ uint32_t s_next, s_pair[WARPS / 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t n_group = *(volatile const uint32_t*)(ctr + 3);
+    const uint32_t n_group = *(volatile const uint32_t*)(ctr + 6);
+    const uint32_t n_pair = *(volatile const uint32_t*)(ctr + 3);
     const uint32_t total = *(volatile const uint32_t*)ctr;
+    auto& block_order = *reinterpret_cast<CellOrder<kBlockGroup, CLUS>*>(smem);
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(ctr + 4, 1u);
         __syncthreads();
         const uint32_t bi = s_next;
         __syncthreads();
         if (bi >= n_group) break;  // uniform across the block
-        const uint32_t w = group_list[bi];
+        const uint32_t w = group_list[cells - 1u - bi];
         const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
         const RowRef<P> r = rows.row(slot);
-        learn_cell_grouped<P>(BlockTeam{}, sm.block, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M, r.m,
+        learn_cell_grouped<P>(BlockTeam{}, block_order, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M, r.m,
                               r.alpha, r.eps, r.Q, r.C, sp, slot, status);
         if (threadIdx.x == 0) cursor[slot] = 0u;
         __syncthreads();
     }
-    // every warp of the block has left phase 1: the shared memory is per warp now
+    // every warp of the block has left phase 1: pairs of warps, each in its own two slabs
+    {
+        const PairTeam team;
+        const int pair = warp >> 1;
+        auto& pair_order = *reinterpret_cast<CellOrder<kPairBucket, CLUS>*>(smem + 2 * pair * L::kSlab);
+        for (;;) {
+            if (team.tid() == 0) s_pair[pair] = atomicAdd(ctr + 7, 1u);
+            team.sync();
+            const uint32_t pi = s_pair[pair];
+            team.sync();
+            if (pi >= n_pair) break;  // uniform across the pair
+            const uint32_t w = group_list[pi];
+            const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
+            const RowRef<P> r = rows.row(slot);
+            learn_cell_grouped<P>(team, pair_order, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M, r.m,
+                                  r.alpha, r.eps, r.Q, r.C, sp, slot, status);
+            if (team.tid() == 0) cursor[slot] = 0u;
+            team.sync();
+        }
+    }
+    // both warps of the pair have left phase 2: the shared memory is per warp now
+    auto& warp_order = *reinterpret_cast<CellOrder<kWarpBucket, CLUS>*>(smem + warp * L::kSlab);
     uint32_t next = 0;
     if (lane == 0) next = atomicAdd(ctr + 5, 1u);
     next = __shfl_sync(0xffffffffu, next, 0);
@@ -466,7 +523,7 @@ k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t*
         if (nr <= kWarpBucket) {
             const RowRef<P> r = rows.row(slot);
             const uint32_t b0 = start[i];
-            learn_cell_grouped<P>(WarpTeam{}, sm.warp[warp], bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M,
+            learn_cell_grouped<P>(WarpTeam{}, warp_order, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M,
                                   r.m, r.alpha, r.eps, r.Q, r.C, sp, slot, status);
             if (lane == 0) cursor[slot] = 0u;
         }
@@ -559,7 +616,7 @@ inline size_t bucketed_scratch_bytes(int64_t n)
 
 // Enqueues the whole learning step for n >= 1 records (cut sizes up to
 // max_cut). The caller has
-// zeroed ctr[0..5] on the stream and holds `cursor` [cells] at zero (left at
+// zeroed ctr[0..7] on the stream and holds `cursor` [cells] at zero (left at
 // zero again); touched, start, len [cells] and lists [2 * cells] are outputs
 // and scratch. Counters: ctr[0] touched cells, [1] claimed records, [2]
 // sorting list, [3] grouping list, [4] and [5] work counters of
@@ -581,16 +638,17 @@ cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uin
     uint32_t* group_list = lists;
     uint32_t* sort_list = lists + cells;
     k_bucket_count<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, n, dec, cursor, touched, ctr);
-    k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(touched, ctr, cursor, start, len, group_list, sort_list);
+    k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(touched, ctr, cursor, start, len, group_list, sort_list,
+                                                      cells);
     k_bucket_scatter<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, dec, cursor, bucket);
     // cuts of at most 64 leaves: per-cluster arrays of 64 entries (30.5 KB of shared memory per
     // block), 56 registers, 6 blocks per SM; larger cuts: 256 entries (44.4 KB), 5 blocks per SM
     if (max_cut <= 64)
         k_learn_buckets<P, 6, 6, 64, Rows, Split><<<sms * 6, 6 * 32, 0, s>>>(bucket, ctr, group_list, touched, start,
-                                                                           len, cursor, rows, sp, status);
+                                                                           len, cursor, rows, sp, status, cells);
     else
-        k_learn_buckets<P, 6, 5, kMaxCut, Rows, Split><<<sms * 5, 6 * 32, 0, s>>>(bucket, ctr, group_list, touched,
-                                                                                start, len, cursor, rows, sp, status);
+        k_learn_buckets<P, 6, 5, kMaxCut, Rows, Split><<<sms * 5, 6 * 32, 0, s>>>(
+            bucket, ctr, group_list, touched, start, len, cursor, rows, sp, status, cells);
     cudaError_t e = big_smem_attribute<P, Rows, Split>(device);
     if (e != cudaSuccess) return e;
     k_learn_big<P, Rows, Split><<<sms * 2, kBigThreads, kBigSmem, s>>>(bucket, wide, rec_val, ctr, touched, start,

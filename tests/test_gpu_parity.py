@@ -421,6 +421,8 @@ def test_long_run_stays_finite(env):
 
 @pytest.mark.parametrize("maker,kw,spp", [
     ("small_frame", dict(), 2),                       # buckets sorted by one warp
+    ("tiny", dict(cell_size=0.125), 4),                # 256 records per cell: two warps
+    ("tiny", dict(cell_size=0.17, precision="bf16"), 4),  # up to ~480 records per cell: two warps
     ("tiny", dict(cell_size=0.25), 4),                 # ~1K records per cell: one block, shared memory
     ("tiny", dict(cell_size=0.5), 4),                  # ~4K records per cell: one block, in place
     ("tiny", dict(cell_size=0.25, precision="fp16"), 4),
@@ -472,6 +474,8 @@ def test_bucketed_learning_matches_sorted_path(env, maker, kw, spp):
 @pytest.mark.parametrize("maker,kw,spp", [
     ("small_frame", dict(), 2),                          # warp path
     ("small_frame", dict(precision="bf16", split_iterations=4), 2),
+    ("tiny", dict(cell_size=0.125), 4),                   # two-warp path
+    ("tiny", dict(cell_size=0.17, precision="fp16"), 4),  # two-warp path, 16-bit tables
     ("tiny", dict(cell_size=0.25), 4),                    # block grouping path
     ("tiny", dict(cell_size=0.5, precision="fp16"), 4),  # block sort in shared memory / in place
     ("tiny", dict(cell_size=4.0), 8),                     # one cell, in-place global sort
