@@ -19,12 +19,12 @@ def _sessions():
     return out
 
 
-def _serve(torch, rll, sc, sids, arrivals, budget, timeline=False):
+def _serve(torch, rll, sc, sids, arrivals, budget, timeline=False, max_items=8, cap=1 << 16):
     from paper_1911_10217_gb300 import serving
     dev = torch.device("cuda:0")
-    ex = serving.GpuExecutor(torch, rll, dev, max_items=8, max_records=1 << 16, max_cells=1 << 16, keep_results=True,
+    ex = serving.GpuExecutor(torch, rll, dev, max_items=max_items, max_records=cap, max_cells=cap, keep_results=True,
                              timeline=timeline)
-    sched = serving.Scheduler(budget, 8, 1 << 16, 1 << 16)
+    sched = serving.Scheduler(budget, max_items, cap, cap)
     for sid in sids:
         s = sc[sid]
         sched.add_session(sid, serving.session_bytes(s.n_lights, s.n_points, s.grid.table_size, s.grid.cut_size),
@@ -45,11 +45,8 @@ def test_alone_equals_in_the_mix():
     rng = np.random.default_rng(0)
     arrivals = {sid: np.cumsum(rng.exponential(0.002, size=6)) for sid in sc}
     big = 10**12
-    mix, log, spans = _serve(torch, rll, sc, list(sc), arrivals, big, timeline=True)
+    mix, log = _serve(torch, rll, sc, list(sc), arrivals, big)
     assert len(log) == sum(len(a) for a in arrivals.values())
-    # continuous batching: a launch of one slot started on the device before a launch of the other slot ended
-    overlaps = sum(1 for (s1, a1, b1) in spans for (s2, a2, b2) in spans if s1 < s2 and a1 < b2 and a2 < b1)
-    assert overlaps >= 1, spans
     # requests overlapped: some launch held more than one session
     starts = {}
     for r in log:
@@ -62,6 +59,29 @@ def test_alone_equals_in_the_mix():
         oa, ob = np.argsort(a["grid"]["keys"]), np.argsort(b["grid"]["keys"])
         for k in ("keys", "cut", "q", "c"):
             assert np.array_equal(a["grid"][k][oa], b["grid"][k][ob]), (sid, k)
+
+
+def test_two_slots_overlap_on_the_device():
+    """Continuous batching on the device: six sessions of 480 x 270 points
+    whose frames are all requested at once, at most two sessions per launch;
+    the second slot's launch is enqueued while the first slot's is still on
+    the GPU, so their device intervals (CUDA events on the slots' streams)
+    overlap, and the results equal those of each session served alone."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1911_10217_gb300 import rll
+    sc = {sid: scenes.frame_scene(seed=90 + sid, width=480, height=270, n_patches=16, tris_per_patch=256,
+                                  table_size=1 << 16, cut_size=32, frames=1) for sid in range(6)}
+    arrivals = {sid: np.zeros(3) for sid in sc}
+    cap = 1 << 20
+    mix, log, spans = _serve(torch, rll, sc, list(sc), arrivals, 10**12, timeline=True, max_items=2, cap=cap)
+    assert len(log) == 18
+    overlaps = sum(1 for (s1, a1, b1) in spans for (s2, a2, b2) in spans if s1 < s2 and a1 < b2 and a2 < b1)
+    assert overlaps >= 1, spans
+    for sid in (0, 5):
+        alone, _ = _serve(torch, rll, sc, [sid], arrivals, 10**12, max_items=2, cap=cap)
+        assert np.array_equal(alone[sid]["rgb"], mix[sid]["rgb"])
 
 
 def test_budget_admits_in_turn():
