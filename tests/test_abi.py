@@ -47,6 +47,8 @@ def test_null_arguments_are_rejected(lib):
     assert lib.rll_tree_num_lights(None) == 0
     assert lib.rll_grid_cut_len(None) == 0
     assert lib.rll_last_error(None) == b"no context"
+    assert lib.rll_grid_touched_cells(None, None, None) == 1
+    assert lib.rll_bounce_vertices(None, None, None, 0, None, 0, None, 0, 0, 1.0, None, None, None) == 1
     del P
 
 
