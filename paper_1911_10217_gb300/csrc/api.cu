@@ -218,6 +218,7 @@ int rll_ctx_destroy(rll_ctx* ctx)
     cudaFree(ctx->d_status);
     cudaFree(ctx->ws);
     cudaFree(ctx->stage);
+    cudaFree(ctx->box_sorted);
     if (ctx->pipe_ready) {
         cudaStreamSynchronize(ctx->up);
         cudaStreamSynchronize(ctx->down);
@@ -655,11 +656,16 @@ int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, con
             e = cudaMemcpyAsync(dst + k * P + b, src + k * P + b, 4 * (size_t)n, kind, st);
         return e;
     };
-    cudaError_t e = cudaEventRecord(ev_start, s);  // the grid's earlier updates come first
+    // the boxes and their sorted copy first (both compute streams wait for them)
+    cudaError_t e = cudaSuccess;
+    if (n_boxes > 0) e = cudaMemcpyAsync(d_box, boxes, 24 * (size_t)n_boxes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "render_pass_host: boxes");
+    const void* sorted = nullptr;
+    rc = sort_boxes(ctx, d_box, n_boxes, s, &sorted);
+    if (rc != RLL_OK) return rc;
+    e = cudaEventRecord(ev_start, s);  // the grid's earlier updates come first
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->comp2, ev_start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->down, ev_start, 0);
-    if (e == cudaSuccess && n_boxes > 0)
-        e = cudaMemcpyAsync(d_box, boxes, 24 * (size_t)n_boxes, cudaMemcpyHostToDevice, ctx->up);
     for (int k = 0; k < nc && e == cudaSuccess && rc == RLL_OK; ++k) {
         const int64_t b = bnd[k], n = bnd[k + 1] - bnd[k];
         e = planes(d_pos, pos, b, n, cudaMemcpyHostToDevice, ctx->up);
@@ -669,7 +675,7 @@ int rll_render_pass_host(rll_ctx* ctx, rll_grid* grid, const rll_tree* tree, con
         if (e == cudaSuccess) e = cudaStreamWaitEvent(sc[k & 1], ev_up[k], 0);
         if (e != cudaSuccess) break;
         rc = rll::sample_and_shade_range(ctx, grid, tree, d_pos, d_nrm, d_alb, nullptr, P, b, b + n, d_box, n_boxes,
-                                         seed, frame, spp, d_rgb, d_key, d_val, nullptr, sc[k & 1]);
+                                         seed, frame, spp, d_rgb, d_key, d_val, nullptr, sc[k & 1], sorted);
         if (rc != RLL_OK) break;
         e = cudaEventRecord(ev_done[k], sc[k & 1]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->down, ev_done[k], 0);

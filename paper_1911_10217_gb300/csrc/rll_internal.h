@@ -38,6 +38,9 @@ struct rll_ctx {
     int host_zero_copy = 1;  // rll_render_pass_host: use mapped host buffers in place
     // launch tuning (rll_ctx_set_option)
     int sample_min_blocks = 4;
+    // occluder boxes sorted by their lower x bound, then their widest x extent, rebuilt by every
+    // sampling call (sample.cu: sort_boxes); allocated on first use
+    void* box_sorted = nullptr;
 };
 
 struct rll_tree {
@@ -153,11 +156,14 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
                      float* rec_val, const rll_sample_debug* dbg);
 // Shades points [p_begin, p_end) of a G-buffer of n_points (the plane stride)
 // on `stream`; sample ids, records and rgb are those of the whole launch.
+// The boxes sorted for sample_and_shade_range (enqueued on `stream`); returns the device
+// buffer through *out (nullptr when there are no boxes).
+int sort_boxes(rll_ctx* ctx, const float* boxes, int n_boxes, cudaStream_t stream, const void** out);
 int sample_and_shade_range(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* pos, const float* nrm,
                            const float* albedo, const float* footprint, int64_t n_points, int64_t p_begin,
                            int64_t p_end, const float* boxes, int n_boxes, uint64_t seed, uint32_t frame, int spp,
                            float* rgb, uint32_t* rec_key, float* rec_val, const rll_sample_debug* dbg,
-                           cudaStream_t stream);
+                           cudaStream_t stream, const void* sorted_boxes);
 int sample_power(rll_ctx* ctx, const rll_tree* t, const float* pos, const float* nrm,
                  const float* albedo, int64_t n_points, const float* boxes, int n_boxes, uint64_t seed,
                  uint32_t frame, int spp, float* rgb, int32_t* light_out);

@@ -15,6 +15,7 @@
 
 #include <cuda_runtime.h>
 
+#include "learn_core.cuh"  // bitonic_sort_u64
 #include "rll_device.cuh"
 #include "rll_internal.h"
 #include "sample_core.cuh"
@@ -33,7 +34,8 @@ template <int P, int MODE, bool DBG, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_sample(SampleArgs a)
 {
     extern __shared__ float4 s_box[];
-    stage_boxes(s_box, a.boxes, a.n_boxes);
+    if (a.boxes_sorted) stage_sorted_boxes(s_box, a.boxes_sorted, a.n_boxes);
+    else stage_boxes(s_box, a.boxes, a.n_boxes);
     __syncthreads();
     const int64_t p = a.p_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.p_end) return;
@@ -81,11 +83,59 @@ __global__ void __launch_bounds__(kThreads) k_sample_power(SampleArgs a, int32_t
     a.rgb[2 * np + p] = acc2 * inv_spp;
 }
 
+// The occluder boxes sorted by their lower x bound (ties by index) for the shadow test's early
+// start and stop: one block, a bitonic network over (ordered min.x << 32 | index) keys in shared
+// memory. Output: [2 K] float4 (min, max) in that order, the min's w holding the running maximum
+// of max.x over the boxes up to this one (nondecreasing).
+constexpr int kSortBoxThreads = 256;
+
+struct BlockBarrier {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+__global__ void __launch_bounds__(kSortBoxThreads) k_sort_boxes(const float* __restrict__ boxes, int n,
+                                                                float4* __restrict__ out)
+{
+    __shared__ unsigned long long s_key[kMaxBoxes];
+    __shared__ float s_hx[kMaxBoxes];  // max.x in sorted order, then its running maximum
+    for (int b = threadIdx.x; b < n; b += blockDim.x)
+        s_key[b] = ((unsigned long long)(uint32_t)(float_to_ordered(boxes[6 * b]) ^ (int)0x80000000) << 32) |
+                   (uint32_t)b;
+    __syncthreads();
+    bitonic_sort_u64(s_key, (uint32_t)n, threadIdx.x, blockDim.x, BlockBarrier{});
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s_hx[i] = boxes[6 * (uint32_t)s_key[i] + 3];
+    __syncthreads();
+    if (threadIdx.x < 32) {  // running maximum: each lane scans a run, the lanes combine by shuffles
+        const int lane = threadIdx.x, per = (n + 31) / 32, b0 = lane * per, b1 = min(n, b0 + per);
+        float m = -INFINITY;
+        for (int i = b0; i < b1; ++i) m = fmaxf(m, s_hx[i]);
+        float incl = m;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = fmaxf(incl, y);
+        }
+        float run = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) run = -INFINITY;
+        for (int i = b0; i < b1; ++i) {
+            run = fmaxf(run, s_hx[i]);
+            s_hx[i] = run;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float* bx = boxes + 6 * (uint32_t)s_key[i];
+        out[2 * i] = make_float4(bx[0], bx[1], bx[2], s_hx[i]);
+        out[2 * i + 1] = make_float4(bx[3], bx[4], bx[5], 0.0f);
+    }
+}
+
 template <int P, int MODE, bool DBG, int THREADS, int MINB>
 cudaError_t launch(const SampleArgs& a, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)((a.p_end - a.p_begin + THREADS - 1) / THREADS);
-    k_sample<P, MODE, DBG, THREADS, MINB><<<blocks, THREADS, sizeof(float4) * 2 * a.n_boxes, s>>>(a);
+    const size_t smem = sizeof(float4) * 2 * (size_t)a.n_boxes;
+    k_sample<P, MODE, DBG, THREADS, MINB><<<blocks, THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -112,18 +162,39 @@ int sample_and_shade(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* 
                      uint32_t frame, int spp, float* rgb, uint32_t* rec_key, float* rec_val,
                      const rll_sample_debug* dbg)
 {
+    const void* sorted = nullptr;
+    const int rc = sort_boxes(ctx, boxes, n_boxes, ctx->stream, &sorted);
+    if (rc != RLL_OK) return rc;
     return sample_and_shade_range(ctx, g, t, pos, nrm, albedo, footprint, n_points, 0, n_points, boxes, n_boxes, seed,
-                                  frame, spp, rgb, rec_key, rec_val, dbg, ctx->stream);
+                                  frame, spp, rgb, rec_key, rec_val, dbg, ctx->stream, sorted);
+}
+
+int sort_boxes(rll_ctx* ctx, const float* boxes, int n_boxes, cudaStream_t stream, const void** out)
+{
+    *out = nullptr;
+    if (n_boxes <= 0) return RLL_OK;
+    if (!ctx->box_sorted) {
+        if (cudaMalloc(&ctx->box_sorted, sizeof(float4) * 2 * (size_t)kMaxBoxes) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->box_sorted = nullptr;
+            return fail(ctx, RLL_E_NOMEM, "cannot allocate the sorted boxes");
+        }
+    }
+    k_sort_boxes<<<1, kSortBoxThreads, 0, stream>>>(boxes, n_boxes, static_cast<float4*>(ctx->box_sorted));
+    const int rc = check_cuda(ctx, cudaGetLastError(), "sort boxes");
+    if (rc == RLL_OK) *out = ctx->box_sorted;
+    return rc;
 }
 
 int sample_and_shade_range(rll_ctx* ctx, rll_grid* g, const rll_tree* t, const float* pos, const float* nrm,
                            const float* albedo, const float* footprint, int64_t n_points, int64_t p_begin,
                            int64_t p_end, const float* boxes, int n_boxes, uint64_t seed, uint32_t frame, int spp,
                            float* rgb, uint32_t* rec_key, float* rec_val, const rll_sample_debug* dbg,
-                           cudaStream_t stream)
+                           cudaStream_t stream, const void* sorted_boxes)
 {
     if (p_end <= p_begin) return RLL_OK;
     SampleArgs a{};
+    a.boxes_sorted = static_cast<const float4*>(sorted_boxes);
     a.pos = pos;
     a.nrm = nrm;
     a.albedo = albedo;

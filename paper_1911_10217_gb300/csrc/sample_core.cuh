@@ -21,6 +21,9 @@ struct SampleArgs {
     int64_t p_begin, p_end;   // points this launch shades (k_sample)
     const float* boxes;
     int n_boxes;
+    // the boxes sorted by their lower x bound ([2 n_boxes] float4 (min, max); min.w the running
+    // maximum of max.x); nullptr: the boxes as given, all tested
+    const float4* boxes_sorted;
     unsigned long long* keys;
     const uint32_t* cut;
     const void* C;
@@ -111,10 +114,13 @@ struct ShadeOut {
     float reward;
 };
 
-// light point, shadow test, contribution (x, n: shading point and normal)
+// light point, shadow test, contribution (x, n: shading point and normal). s_box: the boxes,
+// s_box[2b] min and s_box[2b + 1] max; when `sorted`, in increasing order of min.x, with
+// s_box[2b].w the largest max.x among boxes 0..b.
 __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1, float x2, float n0, float n1,
                                           float n2, float albedo, float p_cut, float p_in, float ua, float ub,
-                                          const float4* s_box, int n_boxes, uint32_t reward_mode)
+                                          const float4* s_box, int n_boxes, uint32_t reward_mode,
+                                          bool sorted = false)
 {
     const float su = fsqrt(ua);
     const float b0 = fsub(1.0f, su), b1 = fmul(ub, su), b2 = fsub(su, b1);
@@ -136,9 +142,25 @@ __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1,
     const float lo0 = fminf(o0, y0) - e0, hi0 = fmaxf(o0, y0) + e0;
     const float lo1 = fminf(o1, y1) - e1, hi1 = fmaxf(o1, y1) + e1;
     const float lo2 = fminf(o2, y2) - e2, hi2 = fmaxf(o2, y2) + e2;
+    // With the boxes sorted by min.x, the boxes before the first one whose running maximum of max.x
+    // reaches lo0 all have max.x < lo0, and those from the first one with min.x > hi0 on all have
+    // min.x > hi0: the prefilter below rejects every box outside that run, so testing the run
+    // alone gives the decision of the full loop.
+    int b = 0;
+    const int b_end = n_boxes;
+    if (sorted) {
+        int lo = 0, hi = n_boxes;  // first box whose running maximum of max.x is >= lo0
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_box[2 * mid].w < lo0) lo = mid + 1;
+            else hi = mid;
+        }
+        b = lo;
+    }
     bool occluded = false;
-    for (int b = 0; b < n_boxes && !occluded; ++b) {
+    for (; b < b_end && !occluded; ++b) {
         const float4 bmin = s_box[2 * b], bmax = s_box[2 * b + 1];
+        if (sorted && bmin.x > hi0) break;
         if (bmin.x > hi0 || bmax.x < lo0 || bmin.y > hi1 || bmax.y < lo1 || bmin.z > hi2 || bmax.z < lo2) continue;
         const float ta0 = __fmaf_rn(bmin.x, i0, q0), tb0 = __fmaf_rn(bmax.x, i0, q0);
         const float ta1 = __fmaf_rn(bmin.y, i1, q1), tb1 = __fmaf_rn(bmax.y, i1, q1);
@@ -182,6 +204,12 @@ __device__ __forceinline__ void stage_boxes(float4* s_box, const float* boxes, i
         s_box[2 * b] = make_float4(bx[0], bx[1], bx[2], 0.0f);
         s_box[2 * b + 1] = make_float4(bx[3], bx[4], bx[5], 0.0f);
     }
+}
+
+// The boxes as sorted by sort_boxes (2 n_boxes float4), copied as they are.
+__device__ __forceinline__ void stage_sorted_boxes(float4* s_box, const float4* sorted, int n_boxes)
+{
+    for (int i = threadIdx.x; i < 2 * n_boxes; i += blockDim.x) s_box[i] = sorted[i];
 }
 
 // Cell, cluster and triangle draws of one sample (draws 0-2 and 4-8).
@@ -413,7 +441,7 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
         }
         const LightRec Lr = load_light(a.lights + light);
         const ShadeOut o = shade(Lr, x0, x1, x2, n0, n1, n2, alb, su.p_cut, p_in, su.ua, su.ub, s_box, a.n_boxes,
-                                 a.reward_mode);
+                                 a.reward_mode, a.boxes_sorted != nullptr);
         acc0 += o.est[0];
         acc1 += o.est[1];
         acc2 += o.est[2];
