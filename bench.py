@@ -263,7 +263,7 @@ def run_reference(args, scene):
     return 0
 
 
-def run_batched(args):
+def batched_measure(n_scenes, scale, steps, warmup, scene_by_scene=True):
     """Many uneven scenes in one persistent launch per stage, replayed as a
     CUDA graph; the tile size and occupancy come from the autotuner. Also
     times the same pass issued scene by scene through the single-grid calls."""
@@ -273,7 +273,7 @@ def run_batched(args):
     stream = torch.cuda.current_stream(dev)
     ctx = rll.Context(0, stream)
     t0 = time.perf_counter()
-    sc = scenes.batched_scenes(n_scenes=args.batched_scenes, scale=args.batched_scale)
+    sc = scenes.batched_scenes(n_scenes=n_scenes, scale=scale)
     gen_s = time.perf_counter() - t0
     objs = []
     for s in sc:
@@ -289,10 +289,10 @@ def run_batched(args):
     batch = rll.Batch(ctx, items)
     tile, minb = batch.tune()
     batch.capture(do_split=True)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.launch()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for e0, e1 in ev:
         e0.record(stream)
         batch.launch()
@@ -300,32 +300,45 @@ def run_batched(args):
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in ev]
     samples = sum(o["s"].n_points * o["s"].spp for o in objs)
-    # the same pass issued scene by scene
-    key = torch.empty(max(o["s"].n_points * o["s"].spp for o in objs), dtype=torch.int32, device=dev)
-    val = torch.empty_like(key, dtype=torch.float32)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for o in objs:
-        s, d = o["s"], o["d"]
-        n = s.n_points * s.spp
-        rll.sample_and_shade(ctx, o["grid"], o["tree"], d["pos"], d["nrm"], d["alb"], d["boxes"], s.seed, 10**6,
-                             s.spp, o["rgb"], key[:n], val[:n])
-        rll.learn_update_split(ctx, o["grid"], o["tree"], key[:n], val[:n])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = e0.elapsed_time(e1)
+    seq_ms = None
+    if scene_by_scene:  # the same pass issued scene by scene
+        key = torch.empty(max(o["s"].n_points * o["s"].spp for o in objs), dtype=torch.int32, device=dev)
+        val = torch.empty_like(key, dtype=torch.float32)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for o in objs:
+            s, d = o["s"], o["d"]
+            n = s.n_points * s.spp
+            rll.sample_and_shade(ctx, o["grid"], o["tree"], d["pos"], d["nrm"], d["alb"], d["boxes"], s.seed, 10**6,
+                                 s.spp, o["rgb"], key[:n], val[:n])
+            rll.learn_update_split(ctx, o["grid"], o["tree"], key[:n], val[:n])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = e0.elapsed_time(e1)
     status = ctx.sync_status()
-    line = {"metric": METRIC, "workload": "batched", "value": samples / (statistics.mean(ms) * 1e-3), "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
-            "p99_ms": float(np.percentile(ms, 99)), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{len(sc)} uneven scenes in one persistent launch per stage, CUDA graph replay",
-                       "scenes": len(sc), "scale": args.batched_scale, "samples_per_step": samples,
-                       "lights_total": sum(o["s"].n_lights for o in objs),
-                       "cut_sizes": sorted(set(o["s"].grid.cut_size for o in objs)),
-                       "tuned_tile_points": tile, "tuned_min_blocks": minb},
-            "scene_by_scene_ms": seq_ms, "speedup_vs_scene_by_scene": seq_ms / statistics.mean(ms),
-            "generation_s": gen_s, "device_status": status}
+    out = {"value": samples / (statistics.mean(ms) * 1e-3), "ms_per_step": statistics.mean(ms),
+           "p99_ms": float(np.percentile(ms, 99)), "steps": steps, "warmup": warmup,
+           "config": {"workload": f"{len(sc)} uneven scenes in one persistent launch per stage, CUDA graph replay",
+                      "scenes": len(sc), "scale": scale, "samples_per_step": samples,
+                      "lights_total": sum(o["s"].n_lights for o in objs),
+                      "cut_sizes": sorted(set(o["s"].grid.cut_size for o in objs)),
+                      "tuned_tile_points": tile, "tuned_min_blocks": minb},
+           "scene_by_scene_ms": seq_ms,
+           "speedup_vs_scene_by_scene": (seq_ms / statistics.mean(ms)) if seq_ms else None,
+           "generation_s": gen_s, "device_status": status}
+    batch.close()
+    for o in objs:
+        o["grid"].close()
+        o["tree"].close()
+    return out
+
+
+def run_batched(args):
+    """The batched workload on its own line."""
+    r = batched_measure(args.batched_scenes, args.batched_scale, args.steps, args.warmup)
+    line = {"metric": METRIC, "workload": "batched", "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic", **r}
     print(json.dumps(line))
     return 0
 
@@ -1084,6 +1097,8 @@ def main():
             cfg, res, st = dynamic_measure(8, ["fp32", "bf16"], mse=False)
             out["extras"]["dynamic_4k"] = {"config": cfg, "precisions": res, "device_status": st}
             out["extras"]["serving"] = serving_measure(16, 16)
+            # the batched form: 256 uneven scenes (166 M samples) per graph replay
+            out["extras"]["batched"] = batched_measure(256, 1.0, 5, 3, scene_by_scene=False)
         if not args.no_cpu_baseline and world == 1:  # the host baseline belongs to the one-GPU line
             out["cpu_baseline"] = cpu_baseline(scene)
         print(json.dumps(out))

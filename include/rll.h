@@ -330,7 +330,8 @@ typedef struct rll_batch rll_batch;
 
 /* Reserves a batch able to hold up to max_items scenes with at most
  * max_records samples and max_cells table slots in total (< 2^26); all
- * device buffers are allocated here, once. */
+ * device buffers are allocated here, once (among them 32 KB per item for the
+ * item's boxes sorted for the shadow test). */
 int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int64_t max_cells,
                       rll_batch** out);
 /* Sets the scenes of the next passes (all grids with the same table

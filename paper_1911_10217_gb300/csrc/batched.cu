@@ -84,7 +84,8 @@ k_sample_batched(const BatchItemDev* __restrict__ items, int n_items, const uint
             const uint32_t* src = reinterpret_cast<const uint32_t*>(&items[it].s);
             uint32_t* dst = reinterpret_cast<uint32_t*>(&s_args);
             for (int i = threadIdx.x; i < (int)(sizeof(SampleArgs) / 4); i += blockDim.x) dst[i] = src[i];
-            stage_boxes(s_box, items[it].s.boxes, items[it].s.n_boxes);
+            if (items[it].s.boxes_sorted) stage_sorted_boxes(s_box, items[it].s.boxes_sorted, items[it].s.n_boxes);
+            else stage_boxes(s_box, items[it].s.boxes, items[it].s.n_boxes);
             cur = it;
         }
         __syncthreads();
@@ -94,6 +95,17 @@ k_sample_batched(const BatchItemDev* __restrict__ items, int n_items, const uint
         for (int64_t p = first + threadIdx.x; p < last; p += blockDim.x) sample_point<P, MODE, false>(a, p, s_box);
         __syncthreads();
     }
+}
+
+// Every item's boxes sorted for the shadow test (sort_boxes_block), one block per item, into the
+// batch's buffer that the item's descriptor points to.
+__global__ void __launch_bounds__(256) k_sort_item_boxes(const BatchItemDev* __restrict__ items, int n_items)
+{
+    const int it = blockIdx.x;
+    if (it >= n_items) return;
+    const SampleArgs& a = items[it].s;
+    if (a.n_boxes > 0 && a.boxes_sorted)
+        sort_boxes_block(a.boxes, a.n_boxes, const_cast<float4*>(a.boxes_sorted));
 }
 
 __device__ __forceinline__ int item_of_cell(const uint32_t* __restrict__ cell_prefix, int n_items, uint32_t cell)
@@ -182,6 +194,7 @@ struct rll_batch {
     uint32_t* n_touched = nullptr;     // [8] learning counters
     int max_boxes = 0;
     uint32_t* status = nullptr;
+    float4* box_sorted = nullptr;      // [cap_items][2 kMaxBoxes] every item's boxes sorted by min.x
     int32_t cap_items = 0;
     int64_t cap_records = 0;
     int64_t cap_cells = 0;
@@ -218,6 +231,7 @@ void free_batch(rll_batch* b)
     cudaFree(b->touched_len);
     cudaFree(b->lists);
     cudaFree(b->n_touched);
+    cudaFree(b->box_sorted);
     if (b->staged) {
         if (b->stage_pending) cudaEventSynchronize(b->staged);
         cudaEventDestroy(b->staged);
@@ -278,6 +292,7 @@ cudaError_t launch_sample_t(rll_batch* b, cudaStream_t s)
     const int blocks = std::max(1, per_sm) * device_sm_count(b->device);
     cudaError_t e = cudaMemsetAsync(b->d_work, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
+    k_sort_item_boxes<<<b->n, 256, 0, s>>>(b->d_items, b->n);
     k_sample_batched<P, MODE, MINB><<<blocks, kBatchThreads, smem, s>>>(b->d_items, b->n, b->d_tile_prefix,
                                                                         b->total_tiles, b->tile_points, b->d_work);
     return cudaGetLastError();
@@ -367,6 +382,7 @@ int rll_batch_reserve(rll_ctx* ctx, int32_t max_items, int64_t max_records, int6
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->touched_len, 4 * (size_t)max_cells);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->lists, 8 * (size_t)max_cells);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->n_touched, 8 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->box_sorted, sizeof(float4) * 2 * kMaxBoxes * (size_t)max_items);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->cursor, 0, 4 * (size_t)max_cells, ctx->stream);
     // the learning step's shared-memory opt-in, now rather than during a graph capture
     if (e == cudaSuccess) e = big_smem_attribute<RLL_PREC_FP32, BatchRows<RLL_PREC_FP32>, NoSplit>(ctx->device);
@@ -463,6 +479,7 @@ int rll_batch_set_items(rll_ctx* ctx, rll_batch* b, const rll_batch_item* items,
         a.n_points = it.n_points;
         a.boxes = it.boxes;
         a.n_boxes = it.n_boxes;
+        a.boxes_sorted = it.n_boxes > 0 ? b->box_sorted + 2 * kMaxBoxes * (size_t)i : nullptr;
         a.keys = g->keys;
         a.cut = g->cut;
         a.C = g->C;

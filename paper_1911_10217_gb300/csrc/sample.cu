@@ -15,7 +15,6 @@
 
 #include <cuda_runtime.h>
 
-#include "learn_core.cuh"  // bitonic_sort_u64
 #include "rll_device.cuh"
 #include "rll_internal.h"
 #include "sample_core.cuh"
@@ -83,51 +82,13 @@ __global__ void __launch_bounds__(kThreads) k_sample_power(SampleArgs a, int32_t
     a.rgb[2 * np + p] = acc2 * inv_spp;
 }
 
-// The occluder boxes sorted by their lower x bound (ties by index) for the shadow test's early
-// start and stop: one block, a bitonic network over (ordered min.x << 32 | index) keys in shared
-// memory. Output: [2 K] float4 (min, max) in that order, the min's w holding the running maximum
-// of max.x over the boxes up to this one (nondecreasing).
+// The occluder boxes sorted for the shadow test (sort_boxes_block in sample_core.cuh), one block.
 constexpr int kSortBoxThreads = 256;
-
-struct BlockBarrier {
-    __device__ __forceinline__ void operator()() const { __syncthreads(); }
-};
 
 __global__ void __launch_bounds__(kSortBoxThreads) k_sort_boxes(const float* __restrict__ boxes, int n,
                                                                 float4* __restrict__ out)
 {
-    __shared__ unsigned long long s_key[kMaxBoxes];
-    __shared__ float s_hx[kMaxBoxes];  // max.x in sorted order, then its running maximum
-    for (int b = threadIdx.x; b < n; b += blockDim.x)
-        s_key[b] = ((unsigned long long)(uint32_t)(float_to_ordered(boxes[6 * b]) ^ (int)0x80000000) << 32) |
-                   (uint32_t)b;
-    __syncthreads();
-    bitonic_sort_u64(s_key, (uint32_t)n, threadIdx.x, blockDim.x, BlockBarrier{});
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s_hx[i] = boxes[6 * (uint32_t)s_key[i] + 3];
-    __syncthreads();
-    if (threadIdx.x < 32) {  // running maximum: each lane scans a run, the lanes combine by shuffles
-        const int lane = threadIdx.x, per = (n + 31) / 32, b0 = lane * per, b1 = min(n, b0 + per);
-        float m = -INFINITY;
-        for (int i = b0; i < b1; ++i) m = fmaxf(m, s_hx[i]);
-        float incl = m;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const float y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl = fmaxf(incl, y);
-        }
-        float run = __shfl_up_sync(0xffffffffu, incl, 1);
-        if (lane == 0) run = -INFINITY;
-        for (int i = b0; i < b1; ++i) {
-            run = fmaxf(run, s_hx[i]);
-            s_hx[i] = run;
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float* bx = boxes + 6 * (uint32_t)s_key[i];
-        out[2 * i] = make_float4(bx[0], bx[1], bx[2], s_hx[i]);
-        out[2 * i + 1] = make_float4(bx[3], bx[4], bx[5], 0.0f);
-    }
+    sort_boxes_block(boxes, n, out);
 }
 
 template <int P, int MODE, bool DBG, int THREADS, int MINB>
