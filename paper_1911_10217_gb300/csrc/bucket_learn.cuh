@@ -39,15 +39,21 @@ constexpr uint32_t kBlockSort = 8192;    // records of a cell one block sorts in
 constexpr size_t kBigSmem = kBlockSort * (sizeof(unsigned long long) + sizeof(uint32_t));
 constexpr int kBigThreads = 512;
 
-// 1. record counts per cell; the first adder appends the cell to the touched
-// list. Each warp takes kTilesPerWarp tiles of 32 consecutive records.
+// 1. record counts per cell and each record's rank among its cell's records
+// (the cell's count before its warp's group, plus the lanes of the group
+// below it); the first adder of a cell appends it to the touched list, one
+// append per block. Each warp takes kTilesPerWarp tiles of 32 consecutive
+// records. The ranks follow arrival order; the per-cell ordering restores
+// sample order.
 template <class Dec>
 __global__ void __launch_bounds__(kBucketThreads)
 k_bucket_count(const uint32_t* __restrict__ rec_key, int64_t n, Dec dec, uint32_t* __restrict__ cursor,
-               uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr)
+               uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr, uint32_t* __restrict__ rank)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t tile0 = ((int64_t)blockIdx.x * (kBucketThreads / 32) + (threadIdx.x >> 5)) * kTilesPerWarp;
+    __shared__ uint32_t s_warp[kBucketThreads / 32];
+    __shared__ uint32_t s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t tile0 = ((int64_t)blockIdx.x * (kBucketThreads / 32) + warp) * kTilesPerWarp;
     uint32_t slot[kTilesPerWarp], peers[kTilesPerWarp], old[kTilesPerWarp];
 #pragma unroll
     for (int u = 0; u < kTilesPerWarp; ++u) {
@@ -63,19 +69,34 @@ k_bucket_count(const uint32_t* __restrict__ rec_key, int64_t n, Dec dec, uint32_
         if (slot[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
             old[u] = atomicAdd(cursor + slot[u], (uint32_t)__popc(peers[u]));
     }
-    // cells this lane saw first: one append per warp for all of them
     uint32_t fresh = 0;
 #pragma unroll
-    for (int u = 0; u < kTilesPerWarp; ++u) fresh += old[u] == 0u;
+    for (int u = 0; u < kTilesPerWarp; ++u) {
+        const uint32_t b = __shfl_sync(0xffffffffu, old[u], __ffs(peers[u]) - 1);
+        if (slot[u] != 0xFFFFFFFFu) rank[(tile0 + u) * 32 + lane] = b + __popc(peers[u] & lanemask_lt());
+        fresh += old[u] == 0u;
+    }
+    // cells this block saw first: one append for all of them
     uint32_t x = fresh;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    uint32_t base = 0;
-    if (lane == 31 && x) base = atomicAdd(ctr, x);
-    base = __shfl_sync(0xffffffffu, base, 31) + x - fresh;
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int w = 0; w < kBucketThreads / 32; ++w) {
+            const uint32_t v = s_warp[w];
+            s_warp[w] = tot;
+            tot += v;
+        }
+        s_base = tot ? atomicAdd(ctr, tot) : 0u;
+    }
+    __syncthreads();
+    if (!fresh) return;
+    uint32_t base = s_base + s_warp[warp] + x - fresh;
 #pragma unroll
     for (int u = 0; u < kTilesPerWarp; ++u)
         if (old[u] == 0u) touched[base++] = slot[u];
@@ -129,50 +150,62 @@ k_bucket_claim(const uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr,
     }
 }
 
-// 3. every record to its cell's bucket: sample id, cluster and reward (a
-// warp's lanes that share a cell take consecutive places; the order inside a
-// bucket depends on scheduling and is restored by the per-cell ordering)
-// Bucket entry of a record: sample id, cluster, reward bits (three arrays)
+// 3. every record to its cell's bucket, at the bucket start (the claim left it
+// in the cell's cursor) plus the record's rank: sample id, cluster and reward;
+// no atomics
+// Bucket entry of a record: sample id, cluster, reward bits. Up to 2^24
+// records: one 8-byte word, cluster << 56 | sample id << 32 | reward bits
+// (one store per record); above: three arrays.
 struct Bucket {
     uint32_t* sid;
     uint8_t* s;
     uint32_t* val;
+    unsigned long long* packed;  // non-null: the one-word form
+    __device__ __forceinline__ void put(uint32_t d, uint32_t id, uint32_t cls, uint32_t bits) const
+    {
+        if (packed) {
+            packed[d] = ((unsigned long long)(cls << 24 | id) << 32) | bits;
+        } else {
+            sid[d] = id;
+            s[d] = (uint8_t)cls;
+            val[d] = bits;
+        }
+    }
+    __device__ __forceinline__ void get(uint32_t d, uint32_t& id, uint32_t& cls, uint32_t& bits) const
+    {
+        if (packed) {
+            const unsigned long long e = packed[d];
+            id = (uint32_t)(e >> 32) & 0xFFFFFFu;
+            cls = (uint32_t)(e >> 56);
+            bits = (uint32_t)e;
+        } else {
+            id = sid[d];
+            cls = s[d];
+            bits = val[d];
+        }
+    }
 };
 
 template <class Dec>
 __global__ void __launch_bounds__(kBucketThreads)
 k_bucket_scatter(const uint32_t* __restrict__ rec_key, const float* __restrict__ rec_val, int64_t n, Dec dec,
-                 uint32_t* __restrict__ cursor, Bucket bucket)
+                 const uint32_t* __restrict__ cursor, const uint32_t* __restrict__ rank, Bucket bucket)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t tile0 = ((int64_t)blockIdx.x * (kBucketThreads / 32) + (threadIdx.x >> 5)) * kTilesPerWarp;
-    uint32_t slot[kTilesPerWarp], clus[kTilesPerWarp], val[kTilesPerWarp], peers[kTilesPerWarp],
-        base[kTilesPerWarp];
+    const int64_t i0 = (int64_t)blockIdx.x * kBucketThreads * kTilesPerWarp + threadIdx.x;
+    uint32_t key[kTilesPerWarp], val[kTilesPerWarp], rk[kTilesPerWarp], at[kTilesPerWarp];
 #pragma unroll
     for (int u = 0; u < kTilesPerWarp; ++u) {
-        const int64_t i = (tile0 + u) * 32 + lane;
-        const uint32_t key = i < n ? __ldg(rec_key + i) : 0xFFFFFFFFu;
+        const int64_t i = i0 + (int64_t)u * kBucketThreads;
+        key[u] = i < n ? __ldg(rec_key + i) : 0xFFFFFFFFu;
         val[u] = i < n ? __float_as_uint(__ldg(rec_val + i)) : 0u;
-        slot[u] = dec.valid(key) ? dec.cell(key) : 0xFFFFFFFFu;
-        clus[u] = dec.valid(key) ? dec.cluster(key) : 0u;
+        rk[u] = i < n ? __ldg(rank + i) : 0u;
     }
 #pragma unroll
-    for (int u = 0; u < kTilesPerWarp; ++u) peers[u] = __match_any_sync(0xffffffffu, slot[u]);
+    for (int u = 0; u < kTilesPerWarp; ++u) at[u] = dec.valid(key[u]) ? __ldg(cursor + dec.cell(key[u])) : 0u;
 #pragma unroll
     for (int u = 0; u < kTilesPerWarp; ++u) {
-        base[u] = 0u;
-        if (slot[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
-            base[u] = atomicAdd(cursor + slot[u], (uint32_t)__popc(peers[u]));
-    }
-#pragma unroll
-    for (int u = 0; u < kTilesPerWarp; ++u) {
-        const uint32_t b = __shfl_sync(0xffffffffu, base[u], __ffs(peers[u]) - 1);
-        if (slot[u] != 0xFFFFFFFFu) {
-            const uint32_t d = b + __popc(peers[u] & lanemask_lt());
-            bucket.sid[d] = (uint32_t)((tile0 + u) * 32 + lane);
-            bucket.s[d] = (uint8_t)clus[u];
-            bucket.val[d] = val[u];
-        }
+        if (!dec.valid(key[u])) continue;
+        bucket.put(at[u] + rk[u], (uint32_t)(i0 + (int64_t)u * kBucketThreads), dec.cluster(key[u]), val[u]);
     }
 }
 
@@ -317,8 +350,7 @@ __device__ void finish_cell(const Split& sp, uint32_t slot, float* q, uint32_t m
 // (cluster, sample) order; warp 0 of the team composes, stores Q and
 // rebuilds C. Called by every thread of the team.
 template <int P, uint32_t CAP, uint32_t CLUS, class Team, class Split>
-__device__ void learn_cell_grouped(Team team, CellOrder<CAP, CLUS>& o, const uint32_t* __restrict__ bsid,
-                                   const uint8_t* __restrict__ bs, const uint32_t* __restrict__ bval, uint32_t nr,
+__device__ void learn_cell_grouped(Team team, CellOrder<CAP, CLUS>& o, const Bucket& bucket, uint32_t b0, uint32_t nr,
                                    uint32_t M, uint32_t m, float alpha, float eps, typename Store<P>::T* qrow,
                                    typename Store<P>::T* crow, const Split& sp, uint32_t slot, uint32_t* status)
 {
@@ -334,9 +366,8 @@ __device__ void learn_cell_grouped(Team team, CellOrder<CAP, CLUS>& o, const uin
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t k = k0 + u * T;
-            rs[u] = k < nr ? bs[k] : 0u;
-            rsid[u] = k < nr ? bsid[k] : 0u;
-            rval[u] = k < nr ? bval[k] : 0u;
+            rs[u] = rsid[u] = rval[u] = 0u;
+            if (k < nr) bucket.get(b0 + k, rsid[u], rs[u], rval[u]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -485,7 +516,7 @@ k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t*
         const uint32_t w = group_list[cells - 1u - bi];
         const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
         const RowRef<P> r = rows.row(slot);
-        learn_cell_grouped<P>(BlockTeam{}, block_order, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M, r.m,
+        learn_cell_grouped<P>(BlockTeam{}, block_order, bucket, b0, nr, r.M, r.m,
                               r.alpha, r.eps, r.Q, r.C, sp, slot, status);
         if (threadIdx.x == 0) cursor[slot] = 0u;
         __syncthreads();
@@ -504,7 +535,7 @@ k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t*
             const uint32_t w = group_list[pi];
             const uint32_t slot = touched[w], b0 = start[w], nr = len[w];
             const RowRef<P> r = rows.row(slot);
-            learn_cell_grouped<P>(team, pair_order, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M, r.m,
+            learn_cell_grouped<P>(team, pair_order, bucket, b0, nr, r.M, r.m,
                                   r.alpha, r.eps, r.Q, r.C, sp, slot, status);
             if (team.tid() == 0) cursor[slot] = 0u;
             team.sync();
@@ -523,7 +554,7 @@ k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t*
         if (nr <= kWarpBucket) {
             const RowRef<P> r = rows.row(slot);
             const uint32_t b0 = start[i];
-            learn_cell_grouped<P>(WarpTeam{}, warp_order, bucket.sid + b0, bucket.s + b0, bucket.val + b0, nr, r.M,
+            learn_cell_grouped<P>(WarpTeam{}, warp_order, bucket, b0, nr, r.M,
                                   r.m, r.alpha, r.eps, r.Q, r.C, sp, slot, status);
             if (lane == 0) cursor[slot] = 0u;
         }
@@ -558,20 +589,28 @@ k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const fl
         const float alpha = r.alpha;
         if (threadIdx.x < 32) load_q_row<P>(r.Q, m, s_q);
         if (nr <= kBlockSort) {
-            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x)
-                s_key[k] = ((unsigned long long)bucket.s[b0 + k] << 45) |
-                           ((unsigned long long)bucket.sid[b0 + k] << 13) | k;
+            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x) {
+                uint32_t id, cls, bits;
+                bucket.get(b0 + k, id, cls, bits);
+                s_key[k] = ((unsigned long long)cls << 45) | ((unsigned long long)id << 13) | k;
+            }
             __syncthreads();
             bitonic_sort_u64(s_key, nr, threadIdx.x, blockDim.x, BlockSync{});
-            for (uint32_t j = threadIdx.x; j < nr; j += blockDim.x)
-                s_val[j] = bucket.val[b0 + (uint32_t)(s_key[j] & (kBlockSort - 1))];
+            for (uint32_t j = threadIdx.x; j < nr; j += blockDim.x) {
+                uint32_t id, cls, bits;
+                bucket.get(b0 + (uint32_t)(s_key[j] & (kBlockSort - 1)), id, cls, bits);
+                s_val[j] = bits;
+            }
             __syncthreads();
             compose_sorted_block<P>([&](uint32_t j) { return (uint32_t)(s_key[j] >> 45); },
                                     [&](uint32_t j) { return s_val[j]; }, nr, M, m, alpha, s_q, s_gs, s_ge);
         } else {
             unsigned long long* rec = wide + b0;
-            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x)
-                rec[k] = ((unsigned long long)bucket.s[b0 + k] << 32) | bucket.sid[b0 + k];
+            for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x) {
+                uint32_t id, cls, bits;
+                bucket.get(b0 + k, id, cls, bits);
+                rec[k] = ((unsigned long long)cls << 32) | id;
+            }
             __syncthreads();
             bitonic_sort_u64(rec, nr, threadIdx.x, blockDim.x, BlockSync{});
             for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x) {
@@ -630,17 +669,21 @@ cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uin
 {
     const size_t n4 = ((size_t)n * 4 + 255) & ~(size_t)255, n1 = ((size_t)n + 255) & ~(size_t)255;
     char* ws = static_cast<char*>(scratch);
+    // one-word entries while sample ids fit 24 bits (the 8 n bytes of the sample id and reward arrays)
     Bucket bucket{reinterpret_cast<uint32_t*>(ws), reinterpret_cast<uint8_t*>(ws + 2 * n4),
-                  reinterpret_cast<uint32_t*>(ws + n4)};
+                  reinterpret_cast<uint32_t*>(ws + n4),
+                  n <= (int64_t)1 << 24 ? reinterpret_cast<unsigned long long*>(ws) : nullptr};
     auto* wide = reinterpret_cast<unsigned long long*>(ws + 2 * n4 + n1);
     const int64_t per_block = (int64_t)kBucketThreads * kTilesPerWarp;
     const unsigned rblocks = (unsigned)((n + per_block - 1) / per_block);
     uint32_t* group_list = lists;
     uint32_t* sort_list = lists + cells;
-    k_bucket_count<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, n, dec, cursor, touched, ctr);
+    // record ranks: the first 4 n bytes of the in-place sort buffer (dead until k_learn_big)
+    uint32_t* rank = reinterpret_cast<uint32_t*>(wide);
+    k_bucket_count<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, n, dec, cursor, touched, ctr, rank);
     k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(touched, ctr, cursor, start, len, group_list, sort_list,
                                                       cells);
-    k_bucket_scatter<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, dec, cursor, bucket);
+    k_bucket_scatter<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, dec, cursor, rank, bucket);
     // cuts of at most 64 leaves: per-cluster arrays of 64 entries (30.5 KB of shared memory per
     // block), 56 registers, 6 blocks per SM; larger cuts: 256 entries (44.4 KB), 5 blocks per SM
     if (max_cut <= 64)
