@@ -510,3 +510,42 @@ def test_fused_learn_split_matches_two_calls(env, maker, kw, spp):
         for k in ("cut", "q", "c"):
             assert np.array_equal(a[k], b[k]), (k, frame, "second split")
     assert changed > 0  # split-collapse changed some cut rows
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_learning_beyond_one_word_bucket_entries(env, precision):
+    """More than 2^24 records in one call: sample ids no longer fit the 24 bits
+    of a one-word bucket entry, and the learning step keeps its buckets in three
+    arrays. The same valid records learned from a (2^24 + 4096)-long record
+    array (the rest invalid keys; valid records spread over it, 2048 of them
+    beyond 2^24) and learned compacted, in the same order, leave identical
+    tables, cut rows and touched sets: Eq. 1 takes each cluster's records in
+    sample order, which the compaction keeps."""
+    torch, rll, ctx, dev = env["torch"], env["rll"], env["ctx"], env["dev"]
+    s = scenes.small_frame_scene()
+    _, dt, d = _trees(env, s)
+    A = rll.Grid(ctx, dt, params_for(rll, s, precision=precision))
+    B = rll.Grid(ctx, dt, params_for(rll, s, precision=precision))
+    rng = np.random.default_rng(21)
+    n_long = (1 << 24) + 4096
+    long_key = torch.empty(n_long, dtype=torch.int32, device=dev)
+    long_val = torch.empty(n_long, device=dev)
+    for frame in range(3):
+        out = run_sample(rll, ctx, A, dt, d, s.seed, frame, 2)
+        st = A.export()
+        B.import_state(st["keys"], st["cut"], st["q"], st["c"])
+        k = int(out["key"].shape[0])
+        pos = np.concatenate([np.sort(rng.choice(1 << 24, size=k - 2048, replace=False)),
+                              (1 << 24) + np.sort(rng.choice(4096, size=2048, replace=False))])
+        idx = torch.from_numpy(pos).to(dev)
+        long_key.fill_(-1)  # 0xFFFFFFFF: no cell
+        long_val.zero_()
+        long_key[idx] = out["key"]
+        long_val[idx] = out["val"]
+        rll.learn_update_split(ctx, A, dt, long_key, long_val)
+        rll.learn_update_split(ctx, B, dt, out["key"], out["val"])
+        assert ctx.sync_status() == 0
+        a, b = A.export(), B.export()
+        for name in ("keys", "cut", "q", "c"):
+            assert np.array_equal(a[name], b[name]), (name, frame)
+        assert A.touched_cells() == B.touched_cells() > 0
