@@ -34,7 +34,6 @@ namespace rll {
 namespace {
 
 constexpr int kBatchThreads = 256;
-constexpr int kWarpsPerBlock = 8;
 
 struct BatchItemDev {
     SampleArgs s;            // sampling arguments (record pointers offset to the item's range)

@@ -252,8 +252,9 @@ __device__ __forceinline__ float block_incl_scan_f32(float v, float* s_warp)
 
 // each block scans kScanBlock consecutive items (kScanItems per thread,
 // thread-contiguous); block totals to sums[blockIdx]
-__global__ void __launch_bounds__(kScanThreads) k_scan_f32(const float* __restrict__ in, float* __restrict__ out,
-                                                           int64_t n, float* __restrict__ sums)
+// in and out may be the same array (the block-sums pass scans in place)
+__global__ void __launch_bounds__(kScanThreads) k_scan_f32(const float* in, float* out, int64_t n,
+                                                           float* __restrict__ sums)
 {
     __shared__ float s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
