@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kBucketThreads)
 k_bucket_count(const uint32_t* __restrict__ rec_key, int64_t n, Dec dec, uint32_t* __restrict__ cursor,
                uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr, uint32_t* __restrict__ rank)
 {
+    pdl_begin();
     __shared__ uint32_t s_warp[kBucketThreads / 32];
     __shared__ uint32_t s_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -108,6 +109,7 @@ k_bucket_claim(const uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr,
                uint32_t* __restrict__ start, uint32_t* __restrict__ len, uint32_t* __restrict__ group_list,
                uint32_t* __restrict__ sort_list, uint32_t cells)
 {
+    pdl_begin();
     const uint32_t total = *(volatile uint32_t*)ctr;
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (blockDim.x >> 5);
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(kBucketThreads)
 k_bucket_scatter(const uint32_t* __restrict__ rec_key, const float* __restrict__ rec_val, int64_t n, Dec dec,
                  const uint32_t* __restrict__ cursor, const uint32_t* __restrict__ rank, Bucket bucket)
 {
+    pdl_begin();
     const int64_t i0 = (int64_t)blockIdx.x * kBucketThreads * kTilesPerWarp + threadIdx.x;
     uint32_t key[kTilesPerWarp], val[kTilesPerWarp], rk[kTilesPerWarp], at[kTilesPerWarp];
 #pragma unroll
@@ -497,6 +500,7 @@ k_learn_buckets(const Bucket bucket, uint32_t* __restrict__ ctr, const uint32_t*
                 const uint32_t* __restrict__ len, uint32_t* __restrict__ cursor, Rows rows, Split sp,
                 uint32_t* __restrict__ status, uint32_t cells)
 {
+    pdl_begin();
     static_assert(WARPS == 6, "three warp pairs, named barriers 1 .. 3");
     using L = LearnSmem<CLUS>;
     static_assert(sizeof(CellOrder<kBlockGroup, CLUS>) <= WARPS * L::kSlab, "block arrays exceed the slabs");
@@ -575,6 +579,7 @@ k_learn_big(const Bucket bucket, unsigned long long* __restrict__ wide, const fl
             const uint32_t* __restrict__ len, const uint32_t* __restrict__ big, uint32_t* __restrict__ cursor,
             Rows rows, Split sp, uint32_t* __restrict__ status)
 {
+    pdl_begin();
     extern __shared__ unsigned long long s_key[];      // kBlockSort keys, then kBlockSort rewards (u32)
     uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kBlockSort);
     __shared__ float s_q[kMaxCut], s_c[kMaxCut];
@@ -680,23 +685,28 @@ cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uin
     uint32_t* sort_list = lists + cells;
     // record ranks: the first 4 n bytes of the in-place sort buffer (dead until k_learn_big)
     uint32_t* rank = reinterpret_cast<uint32_t*>(wide);
-    k_bucket_count<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, n, dec, cursor, touched, ctr, rank);
-    k_bucket_claim<<<sms * 2, kBucketThreads, 0, s>>>(touched, ctr, cursor, start, len, group_list, sort_list,
-                                                      cells);
-    k_bucket_scatter<Dec><<<rblocks, kBucketThreads, 0, s>>>(rec_key, rec_val, n, dec, cursor, rank, bucket);
+    cudaError_t e0 = launch_pdl(k_bucket_count<Dec>, dim3(rblocks), dim3(kBucketThreads), 0, s, rec_key, n, dec,
+                                cursor, touched, ctr, rank);
+    if (e0 == cudaSuccess)
+        e0 = launch_pdl(k_bucket_claim, dim3(sms * 2), dim3(kBucketThreads), 0, s, touched, ctr, cursor, start, len,
+                        group_list, sort_list, cells);
+    if (e0 == cudaSuccess)
+        e0 = launch_pdl(k_bucket_scatter<Dec>, dim3(rblocks), dim3(kBucketThreads), 0, s, rec_key, rec_val, n, dec,
+                        cursor, rank, bucket);
+    if (e0 != cudaSuccess) return e0;
     // cuts of at most 64 leaves: per-cluster arrays of 64 entries (30.5 KB of shared memory per
     // block), 56 registers, 6 blocks per SM; larger cuts: 256 entries (44.4 KB), 5 blocks per SM
     if (max_cut <= 64)
-        k_learn_buckets<P, 6, 6, 64, Rows, Split><<<sms * 6, 6 * 32, 0, s>>>(bucket, ctr, group_list, touched, start,
-                                                                           len, cursor, rows, sp, status, cells);
+        e0 = launch_pdl(k_learn_buckets<P, 6, 6, 64, Rows, Split>, dim3(sms * 6), dim3(6 * 32), 0, s, bucket, ctr,
+                        group_list, touched, start, len, cursor, rows, sp, status, cells);
     else
-        k_learn_buckets<P, 6, 5, kMaxCut, Rows, Split><<<sms * 5, 6 * 32, 0, s>>>(
-            bucket, ctr, group_list, touched, start, len, cursor, rows, sp, status, cells);
+        e0 = launch_pdl(k_learn_buckets<P, 6, 5, kMaxCut, Rows, Split>, dim3(sms * 5), dim3(6 * 32), 0, s, bucket,
+                        ctr, group_list, touched, start, len, cursor, rows, sp, status, cells);
+    if (e0 != cudaSuccess) return e0;
     cudaError_t e = big_smem_attribute<P, Rows, Split>(device);
     if (e != cudaSuccess) return e;
-    k_learn_big<P, Rows, Split><<<sms * 2, kBigThreads, kBigSmem, s>>>(bucket, wide, rec_val, ctr, touched, start,
-                                                                      len, sort_list, cursor, rows, sp, status);
-    return cudaGetLastError();
+    return launch_pdl(k_learn_big<P, Rows, Split>, dim3(sms * 2), dim3(kBigThreads), kBigSmem, s, bucket, wide,
+                      rec_val, ctr, touched, start, len, sort_list, cursor, rows, sp, status);
 }
 
 }  // namespace

@@ -362,6 +362,34 @@ template <> struct Store<RLL_PREC_BF16> {
     __device__ __forceinline__ static T from_bits(uint16_t b) { return __ushort_as_bfloat16(b); }
 };
 
+// Programmatic dependent launch: a kernel launched by launch_pdl may be
+// scheduled while the kernel before it on the stream is finishing; its first
+// statement is pdl_begin(): wait until that kernel (and so all earlier work)
+// has completed and its writes are visible, then let the next kernel be
+// scheduled in turn.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ordered-integer image of a float for atomicMin / atomicMax
 __device__ __forceinline__ int float_to_ordered(float f)
 {

@@ -32,6 +32,7 @@ constexpr int kThreads = 256;
 template <int P, int MODE, bool DBG, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_sample(SampleArgs a)
 {
+    pdl_begin();
     extern __shared__ float4 s_box[];
     if (a.boxes_sorted) stage_sorted_boxes(s_box, a.boxes_sorted, a.n_boxes);
     else stage_boxes(s_box, a.boxes, a.n_boxes);
@@ -88,6 +89,7 @@ constexpr int kSortBoxThreads = 256;
 __global__ void __launch_bounds__(kSortBoxThreads) k_sort_boxes(const float* __restrict__ boxes, int n,
                                                                 float4* __restrict__ out)
 {
+    pdl_begin();
     sort_boxes_block(boxes, n, out);
 }
 
@@ -96,8 +98,7 @@ cudaError_t launch(const SampleArgs& a, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)((a.p_end - a.p_begin + THREADS - 1) / THREADS);
     const size_t smem = sizeof(float4) * 2 * (size_t)a.n_boxes;
-    k_sample<P, MODE, DBG, THREADS, MINB><<<blocks, THREADS, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_sample<P, MODE, DBG, THREADS, MINB>, dim3(blocks), dim3(THREADS), smem, s, a);
 }
 
 template <int P, int MODE>
@@ -141,8 +142,10 @@ int sort_boxes(rll_ctx* ctx, const float* boxes, int n_boxes, cudaStream_t strea
             return fail(ctx, RLL_E_NOMEM, "cannot allocate the sorted boxes");
         }
     }
-    k_sort_boxes<<<1, kSortBoxThreads, 0, stream>>>(boxes, n_boxes, static_cast<float4*>(ctx->box_sorted));
-    const int rc = check_cuda(ctx, cudaGetLastError(), "sort boxes");
+    const int rc = check_cuda(ctx,
+                              launch_pdl(k_sort_boxes, dim3(1), dim3(kSortBoxThreads), 0, stream, boxes, n_boxes,
+                                         static_cast<float4*>(ctx->box_sorted)),
+                              "sort boxes");
     if (rc == RLL_OK) *out = ctx->box_sorted;
     return rc;
 }
