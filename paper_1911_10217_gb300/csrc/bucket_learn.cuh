@@ -659,12 +659,12 @@ inline size_t bucketed_scratch_bytes(int64_t n)
 }
 
 // Enqueues the whole learning step for n >= 1 records (cut sizes up to
-// max_cut). The caller has
-// zeroed ctr[0..7] on the stream and holds `cursor` [cells] at zero (left at
-// zero again); touched, start, len [cells] and lists [2 * cells] are outputs
-// and scratch. Counters: ctr[0] touched cells, [1] claimed records, [2]
-// sorting list, [3] grouping list, [4] and [5] work counters of
-// k_learn_buckets.
+// max_cut), every kernel with the programmatic launch dependency (each waits
+// for its predecessor first). The caller has zeroed ctr[0..7] on the stream
+// and holds `cursor` [cells] at zero (left at zero again); touched, start,
+// len [cells] and lists [2 * cells] are outputs and scratch. Counters: ctr[0]
+// touched cells, [1] claimed records, [2] sorting list, [3] two-warp list,
+// [6] block list, [4] [5] [7] work counters of k_learn_buckets.
 template <int P, class Dec, class Rows, class Split = NoSplit>
 cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uint32_t* rec_key,
                                   const float* rec_val, int64_t n, Dec dec, Rows rows, uint32_t cells,

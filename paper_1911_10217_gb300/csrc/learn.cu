@@ -3,12 +3,14 @@
 //
 // learn_update (records bucketed by cell, then sorted per cell):
 //   1. count: one thread per record; the lanes of a warp that hold the same
-//      cell add their count with one atomic on the cell's cursor, and the
-//      first adder of a cell appends it to the touched-cell list;
+//      cell add their count with one atomic on the cell's cursor, each record
+//      keeps its rank among the cell's records (the returned count plus its
+//      place among the warp's lanes), and the first adder of a cell appends
+//      it to the touched-cell list (one append per block);
 //   2. claim: every touched cell takes a contiguous bucket of its record
 //      count (one atomic per warp) and its cursor becomes the bucket start;
-//   3. scatter: every record writes its sample id at its cell's cursor (a
-//      warp's peers take consecutive places);
+//   3. scatter: every record goes to its bucket start plus its rank (sample
+//      id, cluster, reward; one 8-byte word while sample ids fit 24 bits);
 //   4. one warp per touched cell orders its bucket in shared memory: a
 //      counting sort by cluster, then each record's rank by sample id inside
 //      its cluster group (groups are small), which gives (cluster, sample)
@@ -23,7 +25,8 @@
 //      records; in place in global memory above that), then warps compose
 //      different clusters in parallel.
 // The order inside a bucket depends on thread scheduling; the per-cell sort
-// restores sample order, so the result is deterministic.
+// restores sample order, so the result is deterministic. Every kernel of the
+// step is launched with the programmatic launch dependency (launch_pdl).
 //
 // learn_update_with_scratch (the allocation-free entry point) keeps the
 // earlier form: a stable radix sort of all records by key = slot * M +
