@@ -5,10 +5,12 @@
 // in shared memory once per block. Per sample:
 //   hash lookup / lazy insert of the (jittered) 5-d cell   (64-bit CAS)
 //   binary search of the cell's C for the cluster s        (log2 m loads of one row)
-//   in-cluster choice: bound-driven descent (one 96-byte record of both
+//   in-cluster choice: bound-driven descent (one 80-byte record of both
 //   children per level, both bounds in packed f32x2 arithmetic) or a uniform
 //   pick over the cluster's lights
-//   uniform point on the light triangle, contribution, shadow segment vs boxes
+//   uniform point on the light triangle, contribution, shadow segment vs the
+//   boxes (sorted by min.x once per call; only the run that can meet the
+//   segment is tested)
 //   estimate accumulation and one learning record (key, |c|).
 // The decisions (cell, branch, visibility) are exact binary32 formulas; the
 // cdf and descent comparisons u * total < c are made exactly with one fma.
