@@ -155,35 +155,32 @@ k_bucket_claim(const uint32_t* __restrict__ touched, uint32_t* __restrict__ ctr,
 // 3. every record to its cell's bucket, at the bucket start (the claim left it
 // in the cell's cursor) plus the record's rank: sample id, cluster and reward;
 // no atomics
-// Bucket entry of a record: sample id, cluster, reward bits. Up to 2^24
-// records: one 8-byte word, cluster << 56 | sample id << 32 | reward bits
-// (one store per record); above: three arrays.
+// Bucket entry of a record: sample id, cluster, reward bits in one 8-byte
+// word. Up to 2^24 records: cluster << 56 | sample id << 32 | reward bits (one
+// store per record); above: sample id << 32 | reward bits, the cluster in a
+// byte array beside it.
 struct Bucket {
-    uint32_t* sid;
-    uint8_t* s;
-    uint32_t* val;
-    unsigned long long* packed;  // non-null: the one-word form
+    unsigned long long* word;
+    uint8_t* s;  // nullptr: the cluster is in the word
     __device__ __forceinline__ void put(uint32_t d, uint32_t id, uint32_t cls, uint32_t bits) const
     {
-        if (packed) {
-            packed[d] = ((unsigned long long)(cls << 24 | id) << 32) | bits;
+        if (!s) {
+            word[d] = ((unsigned long long)(cls << 24 | id) << 32) | bits;
         } else {
-            sid[d] = id;
+            word[d] = ((unsigned long long)id << 32) | bits;
             s[d] = (uint8_t)cls;
-            val[d] = bits;
         }
     }
     __device__ __forceinline__ void get(uint32_t d, uint32_t& id, uint32_t& cls, uint32_t& bits) const
     {
-        if (packed) {
-            const unsigned long long e = packed[d];
+        const unsigned long long e = word[d];
+        bits = (uint32_t)e;
+        if (!s) {
             id = (uint32_t)(e >> 32) & 0xFFFFFFu;
             cls = (uint32_t)(e >> 56);
-            bits = (uint32_t)e;
         } else {
-            id = sid[d];
+            id = (uint32_t)(e >> 32);
             cls = s[d];
-            bits = val[d];
         }
     }
 };
@@ -649,9 +646,10 @@ cudaError_t big_smem_attribute(int device)
     return e;
 }
 
-// scratch of launch_bucketed_learn for n records: bucket sample ids (4 B),
-// rewards (4 B), clusters (1 B) and the in-place sort buffer (8 B, used only by
-// cells above kBlockSort records)
+// scratch of launch_bucketed_learn for n records: 8-byte bucket entries,
+// cluster bytes (above 2^24 records), and the record ranks and in-place sort
+// buffer (8 B: the ranks until the scatter, then the sort keys of cells above
+// kBlockSort records)
 inline size_t bucketed_scratch_bytes(int64_t n)
 {
     const size_t n4 = ((size_t)n * 4 + 255) & ~(size_t)255, n1 = ((size_t)n + 255) & ~(size_t)255;
@@ -674,10 +672,10 @@ cudaError_t launch_bucketed_learn(cudaStream_t s, int device, int sms, const uin
 {
     const size_t n4 = ((size_t)n * 4 + 255) & ~(size_t)255, n1 = ((size_t)n + 255) & ~(size_t)255;
     char* ws = static_cast<char*>(scratch);
-    // one-word entries while sample ids fit 24 bits (the 8 n bytes of the sample id and reward arrays)
-    Bucket bucket{reinterpret_cast<uint32_t*>(ws), reinterpret_cast<uint8_t*>(ws + 2 * n4),
-                  reinterpret_cast<uint32_t*>(ws + n4),
-                  n <= (int64_t)1 << 24 ? reinterpret_cast<unsigned long long*>(ws) : nullptr};
+    // 8-byte entries in the first 2 n4 bytes; the cluster bytes after them once sample ids need
+    // more than 24 bits
+    Bucket bucket{reinterpret_cast<unsigned long long*>(ws),
+                  n <= (int64_t)1 << 24 ? nullptr : reinterpret_cast<uint8_t*>(ws + 2 * n4)};
     auto* wide = reinterpret_cast<unsigned long long*>(ws + 2 * n4 + n1);
     const int64_t per_block = (int64_t)kBucketThreads * kTilesPerWarp;
     const unsigned rblocks = (unsigned)((n + per_block - 1) / per_block);
