@@ -515,8 +515,8 @@ def test_fused_learn_split_matches_two_calls(env, maker, kw, spp):
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_learning_beyond_one_word_bucket_entries(env, precision):
     """More than 2^24 records in one call: sample ids no longer fit the 24 bits
-    of a one-word bucket entry, and the learning step keeps its buckets in three
-    arrays. The same valid records learned from a (2^24 + 4096)-long record
+    beside the cluster in a bucket entry, and the learning step keeps each
+    record's cluster in a byte array beside its entries. The same valid records learned from a (2^24 + 4096)-long record
     array (the rest invalid keys; valid records spread over it, 2048 of them
     beyond 2^24) and learned compacted, in the same order, leave identical
     tables, cut rows and touched sets: Eq. 1 takes each cluster's records in
