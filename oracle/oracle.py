@@ -83,6 +83,8 @@ def lib():
                                       ctypes.c_double, P, P]
             L.orc_bound64.restype = ctypes.c_double
             L.orc_half_round.argtypes = [ctypes.c_float, ctypes.c_int]
+            L.orc_shadow32.argtypes = [P, P, ctypes.c_int, P]
+            L.orc_shadow64.argtypes = [P, P, ctypes.c_int, P]
             L.orc_half_round.restype = ctypes.c_float
             L.orc_sample_frame.argtypes = [ctypes.POINTER(_Tree), P, P, ctypes.c_int, P,
                                            ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P, P,
@@ -203,6 +205,23 @@ def bound64(centre, r, cos_t, sin_t, axis, phi, x, nrm):
     xx = np.ascontiguousarray(x, np.float64)
     nn = np.ascontiguousarray(nrm, np.float64)
     return float(lib().orc_bound64(_p(c), float(r), float(cos_t), float(sin_t), _p(a), float(phi), _p(xx), _p(nn)))
+
+
+def occluded32(o, y, boxes):
+    """The binary32 shadow test of the sampler: segment o -> y (t in (0,
+    0.9999)) against boxes [K][6]."""
+    o = np.ascontiguousarray(o, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    b = np.ascontiguousarray(boxes, np.float32).reshape(-1, 6)
+    return bool(lib().orc_shadow32(_p(o), _p(y), int(b.shape[0]), _p(b)))
+
+
+def occluded64(o, y, boxes):
+    """The double shadow test of the brute-force reference (same segment)."""
+    o = np.ascontiguousarray(o, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    b = np.ascontiguousarray(boxes, np.float32).reshape(-1, 6)
+    return bool(lib().orc_shadow64(_p(o), _p(y), int(b.shape[0]), _p(b)))
 
 
 def half_round(x, up):

@@ -978,13 +978,20 @@ static void orc_branch_weights(const float* ra, const float* rc, const float x[3
 /* Shadow test (binary32): segment from o = x + 1e-4 n to the light point y, */
 /* parameter t in (0, 0.9999), slab test against every box (open intervals). */
 /* Each slab plane is t = fma(b, 1/d, -(o * (1/d))): one fused multiply-add, */
-/* correctly rounded (C99 fmaf).                                             */
+/* correctly rounded (C99 fmaf). A direction component with |d| < 2^-100     */
+/* (the segment does not move along that axis; 1/d would be infinite and the */
+/* planes undefined) is taken as 2^-100 with the sign of d: o * 2^100 is     */
+/* exact, so the planes lie at t = (b - o) 2^100 rounded, and the segment is */
+/* inside that slab exactly when b_min < o < b_max, as the double test below */
+/* decides for a parallel segment (one lying on a face plane goes by the     */
+/* sign given to d).                                                         */
 /* ------------------------------------------------------------------------ */
 static int orc_occluded32(const float o[3], const float y[3], int nbox, const float* boxes)
 {
     float d[3], inv[3], oi[3];
     for (int k = 0; k < 3; ++k) {
         d[k] = y[k] - o[k];
+        if (!(fabsf(d[k]) >= 0x1p-100f)) d[k] = copysignf(0x1p-100f, d[k]);
         inv[k] = 1.0f / d[k];
         oi[k] = o[k] * inv[k];
     }
@@ -1499,6 +1506,16 @@ static int orc_occluded64(const double o[3], const double y[3], int nbox, const 
         if (!miss && tn < tf) return 1;
     }
     return 0;
+}
+
+/* The two shadow tests as library entry points (tests compare them). */
+int orc_shadow32(const float o[3], const float y[3], int nbox, const float* boxes)
+{
+    return orc_occluded32(o, y, nbox, boxes);
+}
+int orc_shadow64(const double o[3], const double y[3], int nbox, const float* boxes)
+{
+    return orc_occluded64(o, y, nbox, boxes);
 }
 
 static void orc_tri_quad(const double* a, const double* b, const double* c, int level, const double x[3],

@@ -110,6 +110,16 @@ __device__ __forceinline__ LightRec load_light(const LightRec* p)
     return r;
 }
 
+// A shadow segment's direction component: one with |d| < 2^-100 (the segment
+// does not move along that axis; 1/d would be infinite and the slab planes
+// undefined) is taken as 2^-100 with the sign of d. o * 2^100 is then exact,
+// the planes lie at t = (b - o) 2^100 rounded, and the segment is inside that
+// slab exactly when b_min < o < b_max -- the decision for a parallel segment.
+__device__ __forceinline__ float seg_dir(float d)
+{
+    return fabsf(d) >= 0x1p-100f ? d : copysignf(0x1p-100f, d);
+}
+
 struct ShadeOut {
     float est[3];
     float reward;
@@ -131,7 +141,8 @@ __device__ __forceinline__ ShadeOut shade(const LightRec& L, float x0, float x1,
     const float o0 = fadd(x0, fmul(kShadowOffset, n0));
     const float o1 = fadd(x1, fmul(kShadowOffset, n1));
     const float o2 = fadd(x2, fmul(kShadowOffset, n2));
-    const float i0 = fdiv(1.0f, fsub(y0, o0)), i1 = fdiv(1.0f, fsub(y1, o1)), i2 = fdiv(1.0f, fsub(y2, o2));
+    const float i0 = fdiv(1.0f, seg_dir(fsub(y0, o0))), i1 = fdiv(1.0f, seg_dir(fsub(y1, o1))),
+                i2 = fdiv(1.0f, seg_dir(fsub(y2, o2)));
     const float q0 = -fmul(o0, i0), q1 = -fmul(o1, i1), q2 = -fmul(o2, i2);
     // Conservative prefilter: a box can only block the segment if it meets the
     // segment's bounding box widened by del; del exceeds the rounding error of
