@@ -1096,7 +1096,7 @@ def main():
             grid.close()
             cfg, res, st = dynamic_measure(8, ["fp32", "bf16"], mse=False)
             out["extras"]["dynamic_4k"] = {"config": cfg, "precisions": res, "device_status": st}
-            out["extras"]["serving"] = serving_measure(16, 16)
+            out["extras"]["serving"] = serving_measure(16, 64)
             # the batched form: 256 uneven scenes (166 M samples) per graph replay
             out["extras"]["batched"] = batched_measure(256, 1.0, 5, 3, scene_by_scene=False)
         if not args.no_cpu_baseline and world == 1:  # the host baseline belongs to the one-GPU line
