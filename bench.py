@@ -179,8 +179,10 @@ def _oracle_replica(rank, workers, seed, steps, chunk, seconds, barrier, results
         results.put((rank, done, time.perf_counter() - t0, []))
         return
     times = []
+    chunk = min(chunk, P)
     for i in range(steps):
-        first = (i * chunk) % (P - chunk) + rank * chunk // workers
+        first = (i * chunk) % (P - chunk) if chunk < P else 0
+        first += rank * chunk // workers
         cnt = (rank + 1) * chunk // workers - rank * chunk // workers
         barrier.wait()
         t0 = time.perf_counter()
@@ -245,7 +247,7 @@ def run_reference(args, scene):
     if rank != 0:
         return 0
     cores = _host_cores()
-    chunk = 131072
+    chunk = scene.n_points  # one step = one pass over the whole frame, split over the cores
     res = _run_replicas(cores, scene.seed, steps=args.warmup + args.steps, chunk=chunk)
     per_step = [max(r[3][i] for r in res) for i in range(args.warmup, args.warmup + args.steps)]
     total = sum(per_step)
@@ -255,7 +257,7 @@ def run_reference(args, scene):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(scene),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{chunk} consecutive points of the frame per step, split over {cores} "
+                             "sample": f"the whole frame ({chunk} points) per step, split over {cores} "
                                        "oracle processes (one per host core, each with its own grid), "
                                        "oracle sample+Eq.1+Eq.2+split-collapse; step time = slowest process"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
