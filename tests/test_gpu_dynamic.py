@@ -114,3 +114,18 @@ def test_dynamic_learned_state_fused_step(dyn):
     compare_tables(st, oracle_state(og), m, RTOL["fp32"], check_cut=True, skip=skip | flipped)
     assert ctx.sync_status() == 0
     dg.close()
+
+
+@pytest.mark.parametrize("builder", ["saoh", "median"])
+def test_dynamic_tree_other_builders_bit_exact(dyn, builder):
+    """The surface-area-orientation and median-split builders at 2^20 lights:
+    light order, topology and node records bit-exact with the oracle's."""
+    O, rll, ctx, s = dyn["O"], dyn["rll"], dyn["ctx"], dyn["s"]
+    bound = s.emission_bound()
+    dt = rll.Tree(ctx, dyn["d"]["tri"], dyn["T"](bound), builder=builder)
+    ot = O.Tree(s.tris, bound, builder=builder)
+    ex = dt.export()
+    assert np.array_equal(ex["perm"], ot.perm)
+    assert np.array_equal(ex["left"], ot.left) and np.array_equal(ex["right"], ot.right)
+    assert np.array_equal(ex["rec"].view(np.uint32), ot.rec.view(np.uint32))
+    dt.close()
