@@ -64,7 +64,8 @@ def test_dynamic_frame_slices_match_oracle(dyn, precision):
     dg.close()
 
 
-def test_dynamic_learned_state_fused_step(dyn):
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_dynamic_learned_state_fused_step(dyn, precision):
     """The call the benchmark times at this size, from a learned state: the
     oracle runs two learning passes (sampling with each frame's blinking
     radiance, Eq. 1, Eq. 2, split-collapse) over the whole 3840 x 2160 frame
@@ -72,10 +73,11 @@ def test_dynamic_learned_state_fused_step(dyn):
     over the whole frame, then the device's fused rll_learn_update_split on
     its own records is compared with the oracle's learn + split-collapse on
     every touched cell (cut size 64; cells of more than 240 records take the
-    two-warp and block teams): cuts exact, Q and C within 1e-4. A split
+    two-warp and block teams): cuts exact, Q and C within the table
+    tolerance (1e-4 for binary32, 2e-2 for bfloat16 tables). A split
     decision within the rounding of Eq. 1 in the oracle's own state may go the
     other way; every such cell is checked to be a near-tie (relative gap at
-    most 1e-5) and left out. They are more frequent than at 1080p (here at
+    most 1e-5, or two bfloat16 roundings) and left out. They are more frequent than at 1080p (here at
     most 2 %, measured 0.9 %): with 64-leaf cuts after two passes many leaves
     have seen the same few updates, so their Q values tie exactly in the
     oracle's double arithmetic (broken by range order) and differ only by
@@ -83,7 +85,7 @@ def test_dynamic_learned_state_fused_step(dyn):
     O, rll, ctx, s, d, torch = dyn["O"], dyn["rll"], dyn["ctx"], dyn["s"], dyn["d"], dyn["torch"]
     ctx.sync_status()
     ot, dt = dyn["ot"], dyn["dt"]
-    og = O.Grid.for_scene(ot, s, precision="fp32")
+    og = O.Grid.for_scene(ot, s, precision=precision)
     A = O.scene_arrays(s)
     K = 2
     for f in range(K):
@@ -91,7 +93,7 @@ def test_dynamic_learned_state_fused_step(dyn):
         og.split_collapse(og.learn(o["slot"], o["s"], o["reward"]))
     em = s.emission_at(K)
     dt.update_emission(dyn["T"](em))
-    dg = rll.Grid(ctx, dt, params_for(rll, s, precision="fp32"))
+    dg = rll.Grid(ctx, dt, params_for(rll, s, precision=precision))
     dg.import_state(og.keys, og.cut, og.Q, og.C)
     g = to_host(run_sample(rll, ctx, dg, dt, d, s.seed, K, s.spp))
     o = og.sample_frame(A, s.seed, K, s.spp, emission=em)
@@ -108,10 +110,11 @@ def test_dynamic_learned_state_fused_step(dyn):
     g_rows = rows_by_key(st["keys"], st["cut"])
     o_rows = rows_by_key(og.keys, og.cut)
     flipped = {k for k in o_rows if k in g_rows and not np.array_equal(g_rows[k][0][:m], o_rows[k][0][:m])}
+    tol = {"fp32": 1e-5, "bf16": 2 * 2.0 ** -8}[precision]
     for k in flipped:
-        assert k in pre and split_margin(*pre[k], ot.parent, ot.n, s.grid.threshold) <= 1e-5, k
+        assert k in pre and split_margin(*pre[k], ot.parent, ot.n, s.grid.threshold) <= tol, k
     assert len(flipped) <= max(2, len(pre) // 50), len(flipped)
-    compare_tables(st, oracle_state(og), m, RTOL["fp32"], check_cut=True, skip=skip | flipped)
+    compare_tables(st, oracle_state(og), m, RTOL[precision], check_cut=True, skip=skip | flipped)
     assert ctx.sync_status() == 0
     dg.close()
 
