@@ -272,8 +272,11 @@ __device__ __forceinline__ Bound importance(const DescRec& r, float x0, float x1
 // the same order as importance(), hence bit-identical bounds. d2 - r2 is
 // computed as d2 + (-r2) and d2 <= r2 as d2 - r2 <= 0 (equal under round to
 // nearest with gradual underflow); the early return inside the bounding
-// sphere becomes a per-component select. n*: the normal broadcast to both
-// components.
+// sphere becomes a per-component select. The receiver and emitter branches
+// are evaluated for both components always and selected per component (in a
+// warp some lane nearly always needs them, so the branches only cost their
+// divergence; the values selected are the same). n*: the normal broadcast to
+// both components.
 struct Bound2 {
     float2 num, den;
 };
@@ -298,24 +301,24 @@ __device__ __forceinline__ Bound2 importance2(const PairRec& q, float x0, float 
     const float2 nd = __ffma2_rn(n2, dz, __ffma2_rn(n1, dy, __fmul2_rn(n0, dx)));
     float2 A = d2;
     const bool ra = nd.x < cb.x, rb = nd.y < cb.y;
-    if (ra || rb) {
+    {
         const float2 g = __ffma2_rn(neg2(nd), nd, d2);
         const float2 sq = make_float2(fsqrt(fmaxf(0.0f, g.x)), fsqrt(fmaxf(0.0f, g.y)));
         const float2 v = __ffma2_rn(nd, cb, __fmul2_rn(sq, q.r));
-        if (ra) A.x = fmaxf(0.0f, v.x);
-        if (rb) A.y = fmaxf(0.0f, v.y);
+        A.x = ra ? fmaxf(0.0f, v.x) : A.x;
+        A.y = rb ? fmaxf(0.0f, v.y) : A.y;
     }
     const float2 ad = neg2(__ffma2_rn(q.a2, dz, __ffma2_rn(q.a1, dy, __fmul2_rn(q.a0, dx))));
     const float2 sphi = __ffma2_rn(sin_t, cb, __fmul2_rn(cos_t, q.r));
     const float2 cphi = __ffma2_rn(cos_t, cb, neg2(__fmul2_rn(sin_t, q.r)));
     float2 B = d2;
     const bool ea = !(sphi.x <= 0.0f || cphi.x <= ad.x), eb = !(sphi.y <= 0.0f || cphi.y <= ad.y);
-    if (ea || eb) {
+    {
         const float2 g = __ffma2_rn(neg2(ad), ad, d2);
         const float2 sq = make_float2(fsqrt(fmaxf(0.0f, g.x)), fsqrt(fmaxf(0.0f, g.y)));
         const float2 v = __ffma2_rn(ad, cphi, __fmul2_rn(sq, sphi));
-        if (ea) B.x = fmaxf(0.0f, v.x);
-        if (eb) B.y = fmaxf(0.0f, v.y);
+        B.x = ea ? fmaxf(0.0f, v.x) : B.x;
+        B.y = eb ? fmaxf(0.0f, v.y) : B.y;
     }
     Bound2 o;
     o.num = __fmul2_rn(__fmul2_rn(q.phi, A), B);
