@@ -458,6 +458,7 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
     const float alb = a.albedo[p];
     const uint32_t level = a.footprint ? footprint_level(__ldg(a.footprint + p), a.h, a.levels) : 0u;
     const int64_t nl1 = a.n_lights - 1;
+    const uint32_t nl1u = (uint32_t)nl1;  // internal node ids are below it (at most 2^24 lights)
     float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
     for (int j = 0; j < a.spp; ++j) {
         const uint32_t sid = (uint32_t)(p * a.spp + j);
@@ -474,7 +475,7 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
             light = (int64_t)r.begin + (int64_t)(((unsigned long long)u24v * w) >> 24);
             p_in = 1.0f / (float)w;
         } else if (MODE == RLL_MODE_DESCENT2) {
-            for (uint32_t level = 0; (int64_t)node < nl1 && level < (uint32_t)kMaxTreeDepth; ++level)
+            for (uint32_t level = 0; node < nl1u && level < (uint32_t)kMaxTreeDepth; ++level)
                 descent2_step(a, node, p_in, rs.draw(kDrawDescent + level), x0, x1, x2, n0, n1, n2);
             light = leaf_or_flag(a, node, nl1);
         } else {
@@ -483,15 +484,15 @@ __device__ __forceinline__ void sample_point(const SampleArgs& a, int64_t p, con
             // block, unrolled so that every word index is a constant
             static_assert(kDrawDescent == 9, "descent draws start at word 1 of block 2");
             uint4 w = rs.block_words(2);
-            if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.y), x0, x1, x2, vn0, vn1, vn2);
-            if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.z), x0, x1, x2, vn0, vn1, vn2);
-            if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.w), x0, x1, x2, vn0, vn1, vn2);
-            for (uint32_t b = 3; (int64_t)node < nl1 && b < (uint32_t)(kMaxTreeDepth / 4); ++b) {
+            if (node < nl1u) descent_step(a, node, p_in, u24(w.y), x0, x1, x2, vn0, vn1, vn2);
+            if (node < nl1u) descent_step(a, node, p_in, u24(w.z), x0, x1, x2, vn0, vn1, vn2);
+            if (node < nl1u) descent_step(a, node, p_in, u24(w.w), x0, x1, x2, vn0, vn1, vn2);
+            for (uint32_t b = 3; node < nl1u && b < (uint32_t)(kMaxTreeDepth / 4); ++b) {
                 w = rs.block_words(b);
                 descent_step(a, node, p_in, u24(w.x), x0, x1, x2, vn0, vn1, vn2);
-                if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.y), x0, x1, x2, vn0, vn1, vn2);
-                if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.z), x0, x1, x2, vn0, vn1, vn2);
-                if ((int64_t)node < nl1) descent_step(a, node, p_in, u24(w.w), x0, x1, x2, vn0, vn1, vn2);
+                if (node < nl1u) descent_step(a, node, p_in, u24(w.y), x0, x1, x2, vn0, vn1, vn2);
+                if (node < nl1u) descent_step(a, node, p_in, u24(w.z), x0, x1, x2, vn0, vn1, vn2);
+                if (node < nl1u) descent_step(a, node, p_in, u24(w.w), x0, x1, x2, vn0, vn1, vn2);
             }
             light = leaf_or_flag(a, node, nl1);
         }
