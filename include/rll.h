@@ -203,6 +203,10 @@ int rll_grid_destroy(rll_grid* grid);
  * light inside it (descent or uniform), a point on that triangle, and
  * evaluate the shadowed contribution against the boxes. Writes the
  * per-point mean estimate and one learning record per sample.
+ * Visibility: the segment from x + 1e-4 n to the light point y, parameter
+ * t in (0, 0.9999), misses every box (binary32 slab test, open intervals);
+ * a segment that does not move along an axis (|y - o| < 2^-100 there) is
+ * inside that axis's slab exactly when the box's open interval contains it.
  *   pos, nrm: SoA [3][P] float; albedo [P]; boxes [K][6] (min xyz, max xyz),
  *   K <= 1024; rgb: SoA [3][P] output; rec_key [P*spp]: slot * M + cluster
  *   (0xFFFFFFFF when no cell could be created); rec_val [P*spp]: |c| (Eq. 1
