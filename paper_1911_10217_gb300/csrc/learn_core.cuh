@@ -69,8 +69,13 @@ __device__ void warp_rebuild_cdf(const float* q, int m, float eps, typename Stor
         // the lanes combine by shuffles. The patterns stay within 1 .. one (m <= 256), so the
         // 16-bit values never wrap and the result equals the sequential loops.
         const int one = Store<P>::bits(Store<P>::store(1.0f));
+        constexpr int kIpl = kMaxCut / 32;  // entries a lane holds at most
         int mx = INT_MIN;
-        for (int s = b; s < e && s < m - 1; ++s) mx = max(mx, (int)bits[s] - s);
+#pragma unroll
+        for (int j = 0; j < kIpl; ++j) {
+            const int s = b + j;
+            if (s < e && s < m - 1) mx = max(mx, (int)bits[s] - s);
+        }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, mx, o);
@@ -78,13 +83,21 @@ __device__ void warp_rebuild_cdf(const float* q, int m, float eps, typename Stor
         }
         int up = __shfl_up_sync(0xffffffffu, mx, 1);
         up = lane == 0 ? 1 : max(up, 1);
-        for (int s = b; s < e && s < m - 1; ++s) {
-            up = max(up, (int)bits[s] - s);
-            bits[s] = (uint16_t)(s + up);
+#pragma unroll
+        for (int j = 0; j < kIpl; ++j) {
+            const int s = b + j;
+            if (s < e && s < m - 1) {
+                up = max(up, (int)bits[s] - s);
+                bits[s] = (uint16_t)(s + up);
+            }
         }
         if (b <= m - 1 && m - 1 < e) bits[m - 1] = (uint16_t)one;
         int mn = INT_MAX;
-        for (int s = e - 1; s >= b; --s) mn = min(mn, (int)bits[s] - s);
+#pragma unroll
+        for (int j = kIpl - 1; j >= 0; --j) {
+            const int s = b + j;
+            if (s < e) mn = min(mn, (int)bits[s] - s);
+        }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_down_sync(0xffffffffu, mn, o);
@@ -92,9 +105,13 @@ __device__ void warp_rebuild_cdf(const float* q, int m, float eps, typename Stor
         }
         int down = __shfl_down_sync(0xffffffffu, mn, 1);
         if (lane == 31) down = INT_MAX;
-        for (int s = e - 1; s >= b; --s) {
-            down = min(down, (int)bits[s] - s);
-            bits[s] = (uint16_t)(s + down);
+#pragma unroll
+        for (int j = kIpl - 1; j >= 0; --j) {
+            const int s = b + j;
+            if (s < e) {
+                down = min(down, (int)bits[s] - s);
+                bits[s] = (uint16_t)(s + down);
+            }
         }
         __syncwarp();
         for (int s = lane; s < m; s += 32) out[s] = Store<P>::from_bits(bits[s]);
